@@ -1,0 +1,108 @@
+"""Pins of the oracle's noise model, CGLS, RTO and statistics (CPU only)."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import fem, rto, wave
+
+
+def small_problem(n=2, n_obs=8, n_steps=30, seed=11):
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, S.ALL_FACES, seed)
+    ops = fem.build(xyz, tets, det, n)
+    dt = 0.3 / n
+    p0 = S.gaussian_blobs(xyz, 2, seed)
+    Y = wave.forward(ops, p0, dt, n_steps)
+    y_obs, sigma = rto.add_noise(Y, S.standard_normal(Y.shape, seed + 1), 0.05, dt)
+    return ops, dt, n_steps, y_obs, sigma, Y
+
+
+def test_noise_is_normalised_exactly():
+    Y = S.standard_normal((50, 7), 1) * 3.0
+    eta0 = S.standard_normal((50, 7), 2)
+    y_obs, sigma = rto.add_noise(Y, eta0, 0.01, 0.02)
+    eta = y_obs - Y
+    assert abs(np.linalg.norm(eta) / np.linalg.norm(Y) - 0.01) < 1e-12
+    assert abs(sigma - 0.01 * np.linalg.norm(Y) / np.linalg.norm(eta0)) < 1e-15
+
+
+def test_cgls_reaches_the_least_squares_solution():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((40, 12)) @ np.diag(np.logspace(0, 1.5, 12))
+    b = rng.standard_normal(40)
+    x, hist = rto.cgls(lambda v: (A @ v,), lambda r: A.T @ r[0], (b,), 60, (12,), False)
+    ref = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.abs(x - ref).max() < 1e-9 * np.abs(ref).max()
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])          # residual never grows
+
+
+def test_batched_cgls_equals_columnwise():
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    eta = S.standard_normal((nt, 8, 3), 5)
+    xi = S.standard_normal((N, 3), 6)
+    X, _ = rto.rto_samples(ops, dt, nt, y_obs, sigma, eta, xi, 7)
+    for k in range(3):
+        x, _ = rto.rto_samples(ops, dt, nt, y_obs, sigma, eta[..., k], xi[:, k], 7)
+        assert np.abs(X[:, k] - x).max() < 1e-7 * np.abs(x).max()   # rounding, amplified by CGLS
+
+
+def test_converged_rto_sample_is_the_closed_form_sample():
+    """Appendix A: the minimiser is C_post[G^T y/s^2 + G^T eta/s + L^T L p_prior]."""
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    G = wave.forward_matrix_dense(ops, dt, nt)
+    eta = S.standard_normal((nt, 8), 7)
+    xi = S.standard_normal(N, 8)
+    x, _ = rto.rto_samples(ops, dt, nt, y_obs, sigma, eta, xi, 400)
+    ref = rto.exact_sample(G, ops["ML"], y_obs, sigma, eta, xi)
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_exact_samples_have_posterior_mean_and_covariance():
+    """Monte Carlo: mean -> mu_post and covariance -> C_post (Appendix A)."""
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    G = wave.forward_matrix_dense(ops, dt, nt)
+    C, mu = rto.dense_posterior(G, ops["ML"], y_obs, sigma)
+    rng = np.random.default_rng(9)
+    ns = 4000
+    H = G.T @ G / sigma ** 2 + np.diag(ops["ML"])
+    eta = rng.standard_normal((ns, G.shape[0]))
+    xi = rng.standard_normal((ns, N))
+    rhs = (G.T @ y_obs.ravel() / sigma ** 2)[None] + eta @ G / sigma + xi * np.sqrt(ops["ML"])
+    X = np.linalg.solve(H, rhs.T).T
+    sd = np.sqrt(np.diag(C))
+    assert np.all(np.abs(X.mean(0) - mu) < 5 * sd / np.sqrt(ns))
+    emp = np.cov(X.T)
+    corr_err = (emp - C) / np.outer(sd, sd)
+    assert np.abs(corr_err).max() < 6 / np.sqrt(ns) * 2
+    # the per-sample formula agrees with exact_sample
+    k = 3
+    x3 = rto.exact_sample(G, ops["ML"], y_obs, sigma, eta[k].reshape(nt, -1), xi[k])
+    assert np.abs(x3 - X[k]).max() < 1e-10 * np.abs(X[k]).max()
+
+
+def test_ergodic_estimators():
+    X = S.standard_normal((9, 5), 3)
+    m, s = rto.ergodic_mean_std(X)
+    assert np.allclose(m, np.mean(X, axis=1), rtol=0, atol=1e-15)
+    assert np.allclose(s, np.std(X, axis=1, ddof=1), rtol=1e-14, atol=0)
+
+
+def test_splitmix64_reference_values():
+    """Published SplitMix64 outputs for seed 0 (the first outputs of the reference
+    implementation, as listed e.g. in the xoshiro/splitmix64 documentation)."""
+    from oracle import rng
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.json")))
+    out = rng.splitmix64_output(0, np.arange(1, len(g["outputs"]) + 1, dtype=np.uint64))
+    assert [int(v) for v in out] == [int(v, 16) for v in g["outputs"]]
+
+
+def test_normal_draws_are_standard_normal():
+    from oracle import rng
+    z = rng.normals(7, 0, 20000, 4)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    # a sample's draws do not depend on the batch size
+    assert np.array_equal(rng.normals(7, 1, 100, 8)[:, 3], rng.normals(7, 1, 100, 4)[:, 3])
