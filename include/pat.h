@@ -1,0 +1,242 @@
+/*
+ * pat.h -- C ABI of the B300 photoacoustic RTO library (libpat.so).
+ *
+ * The library computes, on one CUDA device, the hot path of the matrix-free
+ * randomize-then-optimize (RTO) posterior sampler for 3D photoacoustic
+ * tomography of arXiv 2607.21373:
+ *   - the P1 tetrahedral finite-element forward map G: initial pressure p0 ->
+ *     sensor time series Y (Section 3: eq. semi-discrete with lumped mass,
+ *     Stoermer-Verlet time stepping eq. fully-discrete, first-order absorbing
+ *     boundary eq. boundary, sensor interpolation eq. lagrange);
+ *   - its exact algebraic transpose G^T (Section 5.1: eq. backward-recursion
+ *     with the transposed step eq. adjoint-verlet);
+ *   - batched least-squares solves of the extended RTO system
+ *     (eq. extended-matrices, eq. normal-equations, Algorithm 1), K posterior
+ *     samples at a time, and their pointwise mean / std (eq. ergodic).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a pat_status; PAT_OK == 0.  On failure,
+ *     pat_last_error() returns a thread-local, NUL-terminated message that stays
+ *     valid until the next call on the same thread.  No call prints or aborts.
+ *   - "host" pointers are ordinary CPU memory read during the call.  "device"
+ *     pointers are CUDA device memory on the device that was current when the
+ *     mesh was created; the caller owns them.  The library never allocates
+ *     device memory inside a compute call: it uses the caller's workspace.
+ *   - Compute calls are asynchronous and stream-ordered on `stream` (a
+ *     cudaStream_t, NULL = legacy default stream).  Argument errors are
+ *     returned synchronously; a kernel-detected numerical problem is recorded
+ *     on the device and reported by the next call that reads it back
+ *     (pat_rto_status).
+ *   - Stacked samples: a field with K samples is stored node-major, samples
+ *     contiguous: element (i, k) of an [N][K] array is at i*K + k.  Time
+ *     series are [N_T][N_obs][K]: element (n, d, k) at (n*N_obs + d)*K + k,
+ *     n = 0..N_T-1 holding the observation at t = (n+1) dt.
+ *   - "real" is float for PAT_F32 meshes and double for PAT_F64 meshes.
+ *   - Calls on different meshes may run concurrently; calls that share a
+ *     workspace must not overlap on the GPU.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pat_mesh pat_mesh; /* opaque; owns the device copies of the operators */
+
+typedef enum {
+  PAT_OK = 0,
+  PAT_EINVAL = 1,       /* bad argument, shape, mesh or sensor placement        */
+  PAT_ENOMEM = 2,       /* host or device allocation failed (mesh creation only)*/
+  PAT_ECUDA = 3,        /* a CUDA runtime call failed                           */
+  PAT_EUNSTABLE = 4,    /* the time step makes the propagator grow (create)     */
+  PAT_ENUMERIC = 5,     /* non-finite or non-positive CGLS scalar               */
+  PAT_ETIMEOUT = 6,     /* a bounded device wait ran out                        */
+  PAT_EUNSUPPORTED = 7  /* valid request this build does not handle             */
+} pat_status;
+
+typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_prec;
+
+/* pat_mesh_create flags */
+#define PAT_MESH_SKIP_STABILITY 0x1u /* do not run the growth check of the time step */
+#define PAT_MESH_KEEP_ZEROS     0x2u /* keep graph entries that assemble to exactly 0.0 */
+#define PAT_MESH_SINGLE_COEF    0x4u /* PAT_F32: one float per coefficient (no hi+lo split) */
+#define PAT_MESH_HOST_ONLY      0x8u /* assemble on the host only (no device copy); compute
+                                        calls on such a mesh return PAT_EINVAL, exports work */
+
+/*
+ * Assemble the operators of a P1 tetrahedral mesh and copy them to the current
+ * device (Section 3, eq. semi-discrete and the mass-lumping paragraph).
+ *
+ *   xyz      host, [n_nodes][3] double: node coordinates.
+ *   tets     host, [n_tets][4] int32: vertex indices, 0-based, any orientation.
+ *   c2_elem  host, [n_tets] double: squared sound speed per tetrahedron, or NULL
+ *            for c = 1.  It scales the element stiffness only; the absorbing
+ *            boundary matrix is assembled at c = 1 (the paper's nondimensional
+ *            setting).
+ *   det_xyz  host, [n_obs][3] double: sensor positions; each must lie on a
+ *            boundary triangle (a tetrahedron face not shared with another
+ *            tetrahedron), within 1e-9 of the mesh size.  A sensor is read by P1
+ *            interpolation in that triangle (general Pi of Section 5.1).
+ *   dt       time step; n_steps = N_T observation times t_n = n dt, n = 1..N_T.
+ *   prec     state precision of all compute calls on this mesh.
+ *   flags    PAT_MESH_* bits.
+ *   out      receives the new mesh.
+ *
+ * Matrices: K_e = c_e^2 V_e grad(l_a).grad(l_b); lumped mass M_L,i = sum of V_e/4
+ * over the tetrahedra at node i; B_f = (A_f/12)(1 + delta_ab) on every boundary
+ * triangle.  Unless PAT_MESH_SKIP_STABILITY is given, the call runs the
+ * propagator for 300 steps in FP64 on the host from a seeded random state and
+ * returns PAT_EUNSTABLE when the last 100 steps grow faster than 1e-3 per step.
+ * Errors: PAT_EINVAL (index out of range, degenerate tetrahedron, sensor off the
+ * boundary, dt <= 0, n_steps < 1), PAT_EUNSTABLE, PAT_ENOMEM, PAT_ECUDA.
+ */
+pat_status pat_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                           const double* c2_elem, const double* det_xyz, int32_t n_obs, double dt,
+                           int32_t n_steps, pat_prec prec, uint32_t flags, pat_mesh** out);
+
+/* Release a mesh and its device memory.  NULL is accepted. */
+pat_status pat_mesh_destroy(pat_mesh* mesh);
+
+/* Sizes of a mesh (host outputs; any pointer may be NULL). */
+typedef struct {
+  int64_t n_nodes, n_tets, n_boundary_faces, n_boundary_nodes;
+  int64_t nnz_K;        /* stored stiffness entries (after dropping exact zeros) */
+  int64_t nnz_K_graph;  /* entries of the full P1 graph, zeros included          */
+  int64_t nnz_B;
+  int32_t n_obs, n_steps, prec;
+  double dt;
+  double operator_bytes; /* bytes of the forward-step operator read per step   */
+} pat_mesh_info;
+pat_status pat_mesh_query(const pat_mesh* mesh, pat_mesh_info* info);
+
+/*
+ * Copy assembly results to host buffers (each may be NULL):
+ *   lumped_mass [N] double; det_nodes [n_obs][3] int32 and det_w [n_obs][3]
+ *   double (the boundary triangle and P1 weights of each sensor, weights >= 0);
+ *   boundary_faces [F][3] int32 (sorted vertex triples, lexicographic order).
+ */
+pat_status pat_mesh_export(const pat_mesh* mesh, double* lumped_mass, int32_t* det_nodes,
+                           double* det_w, int32_t* boundary_faces);
+
+/*
+ * Stiffness and boundary matrices as host CSR in FP64 (for checking): row_ptr
+ * [N+1] int64, col [nnz] int32, val [nnz] double.  Pass NULL arrays to query
+ * nnz only.  which = 0: K (full graph, exact zeros kept); 1: B.
+ */
+pat_status pat_mesh_export_csr(const pat_mesh* mesh, int32_t which, int64_t* nnz, int64_t* row_ptr,
+                               int32_t* col, double* val);
+
+/* Device workspace (bytes) needed by a compute call with K stacked samples.
+ * op: 0 = pat_forward, 1 = pat_adjoint, 2 = pat_rto_* (CGLS state included). */
+pat_status pat_workspace_bytes(const pat_mesh* mesh, int32_t op, int32_t K, size_t* bytes);
+
+/*
+ * Y = scale * G p0 for K stacked initial pressures (Section 3, eq. fully-discrete
+ * and eq. discrete-wave-matrix; z0 = (p0, 0)).
+ *   p0 device [N][K] real; Y device [N_T][N_obs][K] real (written).
+ *   workspace device, >= pat_workspace_bytes(mesh, 0, K) bytes, 256-byte aligned.
+ */
+pat_status pat_forward(const pat_mesh* mesh, const void* p0, int32_t K, void* Y, double scale,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * p_hat = scale * G^T Yhat (Section 5.1, eq. backward-recursion and
+ * eq. adjoint-verlet): the exact transpose of pat_forward's map, up to rounding.
+ *   Yhat device [N_T][N_obs][K] real; p_hat device [N][K] real (written).
+ *   workspace >= pat_workspace_bytes(mesh, 1, K).
+ */
+pat_status pat_adjoint(const pat_mesh* mesh, const void* Yhat, int32_t K, void* p_hat, double scale,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * RTO: K posterior samples by CGLS on the extended system (eq. extended-matrices
+ * with the independent Gaussian prior C = M_L^{-1} of eq. iid-prior, so the prior
+ * block of b is xi), x0 = 0, exactly n_iter iterations (Algorithm 1; the paper
+ * stops at fixed iteration limits).  FP32 meshes keep fields in FP32 and every
+ * inner product, norm, CGLS scalar and the iterate x in FP64.
+ *   y_obs   device [N_T][N_obs] real: observed data.
+ *   sigma   noise standard deviation (> 0).
+ *   eta     device [N_T][N_obs][K] real, N(0,1) data perturbations, or NULL to
+ *           draw them on the device from `seed` (counter-based generator).
+ *   xi      device [N][K] real, N(0,1) prior draws, or NULL (drawn from `seed`).
+ *   samples device [N][K] double or NULL; mean, stdev device [N] double or NULL
+ *           (stdev needs K >= 2; estimator of eq. ergodic with 1/(K-1)).
+ *   resid   device [n_iter+1][K] double or NULL: ||r_j||^2 of each iterate.
+ *   workspace >= pat_workspace_bytes(mesh, 2, K).
+ * Errors: PAT_EINVAL; PAT_ENUMERIC is reported by pat_rto_status.
+ */
+pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K,
+                          int32_t n_iter, const void* eta, const void* xi, uint64_t seed,
+                          double* samples, double* mean, double* stdev, double* resid,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * The same solve in pieces, for callers that inspect or resume the CGLS state
+ * held in the workspace:
+ *   pat_cgls_begin    r = b, s = A^T r, d = s, gamma = ||s||^2, x = 0;
+ *   pat_cgls_iterate  n_iter CGLS iterations (q = A d, alpha, x, r, s, beta, d);
+ *   pat_cgls_finish   copy x to samples and form mean / stdev.
+ * pat_cgls_layout returns byte offsets into the workspace of the state fields:
+ *   off[0] x [N][K] double, off[1] d [N][K] real, off[2] r_d [N_T][N_obs][K] real,
+ *   off[3] r_p [N][K] real, off[4] s [N][K] real, off[5] gamma [K] double,
+ *   off[6] status word (int32; 0 = ok, else a pat_status).
+ */
+pat_status pat_cgls_begin(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K,
+                          const void* eta, const void* xi, uint64_t seed, void* workspace,
+                          size_t workspace_bytes, void* stream);
+pat_status pat_cgls_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32_t n_iter,
+                            double* resid, void* workspace, size_t workspace_bytes, void* stream);
+pat_status pat_cgls_finish(const pat_mesh* mesh, int32_t K, double* samples, double* mean,
+                           double* stdev, void* workspace, size_t workspace_bytes, void* stream);
+pat_status pat_cgls_layout(const pat_mesh* mesh, int32_t K, size_t* offsets /* [7] */);
+
+/* Synchronise `stream` and read the workspace's status word (PAT_OK, PAT_ENUMERIC ...). */
+pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* workspace, void* stream);
+
+/*
+ * Counter-based N(0,1) draws used when pat_cgls_begin / pat_rto_sample get NULL
+ * eta or xi: out[e*K + k] for e < n_elem, k < K (device, double).  stream_id 0
+ * gives eta (e = flat index n*N_obs + d), 1 gives xi (e = node).  Definition:
+ * SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) output i of seed s is
+ * mix(s + i * 0x9E3779B97F4A7C15); with c = ((k << 1 | stream_id) << 40) | e,
+ * u1 = (out(2c+1) >> 11 + 1) 2^-53, u2 = (out(2c+2) >> 11) 2^-53 and
+ * z = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller, cosine branch).  A sample's
+ * draws depend on its index k and the seed only, not on K.
+ */
+pat_status pat_draw_normals(uint64_t seed, int32_t stream_id, int64_t n_elem, int32_t K, double* out,
+                            void* stream);
+
+/*
+ * Live timing of the hot kernels, for benchmarks.  While enabled on a mesh,
+ * every forward and transposed time loop run by calls on that mesh (pat_forward,
+ * pat_adjoint and the loops inside the CGLS calls) is bracketed by two CUDA
+ * events recorded on the launching stream, and every kernel launch is counted.
+ * pat_profile_enable(mesh, 1) resets the counters; pat_profile_read
+ * synchronises the device and returns the sums.  fwd_ms / adj_ms are the
+ * summed event times of the loops (launch gaps included); *_launches count the
+ * step kernels inside them; total_launches counts every kernel of the library.
+ * Not thread-safe across concurrent calls on one mesh.
+ */
+typedef struct {
+  double fwd_ms, adj_ms;
+  int64_t fwd_loops, adj_loops;
+  int64_t fwd_launches, adj_launches;
+  int64_t total_launches;
+} pat_profile;
+pat_status pat_profile_enable(pat_mesh* mesh, int32_t enable);
+pat_status pat_profile_read(pat_mesh* mesh, pat_profile* out);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* pat_last_error(void);
+
+/* Library version string. */
+const char* pat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAT_H */

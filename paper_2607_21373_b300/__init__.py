@@ -1,0 +1,231 @@
+"""B300-native photoacoustic RTO sampler: Python binding of libpat.so.
+
+Argument marshalling only: every step of the forward map, its transpose and
+the batched CGLS runs in the library's CUDA kernels.  PyTorch provides device
+memory and the current stream.  There is no CPU fallback: without a CUDA
+device or without libpat.so these calls raise.
+
+    mesh = Mesh(xyz, tets, det_xyz, dt, n_steps, precision="f32")
+    Y = mesh.forward(p0)                      # [N_T, N_obs(, K)]
+    g = mesh.adjoint(Y)                       # [N(, K)]
+    out = mesh.rto_sample(y_obs, sigma, K=64, n_iter=100)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PatError
+
+__all__ = ["Mesh", "PatError", "draw_normals", "lib", "F32", "F64"]
+
+F32, F64 = 0, 1
+MESH_SKIP_STABILITY, MESH_KEEP_ZEROS, MESH_SINGLE_COEF, MESH_HOST_ONLY = 0x1, 0x2, 0x4, 0x8
+
+
+def lib():
+    return _lib.load()
+
+
+def _stream(device=None):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _f64c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Mesh:
+    """Device copy of a P1 tetrahedral mesh's operators (pat_mesh_create)."""
+
+    def __init__(self, xyz, tets, det_xyz, dt, n_steps, precision="f32", c2=None, flags=0):
+        L = lib()
+        self.host_only = bool(int(flags) & MESH_HOST_ONLY)
+        if self.host_only:
+            self.device = None          # assembly and exports only; compute calls raise
+        elif not torch.cuda.is_available():
+            raise RuntimeError("paper_2607_21373_b300 needs a CUDA device (no CPU fallback)")
+        else:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        xyz = _f64c(xyz)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        det = _f64c(det_xyz)
+        c2a = None if c2 is None else _f64c(c2)
+        self.prec = F64 if precision in ("f64", F64) else F32
+        self.dtype = torch.float64 if self.prec == F64 else torch.float32
+        h = C.c_void_p()
+        _lib.check(L.pat_mesh_create(
+            xyz.ctypes.data, len(xyz), tets.ctypes.data, len(tets),
+            None if c2a is None else c2a.ctypes.data, det.ctypes.data, len(det), float(dt), int(n_steps),
+            self.prec, int(flags), C.byref(h)))
+        self._h = h
+        info = _lib.MeshInfo()
+        _lib.check(L.pat_mesh_query(h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in _lib.MeshInfo._fields_}
+        self.N = info.n_nodes
+        self.n_obs = info.n_obs
+        self.n_steps = info.n_steps
+        self.dt = info.dt
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._LIB is not None:
+            _lib._LIB.pat_mesh_destroy(h)
+            self._h = None
+
+    # -- host exports ------------------------------------------------------
+    def export(self):
+        """Lumped mass, sensor triangles and weights, boundary faces (host numpy)."""
+        ml = np.empty(self.N)
+        dn = np.empty((self.n_obs, 3), dtype=np.int32)
+        dw = np.empty((self.n_obs, 3))
+        bf = np.empty((self.info["n_boundary_faces"], 3), dtype=np.int32)
+        _lib.check(lib().pat_mesh_export(self._h, ml.ctypes.data, dn.ctypes.data, dw.ctypes.data,
+                                         bf.ctypes.data))
+        return {"ML": ml, "det_nodes": dn, "det_w": dw, "bfaces": bf}
+
+    def export_csr(self, which):
+        """K (which=0, full graph) or B (which=1) as (row_ptr, col, val) host arrays."""
+        L = lib()
+        nnz = C.c_int64()
+        _lib.check(L.pat_mesh_export_csr(self._h, which, C.byref(nnz), None, None, None))
+        rp = np.empty(self.N + 1, dtype=np.int64)
+        col = np.empty(nnz.value, dtype=np.int32)
+        val = np.empty(nnz.value)
+        _lib.check(L.pat_mesh_export_csr(self._h, which, C.byref(nnz), rp.ctypes.data, col.ctypes.data,
+                                         val.ctypes.data))
+        return rp, col, val
+
+    # -- workspace ---------------------------------------------------------
+    def workspace_bytes(self, op, K):
+        b = C.c_size_t()
+        _lib.check(lib().pat_workspace_bytes(self._h, op, K, C.byref(b)))
+        return b.value
+
+    def workspace(self, op, K):
+        """A cached, 256-byte aligned device workspace for (op, K)."""
+        key = (op, K)
+        nb = self.workspace_bytes(op, K)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < nb + 256:
+            ws = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+            self._ws[key] = ws
+        off = (-ws.data_ptr()) % 256
+        return ws[off:off + nb]
+
+    def _check_field(self, t, shape, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous CUDA {self.dtype} tensor")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+    # -- forward map and transpose -------------------------------------------
+    def forward(self, p0, scale=1.0, out=None):
+        """Y = scale * G p0; p0 [N] or [N, K] -> Y [N_T, N_obs] or [N_T, N_obs, K]."""
+        K = 1 if p0.dim() == 1 else p0.shape[1]
+        self._check_field(p0, (self.N,) if p0.dim() == 1 else (self.N, K), "p0")
+        shape = (self.n_steps, self.n_obs) + (() if p0.dim() == 1 else (K,))
+        if out is None:
+            out = torch.empty(shape, dtype=self.dtype, device=self.device)
+        self._check_field(out, shape, "Y")
+        ws = self.workspace(0, K)
+        _lib.check(lib().pat_forward(self._h, _ptr(p0), K, _ptr(out), float(scale), _ptr(ws), ws.numel(),
+                                     _stream()))
+        return out
+
+    def adjoint(self, Yhat, scale=1.0, out=None):
+        """p_hat = scale * G^T Yhat; Yhat [N_T, N_obs(, K)] -> [N(, K)]."""
+        K = 1 if Yhat.dim() == 2 else Yhat.shape[2]
+        self._check_field(Yhat, (self.n_steps, self.n_obs) + (() if Yhat.dim() == 2 else (K,)), "Yhat")
+        shape = (self.N,) if Yhat.dim() == 2 else (self.N, K)
+        if out is None:
+            out = torch.empty(shape, dtype=self.dtype, device=self.device)
+        self._check_field(out, shape, "p_hat")
+        ws = self.workspace(1, K)
+        _lib.check(lib().pat_adjoint(self._h, _ptr(Yhat), K, _ptr(out), float(scale), _ptr(ws), ws.numel(),
+                                     _stream()))
+        return out
+
+    # -- RTO -------------------------------------------------------------
+    def rto_sample(self, y_obs, sigma, K, n_iter, eta=None, xi=None, seed=0, samples=True, resid=False,
+                   mean=True, stdev=None):
+        """K RTO posterior samples by n_iter CGLS iterations (pat_rto_sample)."""
+        self._check_field(y_obs, (self.n_steps, self.n_obs), "y_obs")
+        if eta is not None:
+            self._check_field(eta, (self.n_steps, self.n_obs, K), "eta")
+        if xi is not None:
+            self._check_field(xi, (self.N, K), "xi")
+        stdev = (K >= 2) if stdev is None else stdev
+        dev = self.device
+        out = {}
+        out["samples"] = torch.empty((self.N, K), dtype=torch.float64, device=dev) if samples else None
+        out["mean"] = torch.empty(self.N, dtype=torch.float64, device=dev) if mean else None
+        out["std"] = torch.empty(self.N, dtype=torch.float64, device=dev) if stdev else None
+        out["resid"] = torch.empty((n_iter + 1, K), dtype=torch.float64, device=dev) if resid else None
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_rto_sample(
+            self._h, _ptr(y_obs), float(sigma), K, n_iter, _ptr(eta), _ptr(xi), C.c_uint64(seed),
+            _ptr(out["samples"]), _ptr(out["mean"]), _ptr(out["std"]), _ptr(out["resid"]), _ptr(ws),
+            ws.numel(), _stream()))
+        return out
+
+    def profile_enable(self, on=True):
+        """Start (and reset) or stop live loop timing and launch counting."""
+        _lib.check(lib().pat_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self):
+        """Synchronise and return the loop timings and launch counts since enable."""
+        p = _lib.Profile()
+        _lib.check(lib().pat_profile_read(self._h, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in _lib.Profile._fields_}
+
+    def status(self, K):
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_rto_status(self._h, K, _ptr(ws), _stream()))
+
+    # stepwise CGLS with access to the state (pat_cgls_*)
+    def cgls_begin(self, y_obs, sigma, K, eta=None, xi=None, seed=0):
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_cgls_begin(self._h, _ptr(y_obs), float(sigma), K, _ptr(eta), _ptr(xi),
+                                        C.c_uint64(seed), _ptr(ws), ws.numel(), _stream()))
+
+    def cgls_iterate(self, sigma, K, n_iter, resid=None):
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_cgls_iterate(self._h, float(sigma), K, n_iter, _ptr(resid), _ptr(ws), ws.numel(),
+                                          _stream()))
+
+    def cgls_state(self, K):
+        """Views of the CGLS state in the workspace: x, d, r_d, r_p, s, gamma, status."""
+        off = (C.c_size_t * 7)()
+        _lib.check(lib().pat_cgls_layout(self._h, K, off))
+        ws = self.workspace(2, K)
+        N, D = self.N, self.n_steps * self.n_obs
+        rs = 8 if self.prec == F64 else 4
+
+        def view(o, n, dtype, shape):
+            return ws[o:o + n * (8 if dtype == torch.float64 else 4)].view(dtype).view(shape)
+
+        return {
+            "x": view(off[0], N * K, torch.float64, (N, K)),
+            "d": view(off[1], N * K, self.dtype, (N, K)),
+            "r_d": view(off[2], D * K, self.dtype, (self.n_steps, self.n_obs, K)),
+            "r_p": view(off[3], N * K, self.dtype, (N, K)),
+            "s": view(off[4], N * K, self.dtype, (N, K)),
+            "gamma": view(off[5], K, torch.float64, (K,)),
+            "status": ws[off[6]:off[6] + 4].view(torch.int32),
+        }
+
+
+def draw_normals(seed, stream_id, n_elem, K, device=None):
+    """The library's counter-based N(0,1) draws (pat_draw_normals), [n_elem, K] float64."""
+    out = torch.empty((n_elem, K), dtype=torch.float64, device=device or "cuda")
+    _lib.check(lib().pat_draw_normals(C.c_uint64(seed), stream_id, n_elem, K, _ptr(out), _stream()))
+    return out

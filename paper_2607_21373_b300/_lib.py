@@ -1,0 +1,94 @@
+"""ctypes declarations of libpat.so (the C ABI of include/pat.h)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+c_size_p = C.POINTER(C.c_size_t)
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_boundary_faces", C.c_int64),
+        ("n_boundary_nodes", C.c_int64), ("nnz_K", C.c_int64), ("nnz_K_graph", C.c_int64),
+        ("nnz_B", C.c_int64), ("n_obs", C.c_int32), ("n_steps", C.c_int32), ("prec", C.c_int32),
+        ("dt", C.c_double), ("operator_bytes", C.c_double),
+    ]
+
+
+class Profile(C.Structure):
+    _fields_ = [("fwd_ms", C.c_double), ("adj_ms", C.c_double), ("fwd_loops", C.c_int64),
+                ("adj_loops", C.c_int64), ("fwd_launches", C.c_int64), ("adj_launches", C.c_int64),
+                ("total_launches", C.c_int64)]
+
+
+# name -> (restype, argtypes); every compute call returns pat_status (int)
+SIGNATURES = {
+    "pat_mesh_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                  C.c_int32, C.c_double, C.c_int32, C.c_int, C.c_uint32,
+                                  C.POINTER(C.c_void_p)]),
+    "pat_mesh_destroy": (C.c_int, [C.c_void_p]),
+    "pat_mesh_query": (C.c_int, [C.c_void_p, C.POINTER(MeshInfo)]),
+    "pat_mesh_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pat_mesh_export_csr": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "pat_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, c_size_p]),
+    "pat_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p,
+                              C.c_size_t, C.c_void_p]),
+    "pat_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p,
+                              C.c_size_t, C.c_void_p]),
+    "pat_rto_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p,
+                                 C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_cgls_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_cgls_iterate": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                   C.c_size_t, C.c_void_p]),
+    "pat_cgls_finish": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_size_t, C.c_void_p]),
+    "pat_cgls_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
+    "pat_rto_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pat_draw_normals": (C.c_int, [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pat_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "pat_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
+    "pat_last_error": (C.c_char_p, []),
+    "pat_version": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load (building first if needed) the in-tree libpat.so; raises if that fails."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libpat.so is missing at {path}; run paper_2607_21373_b300/build.py")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+STATUS = {0: "PAT_OK", 1: "PAT_EINVAL", 2: "PAT_ENOMEM", 3: "PAT_ECUDA", 4: "PAT_EUNSTABLE",
+          5: "PAT_ENUMERIC", 6: "PAT_ETIMEOUT", 7: "PAT_EUNSUPPORTED"}
+
+
+class PatError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status: int):
+    if status != 0:
+        raise PatError(status, _LIB.pat_last_error().decode())

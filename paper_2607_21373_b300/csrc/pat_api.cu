@@ -1,0 +1,508 @@
+// C ABI of libpat (declarations and contracts in include/pat.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pat_internal.h"
+#include "pat_solver.cuh"
+
+using namespace pat;
+
+namespace {
+
+template <typename T>
+pat_status upload(const std::vector<T>& h, T** d) {
+  *d = nullptr;
+  if (h.empty()) return PAT_OK;
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("pat_mesh_create: cudaMalloc of %zu bytes failed (%s)", h.size() * sizeof(T), cudaGetErrorString(e));
+    *d = nullptr;
+    return e == cudaErrorMemoryAllocation ? PAT_ENOMEM : PAT_ECUDA;
+  }
+  e = cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_check(e, "pat_mesh_create upload");
+  return PAT_OK;
+}
+
+void free_mesh(DeviceMesh& m) {
+  for (void* e : m.prof.events)
+    if (e) cudaEventDestroy((cudaEvent_t)e);
+  m.prof.events.clear();
+  void* ps[] = {m.fwd.ptr, m.fwd.col, m.fwd.hi, m.fwd.lo, m.adj.ptr, m.adj.col, m.adj.hi, m.adj.lo,
+                m.minv_hi, m.minv_lo, m.ml, m.sqrt_ml, m.det_node, m.det_w};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+}
+
+// Tagged device CSR of one direction, values in double before rounding.
+struct HostRows {
+  std::vector<int32_t> ptr;
+  std::vector<uint32_t> col;
+  std::vector<double> val;
+};
+
+template <typename T>
+pat_status upload_rows(const HostRows& r, bool split, DevCSR& d) {
+  d.nnz = (int64_t)r.col.size();
+  pat_status s = upload(r.ptr, &d.ptr);
+  if (s) return s;
+  s = upload(r.col, &d.col);
+  if (s) return s;
+  std::vector<T> hi(r.val.size());
+  for (size_t e = 0; e < hi.size(); ++e) hi[e] = (T)r.val[e];
+  T* dh = nullptr;
+  s = upload(hi, &dh);
+  d.hi = dh;
+  if (s) return s;
+  if (split) {
+    std::vector<float> lo(r.val.size());
+    for (size_t e = 0; e < lo.size(); ++e) lo[e] = (float)(r.val[e] - (double)hi[e]);
+    s = upload(lo, &d.lo);
+    if (s) return s;
+  }
+  return PAT_OK;
+}
+
+bool check_device(const pat_mesh* mesh, const char* fn) {
+  if (mesh->d.host_only) {
+    set_error("%s: the mesh was created with PAT_MESH_HOST_ONLY", fn);
+    return false;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != mesh->d.device) {
+    set_error("%s: current device %d is not the mesh's device %d", fn, dev, mesh->d.device);
+    return false;
+  }
+  return true;
+}
+
+pat_status check_ws(const pat_mesh* mesh, int op, int K, const void* ws, size_t bytes, const char* fn) {
+  size_t need = 0;
+  pat_status s = pat_workspace_bytes(mesh, op, K, &need);
+  if (s) return s;
+  if (!ws || bytes < need) {
+    set_error("%s: workspace of %zu bytes at %p is too small (need %zu)", fn, bytes, ws, need);
+    return PAT_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("%s: workspace must be 256-byte aligned", fn);
+    return PAT_EINVAL;
+  }
+  return PAT_OK;
+}
+
+bool bad_K(int32_t K, const char* fn) {
+  if (K < 1 || K > 1024) {
+    set_error("%s: K = %d must be in [1, 1024]", fn, K);
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pat_last_error(void) { return pat::last_error(); }
+const char* pat_version(void) { return "pat-b300 0.1 (sm_103a)"; }
+
+pat_status pat_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
+                           const double* c2_elem, const double* det_xyz, int32_t n_obs, double dt, int32_t n_steps,
+                           pat_prec prec, uint32_t flags, pat_mesh** out) {
+  clear_error();
+  if (!out || !xyz || !tets || (!det_xyz && n_obs > 0)) {
+    set_error("pat_mesh_create: NULL argument");
+    return PAT_EINVAL;
+  }
+  *out = nullptr;
+  if (!(dt > 0.0) || !std::isfinite(dt) || n_steps < 1 || n_obs < 1 || (prec != PAT_F32 && prec != PAT_F64)) {
+    set_error("pat_mesh_create: need dt > 0, n_steps >= 1, n_obs >= 1 and a valid precision "
+              "(dt=%g n_steps=%d n_obs=%d prec=%d)", dt, n_steps, n_obs, (int)prec);
+    return PAT_EINVAL;
+  }
+  pat_mesh* mesh = new (std::nothrow) pat_mesh();
+  if (!mesh) {
+    set_error("pat_mesh_create: out of host memory");
+    return PAT_ENOMEM;
+  }
+  DeviceMesh& m = mesh->d;
+  HostMesh& h = m.host;
+  pat_status s;
+  try {
+    s = assemble_host(xyz, n_nodes, tets, n_tets, c2_elem, h);
+    if (s == PAT_OK) s = locate_sensors(det_xyz, n_obs, h);
+    h.dt = dt;
+    h.n_steps = n_steps;
+    if (s == PAT_OK && !(flags & PAT_MESH_SKIP_STABILITY)) s = check_stability(h, nullptr);
+  } catch (const std::bad_alloc&) {
+    set_error("pat_mesh_create: out of host memory");
+    s = PAT_ENOMEM;
+  }
+  if (s != PAT_OK) {
+    delete mesh;
+    return s;
+  }
+  m.N = h.N;
+  m.E = h.E;
+  m.n_obs = n_obs;
+  m.n_steps = n_steps;
+  m.dt = dt;
+  m.prec = prec;
+  m.split = (prec == PAT_F32) && !(flags & PAT_MESH_SINGLE_COEF);
+  const bool keep_zeros = (flags & PAT_MESH_KEEP_ZEROS) != 0;
+  const int64_t N = h.N;
+  m.host_only = (flags & PAT_MESH_HOST_ONLY) != 0;
+  m.device = -1;
+  if (!m.host_only) cudaGetDevice(&m.device);
+
+  // sensor lists per node (for the adjoint's injection entries)
+  std::vector<std::vector<std::pair<int32_t, double>>> inj(N);
+  for (int32_t d = 0; d < n_obs; ++d)
+    for (int a = 0; a < 3; ++a) inj[h.det_node[3 * d + a]].push_back({d, h.det_w[3 * d + a]});
+
+  HostRows F, A;
+  F.ptr.assign(N + 1, 0);
+  A.ptr.assign(N + 1, 0);
+  int64_t nnz_k = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const double mi = h.ml[i];
+    for (int64_t e = h.k_ptr[i]; e < h.k_ptr[i + 1]; ++e) {
+      const double kv = h.k_val[e];
+      if (kv == 0.0 && !keep_zeros) continue;  // an exact zero adds exactly nothing
+      F.col.push_back((uint32_t)h.k_col[e]);
+      F.val.push_back(dt * dt * kv / mi);
+      A.col.push_back((uint32_t)h.k_col[e]);
+      A.val.push_back(dt * dt * kv);
+      ++nnz_k;
+    }
+    for (int64_t e = h.b_ptr[i]; e < h.b_ptr[i + 1]; ++e) {
+      F.col.push_back((uint32_t)h.b_col[e] | kTagB);
+      F.val.push_back(dt * h.b_val[e] / mi);
+      A.col.push_back((uint32_t)h.b_col[e] | kTagB);
+      A.val.push_back(dt * h.b_val[e] / mi);
+    }
+    for (const auto& pr : inj[i]) {
+      A.col.push_back((uint32_t)pr.first | kTagInj);
+      // the same rounded weight as the forward gather, so Pi^T is Pi's exact transpose
+      A.val.push_back(prec == PAT_F32 ? (double)(float)pr.second : pr.second);
+    }
+    if (F.col.size() > 0x7fffffffu || A.col.size() > 0x7fffffffu) {
+      set_error("pat_mesh_create: operator too large for 32-bit row offsets");
+      delete mesh;
+      return PAT_EINVAL;
+    }
+    F.ptr[i + 1] = (int32_t)F.col.size();
+    A.ptr[i + 1] = (int32_t)A.col.size();
+  }
+  // injection values are already rounded to the state precision, so their low part is 0
+  std::vector<double> ml(h.ml), sqml(N), minv(N);
+  for (int64_t i = 0; i < N; ++i) {
+    sqml[i] = std::sqrt(h.ml[i]);
+    minv[i] = 1.0 / h.ml[i];
+  }
+  std::vector<int32_t> det_node(h.det_node);
+  if (m.host_only) {
+    m.fwd.nnz = (int64_t)F.col.size();
+    m.adj.nnz = (int64_t)A.col.size();
+  } else if (prec == PAT_F64) {
+    s = upload_rows<double>(F, false, m.fwd);
+    if (!s) s = upload_rows<double>(A, false, m.adj);
+    double* p = nullptr;
+    if (!s) s = upload(minv, &p);
+    m.minv_hi = p;
+    double* w = nullptr;
+    if (!s) s = upload(h.det_w, &w);
+    m.det_w = w;
+  } else {
+    s = upload_rows<float>(F, m.split, m.fwd);
+    if (!s) s = upload_rows<float>(A, m.split, m.adj);
+    std::vector<float> mh(N), mlo(N), dw(h.det_w.size());
+    for (int64_t i = 0; i < N; ++i) {
+      mh[i] = (float)minv[i];
+      mlo[i] = (float)(minv[i] - (double)mh[i]);
+    }
+    for (size_t e = 0; e < dw.size(); ++e) dw[e] = (float)h.det_w[e];
+    float* p = nullptr;
+    if (!s) s = upload(mh, &p);
+    m.minv_hi = p;
+    if (!s && m.split) s = upload(mlo, &m.minv_lo);
+    float* w = nullptr;
+    if (!s) s = upload(dw, &w);
+    m.det_w = w;
+  }
+  if (!s && !m.host_only) s = upload(ml, &m.ml);
+  if (!s && !m.host_only) s = upload(sqml, &m.sqrt_ml);
+  if (!s && !m.host_only) s = upload(det_node, &m.det_node);
+  if (s) {
+    free_mesh(m);
+    delete mesh;
+    return s;
+  }
+  pat_mesh_info& I = m.info;
+  I.n_nodes = N;
+  I.n_tets = h.E;
+  I.n_boundary_faces = (int64_t)h.bfaces.size() / 3;
+  I.n_boundary_nodes = h.n_boundary_nodes;
+  I.nnz_K = nnz_k;
+  I.nnz_K_graph = (int64_t)h.k_col.size();
+  I.nnz_B = (int64_t)h.b_col.size();
+  I.n_obs = n_obs;
+  I.n_steps = n_steps;
+  I.prec = prec;
+  I.dt = dt;
+  const double vb = prec == PAT_F64 ? 8.0 : (m.split ? 8.0 : 4.0);
+  I.operator_bytes = (double)(N + 1) * 4.0 + (double)m.fwd.nnz * (4.0 + vb);
+  cudaError_t e = m.host_only ? cudaSuccess : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cuda_check(e, "pat_mesh_create");
+    free_mesh(m);
+    delete mesh;
+    return PAT_ECUDA;
+  }
+  *out = mesh;
+  return PAT_OK;
+}
+
+pat_status pat_mesh_destroy(pat_mesh* mesh) {
+  clear_error();
+  if (!mesh) return PAT_OK;
+  free_mesh(mesh->d);
+  delete mesh;
+  return PAT_OK;
+}
+
+pat_status pat_mesh_query(const pat_mesh* mesh, pat_mesh_info* info) {
+  clear_error();
+  if (!mesh || !info) {
+    set_error("pat_mesh_query: NULL argument");
+    return PAT_EINVAL;
+  }
+  *info = mesh->d.info;
+  return PAT_OK;
+}
+
+pat_status pat_mesh_export(const pat_mesh* mesh, double* lumped_mass, int32_t* det_nodes, double* det_w,
+                           int32_t* boundary_faces) {
+  clear_error();
+  if (!mesh) {
+    set_error("pat_mesh_export: NULL mesh");
+    return PAT_EINVAL;
+  }
+  const HostMesh& h = mesh->d.host;
+  if (lumped_mass) std::memcpy(lumped_mass, h.ml.data(), h.ml.size() * sizeof(double));
+  if (det_nodes) std::memcpy(det_nodes, h.det_node.data(), h.det_node.size() * sizeof(int32_t));
+  if (det_w) std::memcpy(det_w, h.det_w.data(), h.det_w.size() * sizeof(double));
+  if (boundary_faces) std::memcpy(boundary_faces, h.bfaces.data(), h.bfaces.size() * sizeof(int32_t));
+  return PAT_OK;
+}
+
+pat_status pat_mesh_export_csr(const pat_mesh* mesh, int32_t which, int64_t* nnz, int64_t* row_ptr, int32_t* col,
+                               double* val) {
+  clear_error();
+  if (!mesh || (which != 0 && which != 1)) {
+    set_error("pat_mesh_export_csr: NULL mesh or which not in {0, 1}");
+    return PAT_EINVAL;
+  }
+  const HostMesh& h = mesh->d.host;
+  const auto& P = which == 0 ? h.k_ptr : h.b_ptr;
+  const auto& C = which == 0 ? h.k_col : h.b_col;
+  const auto& Vv = which == 0 ? h.k_val : h.b_val;
+  if (nnz) *nnz = (int64_t)C.size();
+  if (row_ptr) std::memcpy(row_ptr, P.data(), P.size() * sizeof(int64_t));
+  if (col) std::memcpy(col, C.data(), C.size() * sizeof(int32_t));
+  if (val) std::memcpy(val, Vv.data(), Vv.size() * sizeof(double));
+  return PAT_OK;
+}
+
+pat_status pat_workspace_bytes(const pat_mesh* mesh, int32_t op, int32_t K, size_t* bytes) {
+  clear_error();
+  if (!mesh || !bytes || op < 0 || op > 2) {
+    set_error("pat_workspace_bytes: NULL argument or op not in {0, 1, 2}");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_workspace_bytes")) return PAT_EINVAL;
+  *bytes = (op == 2) ? rto_layout(mesh->d, K).total : state_bytes(mesh->d, K);
+  return PAT_OK;
+}
+
+pat_status pat_forward(const pat_mesh* mesh, const void* p0, int32_t K, void* Y, double scale, void* ws,
+                       size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || !p0 || !Y) {
+    set_error("pat_forward: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_forward") || !check_device(mesh, "pat_forward")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 0, K, ws, ws_bytes, "pat_forward");
+  if (s) return s;
+  return forward(mesh->d, p0, K, Y, scale, ws, (cudaStream_t)stream);
+}
+
+pat_status pat_adjoint(const pat_mesh* mesh, const void* Yhat, int32_t K, void* p_hat, double scale, void* ws,
+                       size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || !Yhat || !p_hat) {
+    set_error("pat_adjoint: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_adjoint") || !check_device(mesh, "pat_adjoint")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 1, K, ws, ws_bytes, "pat_adjoint");
+  if (s) return s;
+  return adjoint(mesh->d, Yhat, K, p_hat, scale, ws, (cudaStream_t)stream);
+}
+
+pat_status pat_cgls_layout(const pat_mesh* mesh, int32_t K, size_t* off) {
+  clear_error();
+  if (!mesh || !off) {
+    set_error("pat_cgls_layout: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_cgls_layout")) return PAT_EINVAL;
+  const RtoLayout L = rto_layout(mesh->d, K);
+  off[0] = L.x;
+  off[1] = L.d;
+  off[2] = L.r_d;
+  off[3] = L.r_p;
+  off[4] = L.s;
+  off[5] = L.gamma;
+  off[6] = L.status;
+  return PAT_OK;
+}
+
+pat_status pat_cgls_begin(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, const void* eta,
+                          const void* xi, uint64_t seed, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || !y_obs) {
+    set_error("pat_cgls_begin: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) {
+    set_error("pat_cgls_begin: sigma must be finite and > 0 (got %g)", sigma);
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_cgls_begin") || !check_device(mesh, "pat_cgls_begin")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_cgls_begin");
+  if (s) return s;
+  return cgls_begin(mesh->d, y_obs, sigma, K, eta, xi, seed, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_cgls_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32_t n_iter, double* resid, void* ws,
+                            size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || n_iter < 0) {
+    set_error("pat_cgls_iterate: NULL mesh or n_iter < 0");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_cgls_iterate") || !check_device(mesh, "pat_cgls_iterate")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_cgls_iterate");
+  if (s) return s;
+  return cgls_iterate(mesh->d, sigma, K, n_iter, resid, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_cgls_finish(const pat_mesh* mesh, int32_t K, double* samples, double* mean, double* stdev, void* ws,
+                           size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh) {
+    set_error("pat_cgls_finish: NULL mesh");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_cgls_finish") || !check_device(mesh, "pat_cgls_finish")) return PAT_EINVAL;
+  if (stdev && K < 2) {
+    set_error("pat_cgls_finish: the std estimator needs K >= 2");
+    return PAT_EINVAL;
+  }
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_cgls_finish");
+  if (s) return s;
+  return cgls_finish(mesh->d, K, samples, mean, stdev, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, int32_t n_iter,
+                          const void* eta, const void* xi, uint64_t seed, double* samples, double* mean,
+                          double* stdev, double* resid, void* ws, size_t ws_bytes, void* stream) {
+  pat_status s = pat_cgls_begin(mesh, y_obs, sigma, K, eta, xi, seed, ws, ws_bytes, stream);
+  if (s) return s;
+  if (resid) {
+    s = residual_norms(mesh->d, K, resid, (char*)ws, (cudaStream_t)stream);
+    if (s) return s;
+  }
+  s = pat_cgls_iterate(mesh, sigma, K, n_iter, resid ? resid + K : nullptr, ws, ws_bytes, stream);
+  if (s) return s;
+  return pat_cgls_finish(mesh, K, samples, mean, stdev, ws, ws_bytes, stream);
+}
+
+pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* ws, void* stream) {
+  clear_error();
+  if (!mesh || !ws) {
+    set_error("pat_rto_status: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_rto_status")) return PAT_EINVAL;
+  const RtoLayout L = rto_layout(mesh->d, K);
+  int word = 0;
+  pat_status s = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "pat_rto_status sync");
+  if (s) return s;
+  s = cuda_check(cudaMemcpy(&word, (const char*)ws + L.status, 4, cudaMemcpyDeviceToHost), "pat_rto_status read");
+  if (s) return s;
+  if (word != 0) {
+    set_error("CGLS produced a non-finite or non-positive scalar (status %d)", word);
+    return (pat_status)word;
+  }
+  return PAT_OK;
+}
+
+pat_status pat_profile_enable(pat_mesh* mesh, int32_t enable) {
+  clear_error();
+  if (!mesh) {
+    set_error("pat_profile_enable: NULL mesh");
+    return PAT_EINVAL;
+  }
+  Profiler& P = mesh->d.prof;
+  P.on = enable != 0;
+  P.used = 0;
+  P.fwd_launches = P.adj_launches = P.total_launches = 0;
+  return PAT_OK;
+}
+
+pat_status pat_profile_read(pat_mesh* mesh, pat_profile* out) {
+  clear_error();
+  if (!mesh || !out) {
+    set_error("pat_profile_read: NULL argument");
+    return PAT_EINVAL;
+  }
+  Profiler& P = mesh->d.prof;
+  pat_status s = cuda_check(cudaDeviceSynchronize(), "pat_profile_read sync");
+  if (s) return s;
+  std::memset(out, 0, sizeof(*out));
+  for (size_t i = 0; i < P.used; ++i) {
+    float ms = 0.0f;
+    s = cuda_check(cudaEventElapsedTime(&ms, (cudaEvent_t)P.events[2 * i], (cudaEvent_t)P.events[2 * i + 1]),
+                   "pat_profile_read elapsed");
+    if (s) return s;
+    if (P.kind[i] == 0) {
+      out->fwd_ms += ms;
+      out->fwd_loops++;
+    } else {
+      out->adj_ms += ms;
+      out->adj_loops++;
+    }
+  }
+  out->fwd_launches = P.fwd_launches;
+  out->adj_launches = P.adj_launches;
+  out->total_launches = P.total_launches;
+  return PAT_OK;
+}
+
+pat_status pat_draw_normals(uint64_t seed, int32_t stream_id, int64_t n_elem, int32_t K, double* out, void* stream) {
+  clear_error();
+  if (!out || n_elem < 0 || K < 1 || (stream_id != 0 && stream_id != 1)) {
+    set_error("pat_draw_normals: bad argument");
+    return PAT_EINVAL;
+  }
+  return draw_normals(seed, stream_id, n_elem, K, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Internal declarations shared by the host assembly, the kernels and the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pat.h"
+
+namespace pat {
+
+// Thread-local error message behind pat_last_error().
+void set_error(const char* fmt, ...);
+void clear_error();
+const char* last_error();
+
+// Column tags of the device CSR rows (see DeviceMesh).
+constexpr uint32_t kTagB = 0x80000000u;    // entry acts on the velocity-like field
+constexpr uint32_t kTagInj = 0x40000000u;  // entry injects a sensor value (adjoint)
+constexpr uint32_t kIdxMask = 0x3FFFFFFFu;
+
+// FP64 assembly on the host (Section 3).
+struct HostMesh {
+  int64_t N = 0, E = 0;
+  int32_t n_obs = 0, n_steps = 0;
+  double dt = 0.0;
+  std::vector<double> xyz;          // [N][3]
+  std::vector<int32_t> tets;        // [E][4]
+  std::vector<double> c2;           // [E]
+  std::vector<double> vol;          // [E]
+  std::vector<double> grads;        // [E][4][3] barycentric gradients
+  std::vector<double> ml;           // [N] lumped mass
+  // stiffness on the full P1 graph (sorted columns, exact zeros kept)
+  std::vector<int64_t> k_ptr;
+  std::vector<int32_t> k_col;
+  std::vector<double> k_val;
+  // boundary mass
+  std::vector<int32_t> bfaces;      // [F][3] sorted triples, lexicographic
+  std::vector<int64_t> b_ptr;
+  std::vector<int32_t> b_col;
+  std::vector<double> b_val;
+  int64_t n_boundary_nodes = 0;
+  // sensors
+  std::vector<int32_t> det_node;    // [n_obs][3]
+  std::vector<double> det_w;        // [n_obs][3]
+};
+
+// Fills everything but the sensors; returns PAT_OK or an error (message set).
+pat_status assemble_host(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
+                         const double* c2, HostMesh& m);
+// Locates sensors on boundary triangles.
+pat_status locate_sensors(const double* det_xyz, int32_t n_obs, HostMesh& m);
+// Growth check of the propagator (FP64, host).  Returns PAT_OK or PAT_EUNSTABLE.
+pat_status check_stability(const HostMesh& m, double* growth_out);
+
+// Device copies.  One CSR per direction, each row holding tagged entries:
+//   forward row i:  K entries  (col j, value dt^2 K_ij / M_i)       acting on a
+//                   B entries  (col j | kTagB, value dt B_ij / M_i)   acting on w
+//   adjoint row i:  K entries  (col j, value dt^2 K_ij)               acting on u
+//                   B entries  (col j | kTagB, value dt B_ij / M_i)   acting on u
+//                   sensor entries (col d | kTagInj, value w_di)      reading yhat
+// Values are split hi + lo (two floats) for FP32 meshes unless single-coefficient
+// storage was requested; FP64 meshes store one double.
+struct DevCSR {
+  int32_t* ptr = nullptr;
+  uint32_t* col = nullptr;
+  void* hi = nullptr;   // float or double
+  float* lo = nullptr;  // FP32 split meshes only
+  int64_t nnz = 0;
+};
+
+// Event-based loop timing and launch counting (pat_profile_*).
+struct Profiler {
+  bool on = false;
+  std::vector<void*> events;  // cudaEvent_t pool, pairs (start, stop)
+  std::vector<int> kind;      // per pair: 0 forward, 1 adjoint
+  size_t used = 0;            // pairs in use
+  int64_t fwd_launches = 0, adj_launches = 0, total_launches = 0;
+};
+
+struct DeviceMesh {
+  int64_t N = 0, E = 0;
+  int32_t n_obs = 0, n_steps = 0;
+  double dt = 0.0;
+  pat_prec prec = PAT_F32;
+  bool split = true;
+  bool host_only = false;
+  int device = 0;
+  DevCSR fwd, adj;
+  void* minv_hi = nullptr;   // [N] real: 1 / M_i
+  float* minv_lo = nullptr;  // [N]
+  double* ml = nullptr;      // [N] double
+  double* sqrt_ml = nullptr; // [N] double
+  int32_t* det_node = nullptr;  // [n_obs][3]
+  void* det_w = nullptr;        // [n_obs][3] real
+  pat_mesh_info info{};
+  HostMesh host;             // kept for export / checks
+  mutable Profiler prof;
+};
+
+}  // namespace pat
+
+struct pat_mesh {
+  pat::DeviceMesh d;
+};

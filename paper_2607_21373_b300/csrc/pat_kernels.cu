@@ -1,0 +1,585 @@
+// Launchers of the time-step kernels and the batched CGLS driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "pat_kernels.cuh"
+#include "pat_solver.cuh"
+
+namespace pat {
+
+pat_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PAT_OK;
+  set_error("%s: CUDA error %d (%s)", what, (int)e, cudaGetErrorString(e));
+  return PAT_ECUDA;
+}
+
+#define PAT_TRY(expr)                       \
+  do {                                      \
+    pat_status _s = (expr);                 \
+    if (_s != PAT_OK) return _s;            \
+  } while (0)
+
+int sm_count() {
+  int dev = 0, n = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
+// Profiling hooks (no-ops unless pat_profile_enable was called on the mesh).
+static void* prof_event(const DeviceMesh& m, size_t idx) {
+  Profiler& P = m.prof;
+  while (P.events.size() <= idx) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    P.events.push_back((void*)e);
+  }
+  return P.events[idx];
+}
+static size_t prof_begin(const DeviceMesh& m, int kind, cudaStream_t st) {
+  Profiler& P = m.prof;
+  if (!P.on) return (size_t)-1;
+  const size_t pair = P.used++;
+  void* e = prof_event(m, 2 * pair);
+  prof_event(m, 2 * pair + 1);
+  if (P.kind.size() <= pair) P.kind.resize(pair + 1);
+  P.kind[pair] = kind;
+  if (e) cudaEventRecord((cudaEvent_t)e, st);
+  return pair;
+}
+static void prof_end(const DeviceMesh& m, size_t pair, int64_t launches, cudaStream_t st) {
+  Profiler& P = m.prof;
+  if (!P.on || pair == (size_t)-1) return;
+  void* e = prof_event(m, 2 * pair + 1);
+  if (e) cudaEventRecord((cudaEvent_t)e, st);
+  (P.kind[pair] == 0 ? P.fwd_launches : P.adj_launches) += launches;
+  P.total_launches += launches;
+}
+static inline void count(const DeviceMesh& m, int64_t n) {
+  if (m.prof.on) m.prof.total_launches += n;
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+static inline size_t real_size(const DeviceMesh& m) { return m.prec == PAT_F64 ? 8 : 4; }
+
+size_t state_bytes(const DeviceMesh& m, int K) { return align256(4 * (size_t)m.N * K * real_size(m)); }
+
+// Widest per-thread vector that divides K and keeps every access aligned.
+template <typename T>
+static int pick_vec(int K, std::initializer_list<const void*> ptrs) {
+  int V = (sizeof(T) == 4) ? 4 : 2;
+  while (V > 1) {
+    bool ok = (K % V) == 0;
+    for (const void* p : ptrs)
+      if (p && (reinterpret_cast<uintptr_t>(p) % (V * sizeof(T))) != 0) ok = false;
+    if (ok) break;
+    V /= 2;
+  }
+  return V;
+}
+
+template <typename T, int V, bool SPLIT>
+static void launch_fwd(const FwdArgs<T>& a, int64_t threads, cudaStream_t st) {
+  const int64_t blocks = (threads + 255) / 256;
+  fwd_step_kernel<T, V, SPLIT><<<(unsigned)blocks, 256, 0, st>>>(a);
+}
+template <typename T, int V, bool SPLIT>
+static void launch_adj(const AdjArgs<T>& a, cudaStream_t st) {
+  const int64_t blocks = (a.row_threads + 255) / 256;
+  adj_step_kernel<T, V, SPLIT><<<(unsigned)blocks, 256, 0, st>>>(a);
+}
+
+template <typename T, int V, bool SPLIT>
+static pat_status forward_t(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
+  const int64_t NK = m.N * (int64_t)K;
+  T* a[2] = {ws, ws + 2 * NK};
+  T* w[2] = {ws + NK, ws + 3 * NK};
+  FwdArgs<T> A{};
+  A.N = m.N;
+  A.K = K;
+  A.n_obs = m.n_obs;
+  A.row_threads = NK / V;
+  A.ptr = m.fwd.ptr;
+  A.col = m.fwd.col;
+  A.hi = static_cast<const T*>(m.fwd.hi);
+  A.lo = m.fwd.lo;
+  A.det_node = m.det_node;
+  A.det_w = static_cast<const T*>(m.det_w);
+  A.scale = scale;
+  const int64_t obs_threads = (int64_t)m.n_obs * K / V;
+  const int64_t ystride = (int64_t)m.n_obs * K;
+  const size_t pp = prof_begin(m, 0, st);
+  for (int s = 0; s < m.n_steps; ++s) {
+    A.a_in = (s == 0) ? p0 : a[(s - 1) & 1];
+    A.w_in = (s == 0) ? nullptr : w[(s - 1) & 1];
+    A.a_out = a[s & 1];
+    A.w_out = w[s & 1];
+    A.y_out = (s == 0) ? nullptr : Y + (int64_t)(s - 1) * ystride;  // observation of state s
+    launch_fwd<T, V, SPLIT>(A, A.row_threads + (s == 0 ? 0 : obs_threads), st);
+  }
+  // observation of the final state N_T
+  A.a_in = a[(m.n_steps - 1) & 1];
+  A.w_in = w[(m.n_steps - 1) & 1];
+  A.a_out = nullptr;
+  A.w_out = nullptr;
+  A.y_out = Y + (int64_t)(m.n_steps - 1) * ystride;
+  FwdArgs<T> G = A;
+  G.row_threads = 0;
+  launch_fwd<T, V, SPLIT>(G, obs_threads, st);
+  prof_end(m, pp, m.n_steps + 1, st);
+  return cuda_check(cudaGetLastError(), "forward step launch");
+}
+
+template <typename T, int V, bool SPLIT>
+static pat_status adjoint_t(const DeviceMesh& m, const T* Yhat, int K, T* out, T scale, T* ws, cudaStream_t st) {
+  const int64_t NK = m.N * (int64_t)K;
+  T* ah[2] = {ws, ws + 2 * NK};
+  T* u[2] = {ws + NK, ws + 3 * NK};
+  AdjArgs<T> A{};
+  A.N = m.N;
+  A.K = K;
+  A.row_threads = NK / V;
+  A.ptr = m.adj.ptr;
+  A.col = m.adj.col;
+  A.hi = static_cast<const T*>(m.adj.hi);
+  A.lo = m.adj.lo;
+  A.minv_hi = static_cast<const T*>(m.minv_hi);
+  A.minv_lo = m.minv_lo;
+  A.inj_scale = scale;
+  const int64_t ystride = (int64_t)m.n_obs * K;
+  const int NT = m.n_steps;
+  // zero state + injection of the last observation time
+  const size_t pp = prof_begin(m, 1, st);
+  A.ah_in = nullptr;
+  A.u_in = nullptr;
+  A.ah_out = ah[0];
+  A.u_out = u[0];
+  A.yhat = Yhat + (int64_t)(NT - 1) * ystride;
+  launch_adj<T, V, SPLIT>(A, st);
+  int cur = 0;
+  for (int mstep = NT; mstep >= 1; --mstep) {
+    A.ah_in = ah[cur];
+    A.u_in = u[cur];
+    A.ah_out = (mstep == 1 && out) ? out : ah[cur ^ 1];
+    A.u_out = u[cur ^ 1];
+    A.yhat = (mstep >= 2) ? Yhat + (int64_t)(mstep - 2) * ystride : nullptr;
+    launch_adj<T, V, SPLIT>(A, st);
+    cur ^= 1;
+  }
+  prof_end(m, pp, NT + 1, st);
+  return cuda_check(cudaGetLastError(), "adjoint step launch");
+}
+
+template <typename T>
+static pat_status forward_disp(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
+  const int V = pick_vec<T>(K, {p0, Y, ws});
+  const bool sp = m.split;
+  if constexpr (sizeof(T) == 4) {
+    if (V == 4) return sp ? forward_t<T, 4, true>(m, p0, K, Y, scale, ws, st) : forward_t<T, 4, false>(m, p0, K, Y, scale, ws, st);
+    if (V == 2) return sp ? forward_t<T, 2, true>(m, p0, K, Y, scale, ws, st) : forward_t<T, 2, false>(m, p0, K, Y, scale, ws, st);
+    return sp ? forward_t<T, 1, true>(m, p0, K, Y, scale, ws, st) : forward_t<T, 1, false>(m, p0, K, Y, scale, ws, st);
+  } else {
+    if (V == 2) return forward_t<T, 2, false>(m, p0, K, Y, scale, ws, st);
+    return forward_t<T, 1, false>(m, p0, K, Y, scale, ws, st);
+  }
+}
+
+template <typename T>
+static pat_status adjoint_disp(const DeviceMesh& m, const T* Yh, int K, T* out, T scale, T* ws, cudaStream_t st) {
+  const int V = pick_vec<T>(K, {Yh, out, ws});
+  const bool sp = m.split;
+  if constexpr (sizeof(T) == 4) {
+    if (V == 4) return sp ? adjoint_t<T, 4, true>(m, Yh, K, out, scale, ws, st) : adjoint_t<T, 4, false>(m, Yh, K, out, scale, ws, st);
+    if (V == 2) return sp ? adjoint_t<T, 2, true>(m, Yh, K, out, scale, ws, st) : adjoint_t<T, 2, false>(m, Yh, K, out, scale, ws, st);
+    return sp ? adjoint_t<T, 1, true>(m, Yh, K, out, scale, ws, st) : adjoint_t<T, 1, false>(m, Yh, K, out, scale, ws, st);
+  } else {
+    if (V == 2) return adjoint_t<T, 2, false>(m, Yh, K, out, scale, ws, st);
+    return adjoint_t<T, 1, false>(m, Yh, K, out, scale, ws, st);
+  }
+}
+
+pat_status forward(const DeviceMesh& m, const void* p0, int K, void* Y, double scale, void* ws, cudaStream_t st) {
+  if (m.prec == PAT_F64)
+    return forward_disp<double>(m, (const double*)p0, K, (double*)Y, scale, (double*)ws, st);
+  return forward_disp<float>(m, (const float*)p0, K, (float*)Y, (float)scale, (float*)ws, st);
+}
+
+pat_status adjoint(const DeviceMesh& m, const void* Yh, int K, void* out, double scale, void* ws, cudaStream_t st) {
+  if (m.prec == PAT_F64)
+    return adjoint_disp<double>(m, (const double*)Yh, K, (double*)out, scale, (double*)ws, st);
+  return adjoint_disp<float>(m, (const float*)Yh, K, (float*)out, (float)scale, (float*)ws, st);
+}
+
+// ===========================================================================
+// Batched CGLS (textbook CGLS on the extended system, eq. extended-matrices;
+// per-sample scalars and the iterate x in FP64)
+// ===========================================================================
+
+// Counter-based normal draws.  SplitMix64 (Steele, Lea, Flood 2014): the i-th
+// output of a generator seeded with s is mix(s + i * 0x9E3779B97F4A7C15).  A
+// draw keyed by (seed, stream, sample k, element e) uses outputs 2c+1 and 2c+2
+// with c = ((k << 1 | stream) << 40) | e as two uniforms for Box-Muller
+// (cosine branch): z = sqrt(-2 ln u1) cos(2 pi u2), u1 in (0, 1].
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double normal_draw(uint64_t seed, int stream, uint64_t k, uint64_t e) {
+  const uint64_t c = (((k << 1) | (uint64_t)stream) << 40) | e;
+  const uint64_t h1 = splitmix_out(seed, 2 * c + 1);
+  const uint64_t h2 = splitmix_out(seed, 2 * c + 2);
+  const double u1 = ((double)(h1 >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(h2 >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+__global__ void draw_normals_kernel(uint64_t seed, int stream, int64_t n_elem, int K, double* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_elem * K) return;
+  const int64_t e = t / K;
+  const int k = (int)(t - e * K);
+  out[t] = normal_draw(seed, stream, (uint64_t)k, (uint64_t)e);
+}
+
+// r_d = y_obs / sigma + eta, r_p = xi  (b of eq. extended-matrices with C = M_L^{-1})
+template <typename T>
+__global__ void rhs_kernel(int64_t n_data, int64_t N, int K, const T* __restrict__ y_obs, const T* __restrict__ eta,
+                           const T* __restrict__ xi, uint64_t seed, double inv_sigma, T* __restrict__ r_d,
+                           T* __restrict__ r_p) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nd = n_data * K;
+  if (t < nd) {
+    const int64_t e = t / K;
+    const int k = (int)(t - e * K);
+    const double et = eta ? (double)eta[t] : normal_draw(seed, 0, (uint64_t)k, (uint64_t)e);
+    r_d[t] = (T)((double)y_obs[e] * inv_sigma + et);
+  } else if (t < nd + N * K) {
+    const int64_t u = t - nd;
+    const int64_t i = u / K;
+    const int k = (int)(u - i * K);
+    r_p[u] = xi ? xi[u] : (T)normal_draw(seed, 1, (uint64_t)k, (uint64_t)i);
+  }
+}
+
+// Deterministic per-sample reductions: block b sums rows b*rpb + r0 + j*grid*rpb
+// for its sample column k = tid % K, then the rpb partial sums of a block are
+// added in order; partial[b][k].  Mode 0: sum x^2; mode 1: sum w_r x^2.
+struct RedShape {
+  int rpb, bdim, grid;
+};
+static RedShape red_shape(int K, int64_t rows, int n_part) {
+  RedShape r;
+  r.rpb = std::max(1, 256 / K);
+  r.bdim = r.rpb * K;
+  r.grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_part, (rows + r.rpb - 1) / r.rpb));
+  return r;
+}
+
+template <typename T, bool WEIGHTED>
+__global__ void sumsq_kernel(const T* __restrict__ X, const double* __restrict__ w, int64_t rows, int K, int rpb,
+                             double* __restrict__ partial) {
+  extern __shared__ double sh[];
+  const int k = threadIdx.x % K;
+  const int r0 = threadIdx.x / K;
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * rpb + r0; r < rows; r += (int64_t)gridDim.x * rpb) {
+    const double x = (double)X[r * K + k];
+    acc += WEIGHTED ? w[r] * x * x : x * x;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (r0 == 0) {
+    double s = 0.0;
+    for (int j = 0; j < rpb; ++j) s += sh[j * K + k];
+    partial[(int64_t)blockIdx.x * K + k] = s;
+  }
+}
+
+// s = ah + sqrt(M_L) r_p (eq. lsqr-transpose-action), optionally d = s, and sum s^2.
+template <typename T>
+__global__ void combine_s_kernel(const T* ah, const T* __restrict__ r_p, const double* __restrict__ sqml,
+                                 int64_t rows, int K, int rpb, T* s_out, T* __restrict__ d_out,
+                                 double* __restrict__ partial) {
+  extern __shared__ double sh[];
+  const int k = threadIdx.x % K;
+  const int r0 = threadIdx.x / K;
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * rpb + r0; r < rows; r += (int64_t)gridDim.x * rpb) {
+    const int64_t i = r * K + k;
+    const T s = (T)((double)ah[i] + sqml[r] * (double)r_p[i]);
+    s_out[i] = s;
+    if (d_out) d_out[i] = s;
+    acc += (double)s * (double)s;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (r0 == 0) {
+    double t = 0.0;
+    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
+    partial[(int64_t)blockIdx.x * K + k] = t;
+  }
+}
+
+__global__ void set_double_kernel(double* p, double v) { *p = v; }
+
+__device__ __forceinline__ void flag(int* status, int code) { atomicCAS(status, 0, code); }
+
+// gamma = sum of partial slot A (first CGLS scalar)
+__global__ void finalize_gamma0_kernel(const double* pa, int na, int K, double* gamma, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  if (!isfinite(s)) flag(status, PAT_ENUMERIC);
+  gamma[k] = s;
+}
+
+// alpha = gamma / ||q||^2, ||q||^2 = ||q_d||^2 + ||M^{1/2} d||^2
+__global__ void finalize_alpha_kernel(const double* pa, int na, const double* pb, int nb, int K, const double* gamma,
+                                      double* alpha, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  for (int b = 0; b < nb; ++b) s += pb[(int64_t)b * K + k];
+  double a = 0.0;
+  if (gamma[k] == 0.0) {
+    a = 0.0;  // converged exactly: keep the iterate
+  } else if (!(s > 0.0) || !isfinite(s) || !isfinite(gamma[k])) {
+    flag(status, PAT_ENUMERIC);
+  } else {
+    a = gamma[k] / s;
+  }
+  alpha[k] = a;
+}
+
+// gamma' = ||s||^2, beta = gamma'/gamma, gamma = gamma'
+__global__ void finalize_beta_kernel(const double* pa, int na, int K, double* gamma, double* beta, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  double bt = 0.0;
+  if (gamma[k] > 0.0 && isfinite(s)) {
+    bt = s / gamma[k];
+  } else if (gamma[k] != 0.0 || !isfinite(s)) {
+    flag(status, PAT_ENUMERIC);
+  }
+  beta[k] = bt;
+  gamma[k] = s;
+}
+
+__global__ void finalize_sum2_kernel(const double* pa, int na, const double* pb, int nb, int K, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  for (int b = 0; b < nb; ++b) s += pb[(int64_t)b * K + k];
+  out[k] = s;
+}
+
+// x += alpha d (FP64), r_p -= alpha sqrt(M_L) d
+template <typename T>
+__global__ void update_x_rp_kernel(int64_t N, int K, const double* __restrict__ alpha, const T* __restrict__ d,
+                                   const double* __restrict__ sqml, double* __restrict__ x, T* __restrict__ r_p) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * K) return;
+  const int64_t i = t / K;
+  const int k = (int)(t - i * K);
+  const double a = alpha[k];
+  const double dv = (double)d[t];
+  x[t] += a * dv;
+  r_p[t] = (T)((double)r_p[t] - a * sqml[i] * dv);
+}
+
+// r_d -= alpha q_d
+template <typename T>
+__global__ void update_rd_kernel(int64_t n, int K, const double* __restrict__ alpha, const T* __restrict__ q,
+                                 T* __restrict__ r) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int k = (int)(t % K);
+  r[t] = (T)((double)r[t] - alpha[k] * (double)q[t]);
+}
+
+// d = s + beta d
+template <typename T>
+__global__ void update_d_kernel(int64_t N, int K, const double* __restrict__ beta, const T* __restrict__ s,
+                                T* __restrict__ d) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * K) return;
+  const int k = (int)(t % K);
+  d[t] = (T)((double)s[t] + beta[k] * (double)d[t]);
+}
+
+// eq. ergodic: mean and std with 1/(K-1), per node, two passes in FP64
+__global__ void mean_std_kernel(int64_t N, int K, const double* __restrict__ x, double* __restrict__ mean,
+                                double* __restrict__ stdev) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* r = x + i * K;
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += r[k];
+  const double m = s / K;
+  if (mean) mean[i] = m;
+  if (stdev) {
+    double v = 0.0;
+    for (int k = 0; k < K; ++k) v += (r[k] - m) * (r[k] - m);
+    stdev[i] = K > 1 ? sqrt(v / (K - 1)) : 0.0;
+  }
+}
+
+RtoLayout rto_layout(const DeviceMesh& m, int K) {
+  RtoLayout L{};
+  const size_t rs = real_size(m);
+  const size_t NK = (size_t)m.N * K;
+  const size_t DK = (size_t)m.n_steps * m.n_obs * K;
+  L.n_part = std::min(1024, 2 * sm_count());
+  size_t o = 0;
+  L.x = o; o = align256(o + NK * 8);
+  L.d = o; o = align256(o + NK * rs);
+  L.r_d = o; o = align256(o + DK * rs);
+  L.q_d = o; o = align256(o + DK * rs);
+  L.r_p = o; o = align256(o + NK * rs);
+  L.s = o; o = align256(o + NK * rs);
+  L.state = o; o = align256(o + 4 * NK * rs);
+  L.gamma = o; o = align256(o + K * 8);
+  L.alpha = o; o = align256(o + K * 8);
+  L.beta = o; o = align256(o + K * 8);
+  L.sigma = o; o = align256(o + 8);
+  L.partial = o; o = align256(o + (size_t)4 * L.n_part * K * 8);
+  L.status = o; o = align256(o + 4);
+  L.total = o;
+  return L;
+}
+
+static inline unsigned nblocks(int64_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T>
+static pat_status begin_t(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
+                          uint64_t seed, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  T* r_d = (T*)(ws + L.r_d);
+  T* r_p = (T*)(ws + L.r_p);
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.status, 0, 4, st), "cgls_begin memset"));
+  set_double_kernel<<<1, 1, 0, st>>>((double*)(ws + L.sigma), sigma);
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.x, 0, (size_t)m.N * K * 8, st), "cgls_begin memset x"));
+  rhs_kernel<T><<<nblocks((ndata + m.N) * K), 256, 0, st>>>(ndata, m.N, K, y_obs, eta, xi, seed, 1.0 / sigma, r_d, r_p);
+  // s = A^T r, d = s, gamma = ||s||^2 (the transpose lands in s, combined in place)
+  T* ah = (T*)(ws + L.s);
+  PAT_TRY(adjoint(m, r_d, K, ah, 1.0 / sigma, ws + L.state, st));
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  double* part = (double*)(ws + L.partial);
+  combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
+      ah, r_p, m.sqrt_ml, m.N, K, rsN.rpb, (T*)(ws + L.s), (T*)(ws + L.d), part);
+  finalize_gamma0_kernel<<<nblocks(K, 128), 128, 0, st>>>(part, rsN.grid, K, (double*)(ws + L.gamma),
+                                                           (int*)(ws + L.status));
+  count(m, 4);
+  return cuda_check(cudaGetLastError(), "cgls_begin launch");
+}
+
+template <typename T>
+static pat_status residual_t(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  double* part = (double*)(ws + L.partial);
+  double* pa = part + 2 * (size_t)L.n_part * K;
+  double* pb = part + 3 * (size_t)L.n_part * K;
+  const RedShape rsD = red_shape(K, ndata, L.n_part);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  sumsq_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>((T*)(ws + L.r_d), nullptr, ndata, K,
+                                                                                 rsD.rpb, pa);
+  sumsq_kernel<T, false><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>((T*)(ws + L.r_p), nullptr, m.N, K,
+                                                                                 rsN.rpb, pb);
+  finalize_sum2_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
+  count(m, 3);
+  return cuda_check(cudaGetLastError(), "residual launch");
+}
+
+template <typename T>
+static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
+                            cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  if (!(sigma > 0.0)) {
+    set_error("pat_cgls_iterate: sigma must be > 0 (got %g)", sigma);
+    return PAT_EINVAL;
+  }
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  T* x_d = (T*)(ws + L.d);
+  T* r_d = (T*)(ws + L.r_d);
+  T* q_d = (T*)(ws + L.q_d);
+  T* r_p = (T*)(ws + L.r_p);
+  T* s = (T*)(ws + L.s);
+  double* x = (double*)(ws + L.x);
+  double* gamma = (double*)(ws + L.gamma);
+  double* alpha = (double*)(ws + L.alpha);
+  double* beta = (double*)(ws + L.beta);
+  int* status = (int*)(ws + L.status);
+  double* part = (double*)(ws + L.partial);
+  double* pa = part;
+  double* pb = part + (size_t)L.n_part * K;
+  const RedShape rsD = red_shape(K, ndata, L.n_part);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  for (int it = 0; it < n_iter; ++it) {
+    // q = A d: q_d = G d / sigma (forward), q_p = M^{1/2} d (implicit)
+    PAT_TRY(forward(m, x_d, K, q_d, 1.0 / sigma, ws + L.state, st));
+    sumsq_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>(q_d, nullptr, ndata, K, rsD.rpb, pa);
+    sumsq_kernel<T, true><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(x_d, m.ml, m.N, K, rsN.rpb, pb);
+    finalize_alpha_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, gamma, alpha, status);
+    update_x_rp_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, alpha, x_d, m.sqrt_ml, x, r_p);
+    update_rd_kernel<T><<<nblocks(ndata * K), 256, 0, st>>>(ndata, K, alpha, q_d, r_d);
+    // s = A^T r = G^T r_d / sigma + M^{1/2} r_p
+    PAT_TRY(adjoint(m, r_d, K, s, 1.0 / sigma, ws + L.state, st));
+    combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(s, r_p, m.sqrt_ml, m.N, K, rsN.rpb, s,
+                                                                               nullptr, pa);
+    finalize_beta_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, gamma, beta, status);
+    update_d_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, beta, s, x_d);
+    count(m, 8);
+    if (resid) PAT_TRY(residual_t<T>(m, K, resid + (int64_t)it * K, ws, st));
+  }
+  return cuda_check(cudaGetLastError(), "cgls_iterate launch");
+}
+
+pat_status cgls_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta, const void* xi,
+                      uint64_t seed, char* ws, cudaStream_t st) {
+  if (m.prec == PAT_F64)
+    return begin_t<double>(m, (const double*)y_obs, sigma, K, (const double*)eta, (const double*)xi, seed, ws, st);
+  return begin_t<float>(m, (const float*)y_obs, sigma, K, (const float*)eta, (const float*)xi, seed, ws, st);
+}
+
+pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
+                        cudaStream_t st) {
+  if (m.prec == PAT_F64) return iterate_t<double>(m, sigma, K, n_iter, resid, ws, st);
+  return iterate_t<float>(m, sigma, K, n_iter, resid, ws, st);
+}
+
+pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st) {
+  if (m.prec == PAT_F64) return residual_t<double>(m, K, out, ws, st);
+  return residual_t<float>(m, K, out, ws, st);
+}
+
+pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean, double* stdev, char* ws,
+                       cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const double* x = (const double*)(ws + L.x);
+  if (samples)
+    PAT_TRY(cuda_check(cudaMemcpyAsync(samples, x, (size_t)m.N * K * 8, cudaMemcpyDeviceToDevice, st),
+                       "cgls_finish copy"));
+  if (mean || stdev) {
+    mean_std_kernel<<<nblocks(m.N), 256, 0, st>>>(m.N, K, x, mean, stdev);
+    count(m, 1);
+  }
+  return cuda_check(cudaGetLastError(), "cgls_finish launch");
+}
+
+pat_status draw_normals(uint64_t seed, int stream_id, int64_t n_elem, int K, double* out, cudaStream_t st) {
+  draw_normals_kernel<<<nblocks(n_elem * K), 256, 0, st>>>(seed, stream_id, n_elem, K, out);
+  return cuda_check(cudaGetLastError(), "draw_normals launch");
+}
+
+}  // namespace pat

@@ -1,0 +1,113 @@
+"""C-ABI checks that need no GPU: exported symbols and the host-side assembly.
+
+The library's FP64 host assembly (pat_mesh_create with PAT_MESH_HOST_ONLY) is
+compared with the oracle's independent assembly: connectivity and sensor
+triangles bit-exact, values to FP64 rounding.
+"""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import fem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pat.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:pat_status|const char\*)\s+(pat_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_21373_b300 import _lib
+    return _lib.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2607_21373_b300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (pat_\w+)", out))
+    decl = declared_symbols()
+    assert len(decl) >= 15
+    missing = [s for s in decl if s not in exported]
+    assert not missing, missing
+    from paper_2607_21373_b300 import _lib
+    assert set(decl) <= set(_lib.SIGNATURES)
+
+
+def host_mesh(n, n_obs, faces, seed, dt_factor=0.3, flags=0x8 | 0x1):
+    from paper_2607_21373_b300 import Mesh
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, faces, seed)
+    m = Mesh(xyz, tets, det, dt_factor / n, 10, precision="f64", flags=flags)
+    return m, xyz, tets, det
+
+
+@pytest.mark.parametrize("n", [3, 8])
+def test_host_assembly_matches_oracle(n):
+    m, xyz, tets, det = host_mesh(n, 40, S.ALL_FACES, 3)
+    ops = fem.build(xyz, tets, det, n)
+    ex = m.export()
+    assert np.abs(ex["ML"] - ops["ML"]).max() < 1e-15
+    for which, A in ((0, ops["K"]), (1, ops["B"])):
+        rp, col, val = m.export_csr(which)
+        A = A.tocsr()
+        A.sort_indices()
+        assert np.array_equal(rp, A.indptr) and np.array_equal(col, A.indices)
+        assert np.abs(val - A.data).max() < 1e-14 * np.abs(A.data).max()
+    bf = np.sort(ops["bfaces"], axis=1)
+    bf = bf[np.lexsort(bf.T[::-1])]
+    assert np.array_equal(ex["bfaces"], bf)
+    # sensors: the (node -> weight) map is unique; nodes bit-exact where the weight is not ~0
+    for d in range(len(det)):
+        a = {int(k): w for k, w in zip(ex["det_nodes"][d], ex["det_w"][d]) if w > 1e-12}
+        b = {int(k): w for k, w in zip(ops["det_nodes"][d], ops["det_w"][d]) if w > 1e-12}
+        assert set(a) == set(b)
+        for k in a:
+            assert abs(a[k] - b[k]) < 1e-13
+    info = m.info
+    assert info["nnz_K_graph"] == ops["K"].nnz
+    rp, col, val = m.export_csr(0)
+    assert info["nnz_K"] == np.count_nonzero(val)     # the device drops entries that assembled to 0.0
+    assert np.all(np.abs(ops["K"].data[np.abs(ops["K"].data) < 1e-14]) < 1e-16)
+    assert info["n_boundary_faces"] == 12 * n * n
+
+
+def test_unstable_time_step_is_refused():
+    from paper_2607_21373_b300 import PatError
+    with pytest.raises(PatError, match="PAT_EUNSTABLE"):
+        host_mesh(8, 32, S.ALL_FACES, 1, dt_factor=0.4, flags=0x8)
+    host_mesh(8, 32, S.ALL_FACES, 1, dt_factor=0.3, flags=0x8)   # stable: no error
+
+
+def test_bad_inputs_are_rejected():
+    from paper_2607_21373_b300 import Mesh, PatError
+    xyz, tets = S.cube_mesh(2)
+    det = S.detector_points(4, S.ALL_FACES, 1)
+    with pytest.raises(PatError, match="PAT_EINVAL"):        # sensor off the boundary
+        Mesh(xyz, tets, det + np.array([0.0, 0.0, 1e-3]) * (det[:, 2:3] < 1), 0.1, 5, "f64", flags=0x8)
+    bad = tets.copy()
+    bad[3, 2] = 10_000
+    with pytest.raises(PatError, match="PAT_EINVAL"):        # vertex index out of range
+        Mesh(xyz, bad, det, 0.1, 5, "f64", flags=0x8)
+    flat = tets.copy()
+    flat[0] = [0, 1, 2, 2]
+    with pytest.raises(PatError, match="PAT_EINVAL"):        # degenerate tetrahedron
+        Mesh(xyz, flat, det, 0.1, 5, "f64", flags=0x8)
+    with pytest.raises(PatError, match="PAT_EINVAL"):        # dt <= 0
+        Mesh(xyz, tets, det, 0.0, 5, "f64", flags=0x8)
+
+
+def test_compute_on_host_only_mesh_is_refused():
+    import torch
+    from paper_2607_21373_b300 import PatError, _lib
+    m, *_ = host_mesh(2, 4, S.ALL_FACES, 1)
+    L = _lib.load()
+    import ctypes as C
+    st = L.pat_forward(m._h, C.c_void_p(16), 1, C.c_void_p(16), 1.0, C.c_void_p(256), 1 << 30, None)
+    assert st == 1 and b"HOST_ONLY" in L.pat_last_error()

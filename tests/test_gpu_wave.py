@@ -1,0 +1,113 @@
+"""GPU parity of the forward map and its transpose against the FP64 oracle.
+
+Tolerances: FP64 meshes 1e-12 relative L2 (rounding only); FP32 meshes 1e-5
+relative L2 for the forward and the transpose, 1e-6 for the dot-product test,
+1e-13 for the FP64 dot test (the paper's "order of machine precision").
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import wave
+from problems import as_precision, cube_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_mesh(P, prec, flags=0):
+    from paper_2607_21373_b300 import Mesh
+    return Mesh(P["xyz"], P["tets"], P["det"], P["dt"], P["n_steps"], precision=prec, flags=flags)
+
+
+def to_dev(a, prec):
+    return torch.tensor(np.asarray(a), dtype=torch.float64 if prec == "f64" else torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("prec,K", [("f64", 1), ("f64", 3), ("f64", 4), ("f32", 1), ("f32", 5), ("f32", 6),
+                                    ("f32", 8)])
+def test_forward_matches_oracle(prec, K):
+    P = cube_problem(8, 32, 200)
+    m = gpu_mesh(P, prec)
+    rng = np.random.default_rng(K)
+    p0 = as_precision(P["p0"][:, None] * rng.uniform(0.5, 1.5, size=(1, K)) + 0.1 * rng.standard_normal((P["xyz"].shape[0], K)), prec)
+    Y = m.forward(to_dev(p0 if K > 1 else p0[:, 0], prec)).cpu().numpy()
+    ref = wave.forward(P["ops"], p0 if K > 1 else p0[:, 0], P["dt"], P["n_steps"])
+    tol = 1e-12 if prec == "f64" else 1e-5
+    assert rel_l2(Y, ref) < tol
+    if K > 1:
+        for k in range(K):
+            assert rel_l2(Y[..., k], ref[..., k]) < tol
+
+
+@pytest.mark.parametrize("prec,K", [("f64", 1), ("f64", 2), ("f32", 1), ("f32", 3), ("f32", 4)])
+def test_adjoint_matches_oracle(prec, K):
+    P = cube_problem(8, 32, 200)
+    m = gpu_mesh(P, prec)
+    yh = as_precision(S.standard_normal((P["n_steps"], 32, K), 9), prec)
+    g = m.adjoint(to_dev(yh if K > 1 else yh[..., 0], prec)).cpu().numpy()
+    ref = wave.adjoint(P["ops"], yh if K > 1 else yh[..., 0], P["dt"])
+    assert rel_l2(g, ref) < (1e-12 if prec == "f64" else 1e-5)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6)])
+def test_dot_product_transpose(prec, tol):
+    """<G p, yhat> = <p, G^T yhat> (Section 6.1) with i.i.d. N(0,1) vectors."""
+    P = cube_problem(8, 32, 200)
+    m = gpu_mesh(P, prec)
+    K = 4
+    p = to_dev(S.standard_normal((P["xyz"].shape[0], K), 3), prec)
+    yh = to_dev(S.standard_normal((P["n_steps"], 32, K), 4), prec)
+    Gp = m.forward(p).double()
+    Gty = m.adjoint(yh).double()
+    lhs = (Gp * yh.double()).sum(dim=(0, 1))
+    rhs = (p.double() * Gty).sum(dim=0)
+    assert torch.all((lhs - rhs).abs() <= tol * lhs.abs())
+
+
+def test_forward_plain_fp32_workload_size():
+    """35,937 nodes, 600 steps, 256 sensors on five faces: the FP32 forward map
+    stays within 1e-5 relative L2 of the FP64 oracle (split coefficients)."""
+    P = cube_problem(32, 256, 600, faces=S.LIMITED_VIEW_FACES, seed=1002, phantom="blobs20+vessels")
+    m = gpu_mesh(P, "f32")
+    p0 = as_precision(P["p0"], "f32")
+    Y = m.forward(to_dev(p0, "f32")).cpu().numpy()
+    assert rel_l2(Y, wave.forward(P["ops"], p0, P["dt"], P["n_steps"])) < 1e-5
+    yh = as_precision(S.standard_normal((600, 256), 5), "f32")
+    g = m.adjoint(to_dev(yh, "f32")).cpu().numpy()
+    assert rel_l2(g, wave.adjoint(P["ops"], yh, P["dt"])) < 1e-5
+
+
+def test_single_coefficient_storage_is_less_accurate():
+    """The hi+lo split is what keeps FP32 within 1e-5: one float per coefficient
+    drifts (the coefficient rounding acts as a wave-speed error)."""
+    from paper_2607_21373_b300 import MESH_SINGLE_COEF
+    P = cube_problem(16, 64, 300, faces=S.LIMITED_VIEW_FACES, seed=7, phantom="blobs20+vessels")
+    p0 = as_precision(P["p0"], "f32")
+    ref = wave.forward(P["ops"], p0, P["dt"], P["n_steps"])
+    e_split = rel_l2(gpu_mesh(P, "f32").forward(to_dev(p0, "f32")).cpu().numpy(), ref)
+    e_single = rel_l2(gpu_mesh(P, "f32", MESH_SINGLE_COEF).forward(to_dev(p0, "f32")).cpu().numpy(), ref)
+    assert e_split < 2e-6 < e_single
+
+
+def test_full_size_batched_forward_sampled_columns():
+    """205,379 nodes, 1000 steps, 1024 sensors, K = 64 in one launch sequence:
+    two of the 64 columns against single-column oracle runs."""
+    P = cube_problem(58, 1024, 1000, faces=S.LIMITED_VIEW_FACES, seed=1003, phantom="blobs20+vessels")
+    m = gpu_mesh(P, "f32")
+    N = P["xyz"].shape[0]
+    rng = np.random.default_rng(0)
+    p0 = as_precision(P["p0"][:, None] * rng.uniform(0.5, 1.5, size=(1, 64)), "f32")
+    Y = m.forward(to_dev(p0, "f32"))
+    for k in (0, 63):
+        ref = wave.forward(P["ops"], p0[:, k], P["dt"], P["n_steps"])
+        assert rel_l2(Y[..., k].cpu().numpy(), ref) < 1e-5
+
+
+def test_gpu_sensor_map_matches_oracle():
+    P = cube_problem(8, 32, 200)
+    ex = gpu_mesh(P, "f64").export()
+    for d in range(32):
+        a = {int(k): w for k, w in zip(ex["det_nodes"][d], ex["det_w"][d]) if w > 1e-12}
+        b = {int(k): w for k, w in zip(P["ops"]["det_nodes"][d], P["ops"]["det_w"][d]) if w > 1e-12}
+        assert set(a) == set(b)
