@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=1, help="timed K=1 batches (0: skip the plain form)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
     return ap.parse_args()
 
 
@@ -194,7 +195,7 @@ def run_ours(a, rank, world, local_rank, dist):
     dev = torch.device("cuda", local_rank)
     cfg = workload_config(a)
     xyz, tets, det, p0, dt = problem(a)
-    mesh = Mesh(xyz, tets, det, dt, a.n_steps, precision="f32")
+    mesh = Mesh(xyz, tets, det, dt, a.n_steps, precision="f32", flags=a.mesh_flags)
     N = mesh.N
     # synthetic observations: Y = G p0 (our forward map), 1% relative noise (eq. noise-model)
     p0_d = torch.tensor(p0, dtype=torch.float32, device=dev)
@@ -246,25 +247,34 @@ def run_ours(a, rank, world, local_rank, dist):
     # roofline of the dominant kernel (forward step; the transposed step is reported beside it)
     info = mesh.info
     n_obs, NT = a.n_obs, a.n_steps
-    state_b = 16.0 * N * K                       # read a, w; write a, w (FP32)
-    gather_b = n_obs * K * (3 * 8 + 4.0)         # sensor reads of a, w at 3 nodes + the observation write
+    two_level = bool(a.mesh_flags & 0x10)
+    # per node and sample: two-level reads a, w and writes a, w (16 B); three-level reads
+    # x_s, x_{s-1} and writes x_{s+1} (12 B)
+    state_b = (16.0 if two_level else 12.0) * N * K
+    gather_b = n_obs * K * (3 * 8 + 4.0)         # sensor reads of two fields at 3 nodes + the observation write
     fwd_loop_bytes = NT * (state_b + info["operator_bytes"]) + NT * gather_b
     fwd_launch_per_loop = NT + 1
     fwd_avg_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
     fwd_bytes_per_launch = fwd_loop_bytes / fwd_launch_per_loop
-    adj_op_b = info["operator_bytes"] + 8.0 * N + n_obs * 3 * 12.0
-    adj_loop_bytes = NT * (state_b + adj_op_b) + NT * n_obs * K * 4.0
+    if two_level:
+        adj_op_b = info["operator_bytes"] + 8.0 * N + n_obs * 3 * 12.0
+        adj_loop_bytes = NT * (state_b + adj_op_b) + NT * n_obs * K * 4.0
+    else:
+        adj_op_b = info["operator_bytes"] + n_obs * 3 * 12.0
+        adj_loop_bytes = NT * (state_b + adj_op_b) + NT * 2 * n_obs * K * 4.0
     adj_avg_ms = prof["adj_ms"] / max(prof["adj_launches"], 1)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     achieved = fwd_bytes_per_launch / (fwd_avg_ms * 1e-3) / 1e9
     adj_achieved = (adj_loop_bytes / (NT + 1)) / (adj_avg_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "fwd_step_kernel<float,4,true>", "achieved": achieved, "peak": peak,
+    kname = "fwd_step_kernel<float,4,true>" if two_level else "step3_kernel<float,4,true,false>"
+    aname = "adj_step_kernel<float,4,true>" if two_level else "step3_kernel<float,4,true,true>"
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": None,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
             "bytes_per_launch": fwd_bytes_per_launch, "avg_launch_us": 1e3 * fwd_avg_ms,
-            "adjoint": {"kernel": "adj_step_kernel<float,4,true>", "achieved": adj_achieved,
+            "adjoint": {"kernel": aname, "achieved": adj_achieved,
                         "frac": adj_achieved / peak, "avg_launch_us": 1e3 * adj_avg_ms}}
 
     # plain one-sample form on the same library and workload

@@ -64,6 +64,8 @@ typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_prec;
 #define PAT_MESH_SKIP_STABILITY 0x1u /* do not run the growth check of the time step */
 #define PAT_MESH_KEEP_ZEROS     0x2u /* keep graph entries that assemble to exactly 0.0 */
 #define PAT_MESH_SINGLE_COEF    0x4u /* PAT_F32: one float per coefficient (no hi+lo split) */
+#define PAT_MESH_TWO_LEVEL      0x10u /* step (p^{n+1/2}, dt v) pairs: 16 B per node and sample
+                                         instead of the default three-level form's 12 B */
 #define PAT_MESH_HOST_ONLY      0x8u /* assemble on the host only (no device copy); compute
                                         calls on such a mesh return PAT_EINVAL, exports work */
 
@@ -98,6 +100,14 @@ pat_status pat_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* te
                            const double* c2_elem, const double* det_xyz, int32_t n_obs, double dt,
                            int32_t n_steps, pat_prec prec, uint32_t flags, pat_mesh** out);
 
+/*
+ * Replace the squared sound speed per tetrahedron (host [n_tets] double) and
+ * rebuild the device operators (same mesh, sensors, dt).  The growth check runs
+ * again unless the mesh was created with PAT_MESH_SKIP_STABILITY; on
+ * PAT_EUNSTABLE the previous c^2 stays in force.  Synchronises the device.
+ */
+pat_status pat_mesh_set_c2(pat_mesh* mesh, const double* c2_elem);
+
 /* Release a mesh and its device memory.  NULL is accepted. */
 pat_status pat_mesh_destroy(pat_mesh* mesh);
 
@@ -131,7 +141,8 @@ pat_status pat_mesh_export_csr(const pat_mesh* mesh, int32_t which, int64_t* nnz
                                int32_t* col, double* val);
 
 /* Device workspace (bytes) needed by a compute call with K stacked samples.
- * op: 0 = pat_forward, 1 = pat_adjoint, 2 = pat_rto_* (CGLS state included). */
+ * op: 0 = pat_forward, 1 = pat_adjoint, 2 = pat_rto_* (CGLS state included),
+ * 3 = pat_grad_c2 (checkpoints included). */
 pat_status pat_workspace_bytes(const pat_mesh* mesh, int32_t op, int32_t K, size_t* bytes);
 
 /*
@@ -175,6 +186,34 @@ pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma,
                           void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Uneven batch: several RTO problems -- meshes of different sizes, time-step
+ * counts and sensor sets, each with its own data, noise level and number of
+ * samples K -- solved together with n_iter CGLS iterations each.  Every
+ * time-step launch covers the rows of all jobs that still have a step at that
+ * index (one launch per step index for the whole batch), the per-sample CGLS
+ * work stays per job.  Each job's fields follow pat_rto_sample (device pointers,
+ * eta/xi NULL = drawn from seed, samples/mean/stdev may be NULL) and its
+ * workspace must hold pat_workspace_bytes(mesh, 2, K).  All meshes must share
+ * precision and coefficient storage and use the three-level form
+ * (PAT_EUNSUPPORTED otherwise).  Results equal separate pat_rto_sample calls.
+ */
+typedef struct {
+  const pat_mesh* mesh;
+  const void* y_obs;
+  double sigma;
+  int32_t K;
+  const void* eta;
+  const void* xi;
+  uint64_t seed;
+  double* samples;
+  double* mean;
+  double* stdev;
+  void* workspace;
+  size_t workspace_bytes;
+} pat_rto_job;
+pat_status pat_rto_sample_multi(int32_t n_jobs, const pat_rto_job* jobs, int32_t n_iter, void* stream);
+
+/*
  * The same solve in pieces, for callers that inspect or resume the CGLS state
  * held in the workspace:
  *   pat_cgls_begin    r = b, s = A^T r, d = s, gamma = ||s||^2, x = 0;
@@ -209,6 +248,23 @@ pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* workspace
  */
 pat_status pat_draw_normals(uint64_t seed, int32_t stream_id, int64_t n_elem, int32_t K, double* out,
                             void* stream);
+
+/*
+ * Derivatives of a data misfit L(p0, theta) whose cotangent with respect to
+ * Y = G(theta) p0 is Yhat (e.g. Yhat = G p0 - y_obs for 1/2 ||G p0 - y_obs||^2),
+ * with theta_e = c_e^2 the per-tetrahedron squared sound speed of the mesh:
+ *   g_c2     device [n_tets] double: dL/dtheta_e summed over the K samples,
+ *            -dt^2 sum_m u_m|_e^T K_e^0 x_{m-1}|_e with x the forward states and
+ *            u the transposed states (Section 5.1 recursion; K_e^0 the c = 1
+ *            element stiffness of Section 3);
+ *   p0_grad  device [N][K] real or NULL: G^T Yhat (dL/dp0).
+ * The forward trajectory is recomputed from ceil(sqrt(N_T)) checkpoints, so the
+ * call costs about two forward sweeps, one transposed sweep and N_T element
+ * passes.  p0 device [N][K] real; Yhat device [N_T][N_obs][K] real;
+ * workspace >= pat_workspace_bytes(mesh, 3, K).
+ */
+pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, int32_t K, double* g_c2,
+                       void* p0_grad, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Live timing of the hot kernels, for benchmarks.  While enabled on a mesh,

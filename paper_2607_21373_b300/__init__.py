@@ -20,10 +20,10 @@ import torch
 from . import _lib
 from ._lib import PatError
 
-__all__ = ["Mesh", "PatError", "draw_normals", "lib", "F32", "F64"]
+__all__ = ["Mesh", "PatError", "draw_normals", "rto_sample_multi", "lib", "F32", "F64"]
 
 F32, F64 = 0, 1
-MESH_SKIP_STABILITY, MESH_KEEP_ZEROS, MESH_SINGLE_COEF, MESH_HOST_ONLY = 0x1, 0x2, 0x4, 0x8
+MESH_SKIP_STABILITY, MESH_KEEP_ZEROS, MESH_SINGLE_COEF, MESH_HOST_ONLY, MESH_TWO_LEVEL = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
 def lib():
@@ -177,6 +177,26 @@ class Mesh:
             ws.numel(), _stream()))
         return out
 
+    def set_c2(self, c2):
+        """Replace the per-tetrahedron squared sound speed (host or device array) and rebuild."""
+        c2 = _f64c(c2.detach().cpu().numpy() if isinstance(c2, torch.Tensor) else c2)
+        if c2.shape != (self.info["n_tets"],):
+            raise ValueError(f"c2 must have shape ({self.info['n_tets']},)")
+        _lib.check(lib().pat_mesh_set_c2(self._h, c2.ctypes.data))
+
+    def grad_c2(self, p0, Yhat, want_p0_grad=True):
+        """(dL/dc2 [n_tets] float64 summed over samples, G^T Yhat or None) for the misfit
+        cotangent Yhat = dL/dY (pat_grad_c2)."""
+        K = 1 if p0.dim() == 1 else p0.shape[1]
+        self._check_field(p0, (self.N,) if p0.dim() == 1 else (self.N, K), "p0")
+        self._check_field(Yhat, (self.n_steps, self.n_obs) + (() if p0.dim() == 1 else (K,)), "Yhat")
+        g = torch.empty(self.info["n_tets"], dtype=torch.float64, device=self.device)
+        pg = torch.empty_like(p0) if want_p0_grad else None
+        ws = self.workspace(3, K)
+        _lib.check(lib().pat_grad_c2(self._h, _ptr(p0), _ptr(Yhat), K, _ptr(g), _ptr(pg), _ptr(ws), ws.numel(),
+                                     _stream()))
+        return g, pg
+
     def profile_enable(self, on=True):
         """Start (and reset) or stop live loop timing and launch counting."""
         _lib.check(lib().pat_profile_enable(self._h, int(bool(on))))
@@ -222,6 +242,34 @@ class Mesh:
             "gamma": view(off[5], K, torch.float64, (K,)),
             "status": ws[off[6]:off[6] + 4].view(torch.int32),
         }
+
+
+def rto_sample_multi(jobs, n_iter, samples=True):
+    """Uneven batch (pat_rto_sample_multi): ``jobs`` is a list of dicts with keys
+    mesh, y_obs, sigma, K and optionally eta, xi, seed.  Returns one output dict
+    per job (samples, mean, std) as in Mesh.rto_sample."""
+    arr = (_lib.RtoJob * len(jobs))()
+    outs, keep = [], []
+    for q, j in zip(arr, jobs):
+        m, K = j["mesh"], j["K"]
+        m._check_field(j["y_obs"], (m.n_steps, m.n_obs), "y_obs")
+        dev = m.device
+        o = {"samples": torch.empty((m.N, K), dtype=torch.float64, device=dev) if samples else None,
+             "mean": torch.empty(m.N, dtype=torch.float64, device=dev),
+             "std": torch.empty(m.N, dtype=torch.float64, device=dev) if K >= 2 else None}
+        ws = m.workspace(2, K)
+        q.mesh, q.y_obs, q.sigma, q.K = m._h.value, j["y_obs"].data_ptr(), float(j["sigma"]), K
+        q.eta = 0 if j.get("eta") is None else j["eta"].data_ptr()
+        q.xi = 0 if j.get("xi") is None else j["xi"].data_ptr()
+        q.seed = int(j.get("seed", 0))
+        q.samples = 0 if o["samples"] is None else o["samples"].data_ptr()
+        q.mean = o["mean"].data_ptr()
+        q.stdev = 0 if o["std"] is None else o["std"].data_ptr()
+        q.workspace, q.workspace_bytes = ws.data_ptr(), ws.numel()
+        outs.append(o)
+        keep.append(ws)
+    _lib.check(lib().pat_rto_sample_multi(len(jobs), arr, int(n_iter), _stream()))
+    return outs
 
 
 def draw_normals(seed, stream_id, n_elem, K, device=None):

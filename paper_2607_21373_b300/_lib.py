@@ -24,12 +24,22 @@ class Profile(C.Structure):
                 ("total_launches", C.c_int64)]
 
 
+class RtoJob(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("y_obs", C.c_void_p), ("sigma", C.c_double), ("K", C.c_int32),
+                ("eta", C.c_void_p), ("xi", C.c_void_p), ("seed", C.c_uint64), ("samples", C.c_void_p),
+                ("mean", C.c_void_p), ("stdev", C.c_void_p), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
 # name -> (restype, argtypes); every compute call returns pat_status (int)
 SIGNATURES = {
     "pat_mesh_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                   C.c_int32, C.c_double, C.c_int32, C.c_int, C.c_uint32,
                                   C.POINTER(C.c_void_p)]),
     "pat_mesh_destroy": (C.c_int, [C.c_void_p]),
+    "pat_mesh_set_c2": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pat_grad_c2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_size_t, C.c_void_p]),
     "pat_mesh_query": (C.c_int, [C.c_void_p, C.POINTER(MeshInfo)]),
     "pat_mesh_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pat_mesh_export_csr": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_void_p, C.c_void_p,
@@ -42,6 +52,7 @@ SIGNATURES = {
     "pat_rto_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p,
                                  C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_rto_sample_multi": (C.c_int, [C.c_int32, C.POINTER(RtoJob), C.c_int32, C.c_void_p]),
     "pat_cgls_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     "pat_cgls_iterate": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,

@@ -28,14 +28,20 @@ pat_status upload(const std::vector<T>& h, T** d) {
   return PAT_OK;
 }
 
-void free_mesh(DeviceMesh& m) {
+void free_device(DeviceMesh& m) {
   for (void* e : m.prof.events)
     if (e) cudaEventDestroy((cudaEvent_t)e);
   m.prof.events.clear();
-  void* ps[] = {m.fwd.ptr, m.fwd.col, m.fwd.hi, m.fwd.lo, m.adj.ptr, m.adj.col, m.adj.hi, m.adj.lo,
-                m.minv_hi, m.minv_lo, m.ml, m.sqrt_ml, m.det_node, m.det_w};
-  for (void* p : ps)
-    if (p) cudaFree(p);
+  m.prof.used = 0;
+  void** ps[] = {(void**)&m.fwd.ptr, (void**)&m.fwd.col, &m.fwd.hi, (void**)&m.fwd.lo,
+                 (void**)&m.adj.ptr, (void**)&m.adj.col, &m.adj.hi, (void**)&m.adj.lo,
+                 (void**)&m.adj3.ptr, (void**)&m.adj3.col, &m.adj3.hi, (void**)&m.adj3.lo,
+                 &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
+                 &m.det_w, (void**)&m.etets, &m.eK0};
+  for (void** p : ps) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
 }
 
 // Tagged device CSR of one direction, values in double before rounding.
@@ -103,6 +109,170 @@ bool bad_K(int32_t K, const char* fn) {
   return false;
 }
 
+// Device copies of the operators from the host assembly (also used after
+// pat_mesh_set_c2, since exact-zero pruning can change the sparsity).
+pat_status build_device(pat_mesh* mesh, uint32_t flags) {
+  DeviceMesh& m = mesh->d;
+  HostMesh& h = m.host;
+  const int32_t n_obs = h.n_obs, n_steps = h.n_steps;
+  const double dt = h.dt;
+  const pat_prec prec = m.prec;
+  pat_status s = PAT_OK;
+  m.N = h.N;
+  m.E = h.E;
+  m.n_obs = n_obs;
+  m.n_steps = n_steps;
+  m.dt = dt;
+  m.split = (prec == PAT_F32) && !(flags & PAT_MESH_SINGLE_COEF);
+  const bool keep_zeros = (flags & PAT_MESH_KEEP_ZEROS) != 0;
+  const int64_t N = h.N;
+  m.host_only = (flags & PAT_MESH_HOST_ONLY) != 0;
+  m.device = -1;
+  if (!m.host_only) cudaGetDevice(&m.device);
+
+  // sensor lists per node (for the adjoint's injection entries)
+  std::vector<std::vector<std::pair<int32_t, double>>> inj(N);
+  for (int32_t d = 0; d < n_obs; ++d)
+    for (int a = 0; a < 3; ++a) inj[h.det_node[3 * d + a]].push_back({d, h.det_w[3 * d + a]});
+
+  m.three_level = !(flags & PAT_MESH_TWO_LEVEL);
+  HostRows F, A, A3;
+  F.ptr.assign(N + 1, 0);
+  A.ptr.assign(N + 1, 0);
+  A3.ptr.assign(N + 1, 0);
+  int64_t nnz_k = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const double mi = h.ml[i];
+    for (int64_t e = h.k_ptr[i]; e < h.k_ptr[i + 1]; ++e) {
+      const double kv = h.k_val[e];
+      if (kv == 0.0 && !keep_zeros) continue;  // an exact zero adds exactly nothing
+      F.col.push_back((uint32_t)h.k_col[e]);
+      F.val.push_back(dt * dt * kv / mi);
+      A.col.push_back((uint32_t)h.k_col[e]);
+      A.val.push_back(dt * dt * kv);
+      ++nnz_k;
+    }
+    for (int64_t e = h.b_ptr[i]; e < h.b_ptr[i + 1]; ++e) {
+      F.col.push_back((uint32_t)h.b_col[e] | kTagB);
+      F.val.push_back(dt * h.b_val[e] / mi);
+      A.col.push_back((uint32_t)h.b_col[e] | kTagB);
+      A.val.push_back(dt * h.b_val[e] / mi);
+    }
+    // three-level transposed rows: the forward row plus w_d / (2 M_i) per sensor at node i
+    A3.col.insert(A3.col.end(), F.col.begin() + F.ptr[i], F.col.end());
+    A3.val.insert(A3.val.end(), F.val.begin() + F.ptr[i], F.val.end());
+    for (const auto& pr : inj[i]) {
+      const double wr = prec == PAT_F32 ? (double)(float)pr.second : pr.second;
+      A3.col.push_back((uint32_t)pr.first | kTagInj);
+      A3.val.push_back(0.5 * wr / mi);
+    }
+    A3.ptr[i + 1] = (int32_t)A3.col.size();
+    for (const auto& pr : inj[i]) {
+      A.col.push_back((uint32_t)pr.first | kTagInj);
+      // the same rounded weight as the forward gather, so Pi^T is Pi's exact transpose
+      A.val.push_back(prec == PAT_F32 ? (double)(float)pr.second : pr.second);
+    }
+    if (F.col.size() > 0x7fffffffu || A.col.size() > 0x7fffffffu) {
+      set_error("pat_mesh_create: operator too large for 32-bit row offsets");
+      return PAT_EINVAL;
+    }
+    F.ptr[i + 1] = (int32_t)F.col.size();
+    A.ptr[i + 1] = (int32_t)A.col.size();
+  }
+  // injection values are already rounded to the state precision, so their low part is 0
+  std::vector<double> ml(h.ml), sqml(N), minv(N);
+  for (int64_t i = 0; i < N; ++i) {
+    sqml[i] = std::sqrt(h.ml[i]);
+    minv[i] = 1.0 / h.ml[i];
+  }
+  std::vector<int32_t> det_node(h.det_node);
+  if (m.host_only) {
+    m.fwd.nnz = (int64_t)F.col.size();
+    m.adj.nnz = (int64_t)A.col.size();
+    m.adj3.nnz = (int64_t)A3.col.size();
+  } else if (prec == PAT_F64) {
+    s = upload_rows<double>(F, false, m.fwd);
+    if (!s) s = upload_rows<double>(A, false, m.adj);
+    if (!s) s = upload_rows<double>(A3, false, m.adj3);
+    double* p = nullptr;
+    if (!s) s = upload(minv, &p);
+    m.minv_hi = p;
+    double* w = nullptr;
+    if (!s) s = upload(h.det_w, &w);
+    m.det_w = w;
+  } else {
+    s = upload_rows<float>(F, m.split, m.fwd);
+    if (!s) s = upload_rows<float>(A, m.split, m.adj);
+    if (!s) s = upload_rows<float>(A3, m.split, m.adj3);
+    std::vector<float> mh(N), mlo(N), dw(h.det_w.size());
+    for (int64_t i = 0; i < N; ++i) {
+      mh[i] = (float)minv[i];
+      mlo[i] = (float)(minv[i] - (double)mh[i]);
+    }
+    for (size_t e = 0; e < dw.size(); ++e) dw[e] = (float)h.det_w[e];
+    float* p = nullptr;
+    if (!s) s = upload(mh, &p);
+    m.minv_hi = p;
+    if (!s && m.split) s = upload(mlo, &m.minv_lo);
+    float* w = nullptr;
+    if (!s) s = upload(dw, &w);
+    m.det_w = w;
+  }
+  if (!s && !m.host_only) s = upload(ml, &m.ml);
+  if (!s && !m.host_only) s = upload(sqml, &m.sqrt_ml);
+  if (!s && !m.host_only) s = upload(det_node, &m.det_node);
+  if (!s && !m.host_only) {
+    // element data of the c^2 gradient: vertices and K_e^0 (upper triangle, c = 1)
+    std::vector<int32_t> et(h.tets);
+    std::vector<double> k0(10 * (size_t)h.E);
+    for (int64_t e = 0; e < h.E; ++e) {
+      const double* g = &h.grads[e * 12];
+      int q = 0;
+      for (int a = 0; a < 4; ++a)
+        for (int b = a; b < 4; ++b)
+          k0[10 * e + q++] = h.vol[e] * (g[3 * a] * g[3 * b] + g[3 * a + 1] * g[3 * b + 1] + g[3 * a + 2] * g[3 * b + 2]);
+    }
+    s = upload(et, &m.etets);
+    if (!s) {
+      if (prec == PAT_F64) {
+        double* p = nullptr;
+        s = upload(k0, &p);
+        m.eK0 = p;
+      } else {
+        std::vector<float> kf(k0.begin(), k0.end());
+        float* p = nullptr;
+        s = upload(kf, &p);
+        m.eK0 = p;
+      }
+    }
+  }
+  if (s) {
+    free_device(m);
+    return s;
+  }
+  pat_mesh_info& I = m.info;
+  I.n_nodes = N;
+  I.n_tets = h.E;
+  I.n_boundary_faces = (int64_t)h.bfaces.size() / 3;
+  I.n_boundary_nodes = h.n_boundary_nodes;
+  I.nnz_K = nnz_k;
+  I.nnz_K_graph = (int64_t)h.k_col.size();
+  I.nnz_B = (int64_t)h.b_col.size();
+  I.n_obs = n_obs;
+  I.n_steps = n_steps;
+  I.prec = prec;
+  I.dt = dt;
+  const double vb = prec == PAT_F64 ? 8.0 : (m.split ? 8.0 : 4.0);
+  I.operator_bytes = (double)(N + 1) * 4.0 + (double)m.fwd.nnz * (4.0 + vb);
+  cudaError_t e = m.host_only ? cudaSuccess : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cuda_check(e, "pat_mesh_create");
+    free_device(m);
+    return PAT_ECUDA;
+  }
+  return PAT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -146,131 +316,53 @@ pat_status pat_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* te
     delete mesh;
     return s;
   }
-  m.N = h.N;
-  m.E = h.E;
-  m.n_obs = n_obs;
-  m.n_steps = n_steps;
-  m.dt = dt;
   m.prec = prec;
-  m.split = (prec == PAT_F32) && !(flags & PAT_MESH_SINGLE_COEF);
-  const bool keep_zeros = (flags & PAT_MESH_KEEP_ZEROS) != 0;
-  const int64_t N = h.N;
-  m.host_only = (flags & PAT_MESH_HOST_ONLY) != 0;
-  m.device = -1;
-  if (!m.host_only) cudaGetDevice(&m.device);
-
-  // sensor lists per node (for the adjoint's injection entries)
-  std::vector<std::vector<std::pair<int32_t, double>>> inj(N);
-  for (int32_t d = 0; d < n_obs; ++d)
-    for (int a = 0; a < 3; ++a) inj[h.det_node[3 * d + a]].push_back({d, h.det_w[3 * d + a]});
-
-  HostRows F, A;
-  F.ptr.assign(N + 1, 0);
-  A.ptr.assign(N + 1, 0);
-  int64_t nnz_k = 0;
-  for (int64_t i = 0; i < N; ++i) {
-    const double mi = h.ml[i];
-    for (int64_t e = h.k_ptr[i]; e < h.k_ptr[i + 1]; ++e) {
-      const double kv = h.k_val[e];
-      if (kv == 0.0 && !keep_zeros) continue;  // an exact zero adds exactly nothing
-      F.col.push_back((uint32_t)h.k_col[e]);
-      F.val.push_back(dt * dt * kv / mi);
-      A.col.push_back((uint32_t)h.k_col[e]);
-      A.val.push_back(dt * dt * kv);
-      ++nnz_k;
-    }
-    for (int64_t e = h.b_ptr[i]; e < h.b_ptr[i + 1]; ++e) {
-      F.col.push_back((uint32_t)h.b_col[e] | kTagB);
-      F.val.push_back(dt * h.b_val[e] / mi);
-      A.col.push_back((uint32_t)h.b_col[e] | kTagB);
-      A.val.push_back(dt * h.b_val[e] / mi);
-    }
-    for (const auto& pr : inj[i]) {
-      A.col.push_back((uint32_t)pr.first | kTagInj);
-      // the same rounded weight as the forward gather, so Pi^T is Pi's exact transpose
-      A.val.push_back(prec == PAT_F32 ? (double)(float)pr.second : pr.second);
-    }
-    if (F.col.size() > 0x7fffffffu || A.col.size() > 0x7fffffffu) {
-      set_error("pat_mesh_create: operator too large for 32-bit row offsets");
-      delete mesh;
-      return PAT_EINVAL;
-    }
-    F.ptr[i + 1] = (int32_t)F.col.size();
-    A.ptr[i + 1] = (int32_t)A.col.size();
-  }
-  // injection values are already rounded to the state precision, so their low part is 0
-  std::vector<double> ml(h.ml), sqml(N), minv(N);
-  for (int64_t i = 0; i < N; ++i) {
-    sqml[i] = std::sqrt(h.ml[i]);
-    minv[i] = 1.0 / h.ml[i];
-  }
-  std::vector<int32_t> det_node(h.det_node);
-  if (m.host_only) {
-    m.fwd.nnz = (int64_t)F.col.size();
-    m.adj.nnz = (int64_t)A.col.size();
-  } else if (prec == PAT_F64) {
-    s = upload_rows<double>(F, false, m.fwd);
-    if (!s) s = upload_rows<double>(A, false, m.adj);
-    double* p = nullptr;
-    if (!s) s = upload(minv, &p);
-    m.minv_hi = p;
-    double* w = nullptr;
-    if (!s) s = upload(h.det_w, &w);
-    m.det_w = w;
-  } else {
-    s = upload_rows<float>(F, m.split, m.fwd);
-    if (!s) s = upload_rows<float>(A, m.split, m.adj);
-    std::vector<float> mh(N), mlo(N), dw(h.det_w.size());
-    for (int64_t i = 0; i < N; ++i) {
-      mh[i] = (float)minv[i];
-      mlo[i] = (float)(minv[i] - (double)mh[i]);
-    }
-    for (size_t e = 0; e < dw.size(); ++e) dw[e] = (float)h.det_w[e];
-    float* p = nullptr;
-    if (!s) s = upload(mh, &p);
-    m.minv_hi = p;
-    if (!s && m.split) s = upload(mlo, &m.minv_lo);
-    float* w = nullptr;
-    if (!s) s = upload(dw, &w);
-    m.det_w = w;
-  }
-  if (!s && !m.host_only) s = upload(ml, &m.ml);
-  if (!s && !m.host_only) s = upload(sqml, &m.sqrt_ml);
-  if (!s && !m.host_only) s = upload(det_node, &m.det_node);
-  if (s) {
-    free_mesh(m);
+  m.flags = flags;
+  s = build_device(mesh, flags);
+  if (s != PAT_OK) {
     delete mesh;
     return s;
-  }
-  pat_mesh_info& I = m.info;
-  I.n_nodes = N;
-  I.n_tets = h.E;
-  I.n_boundary_faces = (int64_t)h.bfaces.size() / 3;
-  I.n_boundary_nodes = h.n_boundary_nodes;
-  I.nnz_K = nnz_k;
-  I.nnz_K_graph = (int64_t)h.k_col.size();
-  I.nnz_B = (int64_t)h.b_col.size();
-  I.n_obs = n_obs;
-  I.n_steps = n_steps;
-  I.prec = prec;
-  I.dt = dt;
-  const double vb = prec == PAT_F64 ? 8.0 : (m.split ? 8.0 : 4.0);
-  I.operator_bytes = (double)(N + 1) * 4.0 + (double)m.fwd.nnz * (4.0 + vb);
-  cudaError_t e = m.host_only ? cudaSuccess : cudaDeviceSynchronize();
-  if (e != cudaSuccess) {
-    cuda_check(e, "pat_mesh_create");
-    free_mesh(m);
-    delete mesh;
-    return PAT_ECUDA;
   }
   *out = mesh;
   return PAT_OK;
 }
 
+pat_status pat_mesh_set_c2(pat_mesh* mesh, const double* c2_elem) {
+  clear_error();
+  if (!mesh || !c2_elem) {
+    set_error("pat_mesh_set_c2: NULL argument");
+    return PAT_EINVAL;
+  }
+  DeviceMesh& m = mesh->d;
+  HostMesh& h = m.host;
+  for (int64_t e = 0; e < h.E; ++e) {
+    if (!(c2_elem[e] > 0.0) || !std::isfinite(c2_elem[e])) {
+      set_error("pat_mesh_set_c2: c2 of tetrahedron %lld is %g (must be finite and > 0)", (long long)e, c2_elem[e]);
+      return PAT_EINVAL;
+    }
+  }
+  std::vector<double> old(h.c2);
+  h.c2.assign(c2_elem, c2_elem + h.E);
+  assemble_stiffness(h);
+  pat_status s = PAT_OK;
+  if (!(m.flags & PAT_MESH_SKIP_STABILITY)) s = check_stability(h, nullptr);
+  if (s != PAT_OK) {  // keep the previous, stable operator
+    h.c2 = old;
+    assemble_stiffness(h);
+    return s;
+  }
+  if (!m.host_only) {
+    s = cuda_check(cudaDeviceSynchronize(), "pat_mesh_set_c2");
+    if (s) return s;
+  }
+  free_device(m);
+  return build_device(mesh, m.flags);
+}
+
 pat_status pat_mesh_destroy(pat_mesh* mesh) {
   clear_error();
   if (!mesh) return PAT_OK;
-  free_mesh(mesh->d);
+  free_device(mesh->d);
   delete mesh;
   return PAT_OK;
 }
@@ -320,12 +412,13 @@ pat_status pat_mesh_export_csr(const pat_mesh* mesh, int32_t which, int64_t* nnz
 
 pat_status pat_workspace_bytes(const pat_mesh* mesh, int32_t op, int32_t K, size_t* bytes) {
   clear_error();
-  if (!mesh || !bytes || op < 0 || op > 2) {
-    set_error("pat_workspace_bytes: NULL argument or op not in {0, 1, 2}");
+  if (!mesh || !bytes || op < 0 || op > 3) {
+    set_error("pat_workspace_bytes: NULL argument or op not in {0, 1, 2, 3}");
     return PAT_EINVAL;
   }
   if (bad_K(K, "pat_workspace_bytes")) return PAT_EINVAL;
-  *bytes = (op == 2) ? rto_layout(mesh->d, K).total : state_bytes(mesh->d, K);
+  *bytes = (op == 3) ? grad_workspace_bytes(mesh->d, K)
+                     : (op == 2) ? rto_layout(mesh->d, K).total : state_bytes(mesh->d, K);
   return PAT_OK;
 }
 
@@ -434,6 +527,47 @@ pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma,
   return pat_cgls_finish(mesh, K, samples, mean, stdev, ws, ws_bytes, stream);
 }
 
+pat_status pat_rto_sample_multi(int32_t n_jobs, const pat_rto_job* jobs, int32_t n_iter, void* stream) {
+  clear_error();
+  if (n_jobs < 1 || !jobs || n_iter < 0) {
+    set_error("pat_rto_sample_multi: need n_jobs >= 1, jobs and n_iter >= 0");
+    return PAT_EINVAL;
+  }
+  std::vector<Job> J;
+  for (int32_t g = 0; g < n_jobs; ++g) {
+    const pat_rto_job& q = jobs[g];
+    if (!q.mesh || !q.y_obs) {
+      set_error("pat_rto_sample_multi: job %d has a NULL mesh or y_obs", g);
+      return PAT_EINVAL;
+    }
+    if (!(q.sigma > 0.0) || !std::isfinite(q.sigma)) {
+      set_error("pat_rto_sample_multi: job %d: sigma must be finite and > 0", g);
+      return PAT_EINVAL;
+    }
+    if (bad_K(q.K, "pat_rto_sample_multi") || !check_device(q.mesh, "pat_rto_sample_multi")) return PAT_EINVAL;
+    if (q.stdev && q.K < 2) {
+      set_error("pat_rto_sample_multi: job %d: the std estimator needs K >= 2", g);
+      return PAT_EINVAL;
+    }
+    pat_status s = check_ws(q.mesh, 2, q.K, q.workspace, q.workspace_bytes, "pat_rto_sample_multi");
+    if (s) return s;
+    const DeviceMesh& m = q.mesh->d;
+    const DeviceMesh& m0 = jobs[0].mesh->d;
+    if (m.prec != m0.prec || m.split != m0.split || !m.three_level || !m0.three_level) {
+      set_error("pat_rto_sample_multi: all meshes must share precision and coefficient storage and use the "
+                "three-level form");
+      return PAT_EUNSUPPORTED;
+    }
+    for (int32_t h = 0; h < g; ++h)
+      if (jobs[h].workspace == q.workspace) {
+        set_error("pat_rto_sample_multi: jobs %d and %d share a workspace", h, g);
+        return PAT_EINVAL;
+      }
+    J.push_back(Job{&m, q.K, q.y_obs, q.sigma, q.eta, q.xi, q.seed, q.samples, q.mean, q.stdev, (char*)q.workspace});
+  }
+  return rto_multi(J, n_iter, (cudaStream_t)stream);
+}
+
 pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* ws, void* stream) {
   clear_error();
   if (!mesh || !ws) {
@@ -452,6 +586,19 @@ pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* ws, void*
     return (pat_status)word;
   }
   return PAT_OK;
+}
+
+pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, int32_t K, double* g_c2,
+                       void* p0_grad, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || !p0 || !Yhat || !g_c2) {
+    set_error("pat_grad_c2: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_grad_c2") || !check_device(mesh, "pat_grad_c2")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 3, K, ws, ws_bytes, "pat_grad_c2");
+  if (s) return s;
+  return grad_c2(mesh->d, p0, Yhat, K, g_c2, p0_grad, (char*)ws, (cudaStream_t)stream);
 }
 
 pat_status pat_profile_enable(pat_mesh* mesh, int32_t enable) {

@@ -94,6 +94,23 @@ static inline int64_t find_col(const std::vector<int64_t>& ptr, const std::vecto
   return (it != e && *it == j) ? (it - col.begin()) : -1;
 }
 
+void assemble_stiffness(HostMesh& m) {
+  m.k_val.assign(m.k_col.size(), 0.0);
+  m.ml.assign(m.N, 0.0);
+  for (int64_t e = 0; e < m.E; ++e) {
+    const int32_t* t = &m.tets[4 * e];
+    const double* g = &m.grads[e * 12];
+    const double s = m.c2[e] * m.vol[e];
+    for (int a = 0; a < 4; ++a) {
+      m.ml[t[a]] += m.vol[e] / 4.0;  // row sum of the consistent P1 mass V/20 (1 + delta_ab)
+      for (int b = 0; b < 4; ++b) {
+        const double v = s * (g[3 * a] * g[3 * b] + g[3 * a + 1] * g[3 * b + 1] + g[3 * a + 2] * g[3 * b + 2]);
+        m.k_val[find_col(m.k_ptr, m.k_col, t[a], t[b])] += v;
+      }
+    }
+  }
+}
+
 pat_status assemble_host(const double* xyz, int64_t N, const int32_t* tets, int64_t E, const double* c2,
                          HostMesh& m) {
   if (N < 4 || E < 1) {
@@ -149,20 +166,7 @@ pat_status assemble_host(const double* xyz, int64_t N, const int32_t* tets, int6
   }
   // stiffness K_e = c^2 V grad l_a . grad l_b on the full P1 graph
   clique_pattern(N, tets, E, 4, m.k_ptr, m.k_col);
-  m.k_val.assign(m.k_col.size(), 0.0);
-  m.ml.assign(N, 0.0);
-  for (int64_t e = 0; e < E; ++e) {
-    const int32_t* t = tets + 4 * e;
-    const double* g = &m.grads[e * 12];
-    double s = m.c2[e] * m.vol[e];
-    for (int a = 0; a < 4; ++a) {
-      m.ml[t[a]] += m.vol[e] / 4.0;  // row sum of the consistent P1 mass V/20 (1 + delta_ab)
-      for (int b = 0; b < 4; ++b) {
-        double v = s * (g[3 * a] * g[3 * b] + g[3 * a + 1] * g[3 * b + 1] + g[3 * a + 2] * g[3 * b + 2]);
-        m.k_val[find_col(m.k_ptr, m.k_col, t[a], t[b])] += v;
-      }
-    }
-  }
+  assemble_stiffness(m);
   for (int64_t i = 0; i < N; ++i) {
     if (!(m.ml[i] > 0.0)) {
       set_error("pat_mesh_create: node %lld belongs to no tetrahedron", (long long)i);

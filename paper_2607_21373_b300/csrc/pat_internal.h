@@ -45,6 +45,8 @@ struct HostMesh {
   std::vector<double> det_w;        // [n_obs][3]
 };
 
+// Re-assembles the stiffness values for the current m.c2 (same graph).
+void assemble_stiffness(HostMesh& m);
 // Fills everything but the sensors; returns PAT_OK or an error (message set).
 pat_status assemble_host(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
                          const double* c2, HostMesh& m);
@@ -86,7 +88,12 @@ struct DeviceMesh {
   bool split = true;
   bool host_only = false;
   int device = 0;
-  DevCSR fwd, adj;
+  DevCSR fwd, adj;          // adj: transposed rows of the two-level form
+  DevCSR adj3;              // forward rows + sensor entries w_d / (2 M_i) (three-level form)
+  bool three_level = true;
+  uint32_t flags = 0;
+  int32_t* etets = nullptr;  // [E][4] element vertices (c^2 gradient)
+  void* eK0 = nullptr;       // [E][10] real: upper triangle of V grad(l_a).grad(l_b) (c = 1)
   void* minv_hi = nullptr;   // [N] real: 1 / M_i
   float* minv_lo = nullptr;  // [N]
   double* ml = nullptr;      // [N] double

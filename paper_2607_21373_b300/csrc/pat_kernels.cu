@@ -172,10 +172,139 @@ static pat_status adjoint_t(const DeviceMesh& m, const T* Yhat, int K, T* out, T
   return cuda_check(cudaGetLastError(), "adjoint step launch");
 }
 
+template <typename T, int V, bool SPLIT, bool ADJ>
+static void launch_step3(const Step3Args<T>& a, int64_t threads, cudaStream_t st) {
+  const int64_t blocks = (threads + 255) / 256;
+  step3_kernel<T, V, SPLIT, ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+}
+
+// Launch i (0 <= i <= N_T) of a three-level forward solve: steps 0..N_T-1, then
+// the observation of state N_T.  Step s reads x_s (p0 for s = 0) and x_{s-1}
+// and writes x_{s+1} into b[s % 3]; it observes state s (s >= 1).
+template <typename T>
+Step3Args<T> fwd3_args(const DeviceMesh& m, int K, int V, const T* p0, T* Y, T scale, T* const b[3], int i,
+                       int64_t* threads) {
+  Step3Args<T> A{};
+  A.N = m.N;
+  A.K = K;
+  A.n_obs = m.n_obs;
+  A.ptr = m.fwd.ptr;
+  A.col = m.fwd.col;
+  A.hi = static_cast<const T*>(m.fwd.hi);
+  A.lo = m.fwd.lo;
+  A.det_node = m.det_node;
+  A.det_w = static_cast<const T*>(m.det_w);
+  A.scale = scale;
+  A.inj_scale = T(0);
+  const int NT = m.n_steps;
+  const int64_t rows = m.N * (int64_t)K / V;
+  const int64_t obs = (int64_t)m.n_obs * K / V;
+  const int64_t ystride = (int64_t)m.n_obs * K;
+  const int s = std::min(i, NT);
+  A.x = (s == 0) ? p0 : b[(s - 1) % 3];
+  A.xp = (s == 0) ? nullptr : (s == 1 ? p0 : b[(s - 2) % 3]);
+  A.prev_mode = (s == 0) ? 1 : 0;  // x_{-1} = x_0: zero initial velocity
+  if (i < NT) {
+    A.xn = b[i % 3];
+    A.row_threads = rows;
+    A.y_out = (i == 0) ? nullptr : Y + (int64_t)(i - 1) * ystride;
+    *threads = rows + (i == 0 ? 0 : obs);
+  } else {
+    A.xn = nullptr;
+    A.row_threads = 0;
+    A.y_out = Y + (int64_t)(NT - 1) * ystride;
+    *threads = obs;
+  }
+  return A;
+}
+
+// Launch i (0 <= i <= N_T) of a three-level transposed solve: i = 0 forms
+// u_{N_T} = M^{-1} I_{N_T} / 2 from the zero state into b[0]; launch i >= 1 is the
+// transposed step m = N_T - i + 1, reading b[(i-1) % 3] (and b[(i-2) % 3]) and
+// injecting yhat^m and yhat^{m-1}.  The last two states end in b[N_T % 3] and
+// b[(N_T-1) % 3] (adj3_finish_kernel).
+template <typename T>
+Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale, T* const b[3], int i,
+                       int64_t* threads) {
+  Step3Args<T> A{};
+  A.N = m.N;
+  A.K = K;
+  A.n_obs = m.n_obs;
+  A.ptr = m.adj3.ptr;
+  A.col = m.adj3.col;
+  A.hi = static_cast<const T*>(m.adj3.hi);
+  A.lo = m.adj3.lo;
+  A.inj_scale = scale;
+  A.scale = T(0);
+  A.row_threads = m.N * (int64_t)K / V;
+  *threads = A.row_threads;
+  const int NT = m.n_steps;
+  const int64_t ystride = (int64_t)m.n_obs * K;
+  A.xn = b[i % 3];
+  if (i == 0) {
+    A.x = nullptr;
+    A.xp = nullptr;
+    A.prev_mode = 2;
+    A.ya = Yhat + (int64_t)(NT - 1) * ystride;
+    A.yb = nullptr;
+  } else {
+    const int mstep = NT - i + 1;
+    A.x = b[(i - 1) % 3];
+    A.xp = (i == 1) ? nullptr : b[(i - 2) % 3];
+    A.prev_mode = (i == 1) ? 2 : 0;  // u_{N_T+1} = 0
+    A.ya = Yhat + (int64_t)(mstep - 1) * ystride;                          // yhat^m
+    A.yb = (mstep >= 2) ? Yhat + (int64_t)(mstep - 2) * ystride : nullptr;  // yhat^{m-1}
+  }
+  return A;
+}
+
+template <typename T, int V, bool SPLIT>
+static pat_status forward3_t(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
+  const int64_t NK = m.N * (int64_t)K;
+  T* const b[3] = {ws, ws + NK, ws + 2 * NK};
+  const size_t pp = prof_begin(m, 0, st);
+  for (int i = 0; i <= m.n_steps; ++i) {
+    int64_t threads = 0;
+    const Step3Args<T> A = fwd3_args<T>(m, K, V, p0, Y, scale, b, i, &threads);
+    launch_step3<T, V, SPLIT, false>(A, threads, st);
+  }
+  prof_end(m, pp, m.n_steps + 1, st);
+  return cuda_check(cudaGetLastError(), "forward step launch");
+}
+
+template <typename T, int V, bool SPLIT>
+static pat_status adjoint3_t(const DeviceMesh& m, const T* Yhat, int K, T* out, T scale, T* ws, cudaStream_t st) {
+  const int64_t NK = m.N * (int64_t)K;
+  T* const b[3] = {ws, ws + NK, ws + 2 * NK};
+  const int NT = m.n_steps;
+  const size_t pp = prof_begin(m, 1, st);
+  for (int i = 0; i <= NT; ++i) {
+    int64_t threads = 0;
+    const Step3Args<T> A = adj3_args<T>(m, K, V, Yhat, scale, b, i, &threads);
+    launch_step3<T, V, SPLIT, true>(A, threads, st);
+  }
+  // G^T yhat = M (u_0 - u_1) + M Bt u_1 from the last two transposed states
+  const int64_t rt = NK / V;
+  adj3_finish_kernel<T, V, SPLIT><<<(unsigned)((rt + 255) / 256), 256, 0, st>>>(
+      rt, K, m.fwd.ptr, m.fwd.col, static_cast<const T*>(m.fwd.hi), m.fwd.lo, m.ml, b[NT % 3], b[(NT - 1) % 3], out);
+  prof_end(m, pp, NT + 2, st);
+  return cuda_check(cudaGetLastError(), "adjoint step launch");
+}
+
 template <typename T>
 static pat_status forward_disp(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
   const int V = pick_vec<T>(K, {p0, Y, ws});
   const bool sp = m.split;
+  if (m.three_level) {
+    if constexpr (sizeof(T) == 4) {
+      if (V == 4) return sp ? forward3_t<T, 4, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 4, false>(m, p0, K, Y, scale, ws, st);
+      if (V == 2) return sp ? forward3_t<T, 2, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 2, false>(m, p0, K, Y, scale, ws, st);
+      return sp ? forward3_t<T, 1, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 1, false>(m, p0, K, Y, scale, ws, st);
+    } else {
+      if (V == 2) return forward3_t<T, 2, false>(m, p0, K, Y, scale, ws, st);
+      return forward3_t<T, 1, false>(m, p0, K, Y, scale, ws, st);
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     if (V == 4) return sp ? forward_t<T, 4, true>(m, p0, K, Y, scale, ws, st) : forward_t<T, 4, false>(m, p0, K, Y, scale, ws, st);
     if (V == 2) return sp ? forward_t<T, 2, true>(m, p0, K, Y, scale, ws, st) : forward_t<T, 2, false>(m, p0, K, Y, scale, ws, st);
@@ -190,6 +319,16 @@ template <typename T>
 static pat_status adjoint_disp(const DeviceMesh& m, const T* Yh, int K, T* out, T scale, T* ws, cudaStream_t st) {
   const int V = pick_vec<T>(K, {Yh, out, ws});
   const bool sp = m.split;
+  if (m.three_level) {
+    if constexpr (sizeof(T) == 4) {
+      if (V == 4) return sp ? adjoint3_t<T, 4, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 4, false>(m, Yh, K, out, scale, ws, st);
+      if (V == 2) return sp ? adjoint3_t<T, 2, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 2, false>(m, Yh, K, out, scale, ws, st);
+      return sp ? adjoint3_t<T, 1, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 1, false>(m, Yh, K, out, scale, ws, st);
+    } else {
+      if (V == 2) return adjoint3_t<T, 2, false>(m, Yh, K, out, scale, ws, st);
+      return adjoint3_t<T, 1, false>(m, Yh, K, out, scale, ws, st);
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     if (V == 4) return sp ? adjoint_t<T, 4, true>(m, Yh, K, out, scale, ws, st) : adjoint_t<T, 4, false>(m, Yh, K, out, scale, ws, st);
     if (V == 2) return sp ? adjoint_t<T, 2, true>(m, Yh, K, out, scale, ws, st) : adjoint_t<T, 2, false>(m, Yh, K, out, scale, ws, st);
@@ -459,28 +598,86 @@ RtoLayout rto_layout(const DeviceMesh& m, int K) {
 
 static inline unsigned nblocks(int64_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
+// CGLS phases around the two wave solves of an iteration (also driven per job
+// by the grouped multi-mesh driver).
+template <typename T>
+pat_status begin_pre(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
+                     uint64_t seed, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.status, 0, 4, st), "cgls_begin memset"));
+  set_double_kernel<<<1, 1, 0, st>>>((double*)(ws + L.sigma), sigma);
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.x, 0, (size_t)m.N * K * 8, st), "cgls_begin memset x"));
+  rhs_kernel<T><<<nblocks((ndata + m.N) * K), 256, 0, st>>>(ndata, m.N, K, y_obs, eta, xi, seed, 1.0 / sigma,
+                                                            (T*)(ws + L.r_d), (T*)(ws + L.r_p));
+  count(m, 2);
+  return cuda_check(cudaGetLastError(), "cgls_begin launch");
+}
+
+// after s = G^T r_d / sigma landed in s: s += M^{1/2} r_p, d = s, gamma = ||s||^2
+template <typename T>
+pat_status begin_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  double* part = (double*)(ws + L.partial);
+  combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
+      (T*)(ws + L.s), (T*)(ws + L.r_p), m.sqrt_ml, m.N, K, rsN.rpb, (T*)(ws + L.s), (T*)(ws + L.d), part);
+  finalize_gamma0_kernel<<<nblocks(K, 128), 128, 0, st>>>(part, rsN.grid, K, (double*)(ws + L.gamma),
+                                                           (int*)(ws + L.status));
+  count(m, 2);
+  return cuda_check(cudaGetLastError(), "cgls_begin launch");
+}
+
+// after q_d = G d / sigma: alpha = gamma / (||q_d||^2 + ||M^{1/2} d||^2); x += alpha d;
+// r_p -= alpha M^{1/2} d; r_d -= alpha q_d
+template <typename T>
+pat_status iter_mid(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  T* d = (T*)(ws + L.d);
+  double* part = (double*)(ws + L.partial);
+  double* pa = part;
+  double* pb = part + (size_t)L.n_part * K;
+  const RedShape rsD = red_shape(K, ndata, L.n_part);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  double* alpha = (double*)(ws + L.alpha);
+  sumsq_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>((T*)(ws + L.q_d), nullptr, ndata, K,
+                                                                                 rsD.rpb, pa);
+  sumsq_kernel<T, true><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(d, m.ml, m.N, K, rsN.rpb, pb);
+  finalize_alpha_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, (double*)(ws + L.gamma),
+                                                          alpha, (int*)(ws + L.status));
+  update_x_rp_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, alpha, d, m.sqrt_ml, (double*)(ws + L.x),
+                                                          (T*)(ws + L.r_p));
+  update_rd_kernel<T><<<nblocks(ndata * K), 256, 0, st>>>(ndata, K, alpha, (T*)(ws + L.q_d), (T*)(ws + L.r_d));
+  count(m, 5);
+  return cuda_check(cudaGetLastError(), "cgls_iterate launch");
+}
+
+// after s = G^T r_d / sigma landed in s: s += M^{1/2} r_p; beta = ||s||^2 / gamma; d = s + beta d
+template <typename T>
+pat_status iter_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  double* pa = (double*)(ws + L.partial);
+  T* s = (T*)(ws + L.s);
+  double* beta = (double*)(ws + L.beta);
+  combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(s, (T*)(ws + L.r_p), m.sqrt_ml, m.N, K,
+                                                                             rsN.rpb, s, nullptr, pa);
+  finalize_beta_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, (double*)(ws + L.gamma), beta,
+                                                         (int*)(ws + L.status));
+  update_d_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, beta, s, (T*)(ws + L.d));
+  count(m, 3);
+  return cuda_check(cudaGetLastError(), "cgls_iterate launch");
+}
+
 template <typename T>
 static pat_status begin_t(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
                           uint64_t seed, char* ws, cudaStream_t st) {
   const RtoLayout L = rto_layout(m, K);
-  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
-  T* r_d = (T*)(ws + L.r_d);
-  T* r_p = (T*)(ws + L.r_p);
-  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.status, 0, 4, st), "cgls_begin memset"));
-  set_double_kernel<<<1, 1, 0, st>>>((double*)(ws + L.sigma), sigma);
-  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.x, 0, (size_t)m.N * K * 8, st), "cgls_begin memset x"));
-  rhs_kernel<T><<<nblocks((ndata + m.N) * K), 256, 0, st>>>(ndata, m.N, K, y_obs, eta, xi, seed, 1.0 / sigma, r_d, r_p);
+  PAT_TRY(begin_pre<T>(m, y_obs, sigma, K, eta, xi, seed, ws, st));
   // s = A^T r, d = s, gamma = ||s||^2 (the transpose lands in s, combined in place)
-  T* ah = (T*)(ws + L.s);
-  PAT_TRY(adjoint(m, r_d, K, ah, 1.0 / sigma, ws + L.state, st));
-  const RedShape rsN = red_shape(K, m.N, L.n_part);
-  double* part = (double*)(ws + L.partial);
-  combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
-      ah, r_p, m.sqrt_ml, m.N, K, rsN.rpb, (T*)(ws + L.s), (T*)(ws + L.d), part);
-  finalize_gamma0_kernel<<<nblocks(K, 128), 128, 0, st>>>(part, rsN.grid, K, (double*)(ws + L.gamma),
-                                                           (int*)(ws + L.status));
-  count(m, 4);
-  return cuda_check(cudaGetLastError(), "cgls_begin launch");
+  PAT_TRY(adjoint(m, ws + L.r_d, K, ws + L.s, 1.0 / sigma, ws + L.state, st));
+  return begin_post<T>(m, K, ws, st);
 }
 
 template <typename T>
@@ -509,40 +706,16 @@ static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter
     set_error("pat_cgls_iterate: sigma must be > 0 (got %g)", sigma);
     return PAT_EINVAL;
   }
-  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
-  T* x_d = (T*)(ws + L.d);
-  T* r_d = (T*)(ws + L.r_d);
-  T* q_d = (T*)(ws + L.q_d);
-  T* r_p = (T*)(ws + L.r_p);
-  T* s = (T*)(ws + L.s);
-  double* x = (double*)(ws + L.x);
-  double* gamma = (double*)(ws + L.gamma);
-  double* alpha = (double*)(ws + L.alpha);
-  double* beta = (double*)(ws + L.beta);
-  int* status = (int*)(ws + L.status);
-  double* part = (double*)(ws + L.partial);
-  double* pa = part;
-  double* pb = part + (size_t)L.n_part * K;
-  const RedShape rsD = red_shape(K, ndata, L.n_part);
-  const RedShape rsN = red_shape(K, m.N, L.n_part);
   for (int it = 0; it < n_iter; ++it) {
     // q = A d: q_d = G d / sigma (forward), q_p = M^{1/2} d (implicit)
-    PAT_TRY(forward(m, x_d, K, q_d, 1.0 / sigma, ws + L.state, st));
-    sumsq_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>(q_d, nullptr, ndata, K, rsD.rpb, pa);
-    sumsq_kernel<T, true><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(x_d, m.ml, m.N, K, rsN.rpb, pb);
-    finalize_alpha_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, gamma, alpha, status);
-    update_x_rp_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, alpha, x_d, m.sqrt_ml, x, r_p);
-    update_rd_kernel<T><<<nblocks(ndata * K), 256, 0, st>>>(ndata, K, alpha, q_d, r_d);
+    PAT_TRY(forward(m, ws + L.d, K, ws + L.q_d, 1.0 / sigma, ws + L.state, st));
+    PAT_TRY(iter_mid<T>(m, K, ws, st));
     // s = A^T r = G^T r_d / sigma + M^{1/2} r_p
-    PAT_TRY(adjoint(m, r_d, K, s, 1.0 / sigma, ws + L.state, st));
-    combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(s, r_p, m.sqrt_ml, m.N, K, rsN.rpb, s,
-                                                                               nullptr, pa);
-    finalize_beta_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, gamma, beta, status);
-    update_d_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, beta, s, x_d);
-    count(m, 8);
+    PAT_TRY(adjoint(m, ws + L.r_d, K, ws + L.s, 1.0 / sigma, ws + L.state, st));
+    PAT_TRY(iter_post<T>(m, K, ws, st));
     if (resid) PAT_TRY(residual_t<T>(m, K, resid + (int64_t)it * K, ws, st));
   }
-  return cuda_check(cudaGetLastError(), "cgls_iterate launch");
+  return PAT_OK;
 }
 
 pat_status cgls_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta, const void* xi,
@@ -575,6 +748,29 @@ pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean
     count(m, 1);
   }
   return cuda_check(cudaGetLastError(), "cgls_finish launch");
+}
+
+template Step3Args<float> fwd3_args<float>(const DeviceMesh&, int, int, const float*, float*, float, float* const[3],
+                                           int, int64_t*);
+template Step3Args<double> fwd3_args<double>(const DeviceMesh&, int, int, const double*, double*, double,
+                                             double* const[3], int, int64_t*);
+template Step3Args<float> adj3_args<float>(const DeviceMesh&, int, int, const float*, float, float* const[3], int,
+                                           int64_t*);
+template Step3Args<double> adj3_args<double>(const DeviceMesh&, int, int, const double*, double, double* const[3],
+                                             int, int64_t*);
+template pat_status begin_pre<float>(const DeviceMesh&, const float*, double, int, const float*, const float*, uint64_t,
+                                     char*, cudaStream_t);
+template pat_status begin_pre<double>(const DeviceMesh&, const double*, double, int, const double*, const double*,
+                                      uint64_t, char*, cudaStream_t);
+template pat_status begin_post<float>(const DeviceMesh&, int, char*, cudaStream_t);
+template pat_status begin_post<double>(const DeviceMesh&, int, char*, cudaStream_t);
+template pat_status iter_mid<float>(const DeviceMesh&, int, char*, cudaStream_t);
+template pat_status iter_mid<double>(const DeviceMesh&, int, char*, cudaStream_t);
+template pat_status iter_post<float>(const DeviceMesh&, int, char*, cudaStream_t);
+template pat_status iter_post<double>(const DeviceMesh&, int, char*, cudaStream_t);
+
+int vec_width(const DeviceMesh& m, int K, std::initializer_list<const void*> ptrs) {
+  return m.prec == PAT_F64 ? pick_vec<double>(K, ptrs) : pick_vec<float>(K, ptrs);
 }
 
 pat_status draw_normals(uint64_t seed, int stream_id, int64_t n_elem, int K, double* out, cudaStream_t st) {

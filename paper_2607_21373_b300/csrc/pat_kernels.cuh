@@ -225,3 +225,247 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const AdjArgs<T> A) {
 }
 
 }  // namespace pat
+
+namespace pat {
+
+// ---------------------------------------------------------------------------
+// Three-level form of the same propagator (12 bytes per node and sample).
+//
+// With x_s = a_s = p^{s+1/2} the scaled Stoermer-Verlet step of fwd_step_kernel
+// reads, after eliminating w_s = x_s - x_{s-1},
+//     x_{s+1} = x_s + w_s - Kt x_s - Bt w_s,   Kt = dt^2 M^{-1} K,  Bt = dt M^{-1} B,
+// and the observation is p^s = x_s - w_s/2 = (x_s + x_{s-1}) / 2.  Forward start:
+// x_0 = p0, x_{-1} = x_0 (v^0 = 0).
+//
+// The transposed step of Section 5.1 has the same three-level form in the
+// variable u = M^{-1}(what + ah) (K, B symmetric):
+//     u_{m-1} = u_m + w - Kt u_m - Bt w + M^{-1}(I_m + I_{m-1}) / 2,   w = u_m - u_{m+1},
+// where I_m = Pi^T yhat^m; it starts from u_{N_T+1} = 0, u_{N_T} = M^{-1} I_{N_T} / 2
+// and ends with G^T yhat = M (u_1 - u_2) + M Bt u_2 (adj3_finish_kernel).
+// The difference x_s - x_{s-1} of two consecutive FP32 states is exact whenever
+// they are within a factor of two (Sterbenz), so nothing is lost against
+// carrying w.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Step3Args {
+  int64_t N;
+  int32_t K;
+  int32_t n_obs;
+  int64_t row_threads;
+  int32_t prev_mode;  // 0: xp is a buffer; 1: xp equals x (zero velocity); 2: xp is zero
+  const int32_t* __restrict__ ptr;
+  const uint32_t* __restrict__ col;
+  const T* __restrict__ hi;
+  const float* __restrict__ lo;
+  const T* __restrict__ x;   // nullptr: zero state (adjoint start)
+  const T* __restrict__ xp;
+  T* __restrict__ xn;
+  // adjoint source: kTagInj entries carry w_d / (2 M_i) and read ya + yb
+  const T* __restrict__ ya;
+  const T* __restrict__ yb;
+  T inj_scale;
+  // forward observation of the current state, scale * Pi (x + xp) / 2
+  const int32_t* __restrict__ det_node;
+  const T* __restrict__ det_w;
+  T* __restrict__ y_out;
+  T scale;
+};
+
+// Rows are walked in chunks of CH entries: the chunk's columns and
+// coefficients are loaded first, then all CH neighbour vectors, then the FMAs,
+// so each thread keeps CH independent 16-byte loads in flight instead of one
+// dependent index->value chain per entry.
+constexpr int kChunk = 8;
+
+template <typename T, int V, bool SPLIT, bool ADJ>
+__device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t t) {
+  const int KV = A.K / V;
+  if (t < A.row_threads) {
+    const int64_t row = t / KV;
+    const int kv = (int)(t - row * KV);
+    const int64_t off = row * A.K + (int64_t)kv * V;
+    T acc[V], accl[V], src[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[q] = accl[q] = src[q] = T(0);
+    const bool have_x = A.x != nullptr;
+    const bool xp_buf = A.prev_mode == 0;
+    const int e0 = A.ptr[row], e1 = A.ptr[row + 1];
+    if (have_x) {
+      for (int e = e0; e < e1; e += kChunk) {
+        uint32_t c[kChunk];
+        T h[kChunk];
+        float l[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+          const bool in = e + q < e1;
+          c[q] = in ? A.col[e + q] : kTagInj;
+          h[q] = in ? A.hi[e + q] : T(0);
+          if constexpr (SPLIT) l[q] = in ? A.lo[e + q] : 0.0f;
+        }
+        Pack<T, V> xv[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+          if (!(c[q] & kTagInj)) {
+            xv[q] = ld<T, V>(A.x + (int64_t)(c[q] & kIdxMask) * A.K + (int64_t)kv * V);
+          } else {
+#pragma unroll
+            for (int r = 0; r < V; ++r) xv[q].v[r] = T(0);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+          if ((c[q] & (kTagB | kTagInj)) == kTagB) {
+            // the boundary term acts on w_j = x_j - xp_j
+            if (xp_buf) {
+              const Pack<T, V> pj = ld<T, V>(A.xp + (int64_t)(c[q] & kIdxMask) * A.K + (int64_t)kv * V);
+#pragma unroll
+              for (int r = 0; r < V; ++r) xv[q].v[r] -= pj.v[r];
+            } else if (A.prev_mode == 1) {
+#pragma unroll
+              for (int r = 0; r < V; ++r) xv[q].v[r] = T(0);
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+#pragma unroll
+          for (int r = 0; r < V; ++r) acc[r] = fma(h[q], xv[q].v[r], acc[r]);
+          if constexpr (SPLIT) {
+#pragma unroll
+            for (int r = 0; r < V; ++r) accl[r] = fma((T)l[q], xv[q].v[r], accl[r]);
+          }
+        }
+      }
+    }
+    if constexpr (ADJ) {
+      // sensor entries sit at the end of the row
+      for (int e = e1 - 1; e >= e0; --e) {
+        const uint32_t c = A.col[e];
+        if (!(c & kTagInj)) break;
+        const int64_t j = (int64_t)(c & kIdxMask);
+        const T h = A.hi[e];
+        Pack<T, V> ys;
+#pragma unroll
+        for (int q = 0; q < V; ++q) ys.v[q] = T(0);
+        if (A.ya) {
+          const Pack<T, V> y = ld<T, V>(A.ya + j * A.K + (int64_t)kv * V);
+#pragma unroll
+          for (int q = 0; q < V; ++q) ys.v[q] += y.v[q];
+        }
+        if (A.yb) {
+          const Pack<T, V> y = ld<T, V>(A.yb + j * A.K + (int64_t)kv * V);
+#pragma unroll
+          for (int q = 0; q < V; ++q) ys.v[q] += y.v[q];
+        }
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fma(h, ys.v[q], src[q]);
+      }
+    }
+    Pack<T, V> xi, xpi, xo;
+    if (have_x) {
+      xi = ld<T, V>(A.x + off);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) xi.v[q] = T(0);
+    }
+    if (xp_buf) {
+      xpi = ld<T, V>(A.xp + off);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const T w = xi.v[q] - xpi.v[q];
+      const T wn = w - (acc[q] + accl[q]) + A.inj_scale * src[q];
+      xo.v[q] = xi.v[q] + wn;
+    }
+    st<T, V>(A.xn + off, xo);
+    return;
+  }
+  if (A.y_out == nullptr) return;
+  const int64_t g = t - A.row_threads;
+  if (g >= (int64_t)A.n_obs * KV) return;
+  const int d = (int)(g / KV);
+  const int kv = (int)(g - (int64_t)d * KV);
+  T acc[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) acc[q] = T(0);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int64_t node = A.det_node[3 * d + s];
+    const T wt = A.det_w[3 * d + s];
+    const Pack<T, V> a = ld<T, V>(A.x + node * A.K + (int64_t)kv * V);
+    if (A.prev_mode == 0) {
+      const Pack<T, V> b = ld<T, V>(A.xp + node * A.K + (int64_t)kv * V);
+#pragma unroll
+      for (int q = 0; q < V; ++q) acc[q] = fma(wt, T(0.5) * (a.v[q] + b.v[q]), acc[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) acc[q] = fma(wt, a.v[q], acc[q]);
+    }
+  }
+  Pack<T, V> y;
+#pragma unroll
+  for (int q = 0; q < V; ++q) y.v[q] = A.scale * acc[q];
+  st<T, V>(A.y_out + (int64_t)d * A.K + (int64_t)kv * V, y);
+}
+
+template <typename T, int V, bool SPLIT, bool ADJ>
+__global__ void __launch_bounds__(256) step3_kernel(const Step3Args<T> A) {
+  step3_body<T, V, SPLIT, ADJ>(A, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Several meshes advanced by one launch: block b belongs to the group member g
+// with block_off[g] <= b < block_off[g+1] (uneven batches of meshes and K).
+constexpr int kMaxGroup = 8;
+template <typename T>
+struct Step3Group {
+  int32_t n;
+  int64_t block_off[kMaxGroup + 1];
+  Step3Args<T> a[kMaxGroup];
+};
+
+template <typename T, int V, bool SPLIT, bool ADJ>
+__global__ void __launch_bounds__(256) step3_group_kernel(const __grid_constant__ Step3Group<T> G) {
+  int g = 0;
+  while (g + 1 < G.n && (int64_t)blockIdx.x >= G.block_off[g + 1]) ++g;
+  const int64_t t = ((int64_t)blockIdx.x - G.block_off[g]) * blockDim.x + threadIdx.x;
+  step3_body<T, V, SPLIT, ADJ>(G.a[g], t);
+}
+
+// G^T yhat = M (u_1 - u_2) + M Bt u_2 from the last two transposed states
+// (B entries of the forward rows carry Bt = dt B_ij / M_i).
+template <typename T, int V, bool SPLIT>
+__global__ void __launch_bounds__(256) adj3_finish_kernel(int64_t row_threads, int K, const int32_t* __restrict__ ptr,
+                                                          const uint32_t* __restrict__ col, const T* __restrict__ hi,
+                                                          const float* __restrict__ lo, const double* __restrict__ ml,
+                                                          const T* __restrict__ u1, const T* __restrict__ u2,
+                                                          T* __restrict__ out) {
+  const int KV = K / V;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= row_threads) return;
+  const int64_t row = t / KV;
+  const int kv = (int)(t - row * KV);
+  const int64_t off = row * K + (int64_t)kv * V;
+  T acc[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) acc[q] = T(0);
+  for (int e = ptr[row]; e < ptr[row + 1]; ++e) {
+    const uint32_t c = col[e];
+    if (!(c & kTagB)) continue;
+    const Pack<T, V> x = ld<T, V>(u2 + (int64_t)(c & kIdxMask) * K + (int64_t)kv * V);
+    T h = hi[e];
+    if constexpr (SPLIT) h += (T)lo[e];
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[q] = fma(h, x.v[q], acc[q]);
+  }
+  const Pack<T, V> a = ld<T, V>(u1 + off), b = ld<T, V>(u2 + off);
+  const T m = (T)ml[row];
+  Pack<T, V> o;
+#pragma unroll
+  for (int q = 0; q < V; ++q) o.v[q] = m * ((a.v[q] - b.v[q]) + acc[q]);
+  st<T, V>(out + off, o);
+}
+
+}  // namespace pat

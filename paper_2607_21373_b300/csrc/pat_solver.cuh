@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <initializer_list>
+#include <vector>
+
 #include "pat_internal.h"
 
 namespace pat {
@@ -30,6 +33,46 @@ pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, do
 pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean, double* stdev, char* ws,
                        cudaStream_t st);
 pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st);
+
+// Building blocks of the grouped (multi-mesh) driver, pat_multi.cu.
+template <typename T>
+struct Step3Args;
+template <typename T>
+Step3Args<T> fwd3_args(const DeviceMesh& m, int K, int V, const T* p0, T* Y, T scale, T* const b[3], int i,
+                       int64_t* threads);
+template <typename T>
+Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale, T* const b[3], int i,
+                       int64_t* threads);
+template <typename T>
+pat_status begin_pre(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
+                     uint64_t seed, char* ws, cudaStream_t st);
+template <typename T>
+pat_status begin_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st);
+template <typename T>
+pat_status iter_mid(const DeviceMesh& m, int K, char* ws, cudaStream_t st);
+template <typename T>
+pat_status iter_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st);
+int vec_width(const DeviceMesh& m, int K, std::initializer_list<const void*> ptrs);
+
+// Grouped RTO over several meshes (pat_multi.cu): one RTO problem per job.
+struct Job {
+  const DeviceMesh* m;
+  int K;
+  const void* y_obs;
+  double sigma;
+  const void* eta;
+  const void* xi;
+  uint64_t seed;
+  double *samples, *mean, *stdev;
+  char* ws;
+};
+
+pat_status rto_multi(const std::vector<Job>& jobs, int n_iter, cudaStream_t st);
+
+// Misfit gradient with respect to per-element c^2 (pat_grad.cu).
+size_t grad_workspace_bytes(const DeviceMesh& m, int K);
+pat_status grad_c2(const DeviceMesh& m, const void* p0, const void* Yhat, int K, double* g, void* p0_grad, char* ws,
+                   cudaStream_t st);
 
 // Counter-based N(0,1) draws (SplitMix64 output function + Box-Muller).
 pat_status draw_normals(uint64_t seed, int stream_id, int64_t n_elem, int K, double* out, cudaStream_t st);

@@ -1,0 +1,117 @@
+"""Differentiation through the forward map (torch.autograd wrappers, c^2 gradient).
+
+Pins: the oracle's adjoint-state gradient (itself pinned by finite differences
+in test_oracle_gradient.py), GPU finite differences along random directions at
+the 35,937-node / 1000-step size, and torch.autograd.gradcheck on a tiny mesh.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import fem, gradient
+from problems import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(n, n_obs, n_steps, prec, seed=1004, flags=0):
+    from paper_2607_21373_b300 import Mesh
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, seed)
+    c2 = S.smoothed_speed_field(n, seed + 7)
+    dt = 0.3 / n / np.sqrt(c2.max())
+    p0 = S.phantom(xyz, "blobs20+vessels", seed + 100, n)
+    if prec == "f32":
+        p0 = p0.astype(np.float32).astype(np.float64)
+    m = Mesh(xyz, tets, det, dt, n_steps, precision=prec, c2=c2, flags=flags)
+    return m, xyz, tets, det, c2, dt, p0
+
+
+def dev(a, prec):
+    return torch.tensor(np.asarray(a), dtype=torch.float64 if prec == "f64" else torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_c2_gradient_matches_oracle(prec, tol):
+    n, n_obs, nt = 4, 12, 60
+    m, xyz, tets, det, c2, dt, p0 = setup(n, n_obs, nt, prec)
+    ops = gradient.with_c2(fem.build(xyz, tets, det, n), tets, c2)
+    y = S.standard_normal((nt, n_obs), 3) * 0.1
+    gp_ref, gt_ref = gradient.gradients(ops, tets, p0, y, dt)
+    Y = m.forward(dev(p0, prec))
+    yhat = (Y.double() - torch.tensor(y, device="cuda")).to(Y.dtype).contiguous()
+    g, pg = m.grad_c2(dev(p0, prec), yhat)
+    assert rel_l2(g.cpu().numpy(), gt_ref) < tol
+    assert rel_l2(pg.cpu().double().numpy(), gp_ref) < tol
+
+
+def test_c2_gradient_sums_stacked_samples():
+    n, n_obs, nt = 3, 10, 40
+    m, xyz, tets, det, c2, dt, p0 = setup(n, n_obs, nt, "f64")
+    ops = gradient.with_c2(fem.build(xyz, tets, det, n), tets, c2)
+    P = np.stack([p0, 0.5 * p0 + 0.1], axis=1)
+    ys = [S.standard_normal((nt, n_obs), 5 + k) * 0.1 for k in range(2)]
+    ref = sum(gradient.gradients(ops, tets, P[:, k], ys[k], dt)[1] for k in range(2))
+    Y = m.forward(dev(P, "f64"))
+    yhat = (Y - torch.tensor(np.stack(ys, axis=2), device="cuda")).contiguous()
+    g, _ = m.grad_c2(dev(P, "f64"), yhat)
+    assert rel_l2(g.cpu().numpy(), ref) < 1e-10
+
+
+def test_c2_gradient_directional_fd_at_full_size():
+    """35,937 nodes, 1000 steps (ceil(sqrt(1000)) = 32 checkpoints), FP64 on the GPU:
+    g . d against a central difference of L along a random direction d."""
+    from paper_2607_21373_b300 import MESH_SKIP_STABILITY
+    n, n_obs, nt = 32, 256, 1000
+    m, xyz, tets, det, c2, dt, p0 = setup(n, n_obs, nt, "f64", flags=MESH_SKIP_STABILITY)
+    y = m.forward(dev(p0 * 0.9, "f64")).clone()       # data from a different initial pressure
+    p = dev(p0, "f64")
+
+    def L(c):
+        m.set_c2(c)
+        r = m.forward(p) - y
+        return 0.5 * float((r * r).sum())
+
+    m.set_c2(c2)
+    yhat = (m.forward(p) - y).contiguous()
+    g, pg = m.grad_c2(p, yhat)
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal(len(c2)) * c2
+    eps = 1e-6
+    fd = (L(c2 + eps * d) - L(c2 - eps * d)) / (2 * eps)
+    assert abs(float(g.cpu().numpy() @ d) - fd) < 1e-6 * abs(fd)
+    # p0 direction, c2 restored
+    m.set_c2(c2)
+    dp = dev(rng.standard_normal(len(p0)), "f64")
+    fdp = (0.5 * float(((m.forward(p + eps * dp) - y) ** 2).sum())
+           - 0.5 * float(((m.forward(p - eps * dp) - y) ** 2).sum())) / (2 * eps)
+    assert abs(float((pg * dp).sum()) - fdp) < 1e-6 * abs(fdp)
+
+
+def test_autograd_gradcheck_tiny_mesh():
+    from paper_2607_21373_b300 import Mesh
+    from paper_2607_21373_b300.autograd import wave_forward
+    n, nt = 2, 12
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(5, S.ALL_FACES, 9)
+    c2 = S.smoothed_speed_field(n, 3)
+    m = Mesh(xyz, tets, det, 0.3 / n / np.sqrt(c2.max() * 1.1), nt, precision="f64", c2=c2)
+    p0 = torch.tensor(S.standard_normal(len(xyz), 4), dtype=torch.float64, device="cuda", requires_grad=True)
+    c2t = torch.tensor(c2, dtype=torch.float64, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda p: wave_forward(p, m), (p0,), eps=1e-6, atol=1e-8)
+    assert torch.autograd.gradcheck(lambda p, c: wave_forward(p, m, c), (p0, c2t), eps=1e-6, atol=1e-7)
+
+
+def test_autograd_backward_is_the_transpose_kernel():
+    from paper_2607_21373_b300.autograd import wave_forward
+    from paper_2607_21373_b300 import Mesh
+    n, nt = 6, 80
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(20, S.ALL_FACES, 2)
+    m = Mesh(xyz, tets, det, 0.3 / n, nt, precision="f32")
+    p0 = torch.tensor(S.standard_normal((len(xyz), 4), 1), dtype=torch.float32, device="cuda", requires_grad=True)
+    Y = wave_forward(p0, m)
+    w = torch.tensor(S.standard_normal(tuple(Y.shape), 2), dtype=torch.float32, device="cuda")
+    (Y * w).sum().backward()
+    assert torch.equal(p0.grad, m.adjoint(w))
