@@ -155,6 +155,28 @@ pat_status pat_forward(const pat_mesh* mesh, const void* p0, int32_t K, void* Y,
                        void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * pat_forward without a workspace, for callers that cannot allocate device
+ * memory where they call it (plug-ins whose host framework owns every device
+ * buffer and passes only inputs and outputs; real-time loops that must not
+ * allocate).  The paper has no counterpart: this is a deployment variant of
+ * pat_forward with the same arguments minus the workspace, and the same result.
+ *   - The time-stepping state lives in a fixed 8 MiB device array inside the
+ *     library (one per device that loads the library, held until the process
+ *     exits), so N*K must not exceed 524,288 for PAT_F32 meshes or 262,144 for
+ *     PAT_F64 meshes; larger requests return PAT_EINVAL with a message naming
+ *     the limit.  The call never allocates or frees device memory.
+ *   - The first call on a device looks up that array's device address (with the
+ *     device current) and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls on a device share the one array: calls that overlap on the GPU
+ *     (other streams, other host threads) race and corrupt each other's
+ *     results; serialise them.  A call never reads what an earlier call left
+ *     in the array.
+ */
+pat_status pat_forward_noalloc(const pat_mesh* mesh, const void* p0, int32_t K, void* Y, double scale,
+                               void* stream);
+
+/*
  * p_hat = scale * G^T Yhat (Section 5.1, eq. backward-recursion and
  * eq. adjoint-verlet): the exact transpose of pat_forward's map, up to rounding.
  *   Yhat device [N_T][N_obs][K] real; p_hat device [N][K] real (written).

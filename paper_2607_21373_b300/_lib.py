@@ -47,6 +47,7 @@ SIGNATURES = {
     "pat_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, c_size_p]),
     "pat_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p,
                               C.c_size_t, C.c_void_p]),
+    "pat_forward_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p]),
     "pat_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_void_p,
                               C.c_size_t, C.c_void_p]),
     "pat_rto_sample": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p,

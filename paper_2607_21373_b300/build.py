@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpat.so")
-SOURCES = ["pat_host.cpp", "pat_kernels.cu", "pat_grad.cu", "pat_multi.cu", "pat_api.cu"]
+SOURCES = ["pat_host.cpp", "pat_kernels.cu", "pat_grad.cu", "pat_multi.cu", "pat_noalloc.cu", "pat_api.cu"]
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-lineinfo", "-O3", "-std=c++17", "-shared",
