@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=58)
+    ap.add_argument("--cells", type=int, default=58, help="cells per cube edge")
     ap.add_argument("--n-steps", type=int, default=1000)
     ap.add_argument("--n-obs", type=int, default=1024)
     ap.add_argument("--K", type=int, default=64)
@@ -52,28 +52,30 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
+    ap.add_argument("--autotune", type=int, default=1, help="0: keep the library's default step-kernel variant")
+    ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4")
     return ap.parse_args()
 
 
 def workload_config(a):
     w = S.BATCHED
     return {
-        "workload": f"cube{a.n}_rto: unit cube {a.n}^3 cells x 6 Kuhn tets, {(a.n + 1) ** 3} nodes, "
+        "workload": f"cube{a.cells}_rto: unit cube {a.cells}^3 cells x 6 Kuhn tets, {(a.cells + 1) ** 3} nodes, "
                     f"N_T={a.n_steps}, dt=0.3h, {a.n_obs} sensors on 5 faces, K={a.K} samples per batch, "
                     f"CGLS k={a.k_iter}, white-noise prior N(0, M_L^-1), 1% noise",
-        "n_nodes": (a.n + 1) ** 3, "n_tets": 6 * a.n ** 3, "n_steps": a.n_steps, "n_obs": a.n_obs,
+        "n_nodes": (a.cells + 1) ** 3, "n_tets": 6 * a.cells ** 3, "n_steps": a.n_steps, "n_obs": a.n_obs,
         "K": a.K, "cgls_iters": a.k_iter, "noise": w.noise,
-        "node_steps_per_sample": (2 * a.k_iter + 1) * a.n_steps * (a.n + 1) ** 3,
+        "node_steps_per_sample": (2 * a.k_iter + 1) * a.n_steps * (a.cells + 1) ** 3,
         "l2": "inputs larger than L2: the K-stacked state is 4*N*K*4 B = %.0f MB per buffer set"
-              % (4 * (a.n + 1) ** 3 * a.K * 4 / 1e6),
+              % (4 * (a.cells + 1) ** 3 * a.K * 4 / 1e6),
     }
 
 
 def problem(a):
-    xyz, tets = S.cube_mesh(a.n)
+    xyz, tets = S.cube_mesh(a.cells)
     det = S.detector_points(a.n_obs, S.LIMITED_VIEW_FACES, S.BATCHED.seed)
-    p0 = S.phantom(xyz, "blobs20+vessels", S.BATCHED.seed + 100, a.n)
-    return xyz, tets, det, p0, 0.3 / a.n
+    p0 = S.phantom(xyz, "blobs20+vessels", S.BATCHED.seed + 100, a.cells)
+    return xyz, tets, det, p0, 0.3 / a.cells
 
 
 # --------------------------------------------------------------------------
@@ -138,8 +140,8 @@ def oracle_rate(a, n_solve_steps, xyz=None, tets=None, det=None, p0=None):
     from oracle import fem, wave
     if xyz is None:
         xyz, tets, det, p0, _ = problem(a)
-    dt = 0.3 / a.n
-    ops = fem.build(xyz, tets, det, a.n)
+    dt = 0.3 / a.cells
+    ops = fem.build(xyz, tets, det, a.cells)
     t0 = time.perf_counter()
     Y = wave.forward(ops, p0, dt, n_solve_steps)
     wave.adjoint(ops, Y, dt)
@@ -154,8 +156,8 @@ def run_reference(a, rank, world):
     nsps = cfg["node_steps_per_sample"]
     xyz, tets, det, p0, _ = problem(a)
     from oracle import fem, wave
-    ops = fem.build(xyz, tets, det, a.n)
-    dt = 0.3 / a.n
+    ops = fem.build(xyz, tets, det, a.cells)
+    dt = 0.3 / a.cells
     n_solve = 50      # one step = one forward + one transposed solve of 50 time steps
 
     def one():
@@ -206,6 +208,19 @@ def run_ours(a, rank, world, local_rank, dist):
     sigma = float(S.BATCHED.noise * torch.linalg.vector_norm(Y.double()) / torch.linalg.vector_norm(eta0.double()))
     y_obs = (Y + sigma * eta0).contiguous()
     K, k = a.K, a.k_iter
+    # pick the step-kernel variant per direction for both sample counts (not timed)
+    tune = {}
+    forced = {"tiled": dict(V=8, packed=2), "v8c2": dict(V=8, packed=1, chunk=2),
+              "v4c4": dict(V=4, packed=1, chunk=4), "v8c2z": dict(V=8, packed=1, chunk=2, zorder=True)}.get(a.variant)
+    if forced:
+        for d in ("fwd", "adj"):
+            mesh.select_variant(K, d, **forced)
+        tune["K%d" % K] = [dict(dict(direction=d, us_per_step=0.0, staged=False, chunk=0), **forced)
+                           for d in ("fwd", "adj")]
+    elif a.autotune and not (a.mesh_flags & 0x10):
+        tune["K%d" % K] = mesh.autotune(K, n_probe=30)
+        if a.plain_steps > 0:
+            tune["K1"] = mesh.autotune(1, n_probe=30)
 
     def batch(K_, seed):
         return mesh.rto_sample(y_obs, sigma, K_, k, seed=seed, samples=False, mean=True, stdev=K_ >= 2)
@@ -214,8 +229,9 @@ def run_ours(a, rank, world, local_rank, dist):
         if dist is not None:
             dist.barrier()
 
+    from paper_2607_21373_b300.dist import allreduce_moments, sample_seed
     for i in range(a.warmup):
-        batch(K, 1000 * rank + i)
+        batch(K, sample_seed(i, rank))
     mesh.status(K)
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -227,7 +243,7 @@ def run_ours(a, rank, world, local_rank, dist):
     torch.cuda.synchronize()
     e0.record(st)
     for i in range(a.steps):
-        batch(K, 1000 * rank + 100 + i)
+        last = batch(K, sample_seed(100 + i, rank))
     e1.record(st)
     torch.cuda.synchronize()
     barrier()
@@ -240,6 +256,8 @@ def run_ours(a, rank, world, local_rank, dist):
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+        # pointwise posterior statistics over every rank's samples (outside the timed region)
+        allreduce_moments(last["mean"], last["std"], K)
     sec = ms / 1e3
     value = world * K * a.steps / sec
     nsps = cfg["node_steps_per_sample"]
@@ -268,8 +286,20 @@ def run_ours(a, rank, world, local_rank, dist):
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     achieved = fwd_bytes_per_launch / (fwd_avg_ms * 1e-3) / 1e9
     adj_achieved = (adj_loop_bytes / (NT + 1)) / (adj_avg_ms * 1e-3) / 1e9
-    kname = "fwd_step_kernel<float,4,true>" if two_level else "step3_kernel<float,4,true,false>"
-    aname = "adj_step_kernel<float,4,true>" if two_level else "step3_kernel<float,4,true,true>"
+    def best(direction):
+        rows = [e for e in tune.get("K%d" % K, []) if e["direction"] == direction]
+        return min(rows, key=lambda e: e["us_per_step"]) if rows else {"V": 4, "staged": False, "packed": True}
+
+    def kernel_name(e, adj):
+        if e.get("packed") == 2:
+            return "step3t_kernel<8,%s>" % ("true" if adj else "false")
+        if e.get("packed"):
+            return "step3f_kernel<%d,%d,%s>%s" % (e["V"], e.get("chunk", 4), "true" if adj else "false",
+                                                  " (Z-order rows)" if e.get("zorder") else "")
+        return "step3_kernel<float,%d,split,%s,staged=%d>" % (e["V"], "adj" if adj else "fwd", e["staged"])
+    bf, ba = best("fwd"), best("adj")
+    kname = "fwd_step_kernel<float,4,true>" if two_level else kernel_name(bf, False)
+    aname = "adj_step_kernel<float,4,true>" if two_level else kernel_name(ba, True)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": None,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
@@ -331,6 +361,7 @@ def run_ours(a, rank, world, local_rank, dist):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["total_launches"],
             "gpu_launches_per_step": prof["total_launches"] / a.steps, "clocks": clk, "plain": plain,
             "batched_over_plain": (value / world) / plain["samples_per_s"] if plain else None,
+            "autotune": tune,
         }
         print(json.dumps(line), flush=True)
 

@@ -66,6 +66,8 @@ typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_prec;
 #define PAT_MESH_SINGLE_COEF    0x4u /* PAT_F32: one float per coefficient (no hi+lo split) */
 #define PAT_MESH_TWO_LEVEL      0x10u /* step (p^{n+1/2}, dt v) pairs: 16 B per node and sample
                                          instead of the default three-level form's 12 B */
+#define PAT_MESH_NO_GRAPHS      0x20u /* launch the CGLS loop's time steps one by one instead of
+                                         replaying each wave solve from a CUDA graph */
 #define PAT_MESH_HOST_ONLY      0x8u /* assemble on the host only (no device copy); compute
                                         calls on such a mesh return PAT_EINVAL, exports work */
 
@@ -200,6 +202,9 @@ pat_status pat_adjoint(const pat_mesh* mesh, const void* Yhat, int32_t K, void* 
  *           (stdev needs K >= 2; estimator of eq. ergodic with 1/(K-1)).
  *   resid   device [n_iter+1][K] double or NULL: ||r_j||^2 of each iterate.
  *   workspace >= pat_workspace_bytes(mesh, 2, K).
+ * Each wave solve of the CGLS loop is captured once into a CUDA graph (per
+ * workspace, K and sigma, cached on the mesh) and replayed, unless the stream
+ * is already being captured or the mesh has PAT_MESH_NO_GRAPHS.
  * Errors: PAT_EINVAL; PAT_ENUMERIC is reported by pat_rto_status.
  */
 pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K,
@@ -287,6 +292,36 @@ pat_status pat_draw_normals(uint64_t seed, int32_t stream_id, int64_t n_elem, in
  */
 pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, int32_t K, double* g_c2,
                        void* p0_grad, void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Autotuning of the time-step kernels for K stacked samples on this mesh:
+ * every variant (samples per thread V in {8, 4, 2, 1} that divides K; for FP32
+ * split coefficients a packed kernel doing two samples per fma.rn.f32x2 with
+ * row chunks of 2, 4 or 8 entries; a generic kernel with the row metadata
+ * staged in shared memory or read directly) runs n_probe forward and
+ * n_probe transposed steps on zeroed buffers of `workspace` (an RTO workspace,
+ * >= pat_workspace_bytes(mesh, 2, K); its CGLS state is overwritten), timed
+ * with CUDA events on `stream`.  The fastest variant per direction is used by
+ * every later call with this K on this mesh.  table (host, may be NULL)
+ * receives up to 64 entries {direction 0 fwd / 1 adj, V, staged, packed, chunk,
+ * min_blocks (resident blocks per SM asked of the compiler), early (own values
+ * loaded before the row walk), zorder (rows processed in Z-order of the node
+ * coordinates), us per step};
+ * *n_entries the number of variants timed.  Synchronises the stream.
+ */
+typedef struct {
+  int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder;
+  double us_per_step;
+} pat_tune_entry;
+pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,
+                        pat_tune_entry* table, int32_t* n_entries, void* stream);
+
+/* Use the given variant (fields as in pat_tune_entry; packed 2 = the
+ * tile-staged kernel, which stages each 32-row tile's source rows in shared
+ * memory by bulk asynchronous copies) for direction 0 (forward) or 1
+ * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not
+ * exist for this K and precision.  Every variant gives bit-identical results. */
+pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* variant);
 
 /*
  * Live timing of the hot kernels, for benchmarks.  While enabled on a mesh,

@@ -23,7 +23,8 @@ from ._lib import PatError
 __all__ = ["Mesh", "PatError", "draw_normals", "rto_sample_multi", "lib", "F32", "F64"]
 
 F32, F64 = 0, 1
-MESH_SKIP_STABILITY, MESH_KEEP_ZEROS, MESH_SINGLE_COEF, MESH_HOST_ONLY, MESH_TWO_LEVEL = 0x1, 0x2, 0x4, 0x8, 0x10
+MESH_SKIP_STABILITY, MESH_KEEP_ZEROS, MESH_SINGLE_COEF, MESH_HOST_ONLY, MESH_TWO_LEVEL, MESH_NO_GRAPHS = (
+    0x1, 0x2, 0x4, 0x8, 0x10, 0x20)
 
 
 def lib():
@@ -196,6 +197,26 @@ class Mesh:
         _lib.check(lib().pat_grad_c2(self._h, _ptr(p0), _ptr(Yhat), K, _ptr(g), _ptr(pg), _ptr(ws), ws.numel(),
                                      _stream()))
         return g, pg
+
+    def autotune(self, K, n_probe=20):
+        """Time every step-kernel variant for K samples and keep the fastest (pat_autotune).
+        Returns the timing table as a list of dicts."""
+        ws = self.workspace(2, K)
+        table = (_lib.TuneEntry * 64)()
+        n = C.c_int32()
+        _lib.check(lib().pat_autotune(self._h, K, _ptr(ws), ws.numel(), int(n_probe), table, C.byref(n),
+                                      _stream()))
+        return [{"direction": ("fwd", "adj")[e.direction], "V": e.V, "staged": bool(e.staged),
+                 "packed": int(e.packed), "chunk": e.chunk, "min_blocks": e.min_blocks,
+                 "early": bool(e.early), "zorder": bool(e.zorder), "us_per_step": e.us_per_step}
+                for e in table[:min(n.value, 64)]]
+
+    def select_variant(self, K, direction, V, packed=1, chunk=4, staged=False, min_blocks=1, early=False,
+                       zorder=False):
+        """Force a step-kernel variant (pat_select_variant); direction 'fwd' or 'adj'."""
+        e = _lib.TuneEntry(0 if direction == "fwd" else 1, V, int(staged), int(packed), int(chunk), int(min_blocks),
+                           int(early), int(zorder), 0.0)
+        _lib.check(lib().pat_select_variant(self._h, K, 0 if direction == "fwd" else 1, C.byref(e)))
 
     def profile_enable(self, on=True):
         """Start (and reset) or stop live loop timing and launch counting."""

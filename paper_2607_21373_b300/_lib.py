@@ -31,6 +31,12 @@ class RtoJob(C.Structure):
                 ("workspace_bytes", C.c_size_t)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("direction", C.c_int32), ("V", C.c_int32), ("staged", C.c_int32), ("packed", C.c_int32),
+                ("chunk", C.c_int32), ("min_blocks", C.c_int32), ("early", C.c_int32), ("zorder", C.c_int32),
+                ("us_per_step", C.c_double)]
+
+
 # name -> (restype, argtypes); every compute call returns pat_status (int)
 SIGNATURES = {
     "pat_mesh_create": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -63,6 +69,9 @@ SIGNATURES = {
     "pat_cgls_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
     "pat_rto_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_draw_normals": (C.c_int, [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pat_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(TuneEntry),
+                               C.POINTER(C.c_int32), C.c_void_p]),
+    "pat_select_variant": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(TuneEntry)]),
     "pat_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "pat_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "pat_last_error": (C.c_char_p, []),

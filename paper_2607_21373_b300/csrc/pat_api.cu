@@ -1,6 +1,7 @@
 // C ABI of libpat (declarations and contracts in include/pat.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -29,6 +30,16 @@ pat_status upload(const std::vector<T>& h, T** d) {
 }
 
 void free_device(DeviceMesh& m) {
+  if (m.capture_stream) {
+    cudaStreamDestroy((cudaStream_t)m.capture_stream);
+    m.capture_stream = nullptr;
+  }
+  {
+    std::lock_guard<std::mutex> lock(m.graph_mutex);
+    for (auto& kv : m.graphs)
+      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+    m.graphs.clear();
+  }
   for (void* e : m.prof.events)
     if (e) cudaEventDestroy((cudaEvent_t)e);
   m.prof.events.clear();
@@ -36,8 +47,12 @@ void free_device(DeviceMesh& m) {
   void** ps[] = {(void**)&m.fwd.ptr, (void**)&m.fwd.col, &m.fwd.hi, (void**)&m.fwd.lo,
                  (void**)&m.adj.ptr, (void**)&m.adj.col, &m.adj.hi, (void**)&m.adj.lo,
                  (void**)&m.adj3.ptr, (void**)&m.adj3.col, &m.adj3.hi, (void**)&m.adj3.lo,
+                 (void**)&m.fwd.hl, (void**)&m.adj.hl, (void**)&m.adj3.hl,
                  &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
-                 &m.det_w, (void**)&m.etets, &m.eK0};
+                 &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
+                 (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
+                 (void**)&m.tile_range_slot, (void**)&m.tile_slots, (void**)&m.tile_slot_fwd,
+                 (void**)&m.tile_slot_adj, (void**)&m.d_status, (void**)&m.row_order};
   for (void** p : ps) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -68,6 +83,10 @@ pat_status upload_rows(const HostRows& r, bool split, DevCSR& d) {
     std::vector<float> lo(r.val.size());
     for (size_t e = 0; e < lo.size(); ++e) lo[e] = (float)(r.val[e] - (double)hi[e]);
     s = upload(lo, &d.lo);
+    if (s) return s;
+    std::vector<float2> hl(r.val.size());
+    for (size_t e = 0; e < hl.size(); ++e) hl[e] = make_float2((float)hi[e], lo[e]);
+    s = upload(hl, &d.hl);
     if (s) return s;
   }
   return PAT_OK;
@@ -109,6 +128,100 @@ bool bad_K(int32_t K, const char* fn) {
   return false;
 }
 
+// Tiles of kTileRows consecutive rows: the union of the source rows of their
+// stiffness / boundary entries as contiguous ranges (gaps of up to 4 rows are
+// bridged), each entry's slot in the tile's staged rows, and the largest tile.
+pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, const std::vector<uint8_t>& ninj,
+                       bool upload_tables) {
+  constexpr int R = 32;
+  const int64_t N = m.N;
+  const int32_t T = (int32_t)((N + R - 1) / R);
+  std::vector<int32_t> rptr(1, 0), rsrc, rcnt, rslot, tslots(T);
+  std::vector<uint16_t> sf(F.col.size(), 0), sa(A3.col.size(), 0);
+  std::vector<int32_t> srcs;
+  int32_t max_slots = 0;
+  for (int32_t t = 0; t < T; ++t) {
+    const int64_t a = (int64_t)t * R, b = std::min<int64_t>(N, a + R);
+    srcs.clear();
+    for (int64_t i = a; i < b; ++i)
+      for (int32_t e = F.ptr[i]; e < F.ptr[i + 1]; ++e) srcs.push_back((int32_t)(F.col[e] & kIdxMask));
+    std::sort(srcs.begin(), srcs.end());
+    srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
+    // ranges with small gaps bridged; slot of every source row
+    std::vector<std::pair<int32_t, int32_t>> ranges;  // (start, count)
+    for (int32_t j : srcs) {
+      if (!ranges.empty() && j - (ranges.back().first + ranges.back().second) <= 4)
+        ranges.back().second = j - ranges.back().first + 1;
+      else
+        ranges.push_back({j, 1});
+    }
+    int32_t slot = 0;
+    for (auto& rg : ranges) {
+      rsrc.push_back(rg.first);
+      rcnt.push_back(rg.second);
+      rslot.push_back(slot);
+      slot += rg.second;
+    }
+    if (slot > 65535) {
+      set_error("pat_mesh_create: a 32-row tile reads %d distinct rows (more than 65535)", slot);
+      return PAT_EUNSUPPORTED;
+    }
+    rptr.push_back((int32_t)rsrc.size());
+    tslots[t] = slot;
+    max_slots = std::max(max_slots, slot);
+    auto slot_of = [&](int32_t j) {
+      // the range holding j (ranges are sorted by start)
+      int lo = rptr[t], hi = (int)rsrc.size() - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (rsrc[mid] <= j) lo = mid; else hi = mid - 1;
+      }
+      return (uint16_t)(rslot[lo] + (j - rsrc[lo]));
+    };
+    // every slot must map back to its entry's source row (checked here, on the host,
+    // because the kernel trusts these tables for its shared-memory reads)
+    auto src_of = [&](uint16_t sl) {
+      int q = rptr[t];
+      while (q + 1 < (int)rsrc.size() && rslot[q + 1] <= sl) ++q;
+      return rsrc[q] + (sl - rslot[q]);
+    };
+    for (int64_t i = a; i < b; ++i) {
+      for (int32_t e = F.ptr[i]; e < F.ptr[i + 1]; ++e) {
+        const int32_t j = (int32_t)(F.col[e] & kIdxMask);
+        sf[e] = slot_of(j);
+        if (sf[e] >= slot || src_of(sf[e]) != j) {
+          set_error("pat_mesh_create: internal error building the shared-memory tiles (row %lld)", (long long)i);
+          return PAT_EUNSUPPORTED;
+        }
+      }
+      const int32_t eA = A3.ptr[i + 1] - ninj[i];
+      for (int32_t e = A3.ptr[i]; e < eA; ++e) {
+        const int32_t j = (int32_t)(A3.col[e] & kIdxMask);
+        sa[e] = slot_of(j);
+        if (sa[e] >= slot || src_of(sa[e]) != j) {
+          set_error("pat_mesh_create: internal error building the shared-memory tiles (row %lld)", (long long)i);
+          return PAT_EUNSUPPORTED;
+        }
+      }
+    }
+  }
+  m.n_tiles = T;
+  m.tile_max_slots = max_slots;
+  if (!upload_tables) return PAT_OK;
+  pat_status s = upload(rptr, &m.tile_range_ptr);
+  if (!s) s = upload(rsrc, &m.tile_range_src);
+  if (!s) s = upload(rcnt, &m.tile_range_cnt);
+  if (!s) s = upload(rslot, &m.tile_range_slot);
+  if (!s) s = upload(tslots, &m.tile_slots);
+  if (!s) s = upload(sf, &m.tile_slot_fwd);
+  if (!s) s = upload(sa, &m.tile_slot_adj);
+  if (!s) {
+    std::vector<int32_t> z(1, 0);
+    s = upload(z, &m.d_status);
+  }
+  return s;
+}
+
 // Device copies of the operators from the host assembly (also used after
 // pat_mesh_set_c2, since exact-zero pruning can change the sparsity).
 pat_status build_device(pat_mesh* mesh, uint32_t flags) {
@@ -137,6 +250,7 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
 
   m.three_level = !(flags & PAT_MESH_TWO_LEVEL);
   HostRows F, A, A3;
+  std::vector<uint8_t> row_nb(N, 0), row_ninj(N, 0);
   F.ptr.assign(N + 1, 0);
   A.ptr.assign(N + 1, 0);
   A3.ptr.assign(N + 1, 0);
@@ -152,6 +266,12 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
       A.val.push_back(dt * dt * kv);
       ++nnz_k;
     }
+    if (h.b_ptr[i + 1] - h.b_ptr[i] > 255 || inj[i].size() > 255) {
+      set_error("pat_mesh_create: node %lld has more than 255 boundary or sensor entries", (long long)i);
+      return PAT_EUNSUPPORTED;
+    }
+    row_nb[i] = (uint8_t)(h.b_ptr[i + 1] - h.b_ptr[i]);
+    row_ninj[i] = (uint8_t)inj[i].size();
     for (int64_t e = h.b_ptr[i]; e < h.b_ptr[i + 1]; ++e) {
       F.col.push_back((uint32_t)h.b_col[e] | kTagB);
       F.val.push_back(dt * h.b_val[e] / mi);
@@ -186,6 +306,12 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
     minv[i] = 1.0 / h.ml[i];
   }
   std::vector<int32_t> det_node(h.det_node);
+  m.fwd_ptr_h = F.ptr;
+  m.adj3_ptr_h = A3.ptr;
+  {
+    std::lock_guard<std::mutex> lock(m.stage_mutex);
+    m.stage_span.clear();
+  }
   if (m.host_only) {
     m.fwd.nnz = (int64_t)F.col.size();
     m.adj.nnz = (int64_t)A.col.size();
@@ -221,6 +347,41 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
   if (!s && !m.host_only) s = upload(ml, &m.ml);
   if (!s && !m.host_only) s = upload(sqml, &m.sqrt_ml);
   if (!s && !m.host_only) s = upload(det_node, &m.det_node);
+  if (!s) s = build_tiles(m, F, A3, row_ninj, !m.host_only);
+  if (!s && !m.host_only) {
+    // Z-order (Morton) of the node coordinates quantised to 2^10 cells per axis
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < N; ++i)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(lo[c], h.xyz[3 * i + c]);
+        hi[c] = std::max(hi[c], h.xyz[3 * i + c]);
+      }
+    auto spread = [](uint64_t v) {  // insert two zero bits between the 10 bits of v
+      uint64_t r = 0;
+      for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+      return r;
+    };
+    std::vector<std::pair<uint64_t, int32_t>> key(N);
+    for (int64_t i = 0; i < N; ++i) {
+      uint64_t q[3];
+      for (int c = 0; c < 3; ++c) {
+        const double u = hi[c] > lo[c] ? (h.xyz[3 * i + c] - lo[c]) / (hi[c] - lo[c]) : 0.0;
+        q[c] = (uint64_t)std::min(1023.0, std::floor(u * 1024.0));
+      }
+      key[i] = {(spread(q[0]) << 2) | (spread(q[1]) << 1) | spread(q[2]), (int32_t)i};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> order(N);
+    for (int64_t i = 0; i < N; ++i) order[i] = key[i].second;
+    s = upload(order, &m.row_order);
+  }
+  if (!s && !m.host_only) {
+    cudaStream_t cs = nullptr;
+    s = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "pat_mesh_create capture stream");
+    m.capture_stream = cs;
+  }
+  if (!s && !m.host_only) s = upload(row_nb, &m.row_nb);
+  if (!s && !m.host_only) s = upload(row_ninj, &m.row_ninj);
   if (!s && !m.host_only) {
     // element data of the c^2 gradient: vertices and K_e^0 (upper triangle, c = 1)
     std::vector<int32_t> et(h.tets);
@@ -585,6 +746,14 @@ pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* ws, void*
     set_error("CGLS produced a non-finite or non-positive scalar (status %d)", word);
     return (pat_status)word;
   }
+  if (mesh->d.d_status) {
+    s = cuda_check(cudaMemcpy(&word, mesh->d.d_status, 4, cudaMemcpyDeviceToHost), "pat_rto_status read");
+    if (s) return s;
+    if (word != 0) {
+      set_error("a time-step kernel gave up waiting for its shared-memory copies (status %d)", word);
+      return (pat_status)word;
+    }
+  }
   return PAT_OK;
 }
 
@@ -599,6 +768,65 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
   pat_status s = check_ws(mesh, 3, K, ws, ws_bytes, "pat_grad_c2");
   if (s) return s;
   return grad_c2(mesh->d, p0, Yhat, K, g_c2, p0_grad, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* v) {
+  clear_error();
+  if (!mesh || !v || direction < 0 || direction > 1) {
+    set_error("pat_select_variant: NULL argument or direction not in {0, 1}");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_select_variant")) return PAT_EINVAL;
+  const bool f32s = mesh->d.prec == PAT_F32 && mesh->d.split;
+  const bool ok_v = (v->V == 1 || v->V == 2 || v->V == 4 || v->V == 8) && K % v->V == 0 &&
+                    (mesh->d.prec == PAT_F32 || v->V <= 2);
+  const bool ok_p = v->packed == 0 ? v->V != 8
+                    : v->packed == 1 ? f32s && (v->V == 4 || v->V == 8) && (v->chunk == 2 || v->chunk == 4 ||
+                                                                             (v->chunk == 8 && v->V == 4))
+                    : v->packed == 2 ? f32s && v->V == 8 && K <= 256
+                                     : false;
+  if (!ok_v || !ok_p || (v->staged && K / v->V < 2) || (v->min_blocks != 1 && v->min_blocks != 6)) {
+    set_error("pat_select_variant: variant V=%d packed=%d chunk=%d staged=%d is not available for K=%d on this mesh",
+              v->V, v->packed, v->chunk, v->staged, K);
+    return PAT_EINVAL;
+  }
+  TuneCfg c;
+  c.V = v->V;
+  c.stage = v->staged;
+  c.packed = v->packed;
+  c.chunk = v->chunk ? v->chunk : 4;
+  c.minb = v->min_blocks;
+  c.early = v->early;
+  c.order = v->zorder;
+  {
+    std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
+    mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
+  }
+  std::lock_guard<std::mutex> lock(mesh->d.graph_mutex);
+  for (auto& kv : mesh->d.graphs)
+    if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+  mesh->d.graphs.clear();
+  return PAT_OK;
+}
+
+pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* ws, size_t ws_bytes, int32_t n_probe, pat_tune_entry* table,
+                        int32_t* n_entries, void* stream) {
+  clear_error();
+  if (!mesh || n_probe < 1) {
+    set_error("pat_autotune: NULL mesh or n_probe < 1");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_autotune") || !check_device(mesh, "pat_autotune")) return PAT_EINVAL;
+  if (!mesh->d.three_level) {
+    set_error("pat_autotune: only the three-level form has tunable variants");
+    return PAT_EUNSUPPORTED;
+  }
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_autotune");
+  if (s) return s;
+  int n = 0;
+  s = autotune(mesh->d, K, (char*)ws, n_probe, table, &n, (cudaStream_t)stream);
+  if (n_entries) *n_entries = n;
+  return s;
 }
 
 pat_status pat_profile_enable(pat_mesh* mesh, int32_t enable) {

@@ -94,6 +94,8 @@ static void step(const DeviceMesh& m, const DevCSR& csr, int K, const T* x, cons
   A.col = csr.col;
   A.hi = static_cast<const T*>(csr.hi);
   A.lo = csr.lo;
+  A.nb = m.row_nb;
+  A.ninj = m.row_ninj;
   A.x = x;
   A.xp = xp;
   A.xn = xn;
@@ -101,10 +103,11 @@ static void step(const DeviceMesh& m, const DevCSR& csr, int K, const T* x, cons
   A.yb = yb;
   A.inj_scale = inj_scale;
   const unsigned blocks = (unsigned)((A.row_threads + 255) / 256);
+  A.stage_cap = 0;  // V = 1, K small: one thread per row, no staging
   if (&csr == &m.adj3)
-    step3_kernel<T, V, SPLIT, true><<<blocks, 256, 0, st>>>(A);
+    step3_kernel<T, V, SPLIT, true, false><<<blocks, 256, 0, st>>>(A);
   else
-    step3_kernel<T, V, SPLIT, false><<<blocks, 256, 0, st>>>(A);
+    step3_kernel<T, V, SPLIT, false, false><<<blocks, 256, 0, st>>>(A);
 }
 
 template <typename T, int V, bool SPLIT>

@@ -2,8 +2,13 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
+#include <tuple>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <vector_types.h>
 
 #include "../../include/pat.h"
 
@@ -68,6 +73,7 @@ struct DevCSR {
   uint32_t* col = nullptr;
   void* hi = nullptr;   // float or double
   float* lo = nullptr;  // FP32 split meshes only
+  float2* hl = nullptr; // FP32 split meshes: (hi, lo) interleaved
   int64_t nnz = 0;
 };
 
@@ -78,6 +84,17 @@ struct Profiler {
   std::vector<int> kind;      // per pair: 0 forward, 1 adjoint
   size_t used = 0;            // pairs in use
   int64_t fwd_launches = 0, adj_launches = 0, total_launches = 0;
+};
+
+// Kernel variant of the three-level step: samples per thread and row staging.
+struct TuneCfg {
+  int V = 4;
+  int stage = 0;   // row metadata staged in shared memory (generic kernel)
+  int packed = 1;  // packed f32x2 kernel (FP32 split coefficients, V = 4 or 8)
+  int chunk = 4;   // packed kernel: row entries per pipelined chunk (2, 4 or 8)
+  int minb = 1;    // packed kernel: minimum resident blocks per SM asked of the compiler
+  int early = 0;   // packed kernel: load the node's own values before the row walk
+  int order = 0;   // packed kernel: process rows in Z-order of the node coordinates
 };
 
 struct DeviceMesh {
@@ -92,6 +109,16 @@ struct DeviceMesh {
   DevCSR adj3;              // forward rows + sensor entries w_d / (2 M_i) (three-level form)
   bool three_level = true;
   uint32_t flags = 0;
+  uint8_t* row_nb = nullptr;    // [N] boundary entries per forward / three-level adjoint row
+  uint8_t* row_ninj = nullptr;  // [N] sensor entries per three-level adjoint row
+  // tiles of 32 rows for the tile-staged kernel: per tile, contiguous source-row
+  // ranges to stage in shared memory, and per CSR entry its 16-bit slot
+  int32_t n_tiles = 0, tile_max_slots = 0;
+  int32_t *tile_range_ptr = nullptr, *tile_range_src = nullptr, *tile_range_cnt = nullptr,
+          *tile_range_slot = nullptr, *tile_slots = nullptr;
+  uint16_t *tile_slot_fwd = nullptr, *tile_slot_adj = nullptr;
+  int32_t* d_status = nullptr;  // device status word of the tile kernels (PAT_ETIMEOUT)
+  int32_t* row_order = nullptr;  // [N] rows sorted by the Z-order (Morton) key of their coordinates
   int32_t* etets = nullptr;  // [E][4] element vertices (c^2 gradient)
   void* eK0 = nullptr;       // [E][10] real: upper triangle of V grad(l_a).grad(l_b) (c = 1)
   void* minv_hi = nullptr;   // [N] real: 1 / M_i
@@ -103,6 +130,19 @@ struct DeviceMesh {
   pat_mesh_info info{};
   HostMesh host;             // kept for export / checks
   mutable Profiler prof;
+  // host copies of the forward / three-level adjoint row pointers, and the
+  // largest CSR range a 256-thread block covers for a given threads-per-row
+  std::vector<int32_t> fwd_ptr_h, adj3_ptr_h;
+  mutable std::map<std::pair<int, int>, int> stage_span;
+  mutable std::mutex stage_mutex;
+  // CUDA graphs of whole forward / transposed solves inside the CGLS loop,
+  // keyed by (direction, workspace, K, scale bits); cudaGraphExec_t handles
+  mutable std::map<std::tuple<int, const void*, int, uint64_t>, void*> graphs;
+  void* capture_stream = nullptr;  // private cudaStream_t the graphs are captured on
+  mutable std::mutex graph_mutex;
+  // variants picked by pat_autotune per (direction 0 fwd / 1 adj, K)
+  mutable std::map<std::pair<int, int>, TuneCfg> tuned;
+  mutable std::mutex tune_mutex;
 };
 
 }  // namespace pat

@@ -4,8 +4,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "pat_kernels.cuh"
+#include "pat_tile.cuh"
 #include "pat_solver.cuh"
 
 namespace pat {
@@ -69,7 +71,7 @@ size_t state_bytes(const DeviceMesh& m, int K) { return align256(4 * (size_t)m.N
 // Widest per-thread vector that divides K and keeps every access aligned.
 template <typename T>
 static int pick_vec(int K, std::initializer_list<const void*> ptrs) {
-  int V = (sizeof(T) == 4) ? 4 : 2;
+  int V = (sizeof(T) == 4) ? 8 : 2;
   while (V > 1) {
     bool ok = (K % V) == 0;
     for (const void* p : ptrs)
@@ -172,10 +174,121 @@ static pat_status adjoint_t(const DeviceMesh& m, const T* Yhat, int K, T* out, T
   return cuda_check(cudaGetLastError(), "adjoint step launch");
 }
 
+// Largest CSR range covered by one 256-thread block of a row phase with KV
+// threads per row (cached per mesh, direction and KV).
+int stage_span(const DeviceMesh& m, bool adj, int KV) {
+  std::lock_guard<std::mutex> lock(m.stage_mutex);
+  auto key = std::make_pair(adj ? 1 : 0, KV);
+  auto it = m.stage_span.find(key);
+  if (it != m.stage_span.end()) return it->second;
+  const std::vector<int32_t>& ptr = adj ? m.adj3_ptr_h : m.fwd_ptr_h;
+  const int64_t rows_threads = m.N * (int64_t)KV;
+  int span = 0;
+  for (int64_t tb0 = 0; tb0 < rows_threads; tb0 += 256) {
+    const int64_t r0 = tb0 / KV;
+    const int64_t r1 = (std::min(tb0 + 256, rows_threads) - 1) / KV;
+    span = std::max(span, ptr[r1 + 1] - ptr[r0]);
+  }
+  m.stage_span[key] = span;
+  return span;
+}
+
+// Shared-memory staging pays when several threads share a row and the block's
+// rows fit in 48 KB.
+template <typename T, bool SPLIT>
+static int stage_cap_for(const DeviceMesh& m, bool adj, int K, int V) {
+  const int KV = K / V;
+  if (KV < 2) return 0;
+  const int span = stage_span(m, adj, KV);
+  return stage_bytes<T, SPLIT>(span) <= 48 * 1024 ? span : 0;
+}
+
+// Variant selection: a forced variant (autotuning probes) wins, then the
+// autotuned one for (direction, K), then the default (widest vector, staged).
+namespace {
+thread_local bool g_force_on = false;
+thread_local TuneCfg g_force;
+}  // namespace
+
+static bool variant(const DeviceMesh& m, int dir, int K, TuneCfg* out) {
+  if (g_force_on) {
+    *out = g_force;
+    return true;
+  }
+  std::lock_guard<std::mutex> lock(m.tune_mutex);
+  auto it = m.tuned.find(std::make_pair(dir, K));
+  if (it == m.tuned.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+// Tile-staged launch (variant packed == 2): one block per 32-row tile plus
+// gather blocks; its shared memory holds the tile's staged source rows.
+template <bool ADJ>
+static bool launch_tiled(const DeviceMesh& m, const Step3Args<float>& a, cudaStream_t st) {
+  // the tiles update every row: launches without rows to update (the final
+  // observation-only launch of a forward solve) and the zero-state adjoint start
+  // go to the packed kernel
+  if (a.x == nullptr || a.xn == nullptr || a.row_threads == 0 || a.K % 8 || a.K > 256 || !m.fwd.hl ||
+      m.n_tiles == 0)
+    return false;
+  const size_t smem = 128 + (size_t)m.tile_max_slots * a.K * 4;
+  if (smem > 200 * 1024) return false;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(step3t_kernel<8, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
+  TileArgs Tl{m.tile_range_ptr, m.tile_range_src, m.tile_range_cnt, m.tile_range_slot, m.tile_slots,
+              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles};
+  Step3Args<float> A = a;
+  A.hl = ADJ ? m.adj3.hl : m.fwd.hl;
+  const int bdim = kTileRows * (a.K / 8);
+  const int64_t gather_threads = (!ADJ && a.y_out) ? (int64_t)a.n_obs * (a.K / 8) : 0;
+  const int64_t blocks = m.n_tiles + (gather_threads + bdim - 1) / bdim;
+  step3t_kernel<8, ADJ><<<(unsigned)blocks, bdim, smem, st>>>(A, Tl);
+  return true;
+}
+
 template <typename T, int V, bool SPLIT, bool ADJ>
-static void launch_step3(const Step3Args<T>& a, int64_t threads, cudaStream_t st) {
+static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, cudaStream_t st) {
   const int64_t blocks = (threads + 255) / 256;
-  step3_kernel<T, V, SPLIT, ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+  TuneCfg c;  // defaults: packed, unstaged
+  variant(m, ADJ ? 1 : 0, a.K, &c);
+  if constexpr (sizeof(T) == 4 && SPLIT && V == 8) {
+    if (c.packed == 2 && launch_tiled<ADJ>(m, a, st)) return;
+  }
+  if constexpr (sizeof(T) == 4 && SPLIT && (V == 4 || V == 8)) {
+    if (c.packed) {
+      a.hl = (ADJ ? m.adj3.hl : m.fwd.hl);
+      a.order = c.order ? m.row_order : nullptr;
+      const unsigned nb = (unsigned)blocks;
+      if (c.minb == 6) {
+        if (c.chunk == 2)
+          step3f_occ_kernel<V, 2, ADJ><<<nb, 256, 0, st>>>(a);
+        else
+          step3f_occ_kernel<V, 4, ADJ><<<nb, 256, 0, st>>>(a);
+      } else if (c.early) {
+        if (c.chunk == 2)
+          step3f_kernel<V, 2, ADJ, true><<<nb, 256, 0, st>>>(a);
+        else
+          step3f_kernel<V, 4, ADJ, true><<<nb, 256, 0, st>>>(a);
+      } else {
+        if (c.chunk == 2)
+          step3f_kernel<V, 2, ADJ, false><<<nb, 256, 0, st>>>(a);
+        else if (c.chunk == 8 && V == 4)
+          step3f_kernel<V, 8, ADJ, false><<<nb, 256, 0, st>>>(a);
+        else
+          step3f_kernel<V, 4, ADJ, false><<<nb, 256, 0, st>>>(a);
+      }
+      return;
+    }
+  }
+  const bool allow = c.stage != 0;
+  a.stage_cap = allow ? stage_cap_for<T, SPLIT>(m, ADJ, a.K, V) : 0;
+  if (a.stage_cap > 0)
+    step3_kernel<T, V, SPLIT, ADJ, true><<<(unsigned)blocks, 256, stage_bytes<T, SPLIT>(a.stage_cap), st>>>(a);
+  else
+    step3_kernel<T, V, SPLIT, ADJ, false><<<(unsigned)blocks, 256, 0, st>>>(a);
 }
 
 // Launch i (0 <= i <= N_T) of a three-level forward solve: steps 0..N_T-1, then
@@ -192,6 +305,8 @@ Step3Args<T> fwd3_args(const DeviceMesh& m, int K, int V, const T* p0, T* Y, T s
   A.col = m.fwd.col;
   A.hi = static_cast<const T*>(m.fwd.hi);
   A.lo = m.fwd.lo;
+  A.nb = m.row_nb;
+  A.ninj = m.row_ninj;
   A.det_node = m.det_node;
   A.det_w = static_cast<const T*>(m.det_w);
   A.scale = scale;
@@ -234,6 +349,8 @@ Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale
   A.col = m.adj3.col;
   A.hi = static_cast<const T*>(m.adj3.hi);
   A.lo = m.adj3.lo;
+  A.nb = m.row_nb;
+  A.ninj = m.row_ninj;
   A.inj_scale = scale;
   A.scale = T(0);
   A.row_threads = m.N * (int64_t)K / V;
@@ -266,7 +383,7 @@ static pat_status forward3_t(const DeviceMesh& m, const T* p0, int K, T* Y, T sc
   for (int i = 0; i <= m.n_steps; ++i) {
     int64_t threads = 0;
     const Step3Args<T> A = fwd3_args<T>(m, K, V, p0, Y, scale, b, i, &threads);
-    launch_step3<T, V, SPLIT, false>(A, threads, st);
+    launch_step3<T, V, SPLIT, false>(m, A, threads, st);
   }
   prof_end(m, pp, m.n_steps + 1, st);
   return cuda_check(cudaGetLastError(), "forward step launch");
@@ -281,7 +398,7 @@ static pat_status adjoint3_t(const DeviceMesh& m, const T* Yhat, int K, T* out, 
   for (int i = 0; i <= NT; ++i) {
     int64_t threads = 0;
     const Step3Args<T> A = adj3_args<T>(m, K, V, Yhat, scale, b, i, &threads);
-    launch_step3<T, V, SPLIT, true>(A, threads, st);
+    launch_step3<T, V, SPLIT, true>(m, A, threads, st);
   }
   // G^T yhat = M (u_0 - u_1) + M Bt u_1 from the last two transposed states
   const int64_t rt = NK / V;
@@ -293,10 +410,14 @@ static pat_status adjoint3_t(const DeviceMesh& m, const T* Yhat, int K, T* out, 
 
 template <typename T>
 static pat_status forward_disp(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
-  const int V = pick_vec<T>(K, {p0, Y, ws});
+  int V = pick_vec<T>(K, {p0, Y, ws});
   const bool sp = m.split;
+  TuneCfg cfg;
+  variant(m, 0, K, &cfg);
+  V = std::min(V, m.three_level ? cfg.V : 4);
   if (m.three_level) {
     if constexpr (sizeof(T) == 4) {
+      if (V == 8) return sp ? forward3_t<T, 8, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 8, false>(m, p0, K, Y, scale, ws, st);
       if (V == 4) return sp ? forward3_t<T, 4, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 4, false>(m, p0, K, Y, scale, ws, st);
       if (V == 2) return sp ? forward3_t<T, 2, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 2, false>(m, p0, K, Y, scale, ws, st);
       return sp ? forward3_t<T, 1, true>(m, p0, K, Y, scale, ws, st) : forward3_t<T, 1, false>(m, p0, K, Y, scale, ws, st);
@@ -317,10 +438,14 @@ static pat_status forward_disp(const DeviceMesh& m, const T* p0, int K, T* Y, T 
 
 template <typename T>
 static pat_status adjoint_disp(const DeviceMesh& m, const T* Yh, int K, T* out, T scale, T* ws, cudaStream_t st) {
-  const int V = pick_vec<T>(K, {Yh, out, ws});
+  int V = pick_vec<T>(K, {Yh, out, ws});
   const bool sp = m.split;
+  TuneCfg cfg;
+  variant(m, 1, K, &cfg);
+  V = std::min(V, m.three_level ? cfg.V : 4);
   if (m.three_level) {
     if constexpr (sizeof(T) == 4) {
+      if (V == 8) return sp ? adjoint3_t<T, 8, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 8, false>(m, Yh, K, out, scale, ws, st);
       if (V == 4) return sp ? adjoint3_t<T, 4, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 4, false>(m, Yh, K, out, scale, ws, st);
       if (V == 2) return sp ? adjoint3_t<T, 2, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 2, false>(m, Yh, K, out, scale, ws, st);
       return sp ? adjoint3_t<T, 1, true>(m, Yh, K, out, scale, ws, st) : adjoint3_t<T, 1, false>(m, Yh, K, out, scale, ws, st);
@@ -598,6 +723,64 @@ RtoLayout rto_layout(const DeviceMesh& m, int K) {
 
 static inline unsigned nblocks(int64_t n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
 
+// One forward (dir 0: d -> q_d) or transposed (dir 1: r_d -> s) solve of the
+// CGLS loop, replayed from a CUDA graph captured on first use (N_T + 1 or
+// N_T + 2 launches become one graph launch).  Falls back to direct launches
+// when the stream is already being captured or graphs are disabled.
+static pat_status cgls_solve(const DeviceMesh& m, int dir, int K, double sigma, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  auto direct = [&](cudaStream_t s) {
+    return dir == 0 ? forward(m, ws + L.d, K, ws + L.q_d, 1.0 / sigma, ws + L.state, s)
+                    : adjoint(m, ws + L.r_d, K, ws + L.s, 1.0 / sigma, ws + L.state, s);
+  };
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((m.flags & PAT_MESH_NO_GRAPHS) || !m.capture_stream || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return direct(st);
+  }
+  uint64_t sbits;
+  std::memcpy(&sbits, &sigma, 8);
+  const auto key = std::make_tuple(dir, (const void*)ws, K, sbits);
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(m.graph_mutex);
+    auto it = m.graphs.find(key);
+    if (it != m.graphs.end()) exec = (cudaGraphExec_t)it->second;
+  }
+  if (!exec) {
+    // capture on the mesh's private stream (the caller's may be the legacy
+    // default stream, which cannot be captured); the graph then runs on st
+    cudaStream_t cap = (cudaStream_t)m.capture_stream;
+    const bool prof_on = m.prof.on;
+    m.prof.on = false;  // no event records inside the graph
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      m.prof.on = prof_on;
+      cudaGetLastError();
+      return direct(st);
+    }
+    const pat_status s = direct(cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    m.prof.on = prof_on;
+    if (s != PAT_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return s != PAT_OK ? s : cuda_check(e, "graph end capture");
+    }
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    PAT_TRY(cuda_check(e, "graph instantiate"));
+    std::lock_guard<std::mutex> lock(m.graph_mutex);
+    m.graphs[key] = (void*)exec;
+  }
+  const size_t pp = prof_begin(m, dir, st);
+  PAT_TRY(cuda_check(cudaGraphLaunch(exec, st), "graph launch"));
+  prof_end(m, pp, dir == 0 ? m.n_steps + 1 : m.n_steps + (m.three_level ? 2 : 1), st);
+  return PAT_OK;
+}
+
 // CGLS phases around the two wave solves of an iteration (also driven per job
 // by the grouped multi-mesh driver).
 template <typename T>
@@ -676,7 +859,7 @@ static pat_status begin_t(const DeviceMesh& m, const T* y_obs, double sigma, int
   const RtoLayout L = rto_layout(m, K);
   PAT_TRY(begin_pre<T>(m, y_obs, sigma, K, eta, xi, seed, ws, st));
   // s = A^T r, d = s, gamma = ||s||^2 (the transpose lands in s, combined in place)
-  PAT_TRY(adjoint(m, ws + L.r_d, K, ws + L.s, 1.0 / sigma, ws + L.state, st));
+  PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
   return begin_post<T>(m, K, ws, st);
 }
 
@@ -708,10 +891,10 @@ static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter
   }
   for (int it = 0; it < n_iter; ++it) {
     // q = A d: q_d = G d / sigma (forward), q_p = M^{1/2} d (implicit)
-    PAT_TRY(forward(m, ws + L.d, K, ws + L.q_d, 1.0 / sigma, ws + L.state, st));
+    PAT_TRY(cgls_solve(m, 0, K, sigma, ws, st));
     PAT_TRY(iter_mid<T>(m, K, ws, st));
     // s = A^T r = G^T r_d / sigma + M^{1/2} r_p
-    PAT_TRY(adjoint(m, ws + L.r_d, K, ws + L.s, 1.0 / sigma, ws + L.state, st));
+    PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
     PAT_TRY(iter_post<T>(m, K, ws, st));
     if (resid) PAT_TRY(residual_t<T>(m, K, resid + (int64_t)it * K, ws, st));
   }
@@ -771,6 +954,143 @@ template pat_status iter_post<double>(const DeviceMesh&, int, char*, cudaStream_
 
 int vec_width(const DeviceMesh& m, int K, std::initializer_list<const void*> ptrs) {
   return m.prec == PAT_F64 ? pick_vec<double>(K, ptrs) : pick_vec<float>(K, ptrs);
+}
+
+// Autotuning of the three-level step: every variant (V samples per thread,
+// row staging on/off) runs n_probe forward and n_probe transposed steps on
+// zeroed buffers of an RTO workspace, timed with CUDA events; the fastest per
+// direction is kept for (mesh, K).
+template <typename T>
+static pat_status probe_t(const DeviceMesh& m, int K, char* ws, int n_probe, int dir, cudaStream_t st, float* us) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t NK = m.N * (int64_t)K;
+  T* const b[3] = {(T*)(ws + L.state), (T*)(ws + L.state) + NK, (T*)(ws + L.state) + 2 * NK};
+  cudaEvent_t e0, e1;
+  PAT_TRY(cuda_check(cudaEventCreate(&e0), "autotune event"));
+  PAT_TRY(cuda_check(cudaEventCreate(&e1), "autotune event"));
+  const int V = std::min(g_force.V, pick_vec<T>(K, {ws + L.d, ws + L.q_d, ws + L.r_d, ws + L.state}));
+  auto run = [&](bool timed) {
+    if (timed) cudaEventRecord(e0, st);
+    for (int i = 0; i < n_probe; ++i) {
+      int64_t thr = 0;
+      if (dir == 0) {
+        const Step3Args<T> A = fwd3_args<T>(m, K, V, (const T*)(ws + L.d), (T*)(ws + L.q_d), T(1), b, i, &thr);
+        if constexpr (sizeof(T) == 4) {
+          if (m.split) {
+            if (V == 8) launch_step3<T, 8, true, false>(m, A, thr, st);
+            else if (V == 4) launch_step3<T, 4, true, false>(m, A, thr, st);
+            else if (V == 2) launch_step3<T, 2, true, false>(m, A, thr, st);
+            else launch_step3<T, 1, true, false>(m, A, thr, st);
+          } else {
+            if (V == 4) launch_step3<T, 4, false, false>(m, A, thr, st);
+            else if (V == 2) launch_step3<T, 2, false, false>(m, A, thr, st);
+            else launch_step3<T, 1, false, false>(m, A, thr, st);
+          }
+        } else {
+          if (V == 2) launch_step3<T, 2, false, false>(m, A, thr, st);
+          else launch_step3<T, 1, false, false>(m, A, thr, st);
+        }
+      } else {
+        const Step3Args<T> A = adj3_args<T>(m, K, V, (const T*)(ws + L.r_d), T(1), b, i, &thr);
+        if constexpr (sizeof(T) == 4) {
+          if (m.split) {
+            if (V == 8) launch_step3<T, 8, true, true>(m, A, thr, st);
+            else if (V == 4) launch_step3<T, 4, true, true>(m, A, thr, st);
+            else if (V == 2) launch_step3<T, 2, true, true>(m, A, thr, st);
+            else launch_step3<T, 1, true, true>(m, A, thr, st);
+          } else {
+            if (V == 4) launch_step3<T, 4, false, true>(m, A, thr, st);
+            else if (V == 2) launch_step3<T, 2, false, true>(m, A, thr, st);
+            else launch_step3<T, 1, false, true>(m, A, thr, st);
+          }
+        } else {
+          if (V == 2) launch_step3<T, 2, false, true>(m, A, thr, st);
+          else launch_step3<T, 1, false, true>(m, A, thr, st);
+        }
+      }
+    }
+    if (timed) cudaEventRecord(e1, st);
+  };
+  run(false);
+  run(true);
+  pat_status s = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+  float ms = 0.0f;
+  if (!s) s = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "autotune elapsed");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *us = 1e3f * ms / n_probe;
+  return s;
+}
+
+pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_entry* table, int* n_entries,
+                    cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  n_probe = std::max(2, std::min(n_probe, m.n_steps));
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.d, 0, L.q_d - L.d, st), "autotune memset"));
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.q_d, 0, L.r_p - L.q_d, st), "autotune memset"));
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.r_d, 0, L.q_d - L.r_d, st), "autotune memset"));
+  PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.state, 0, L.gamma - L.state, st), "autotune memset"));
+  const int vmax = m.prec == PAT_F64 ? 2 : 8;
+  int n = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    TuneCfg best;
+    float best_us = 1e30f;
+    for (int V = vmax; V >= 1; V /= 2) {
+      if (K % V) continue;
+      for (int variant_id = 0; variant_id < 12; ++variant_id) {
+        // packed f32x2 kernels (FP32 split, V = 4 or 8):
+        //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
+        //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
+        // generic kernels: 7 row metadata staged in shared memory; 8 read directly
+        // 9: tile-staged kernel (source rows of 32-row tiles staged by bulk copies);
+        // 10, 11: packed, chunks of 2 / 4, rows processed in Z-order
+        const int packed = (variant_id <= 6 || variant_id >= 10) ? 1 : (variant_id == 9 ? 2 : 0),
+                  stage = variant_id == 7;
+        const int chunk = (variant_id == 0 || variant_id == 3 || variant_id == 5 || variant_id == 10) ? 2
+                          : (variant_id == 2 ? 8 : 4);
+        const int zorder = variant_id >= 10 ? 1 : 0;
+        const int minb = (variant_id == 5 || variant_id == 6) ? 6 : 1;
+        const int early = (variant_id == 3 || variant_id == 4) ? 1 : 0;
+        if (minb > 1 && V == 8) continue;  // would spill
+        if (packed == 1 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8))) continue;
+        if (packed == 2 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 256 && m.n_tiles > 0)) continue;
+        if (packed == 1 && chunk == 8 && V == 8) continue;
+        if (!packed && V == 8) continue;
+        if (stage && K / V < 2) continue;
+        g_force_on = true;
+        g_force.V = V;
+        g_force.stage = stage;
+        g_force.packed = packed;
+        g_force.chunk = chunk;
+        g_force.minb = minb;
+        g_force.early = early;
+        g_force.order = zorder;
+        float us = 0.0f;
+        pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
+                                         : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
+        g_force_on = false;
+        if (s) return s;
+        if (table && n < 64)
+          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, (double)us};
+        ++n;
+        if (us < best_us) {
+          best_us = us;
+          best = g_force;
+        }
+      }
+    }
+    std::lock_guard<std::mutex> lock(m.tune_mutex);
+    m.tuned[std::make_pair(dir, K)] = best;
+  }
+  {
+    // captured solves still hold the previous variant
+    std::lock_guard<std::mutex> lock(m.graph_mutex);
+    for (auto& kv : m.graphs)
+      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+    m.graphs.clear();
+  }
+  if (n_entries) *n_entries = n;
+  return PAT_OK;
 }
 
 pat_status draw_normals(uint64_t seed, int stream_id, int64_t n_elem, int K, double* out, cudaStream_t st) {

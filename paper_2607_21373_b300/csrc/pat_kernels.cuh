@@ -253,6 +253,11 @@ struct Step3Args {
   int32_t n_obs;
   int64_t row_threads;
   int32_t prev_mode;  // 0: xp is a buffer; 1: xp equals x (zero velocity); 2: xp is zero
+  int32_t stage_cap;  // shared-memory entries per block (STAGE kernels)
+  const float2* __restrict__ hl;     // (hi, lo) pairs of FP32 split coefficients
+  const int32_t* __restrict__ order; // processing order of the rows (nullptr: 0, 1, 2, ...)
+  const uint8_t* __restrict__ nb;    // [N] boundary entries per row
+  const uint8_t* __restrict__ ninj;  // [N] sensor entries per row (adjoint rows)
   const int32_t* __restrict__ ptr;
   const uint32_t* __restrict__ col;
   const T* __restrict__ hi;
@@ -271,104 +276,160 @@ struct Step3Args {
   T scale;
 };
 
-// Rows are walked in chunks of CH entries: the chunk's columns and
-// coefficients are loaded first, then all CH neighbour vectors, then the FMAs,
-// so each thread keeps CH independent 16-byte loads in flight instead of one
-// dependent index->value chain per entry.
-constexpr int kChunk = 8;
+// Row metadata staging.  With STAGE, the block first copies the column /
+// coefficient entries of all rows it covers (a contiguous CSR range) into
+// shared memory with coalesced loads, so the K/V threads of a row read them
+// from shared memory instead of each issuing its own global loads.  The host
+// guarantees that the staged range fits A.stage_cap entries.
+//
+// Every row lists its stiffness entries, then its boundary entries (count
+// nb[row]), then (adjoint rows) its sensor entries (count ninj[row]).  All
+// stiffness and boundary entries multiply x_j; the boundary entries, which act
+// on w_j = x_j - xp_j, then get the xp_j part subtracted in a short second
+// loop over the boundary rows only.  The main loop has no per-entry branches.
+template <typename T, bool SPLIT>
+struct CoefT;
+template <>
+struct CoefT<float, true> {
+  using type = float2;
+};
+template <>
+struct CoefT<float, false> {
+  using type = float;
+};
+template <>
+struct CoefT<double, false> {
+  using type = double;
+};
 
-template <typename T, int V, bool SPLIT, bool ADJ>
-__device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t t) {
+template <typename T, bool SPLIT>
+__device__ __forceinline__ typename CoefT<T, SPLIT>::type coef_ld(const T* hi, const float* lo, int64_t e) {
+  if constexpr (SPLIT) {
+    return make_float2(hi[e], lo[e]);
+  } else {
+    return hi[e];
+  }
+}
+
+template <typename T, int V, bool SPLIT>
+__device__ __forceinline__ void coef_fma(const typename CoefT<T, SPLIT>::type c, const Pack<T, V>& x, T (&acc)[V],
+                                         T (&accl)[V]) {
+  if constexpr (SPLIT) {
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+      acc[r] = fma(c.x, x.v[r], acc[r]);
+      accl[r] = fma(c.y, x.v[r], accl[r]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < V; ++r) acc[r] = fma(c, x.v[r], acc[r]);
+  }
+}
+
+template <typename T, int V, bool SPLIT, bool ADJ, bool STAGE>
+__device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t tb0, unsigned char* smem) {
+  using C = typename CoefT<T, SPLIT>::type;
   const int KV = A.K / V;
+  const int64_t t = tb0 + threadIdx.x;
+  const uint32_t* mcol = A.col;
+  const C* mval = nullptr;  // staged coefficients
+  int64_t base = 0;
+  if constexpr (STAGE) {
+    if (tb0 < A.row_threads) {  // uniform over the block
+      C* s_val = reinterpret_cast<C*>(smem);
+      uint32_t* s_col = reinterpret_cast<uint32_t*>(smem + ((size_t)A.stage_cap * sizeof(C) + 15) / 16 * 16);
+      const int64_t r0 = tb0 / KV;
+      const int64_t tl = (tb0 + (int64_t)blockDim.x < A.row_threads ? tb0 + (int64_t)blockDim.x : A.row_threads) - 1;
+      const int64_t r1 = tl / KV;
+      base = A.ptr[r0];
+      const int n = (int)(A.ptr[r1 + 1] - base);
+      for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        s_col[q] = A.col[base + q];
+        s_val[q] = coef_ld<T, SPLIT>(A.hi, A.lo, base + q);
+      }
+      __syncthreads();
+      mcol = s_col;
+      mval = s_val;
+    }
+  }
   if (t < A.row_threads) {
     const int64_t row = t / KV;
     const int kv = (int)(t - row * KV);
     const int64_t off = row * A.K + (int64_t)kv * V;
-    T acc[V], accl[V], src[V];
+    T acc[V], accl[V];
 #pragma unroll
-    for (int q = 0; q < V; ++q) acc[q] = accl[q] = src[q] = T(0);
-    const bool have_x = A.x != nullptr;
-    const bool xp_buf = A.prev_mode == 0;
-    const int e0 = A.ptr[row], e1 = A.ptr[row + 1];
-    if (have_x) {
-      for (int e = e0; e < e1; e += kChunk) {
-        uint32_t c[kChunk];
-        T h[kChunk];
-        float l[kChunk];
+    for (int q = 0; q < V; ++q) acc[q] = accl[q] = T(0);
+    const int e0 = (int)(A.ptr[row] - base), e1 = (int)(A.ptr[row + 1] - base);
+    const int ni = ADJ ? (int)A.ninj[row] : 0;
+    const int eA = e1 - ni;             // end of the stiffness + boundary entries
+    const int eB = eA - (int)A.nb[row];  // first boundary entry
+    const uint32_t Ku = (uint32_t)A.K;
+    auto coef = [&](int e) -> C {
+      if constexpr (STAGE) {
+        return mval[e];
+      } else {
+        return coef_ld<T, SPLIT>(A.hi, A.lo, e);
+      }
+    };
+    if (A.x) {
+      const T* xk = A.x + (int64_t)kv * V;
+#pragma unroll 4
+      for (int e = e0; e < eA; ++e) {
+        const uint32_t j = mcol[e] & kIdxMask;
+        const Pack<T, V> xj = ld<T, V>(xk + j * Ku);
+        coef_fma<T, V, SPLIT>(coef(e), xj, acc, accl);
+      }
+      if (eB < eA && A.prev_mode != 2) {
+        // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
+        // (same accumulation order as the packed kernel, so variants agree bitwise)
+        const T* pk = (A.prev_mode == 0 ? A.xp : A.x) + (int64_t)kv * V;
+        for (int e = eB; e < eA; ++e) {
+          const uint32_t j = mcol[e] & kIdxMask;
+          const Pack<T, V> pj = ld<T, V>(pk + j * Ku);
+          Pack<T, V> neg;
 #pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-          const bool in = e + q < e1;
-          c[q] = in ? A.col[e + q] : kTagInj;
-          h[q] = in ? A.hi[e + q] : T(0);
-          if constexpr (SPLIT) l[q] = in ? A.lo[e + q] : 0.0f;
-        }
-        Pack<T, V> xv[kChunk];
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-          if (!(c[q] & kTagInj)) {
-            xv[q] = ld<T, V>(A.x + (int64_t)(c[q] & kIdxMask) * A.K + (int64_t)kv * V);
-          } else {
-#pragma unroll
-            for (int r = 0; r < V; ++r) xv[q].v[r] = T(0);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-          if ((c[q] & (kTagB | kTagInj)) == kTagB) {
-            // the boundary term acts on w_j = x_j - xp_j
-            if (xp_buf) {
-              const Pack<T, V> pj = ld<T, V>(A.xp + (int64_t)(c[q] & kIdxMask) * A.K + (int64_t)kv * V);
-#pragma unroll
-              for (int r = 0; r < V; ++r) xv[q].v[r] -= pj.v[r];
-            } else if (A.prev_mode == 1) {
-#pragma unroll
-              for (int r = 0; r < V; ++r) xv[q].v[r] = T(0);
-            }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-#pragma unroll
-          for (int r = 0; r < V; ++r) acc[r] = fma(h[q], xv[q].v[r], acc[r]);
-          if constexpr (SPLIT) {
-#pragma unroll
-            for (int r = 0; r < V; ++r) accl[r] = fma((T)l[q], xv[q].v[r], accl[r]);
-          }
+          for (int q = 0; q < V; ++q) neg.v[q] = -pj.v[q];
+          coef_fma<T, V, SPLIT>(coef(e), neg, acc, accl);
         }
       }
     }
+    T src[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) src[q] = T(0);
     if constexpr (ADJ) {
-      // sensor entries sit at the end of the row
-      for (int e = e1 - 1; e >= e0; --e) {
-        const uint32_t c = A.col[e];
-        if (!(c & kTagInj)) break;
-        const int64_t j = (int64_t)(c & kIdxMask);
-        const T h = A.hi[e];
-        Pack<T, V> ys;
-#pragma unroll
-        for (int q = 0; q < V; ++q) ys.v[q] = T(0);
+      for (int e = eA; e < e1; ++e) {
+        const uint32_t j = mcol[e] & kIdxMask;
+        T h;
+        if constexpr (STAGE) {
+          if constexpr (SPLIT) {
+            h = mval[e].x;
+          } else {
+            h = mval[e];
+          }
+        } else {
+          h = A.hi[e];
+        }
+        // same accumulation order as the packed kernels (variants agree bitwise)
         if (A.ya) {
-          const Pack<T, V> y = ld<T, V>(A.ya + j * A.K + (int64_t)kv * V);
+          const Pack<T, V> y = ld<T, V>(A.ya + (int64_t)j * A.K + (int64_t)kv * V);
 #pragma unroll
-          for (int q = 0; q < V; ++q) ys.v[q] += y.v[q];
+          for (int q = 0; q < V; ++q) src[q] = fma(h, y.v[q], src[q]);
         }
         if (A.yb) {
-          const Pack<T, V> y = ld<T, V>(A.yb + j * A.K + (int64_t)kv * V);
+          const Pack<T, V> y = ld<T, V>(A.yb + (int64_t)j * A.K + (int64_t)kv * V);
 #pragma unroll
-          for (int q = 0; q < V; ++q) ys.v[q] += y.v[q];
+          for (int q = 0; q < V; ++q) src[q] = fma(h, y.v[q], src[q]);
         }
-#pragma unroll
-        for (int q = 0; q < V; ++q) src[q] = fma(h, ys.v[q], src[q]);
       }
     }
     Pack<T, V> xi, xpi, xo;
-    if (have_x) {
+    if (A.x) {
       xi = ld<T, V>(A.x + off);
     } else {
 #pragma unroll
       for (int q = 0; q < V; ++q) xi.v[q] = T(0);
     }
-    if (xp_buf) {
+    if (A.prev_mode == 0) {
       xpi = ld<T, V>(A.xp + off);
     } else {
 #pragma unroll
@@ -411,9 +472,16 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
   st<T, V>(A.y_out + (int64_t)d * A.K + (int64_t)kv * V, y);
 }
 
-template <typename T, int V, bool SPLIT, bool ADJ>
+// bytes of dynamic shared memory for stage_cap entries
+template <typename T, bool SPLIT>
+__host__ __device__ constexpr size_t stage_bytes(int cap) {
+  return ((size_t)cap * (SPLIT ? 8 : sizeof(T)) + 15) / 16 * 16 + (size_t)cap * 4;
+}
+
+template <typename T, int V, bool SPLIT, bool ADJ, bool STAGE>
 __global__ void __launch_bounds__(256) step3_kernel(const Step3Args<T> A) {
-  step3_body<T, V, SPLIT, ADJ>(A, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  extern __shared__ __align__(16) unsigned char smem[];
+  step3_body<T, V, SPLIT, ADJ, STAGE>(A, (int64_t)blockIdx.x * blockDim.x, smem);
 }
 
 // Several meshes advanced by one launch: block b belongs to the group member g
@@ -426,13 +494,229 @@ struct Step3Group {
   Step3Args<T> a[kMaxGroup];
 };
 
-template <typename T, int V, bool SPLIT, bool ADJ>
+template <typename T, int V, bool SPLIT, bool ADJ, bool STAGE>
 __global__ void __launch_bounds__(256) step3_group_kernel(const __grid_constant__ Step3Group<T> G) {
+  extern __shared__ __align__(16) unsigned char smem[];
   int g = 0;
   while (g + 1 < G.n && (int64_t)blockIdx.x >= G.block_off[g + 1]) ++g;
-  const int64_t t = ((int64_t)blockIdx.x - G.block_off[g]) * blockDim.x + threadIdx.x;
-  step3_body<T, V, SPLIT, ADJ>(G.a[g], t);
+  step3_body<T, V, SPLIT, ADJ, STAGE>(G.a[g], ((int64_t)blockIdx.x - G.block_off[g]) * blockDim.x, smem);
 }
+
+// ---------------------------------------------------------------------------
+// Packed fast path of the three-level step for FP32 fields with hi+lo
+// coefficients: V = 4 or 8 samples per thread held as float pairs, every
+// product-accumulate a packed fma.rn.f32x2 (two samples per instruction), the
+// row walked in predicated chunks so that a row's neighbour loads are issued
+// together, the (hi, lo) coefficient pair read as one 8-byte load.
+// ---------------------------------------------------------------------------
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 dup2(float c) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(c));
+  return r;
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float2 unpack2(u64 v) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(v));
+  return f;
+}
+template <int P>
+__device__ __forceinline__ void ld_pairs(const float* p, u64 (&out)[P]) {
+  if constexpr (P == 2) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+    out[0] = v.x;
+    out[1] = v.y;
+  } else {
+    const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(p + 4);
+    out[0] = v0.x;
+    out[1] = v0.y;
+    out[2] = v1.x;
+    out[3] = v1.y;
+  }
+}
+
+template <int V, int CH, bool ADJ, bool EARLY>
+__device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int64_t tb0) {
+  constexpr int P = V / 2;  // CH = entries per chunk
+  const int KV = A.K / V;
+  const int64_t t = tb0 + threadIdx.x;
+  if (t >= A.row_threads) {
+    // sensor gather of the input state (forward launches only)
+    if (A.y_out == nullptr) return;
+    const int64_t g = t - A.row_threads;
+    if (g >= (int64_t)A.n_obs * KV) return;
+    const int d = (int)(g / KV);
+    const int kv = (int)(g - (int64_t)d * KV);
+    float acc[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[q] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int64_t node = A.det_node[3 * d + s];
+      const float wt = A.det_w[3 * d + s];
+      const Pack<float, V> a = ld<float, V>(A.x + node * A.K + (int64_t)kv * V);
+      if (A.prev_mode == 0) {
+        const Pack<float, V> b = ld<float, V>(A.xp + node * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = fmaf(wt, 0.5f * (a.v[q] + b.v[q]), acc[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) acc[q] = fmaf(wt, a.v[q], acc[q]);
+      }
+    }
+    Pack<float, V> y;
+#pragma unroll
+    for (int q = 0; q < V; ++q) y.v[q] = A.scale * acc[q];
+    st<float, V>(A.y_out + (int64_t)d * A.K + (int64_t)kv * V, y);
+    return;
+  }
+  const int64_t rowi = t / KV;
+  const int kv = (int)(t - rowi * KV);
+  // rows are independent within a step, so they may be processed in any order;
+  // a spatially local order (Z-order of the nodes) keeps a block's neighbour
+  // rows in its SM's L1
+  const int64_t row = A.order ? (int64_t)A.order[rowi] : rowi;
+  const int64_t off = row * A.K + (int64_t)kv * V;
+  // EARLY: the node's own x and xp are loaded before the row walk so that their
+  // latency overlaps the neighbour loads (more registers held across the walk)
+  Pack<float, V> xi, xpi;
+  auto load_own = [&]() {
+    if (A.x) {
+      xi = ld<float, V>(A.x + off);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
+    }
+    if (A.prev_mode == 0) {
+      xpi = ld<float, V>(A.xp + off);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+    }
+  };
+  if constexpr (EARLY) load_own();
+  const int e0 = A.ptr[row], e1 = A.ptr[row + 1];
+  const int ni = ADJ ? (int)A.ninj[row] : 0;
+  const int eA = e1 - ni;
+  const int eB = eA - (int)A.nb[row];
+  const uint32_t Ku = (uint32_t)A.K;
+  u64 acc[P], accl[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
+  if (A.x) {
+    const float* xk = A.x + (int64_t)kv * V;
+    // software pipeline: the next chunk's columns and coefficients are loaded
+    // while the current chunk's neighbour loads are in flight
+    uint32_t j[CH];
+    float2 c[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const bool in = e0 + q < eA;
+      j[q] = in ? (A.col[e0 + q] & kIdxMask) : 0u;
+      c[q] = in ? A.hl[e0 + q] : make_float2(0.0f, 0.0f);
+    }
+    for (int e = e0; e < eA; e += CH) {
+      u64 x[CH][P];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        if (e + q < eA) {
+          ld_pairs<P>(xk + j[q] * Ku, x[q]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+        }
+      }
+      float2 cc[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        cc[q] = c[q];
+        const int en = e + CH + q;
+        const bool in = en < eA;
+        j[q] = in ? (A.col[en] & kIdxMask) : 0u;
+        c[q] = in ? A.hl[en] : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const u64 ch = dup2(cc[q].x), cl = dup2(cc[q].y);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          acc[p] = ffma2(ch, x[q][p], acc[p]);
+          accl[p] = ffma2(cl, x[q][p], accl[p]);
+        }
+      }
+    }
+    if (eB < eA && A.prev_mode != 2) {
+      // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
+      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + (int64_t)kv * V;
+      for (int e = eB; e < eA; ++e) {
+        const float2 c = A.hl[e];
+        u64 x[P];
+        ld_pairs<P>(pk + (A.col[e] & kIdxMask) * Ku, x);
+        const u64 ch = dup2(-c.x), cl = dup2(-c.y);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          acc[p] = ffma2(ch, x[p], acc[p]);
+          accl[p] = ffma2(cl, x[p], accl[p]);
+        }
+      }
+    }
+  }
+  float src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = eA; e < e1; ++e) {
+      const int64_t j = (int64_t)(A.col[e] & kIdxMask);
+      const float h = A.hl[e].x;
+      if (A.ya) {
+        const Pack<float, V> y = ld<float, V>(A.ya + j * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(h, y.v[q], src[q]);
+      }
+      if (A.yb) {
+        const Pack<float, V> y = ld<float, V>(A.yb + j * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(h, y.v[q], src[q]);
+      }
+    }
+  }
+  if constexpr (!EARLY) load_own();
+  Pack<float, V> xo;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+    const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+    xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+    xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+  }
+  st<float, V>(A.xn + off, xo);
+}
+
+template <int V, int CH, bool ADJ, bool EARLY>
+__global__ void __launch_bounds__(256) step3f_kernel(const Step3Args<float> A) {
+  step3f_body<V, CH, ADJ, EARLY>(A, (int64_t)blockIdx.x * blockDim.x);
+}
+
+// the same with at least 6 resident blocks per SM asked of the compiler (<= 40 registers)
+template <int V, int CH, bool ADJ>
+__global__ void __launch_bounds__(256, 6) step3f_occ_kernel(const Step3Args<float> A) {
+  step3f_body<V, CH, ADJ, false>(A, (int64_t)blockIdx.x * blockDim.x);
+}
+
+template <int V, int CH, bool ADJ>
+__global__ void __launch_bounds__(256) step3f_group_kernel(const __grid_constant__ Step3Group<float> G) {
+  int g = 0;
+  while (g + 1 < G.n && (int64_t)blockIdx.x >= G.block_off[g + 1]) ++g;
+  step3f_body<V, CH, ADJ, false>(G.a[g], ((int64_t)blockIdx.x - G.block_off[g]) * blockDim.x);
+}
+
 
 // G^T yhat = M (u_1 - u_2) + M Bt u_2 from the last two transposed states
 // (B entries of the forward rows carry Bt = dt B_ij / M_i).

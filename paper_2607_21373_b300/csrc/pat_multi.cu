@@ -14,19 +14,41 @@
 namespace pat {
 
 template <typename T, int V, bool SPLIT, bool ADJ>
-static void launch_group(const std::vector<Step3Args<T>>& a, const std::vector<int64_t>& thr, cudaStream_t st) {
+static void launch_group(const std::vector<const DeviceMesh*>& ms, const std::vector<Step3Args<T>>& a,
+                         const std::vector<int64_t>& thr, cudaStream_t st) {
   for (size_t base = 0; base < a.size(); base += kMaxGroup) {
     Step3Group<T> G{};
     G.n = (int)std::min<size_t>(kMaxGroup, a.size() - base);
     int64_t off = 0;
+    int cap = 0;
+    bool stage = true;
     for (int g = 0; g < G.n; ++g) {
       G.block_off[g] = off;
       G.a[g] = a[base + g];
+      const int KV = G.a[g].K / V;
+      const int span = KV >= 2 ? stage_span(*ms[base + g], ADJ, KV) : 0;
+      G.a[g].stage_cap = span;
+      cap = std::max(cap, span);
+      stage = stage && KV >= 2;
       off += (thr[base + g] + 255) / 256;
     }
     G.block_off[G.n] = off;
     for (int g = G.n + 1; g <= kMaxGroup; ++g) G.block_off[g] = off;
-    if (off > 0) step3_group_kernel<T, V, SPLIT, ADJ><<<(unsigned)off, 256, 0, st>>>(G);
+    const size_t smem = stage_bytes<T, SPLIT>(cap);
+    if (off == 0) continue;
+    if constexpr (sizeof(T) == 4 && SPLIT && (V == 4 || V == 8)) {
+      // packed f32x2 kernel (the default variant of the single-mesh launches)
+      for (int g = 0; g < G.n; ++g) G.a[g].hl = ADJ ? ms[base + g]->adj3.hl : ms[base + g]->fwd.hl;
+      step3f_group_kernel<V, 4, ADJ><<<(unsigned)off, 256, 0, st>>>(G);
+      continue;
+    }
+    if (stage && smem <= 48 * 1024) {
+      // every member addresses the block's shared memory with the common capacity
+      for (int g = 0; g < G.n; ++g) G.a[g].stage_cap = cap;
+      step3_group_kernel<T, V, SPLIT, ADJ, true><<<(unsigned)off, 256, smem, st>>>(G);
+    } else {
+      step3_group_kernel<T, V, SPLIT, ADJ, false><<<(unsigned)off, 256, 0, st>>>(G);
+    }
   }
 }
 
@@ -42,16 +64,18 @@ static void grouped_forward(const std::vector<Job>& jobs, int max_nt, cudaStream
   for (int i = 0; i <= max_nt; ++i) {
     std::vector<Step3Args<T>> a;
     std::vector<int64_t> thr;
+    std::vector<const DeviceMesh*> ms;
     for (const Job& j : jobs) {
       if (i > j.m->n_steps) continue;
       const RtoLayout L = rto_layout(*j.m, j.K);
       T* const b[3] = {state_buf<T>(j, 0), state_buf<T>(j, 1), state_buf<T>(j, 2)};
       int64_t t = 0;
+      ms.push_back(j.m);
       a.push_back(fwd3_args<T>(*j.m, j.K, V, (const T*)(j.ws + L.d), (T*)(j.ws + L.q_d), (T)(1.0 / j.sigma), b, i,
                                &t));
       thr.push_back(t);
     }
-    launch_group<T, V, SPLIT, false>(a, thr, st);
+    launch_group<T, V, SPLIT, false>(ms, a, thr, st);
   }
 }
 
@@ -61,15 +85,17 @@ static void grouped_adjoint(const std::vector<Job>& jobs, int max_nt, cudaStream
   for (int i = 0; i <= max_nt; ++i) {
     std::vector<Step3Args<T>> a;
     std::vector<int64_t> thr;
+    std::vector<const DeviceMesh*> ms;
     for (const Job& j : jobs) {
       if (i > j.m->n_steps) continue;
       const RtoLayout L = rto_layout(*j.m, j.K);
       T* const b[3] = {state_buf<T>(j, 0), state_buf<T>(j, 1), state_buf<T>(j, 2)};
       int64_t t = 0;
+      ms.push_back(j.m);
       a.push_back(adj3_args<T>(*j.m, j.K, V, (const T*)(j.ws + L.r_d), (T)(1.0 / j.sigma), b, i, &t));
       thr.push_back(t);
     }
-    launch_group<T, V, SPLIT, true>(a, thr, st);
+    launch_group<T, V, SPLIT, true>(ms, a, thr, st);
   }
   for (const Job& j : jobs) {
     const DeviceMesh& m = *j.m;

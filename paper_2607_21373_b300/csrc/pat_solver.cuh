@@ -53,6 +53,9 @@ pat_status iter_mid(const DeviceMesh& m, int K, char* ws, cudaStream_t st);
 template <typename T>
 pat_status iter_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st);
 int vec_width(const DeviceMesh& m, int K, std::initializer_list<const void*> ptrs);
+int stage_span(const DeviceMesh& m, bool adj, int KV);
+pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_entry* table, int* n_entries,
+                    cudaStream_t st);
 
 // Grouped RTO over several meshes (pat_multi.cu): one RTO problem per job.
 struct Job {

@@ -1,0 +1,221 @@
+// Tile-staged three-level step for K-stacked FP32 fields (K a multiple of 8).
+//
+// A block owns a tile of R = 32 consecutive rows.  Before it computes, the rows
+// of x_s that its stiffness/boundary entries read -- the union of the tile's
+// neighbourhoods, precomputed on the host as a few contiguous row ranges --
+// are copied global -> shared memory by asynchronous bulk copies
+// (cp.async.bulk with mbarrier completion), so the many neighbour reads of
+// the tile hit shared memory and the memory system sees a handful of large
+// contiguous transfers per tile instead of one 16-32 byte load per thread
+// per entry.  Column indices are replaced by 16-bit shared-memory slots.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pat_kernels.cuh"
+
+namespace pat {
+
+constexpr int kTileRows = 32;
+
+struct TileArgs {
+  const int32_t* __restrict__ range_ptr;  // [T+1] into the range arrays
+  const int32_t* __restrict__ range_src;  // first source row of a range
+  const int32_t* __restrict__ range_cnt;  // rows in a range
+  const int32_t* __restrict__ range_slot; // first shared-memory slot of a range
+  const int32_t* __restrict__ tile_slots; // [T] staged rows per tile
+  const uint16_t* __restrict__ slot;      // per CSR entry: shared-memory slot of its source row
+  int32_t* status;                        // device status word (PAT_ETIMEOUT on a stuck copy)
+  int32_t n_tiles;                        // blocks beyond the tiles gather the sensor observations
+};
+
+// observation of the input state by thread g of the gather blocks
+template <int V>
+__device__ __forceinline__ void gather_obs(const Step3Args<float>& A, int64_t g) {
+  const int KV = A.K / V;
+  if (A.y_out == nullptr || g >= (int64_t)A.n_obs * KV) return;
+  const int d = (int)(g / KV);
+  const int kv = (int)(g - (int64_t)d * KV);
+  float acc[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) acc[q] = 0.0f;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const int64_t node = A.det_node[3 * d + s];
+    const float wt = A.det_w[3 * d + s];
+    const Pack<float, V> a = ld<float, V>(A.x + node * A.K + (int64_t)kv * V);
+    if (A.prev_mode == 0) {
+      const Pack<float, V> b = ld<float, V>(A.xp + node * A.K + (int64_t)kv * V);
+#pragma unroll
+      for (int q = 0; q < V; ++q) acc[q] = fmaf(wt, 0.5f * (a.v[q] + b.v[q]), acc[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) acc[q] = fmaf(wt, a.v[q], acc[q]);
+    }
+  }
+  Pack<float, V> y;
+#pragma unroll
+  for (int q = 0; q < V; ++q) y.v[q] = A.scale * acc[q];
+  st<float, V>(A.y_out + (int64_t)d * A.K + (int64_t)kv * V, y);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Bounded wait for phase 0 of an mbarrier: false once `cycles` SM clock cycles
+// have passed without completion.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int V, bool ADJ>
+__global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, const TileArgs Tl) {
+  static_assert(V == 8, "tile kernel handles 8 samples per thread");
+  constexpr int P = V / 2;
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tile_smem);
+  float* rows = reinterpret_cast<float*>(tile_smem + 128);
+  const int KV = A.K / V;
+  const int tile = blockIdx.x;
+  if (tile >= Tl.n_tiles) {
+    gather_obs<V>(A, (int64_t)(tile - Tl.n_tiles) * blockDim.x + threadIdx.x);
+    return;
+  }
+  if (A.xn == nullptr || A.row_threads == 0) return;  // no rows to update (the host never launches this)
+  const int64_t r0 = (int64_t)tile * kTileRows;
+  const uint32_t bar_s = smem_u32(bar);
+  const size_t row_bytes = (size_t)A.K * 4;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int q0 = Tl.range_ptr[tile], q1 = Tl.range_ptr[tile + 1];
+    const uint32_t bytes = (uint32_t)((size_t)Tl.tile_slots[tile] * row_bytes);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(bytes) : "memory");
+    for (int q = q0; q < q1; ++q) {
+      const float* src = A.x + (int64_t)Tl.range_src[q] * A.K;
+      const uint32_t dst = smem_u32(rows + (size_t)Tl.range_slot[q] * A.K);
+      const uint32_t n = (uint32_t)((size_t)Tl.range_cnt[q] * row_bytes);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+          "l"(src), "r"(n), "r"(bar_s)
+          : "memory");
+    }
+  }
+  const int lr = threadIdx.x / KV;  // row within the tile
+  const int kv = threadIdx.x - lr * KV;
+  const int64_t row = r0 + lr;
+  const bool active = row < A.N;
+  const int64_t off = row * A.K + (int64_t)kv * V;
+  // the node's previous value comes from global memory while the copies run
+  Pack<float, V> xpi;
+  if (active && A.prev_mode == 0) xpi = ld<float, V>(A.xp + off);
+  // about two seconds at 2 GHz: far beyond any copy, short enough to report a stuck one
+  constexpr long long kWait = 4000000000ll;
+  if (!mbar_wait(bar_s, kWait)) {
+    atomicExch(Tl.status, (int)PAT_ETIMEOUT);
+    mbar_wait(bar_s, kWait);  // let the copies land before the block's memory is released
+    return;
+  }
+  if (!active) return;
+  const int e0 = A.ptr[row], e1 = A.ptr[row + 1];
+  const int ni = ADJ ? (int)A.ninj[row] : 0;
+  const int eA = e1 - ni;
+  const int eB = eA - (int)A.nb[row];
+  u64 acc[P], accl[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
+  const float* sk = rows + kv * V;
+#pragma unroll 4
+  for (int e = e0; e < eA; ++e) {
+    const float2 c = A.hl[e];
+    const float* sp = sk + (size_t)Tl.slot[e] * A.K;
+    const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sp);
+    const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sp + 4);
+    const u64 ch = dup2(c.x), cl = dup2(c.y);
+    acc[0] = ffma2(ch, v0.x, acc[0]);
+    accl[0] = ffma2(cl, v0.x, accl[0]);
+    acc[1] = ffma2(ch, v0.y, acc[1]);
+    accl[1] = ffma2(cl, v0.y, accl[1]);
+    acc[2] = ffma2(ch, v1.x, acc[2]);
+    accl[2] = ffma2(cl, v1.x, accl[2]);
+    acc[3] = ffma2(ch, v1.y, acc[3]);
+    accl[3] = ffma2(cl, v1.y, accl[3]);
+  }
+  const uint32_t Ku = (uint32_t)A.K;
+  if (eB < eA && A.prev_mode != 2) {
+    // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
+    for (int e = eB; e < eA; ++e) {
+      const float2 c = A.hl[e];
+      u64 x[P];
+      if (A.prev_mode == 0) {
+        ld_pairs<P>(A.xp + (int64_t)kv * V + (A.col[e] & kIdxMask) * Ku, x);
+      } else {
+        const float* sp = sk + (size_t)Tl.slot[e] * A.K;  // xp = x
+        const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sp);
+        const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sp + 4);
+        x[0] = v0.x;
+        x[1] = v0.y;
+        x[2] = v1.x;
+        x[3] = v1.y;
+      }
+      const u64 ch = dup2(-c.x), cl = dup2(-c.y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        acc[p] = ffma2(ch, x[p], acc[p]);
+        accl[p] = ffma2(cl, x[p], accl[p]);
+      }
+    }
+  }
+  float src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = eA; e < e1; ++e) {
+      const int64_t j = (int64_t)(A.col[e] & kIdxMask);
+      const float h = A.hl[e].x;
+      if (A.ya) {
+        const Pack<float, V> y = ld<float, V>(A.ya + j * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(h, y.v[q], src[q]);
+      }
+      if (A.yb) {
+        const Pack<float, V> y = ld<float, V>(A.yb + j * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(h, y.v[q], src[q]);
+      }
+    }
+  }
+  // own x from the staged rows (the row itself is one of its entries' sources)
+  const Pack<float, V> xi = ld<float, V>(A.x + off);
+  if (A.prev_mode != 0) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+  }
+  Pack<float, V> xo;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+    const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+    xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+    xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+  }
+  st<float, V>(A.xn + off, xo);
+}
+
+}  // namespace pat
