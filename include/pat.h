@@ -122,6 +122,9 @@ typedef struct {
   int32_t n_obs, n_steps, prec;
   double dt;
   double operator_bytes; /* bytes of the forward-step operator read per step   */
+  int32_t tile_rows;     /* rows per tile of the tile-staged kernel             */
+  int32_t tile_max_staged; /* most source rows any tile stages in shared memory */
+  double tile_mean_staged; /* mean source rows staged per tile                   */
 } pat_mesh_info;
 pat_status pat_mesh_query(const pat_mesh* mesh, pat_mesh_info* info);
 
@@ -318,7 +321,8 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
 
 /* Use the given variant (fields as in pat_tune_entry; packed 2 = the
  * tile-staged kernel, which stages each 32-row tile's source rows in shared
- * memory by bulk asynchronous copies) for direction 0 (forward) or 1
+ * memory by bulk asynchronous copies; packed 3 = the fixed-width kernel, whose
+ * rows' first 8 entries sit at fixed positions) for direction 0 (forward) or 1
  * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not
  * exist for this K and precision.  Every variant gives bit-identical results. */
 pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* variant);

@@ -14,7 +14,8 @@ class MeshInfo(C.Structure):
         ("n_nodes", C.c_int64), ("n_tets", C.c_int64), ("n_boundary_faces", C.c_int64),
         ("n_boundary_nodes", C.c_int64), ("nnz_K", C.c_int64), ("nnz_K_graph", C.c_int64),
         ("nnz_B", C.c_int64), ("n_obs", C.c_int32), ("n_steps", C.c_int32), ("prec", C.c_int32),
-        ("dt", C.c_double), ("operator_bytes", C.c_double),
+        ("dt", C.c_double), ("operator_bytes", C.c_double), ("tile_rows", C.c_int32),
+        ("tile_max_staged", C.c_int32), ("tile_mean_staged", C.c_double),
     ]
 
 

@@ -9,6 +9,7 @@
 
 #include "pat_internal.h"
 #include "pat_solver.cuh"
+#include "pat_tile.cuh"
 
 using namespace pat;
 
@@ -48,6 +49,9 @@ void free_device(DeviceMesh& m) {
                  (void**)&m.adj.ptr, (void**)&m.adj.col, &m.adj.hi, (void**)&m.adj.lo,
                  (void**)&m.adj3.ptr, (void**)&m.adj3.col, &m.adj3.hi, (void**)&m.adj3.lo,
                  (void**)&m.fwd.hl, (void**)&m.adj.hl, (void**)&m.adj3.hl,
+                 (void**)&m.fwd.ell_col, (void**)&m.fwd.ell_hl, (void**)&m.fwd.ell_desc, (void**)&m.fwd.ovf_ptr,
+                 (void**)&m.fwd.ovf_col, (void**)&m.fwd.ovf_hl, (void**)&m.adj3.ell_col, (void**)&m.adj3.ell_hl,
+                 (void**)&m.adj3.ell_desc, (void**)&m.adj3.ovf_ptr, (void**)&m.adj3.ovf_col, (void**)&m.adj3.ovf_hl,
                  &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
                  &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
                  (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
@@ -132,8 +136,8 @@ bool bad_K(int32_t K, const char* fn) {
 // stiffness / boundary entries as contiguous ranges (gaps of up to 4 rows are
 // bridged), each entry's slot in the tile's staged rows, and the largest tile.
 pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, const std::vector<uint8_t>& ninj,
-                       bool upload_tables) {
-  constexpr int R = 32;
+                       const std::vector<int32_t>& order, bool upload_tables) {
+  constexpr int R = kTileRows;  // rows order[t*R .. t*R+R) form tile t (a compact Z-order brick)
   const int64_t N = m.N;
   const int32_t T = (int32_t)((N + R - 1) / R);
   std::vector<int32_t> rptr(1, 0), rsrc, rcnt, rslot, tslots(T);
@@ -143,14 +147,16 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
   for (int32_t t = 0; t < T; ++t) {
     const int64_t a = (int64_t)t * R, b = std::min<int64_t>(N, a + R);
     srcs.clear();
-    for (int64_t i = a; i < b; ++i)
+    for (int64_t ii = a; ii < b; ++ii) {
+      const int64_t i = order[ii];
       for (int32_t e = F.ptr[i]; e < F.ptr[i + 1]; ++e) srcs.push_back((int32_t)(F.col[e] & kIdxMask));
+    }
     std::sort(srcs.begin(), srcs.end());
     srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
     // ranges with small gaps bridged; slot of every source row
     std::vector<std::pair<int32_t, int32_t>> ranges;  // (start, count)
     for (int32_t j : srcs) {
-      if (!ranges.empty() && j - (ranges.back().first + ranges.back().second) <= 4)
+      if (!ranges.empty() && j - (ranges.back().first + ranges.back().second) <= 2)
         ranges.back().second = j - ranges.back().first + 1;
       else
         ranges.push_back({j, 1});
@@ -163,7 +169,7 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
       slot += rg.second;
     }
     if (slot > 65535) {
-      set_error("pat_mesh_create: a 32-row tile reads %d distinct rows (more than 65535)", slot);
+      set_error("pat_mesh_create: a tile reads %d distinct rows (more than 65535)", slot);
       return PAT_EUNSUPPORTED;
     }
     rptr.push_back((int32_t)rsrc.size());
@@ -185,7 +191,8 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
       while (q + 1 < (int)rsrc.size() && rslot[q + 1] <= sl) ++q;
       return rsrc[q] + (sl - rslot[q]);
     };
-    for (int64_t i = a; i < b; ++i) {
+    for (int64_t ii = a; ii < b; ++ii) {
+      const int64_t i = order[ii];
       for (int32_t e = F.ptr[i]; e < F.ptr[i + 1]; ++e) {
         const int32_t j = (int32_t)(F.col[e] & kIdxMask);
         sf[e] = slot_of(j);
@@ -207,6 +214,13 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
   }
   m.n_tiles = T;
   m.tile_max_slots = max_slots;
+  m.info.tile_rows = R;
+  m.info.tile_max_staged = max_slots;
+  {
+    double tot = 0.0;
+    for (int32_t t = 0; t < T; ++t) tot += tslots[t];
+    m.info.tile_mean_staged = T ? tot / T : 0.0;
+  }
   if (!upload_tables) return PAT_OK;
   pat_status s = upload(rptr, &m.tile_range_ptr);
   if (!s) s = upload(rsrc, &m.tile_range_src);
@@ -219,6 +233,54 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
     std::vector<int32_t> z(1, 0);
     s = upload(z, &m.d_status);
   }
+  return s;
+}
+
+// Fixed-width (8) copy of a three-level CSR for the ELL kernel (FP32 split only).
+pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const std::vector<uint8_t>& ninj,
+                     DevCSR& d) {
+  const int64_t N = (int64_t)R.ptr.size() - 1;
+  std::vector<uint32_t> col(N * 8), desc(N);
+  std::vector<float2> hl(N * 8);
+  std::vector<int32_t> optr(N + 1, 0);
+  std::vector<uint32_t> ocol;
+  std::vector<float2> ohl;
+  auto pair = [](double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  };
+  for (int64_t i = 0; i < N; ++i) {
+    const int32_t e0 = R.ptr[i], n = R.ptr[i + 1] - e0;
+    if (n > 255) {
+      set_error("pat_mesh_create: row %lld has %d entries (more than 255)", (long long)i, n);
+      return PAT_EUNSUPPORTED;
+    }
+    desc[i] = (uint32_t)n | ((uint32_t)nb[i] << 8) | ((uint32_t)ninj[i] << 16);
+    for (int q = 0; q < 8; ++q) {
+      if (q < n) {
+        col[i * 8 + q] = R.col[e0 + q] & kIdxMask;
+        hl[i * 8 + q] = pair(R.val[e0 + q]);
+      } else {
+        col[i * 8 + q] = (uint32_t)i;  // padding reads the row itself with a zero coefficient
+        hl[i * 8 + q] = make_float2(0.0f, 0.0f);
+      }
+    }
+    for (int q = 8; q < n; ++q) {
+      ocol.push_back(R.col[e0 + q] & kIdxMask);
+      ohl.push_back(pair(R.val[e0 + q]));
+    }
+    optr[i + 1] = (int32_t)ocol.size();
+  }
+  if (ocol.empty()) {  // keep valid (unused) device arrays
+    ocol.push_back(0);
+    ohl.push_back(make_float2(0.0f, 0.0f));
+  }
+  pat_status s = upload(col, &d.ell_col);
+  if (!s) s = upload(hl, &d.ell_hl);
+  if (!s) s = upload(desc, &d.ell_desc);
+  if (!s) s = upload(optr, &d.ovf_ptr);
+  if (!s) s = upload(ocol, &d.ovf_col);
+  if (!s) s = upload(ohl, &d.ovf_hl);
   return s;
 }
 
@@ -347,8 +409,8 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
   if (!s && !m.host_only) s = upload(ml, &m.ml);
   if (!s && !m.host_only) s = upload(sqml, &m.sqrt_ml);
   if (!s && !m.host_only) s = upload(det_node, &m.det_node);
-  if (!s) s = build_tiles(m, F, A3, row_ninj, !m.host_only);
-  if (!s && !m.host_only) {
+  std::vector<int32_t> order(N);
+  {
     // Z-order (Morton) of the node coordinates quantised to 2^10 cells per axis
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int64_t i = 0; i < N; ++i)
@@ -371,9 +433,14 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
       key[i] = {(spread(q[0]) << 2) | (spread(q[1]) << 1) | spread(q[2]), (int32_t)i};
     }
     std::sort(key.begin(), key.end());
-    std::vector<int32_t> order(N);
     for (int64_t i = 0; i < N; ++i) order[i] = key[i].second;
-    s = upload(order, &m.row_order);
+  }
+  if (!s && !m.host_only) s = upload(order, &m.row_order);
+  if (!s) s = build_tiles(m, F, A3, row_ninj, order, !m.host_only);
+  if (!s && !m.host_only && prec == PAT_F32 && m.split) {
+    std::vector<uint8_t> no_inj(N, 0);
+    s = build_ell(F, row_nb, no_inj, m.fwd);
+    if (!s) s = build_ell(A3, row_nb, row_ninj, m.adj3);
   }
   if (!s && !m.host_only) {
     cudaStream_t cs = nullptr;
@@ -780,10 +847,11 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   const bool f32s = mesh->d.prec == PAT_F32 && mesh->d.split;
   const bool ok_v = (v->V == 1 || v->V == 2 || v->V == 4 || v->V == 8) && K % v->V == 0 &&
                     (mesh->d.prec == PAT_F32 || v->V <= 2);
-  const bool ok_p = v->packed == 0 ? v->V != 8
+  const bool ok_p = v->packed == 0 ? v->V != 8 && !(v->V == 1 && v->packed)
                     : v->packed == 1 ? f32s && (v->V == 4 || v->V == 8) && (v->chunk == 2 || v->chunk == 4 ||
                                                                              (v->chunk == 8 && v->V == 4))
-                    : v->packed == 2 ? f32s && v->V == 8 && K <= 256
+                    : v->packed == 2 ? f32s && v->V == 8 && K <= 8 * 1024 / kTileRows
+                    : v->packed == 3 ? f32s && (v->V == 4 || v->V == 8 || (v->V == 1 && K == 1))
                                      : false;
   if (!ok_v || !ok_p || (v->staged && K / v->V < 2) || (v->min_blocks != 1 && v->min_blocks != 6)) {
     set_error("pat_select_variant: variant V=%d packed=%d chunk=%d staged=%d is not available for K=%d on this mesh",

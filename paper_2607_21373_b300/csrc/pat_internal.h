@@ -75,6 +75,15 @@ struct DevCSR {
   float* lo = nullptr;  // FP32 split meshes only
   float2* hl = nullptr; // FP32 split meshes: (hi, lo) interleaved
   int64_t nnz = 0;
+  // fixed-width copy (FP32 split meshes): the first 8 entries of every row at
+  // [row][8] (padding: column = the row, coefficient 0), the rest of a longer
+  // row in an overflow CSR; desc[row] = entries | boundary << 8 | sensors << 16
+  uint32_t* ell_col = nullptr;
+  float2* ell_hl = nullptr;
+  uint32_t* ell_desc = nullptr;
+  int32_t* ovf_ptr = nullptr;
+  uint32_t* ovf_col = nullptr;
+  float2* ovf_hl = nullptr;
 };
 
 // Event-based loop timing and launch counting (pat_profile_*).

@@ -229,8 +229,8 @@ static bool launch_tiled(const DeviceMesh& m, const Step3Args<float>& a, cudaStr
   // the tiles update every row: launches without rows to update (the final
   // observation-only launch of a forward solve) and the zero-state adjoint start
   // go to the packed kernel
-  if (a.x == nullptr || a.xn == nullptr || a.row_threads == 0 || a.K % 8 || a.K > 256 || !m.fwd.hl ||
-      m.n_tiles == 0)
+  if (a.x == nullptr || a.xn == nullptr || a.row_threads == 0 || a.K % 8 || a.K > 8 * 1024 / kTileRows ||
+      !m.fwd.hl || m.n_tiles == 0 || !m.row_order)
     return false;
   const size_t smem = 128 + (size_t)m.tile_max_slots * a.K * 4;
   if (smem > 200 * 1024) return false;
@@ -239,7 +239,7 @@ static bool launch_tiled(const DeviceMesh& m, const Step3Args<float>& a, cudaStr
     cudaFuncSetAttribute(step3t_kernel<8, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   TileArgs Tl{m.tile_range_ptr, m.tile_range_src, m.tile_range_cnt, m.tile_range_slot, m.tile_slots,
-              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles};
+              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles, m.row_order};
   Step3Args<float> A = a;
   A.hl = ADJ ? m.adj3.hl : m.fwd.hl;
   const int bdim = kTileRows * (a.K / 8);
@@ -256,6 +256,32 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
   variant(m, ADJ ? 1 : 0, a.K, &c);
   if constexpr (sizeof(T) == 4 && SPLIT && V == 8) {
     if (c.packed == 2 && launch_tiled<ADJ>(m, a, st)) return;
+  }
+  if constexpr (sizeof(T) == 4 && SPLIT && V == 1) {
+    const DevCSR& E = ADJ ? m.adj3 : m.fwd;
+    if (c.packed == 3 && E.ell_col && a.K == 1) {  // fixed-width rows, one sample
+      a.ell_col = E.ell_col;
+      a.ell_hl = E.ell_hl;
+      a.ell_desc = E.ell_desc;
+      a.ovf_ptr = E.ovf_ptr;
+      a.ovf_col = E.ovf_col;
+      a.ovf_hl = E.ovf_hl;
+      step3e1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+      return;
+    }
+  }
+  if constexpr (sizeof(T) == 4 && SPLIT && (V == 4 || V == 8)) {
+    const DevCSR& E = ADJ ? m.adj3 : m.fwd;
+    if (c.packed == 3 && E.ell_col) {  // fixed-width rows
+      a.ell_col = E.ell_col;
+      a.ell_hl = E.ell_hl;
+      a.ell_desc = E.ell_desc;
+      a.ovf_ptr = E.ovf_ptr;
+      a.ovf_col = E.ovf_col;
+      a.ovf_hl = E.ovf_hl;
+      step3e_kernel<V, ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+      return;
+    }
   }
   if constexpr (sizeof(T) == 4 && SPLIT && (V == 4 || V == 8)) {
     if (c.packed) {
@@ -1037,14 +1063,17 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 12; ++variant_id) {
+      for (int variant_id = 0; variant_id < 13; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
         // generic kernels: 7 row metadata staged in shared memory; 8 read directly
         // 9: tile-staged kernel (source rows of 32-row tiles staged by bulk copies);
         // 10, 11: packed, chunks of 2 / 4, rows processed in Z-order
-        const int packed = (variant_id <= 6 || variant_id >= 10) ? 1 : (variant_id == 9 ? 2 : 0),
+        // 12: fixed-width (ELL) packed kernel
+        const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11)
+                               ? 1
+                               : (variant_id == 9 ? 2 : (variant_id == 12 ? 3 : 0)),
                   stage = variant_id == 7;
         const int chunk = (variant_id == 0 || variant_id == 3 || variant_id == 5 || variant_id == 10) ? 2
                           : (variant_id == 2 ? 8 : 4);
@@ -1053,7 +1082,11 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         const int early = (variant_id == 3 || variant_id == 4) ? 1 : 0;
         if (minb > 1 && V == 8) continue;  // would spill
         if (packed == 1 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8))) continue;
-        if (packed == 2 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 256 && m.n_tiles > 0)) continue;
+        if (packed == 2 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 8 * 1024 / kTileRows && m.n_tiles > 0))
+          continue;
+        if (packed == 3 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8 || (V == 1 && K == 1)) &&
+                             m.fwd.ell_col))
+          continue;
         if (packed == 1 && chunk == 8 && V == 8) continue;
         if (!packed && V == 8) continue;
         if (stage && K / V < 2) continue;

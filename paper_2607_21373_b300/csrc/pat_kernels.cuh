@@ -256,6 +256,13 @@ struct Step3Args {
   int32_t stage_cap;  // shared-memory entries per block (STAGE kernels)
   const float2* __restrict__ hl;     // (hi, lo) pairs of FP32 split coefficients
   const int32_t* __restrict__ order; // processing order of the rows (nullptr: 0, 1, 2, ...)
+  // fixed-width copy of the rows (ELL kernel)
+  const uint32_t* __restrict__ ell_col;
+  const float2* __restrict__ ell_hl;
+  const uint32_t* __restrict__ ell_desc;
+  const int32_t* __restrict__ ovf_ptr;
+  const uint32_t* __restrict__ ovf_col;
+  const float2* __restrict__ ovf_hl;
   const uint8_t* __restrict__ nb;    // [N] boundary entries per row
   const uint8_t* __restrict__ ninj;  // [N] sensor entries per row (adjoint rows)
   const int32_t* __restrict__ ptr;

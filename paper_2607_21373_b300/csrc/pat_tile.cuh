@@ -1,6 +1,7 @@
 // Tile-staged three-level step for K-stacked FP32 fields (K a multiple of 8).
 //
-// A block owns a tile of R = 32 consecutive rows.  Before it computes, the rows
+// A block owns a tile of R = 64 rows that are consecutive in the Z-order of the
+// node coordinates (a compact brick of the mesh).  Before it computes, the rows
 // of x_s that its stiffness/boundary entries read -- the union of the tile's
 // neighbourhoods, precomputed on the host as a few contiguous row ranges --
 // are copied global -> shared memory by asynchronous bulk copies
@@ -18,7 +19,7 @@
 
 namespace pat {
 
-constexpr int kTileRows = 32;
+constexpr int kTileRows = 64;
 
 struct TileArgs {
   const int32_t* __restrict__ range_ptr;  // [T+1] into the range arrays
@@ -29,6 +30,7 @@ struct TileArgs {
   const uint16_t* __restrict__ slot;      // per CSR entry: shared-memory slot of its source row
   int32_t* status;                        // device status word (PAT_ETIMEOUT on a stuck copy)
   int32_t n_tiles;                        // blocks beyond the tiles gather the sensor observations
+  const int32_t* __restrict__ order;      // rows of tile t: order[t*R .. t*R+R)
 };
 
 // observation of the input state by thread g of the gather blocks
@@ -103,11 +105,16 @@ __global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0: lane 0 announces the tile's bytes, then the lanes issue the
+    // range copies in parallel
     const int q0 = Tl.range_ptr[tile], q1 = Tl.range_ptr[tile + 1];
-    const uint32_t bytes = (uint32_t)((size_t)Tl.tile_slots[tile] * row_bytes);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(bytes) : "memory");
-    for (int q = q0; q < q1; ++q) {
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = (uint32_t)((size_t)Tl.tile_slots[tile] * row_bytes);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s), "r"(bytes) : "memory");
+    }
+    __syncwarp();
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += 32) {
       const float* src = A.x + (int64_t)Tl.range_src[q] * A.K;
       const uint32_t dst = smem_u32(rows + (size_t)Tl.range_slot[q] * A.K);
       const uint32_t n = (uint32_t)((size_t)Tl.range_cnt[q] * row_bytes);
@@ -119,8 +126,8 @@ __global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, 
   }
   const int lr = threadIdx.x / KV;  // row within the tile
   const int kv = threadIdx.x - lr * KV;
-  const int64_t row = r0 + lr;
-  const bool active = row < A.N;
+  const bool active = r0 + lr < A.N;
+  const int64_t row = active ? (int64_t)Tl.order[r0 + lr] : 0;
   const int64_t off = row * A.K + (int64_t)kv * V;
   // the node's previous value comes from global memory while the copies run
   Pack<float, V> xpi;
@@ -216,6 +223,225 @@ __global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, 
     xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
   }
   st<float, V>(A.xn + off, xo);
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-width (ELL) packed kernel: a row's first 8 entries sit at [row][8], so
+// their columns and coefficients arrive in one round of broadcast loads with no
+// row-pointer load in front (padding slots read the row itself with a zero
+// coefficient); longer rows continue in an overflow CSR.  Entries 0..7 are
+// then processed as two chunks of 4 neighbour rows.
+// ---------------------------------------------------------------------------
+template <int V>
+__device__ __forceinline__ void ell_entry(const Step3Args<float>& A, int64_t row, int e, uint32_t* col, float2* c) {
+  if (e < 8) {
+    *col = A.ell_col[row * 8 + e];
+    *c = A.ell_hl[row * 8 + e];
+  } else {
+    const int64_t o = A.ovf_ptr[row] + (e - 8);
+    *col = A.ovf_col[o];
+    *c = A.ovf_hl[o];
+  }
+}
+
+template <int V, bool ADJ>
+__global__ void __launch_bounds__(256) step3e_kernel(const Step3Args<float> A) {
+  constexpr int P = V / 2;
+  const int KV = A.K / V;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.row_threads) {
+    gather_obs<V>(A, t - A.row_threads);
+    return;
+  }
+  const int64_t row = t / KV;
+  const int kv = (int)(t - row * KV);
+  const int64_t off = row * A.K + (int64_t)kv * V;
+  const uint32_t desc = A.ell_desc[row];
+  const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
+  const int eA = n - ni;  // stiffness + boundary entries
+  const uint4 c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
+  const uint4 c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
+  const float4 h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
+  const float4 h23 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 2);
+  const float4 h45 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4);
+  const float4 h67 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 6);
+  const uint32_t cols[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  const float2 cf[8] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
+                        make_float2(h23.z, h23.w), make_float2(h45.x, h45.y), make_float2(h45.z, h45.w),
+                        make_float2(h67.x, h67.y), make_float2(h67.z, h67.w)};
+  const uint32_t Ku = (uint32_t)A.K;
+  u64 acc[P], accl[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
+  if (A.x) {
+    const float* xk = A.x + (int64_t)kv * V;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      u64 x[4][P];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (4 * h + q < eA) {
+          ld_pairs<P>(xk + cols[4 * h + q] * Ku, x[q]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 c = (4 * h + q < eA) ? cf[4 * h + q] : make_float2(0.0f, 0.0f);
+        const u64 ch = dup2(c.x), cl = dup2(c.y);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          acc[p] = ffma2(ch, x[q][p], acc[p]);
+          accl[p] = ffma2(cl, x[q][p], accl[p]);
+        }
+      }
+    }
+    for (int e = 8; e < eA; ++e) {  // overflow of long (boundary) rows
+      uint32_t col;
+      float2 c;
+      ell_entry<V>(A, row, e, &col, &c);
+      u64 x[P];
+      ld_pairs<P>(xk + col * Ku, x);
+      const u64 ch = dup2(c.x), cl = dup2(c.y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        acc[p] = ffma2(ch, x[p], acc[p]);
+        accl[p] = ffma2(cl, x[p], accl[p]);
+      }
+    }
+    if (nb > 0 && A.prev_mode != 2) {
+      // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
+      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + (int64_t)kv * V;
+      for (int e = eA - nb; e < eA; ++e) {
+        uint32_t col;
+        float2 c;
+        ell_entry<V>(A, row, e, &col, &c);
+        u64 x[P];
+        ld_pairs<P>(pk + col * Ku, x);
+        const u64 ch = dup2(-c.x), cl = dup2(-c.y);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          acc[p] = ffma2(ch, x[p], acc[p]);
+          accl[p] = ffma2(cl, x[p], accl[p]);
+        }
+      }
+    }
+  }
+  float src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = eA; e < n; ++e) {
+      uint32_t col;
+      float2 c;
+      ell_entry<V>(A, row, e, &col, &c);
+      const int64_t j = (int64_t)col;
+      if (A.ya) {
+        const Pack<float, V> y = ld<float, V>(A.ya + j * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+      }
+      if (A.yb) {
+        const Pack<float, V> y = ld<float, V>(A.yb + j * A.K + (int64_t)kv * V);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+      }
+    }
+  }
+  Pack<float, V> xi, xpi, xo;
+  if (A.x) {
+    xi = ld<float, V>(A.x + off);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
+  }
+  if (A.prev_mode == 0) {
+    xpi = ld<float, V>(A.xp + off);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+    const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+    xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+    xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+  }
+  st<float, V>(A.xn + off, xo);
+}
+
+// Fixed-width kernel for one sample (K = 1): one thread per row, the row's 8
+// fixed slots (columns and coefficient pairs: six 16-byte loads) arrive in one
+// round and its 8 neighbour values in the next, instead of the row-pointer ->
+// column -> value chain of the CSR walk.
+template <bool ADJ>
+__global__ void __launch_bounds__(256) step3e1_kernel(const Step3Args<float> A) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.row_threads) {
+    gather_obs<1>(A, t - A.row_threads);
+    return;
+  }
+  const int64_t row = t;
+  const uint32_t desc = A.ell_desc[row];
+  const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
+  const int eA = n - ni;
+  const uint4 c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
+  const uint4 c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
+  const float4 h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
+  const float4 h23 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 2);
+  const float4 h45 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4);
+  const float4 h67 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 6);
+  const uint32_t cols[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  const float hs[8] = {h01.x, h01.z, h23.x, h23.z, h45.x, h45.z, h67.x, h67.z};
+  const float ls[8] = {h01.y, h01.w, h23.y, h23.w, h45.y, h45.w, h67.y, h67.w};
+  float acc = 0.0f, accl = 0.0f;
+  if (A.x) {
+    float xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) xv[q] = q < eA ? A.x[cols[q]] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float h = q < eA ? hs[q] : 0.0f, l = q < eA ? ls[q] : 0.0f;
+      acc = fmaf(h, xv[q], acc);
+      accl = fmaf(l, xv[q], accl);
+    }
+    for (int e = 8; e < eA; ++e) {
+      uint32_t col;
+      float2 c;
+      ell_entry<1>(A, row, e, &col, &c);
+      const float x = A.x[col];
+      acc = fmaf(c.x, x, acc);
+      accl = fmaf(c.y, x, accl);
+    }
+    if (nb > 0 && A.prev_mode != 2) {
+      const float* pk = A.prev_mode == 0 ? A.xp : A.x;
+      for (int e = eA - nb; e < eA; ++e) {
+        uint32_t col;
+        float2 c;
+        ell_entry<1>(A, row, e, &col, &c);
+        const float x = pk[col];
+        acc = fmaf(-c.x, x, acc);
+        accl = fmaf(-c.y, x, accl);
+      }
+    }
+  }
+  float src = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = eA; e < n; ++e) {
+      uint32_t col;
+      float2 c;
+      ell_entry<1>(A, row, e, &col, &c);
+      if (A.ya) src = fmaf(c.x, A.ya[col], src);
+      if (A.yb) src = fmaf(c.x, A.yb[col], src);
+    }
+  }
+  const float xi = A.x ? A.x[row] : 0.0f;
+  const float xpi = A.prev_mode == 0 ? A.xp[row] : (A.prev_mode == 1 ? xi : 0.0f);
+  const float w = xi - xpi;
+  A.xn[row] = xi + (w - (acc + accl) + A.inj_scale * src);
 }
 
 }  // namespace pat

@@ -35,7 +35,7 @@ VARIANTS = [dict(V=8, packed=2), dict(V=8, packed=1, chunk=2), dict(V=8, packed=
             dict(V=4, packed=1, chunk=4), dict(V=4, packed=1, chunk=8), dict(V=4, packed=1, chunk=2, min_blocks=6),
             dict(V=4, packed=1, chunk=4, early=True), dict(V=4, packed=0, staged=True), dict(V=4, packed=0),
             dict(V=2, packed=0), dict(V=1, packed=0), dict(V=8, packed=1, chunk=2, zorder=True),
-            dict(V=4, packed=1, chunk=4, zorder=True)]
+            dict(V=4, packed=1, chunk=4, zorder=True), dict(V=8, packed=3), dict(V=4, packed=3)]
 
 
 @pytest.mark.parametrize("K", [16, 64])
@@ -53,5 +53,21 @@ def test_every_variant_is_bit_identical(K):
     for v in VARIANTS:
         for d in ("fwd", "adj"):
             m.select_variant(K, d, **v)
+        assert torch.equal(m.forward(p0), Y0), v
+        assert torch.equal(m.adjoint(yh), g0), v
+
+
+def test_single_sample_variants_are_bit_identical():
+    from paper_2607_21373_b300 import Mesh
+    n, n_obs, nt = 10, 48, 60
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, 7)
+    m = Mesh(xyz, tets, det, 0.3 / n, nt, precision="f32")
+    p0 = torch.tensor(S.standard_normal(len(xyz), 5), dtype=torch.float32, device="cuda")
+    yh = torch.tensor(S.standard_normal((nt, n_obs), 6), dtype=torch.float32, device="cuda")
+    Y0, g0 = m.forward(p0).clone(), m.adjoint(yh).clone()
+    for v in (dict(V=1, packed=3), dict(V=1, packed=0, staged=False)):
+        for d in ("fwd", "adj"):
+            m.select_variant(1, d, **v)
         assert torch.equal(m.forward(p0), Y0), v
         assert torch.equal(m.adjoint(yh), g0), v
