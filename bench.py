@@ -212,7 +212,7 @@ def run_ours(a, rank, world, local_rank, dist):
     tune = {}
     forced = {"tiled": dict(V=8, packed=2), "v8c2": dict(V=8, packed=1, chunk=2),
               "v4c4": dict(V=4, packed=1, chunk=4), "v8c2z": dict(V=8, packed=1, chunk=2, zorder=True),
-              "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3)}.get(a.variant)
+              "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3), "pipe": dict(V=8, packed=4)}.get(a.variant)
     if forced:
         for d in ("fwd", "adj"):
             mesh.select_variant(K, d, **forced)
@@ -294,6 +294,8 @@ def run_ours(a, rank, world, local_rank, dist):
     def kernel_name(e, adj):
         if e.get("packed") == 2:
             return "step3t_kernel<8,%s>" % ("true" if adj else "false")
+        if e.get("packed") == 4:
+            return "step3p_kernel<%s> (persistent double-buffered tiles)" % ("true" if adj else "false")
         if e.get("packed") == 3:
             return "step3e_kernel<%d,%s>" % (e["V"], "true" if adj else "false")
         if e.get("packed"):

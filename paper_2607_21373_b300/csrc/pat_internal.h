@@ -104,6 +104,7 @@ struct TuneCfg {
   int minb = 1;    // packed kernel: minimum resident blocks per SM asked of the compiler
   int early = 0;   // packed kernel: load the node's own values before the row walk
   int order = 0;   // packed kernel: process rows in Z-order of the node coordinates
+  int big = 0;     // packed kernels: 1024-thread blocks
 };
 
 struct DeviceMesh {

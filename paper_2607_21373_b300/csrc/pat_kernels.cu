@@ -249,6 +249,35 @@ static bool launch_tiled(const DeviceMesh& m, const Step3Args<float>& a, cudaStr
   return true;
 }
 
+// Persistent double-buffered tile launch (variant packed == 4): enough blocks
+// to fill every SM, each walking a strided subset of the tiles.
+template <bool ADJ>
+static bool launch_pipelined(const DeviceMesh& m, const Step3Args<float>& a, cudaStream_t st) {
+  if (a.x == nullptr || a.xn == nullptr || a.row_threads == 0 || a.K % 8 || a.K > 8 * 512 / kTileRows ||
+      !m.fwd.hl || m.n_tiles == 0 || !m.row_order)
+    return false;
+  const size_t smem = 128 + 2 * (size_t)m.tile_max_slots * a.K * 4;
+  if (smem > 220 * 1024) return false;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(step3p_kernel<ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  });
+  const int bdim = kTileRows * (a.K / 8);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step3p_kernel<ADJ>, bdim, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  TileArgs Tl{m.tile_range_ptr, m.tile_range_src, m.tile_range_cnt, m.tile_range_slot, m.tile_slots,
+              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles, m.row_order};
+  Step3Args<float> A = a;
+  A.hl = ADJ ? m.adj3.hl : m.fwd.hl;
+  const int blocks = std::min(m.n_tiles, per_sm * sm_count());
+  step3p_kernel<ADJ><<<(unsigned)blocks, bdim, smem, st>>>(A, Tl, m.tile_max_slots);
+  return true;
+}
+
 template <typename T, int V, bool SPLIT, bool ADJ>
 static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, cudaStream_t st) {
   const int64_t blocks = (threads + 255) / 256;
@@ -256,6 +285,7 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
   variant(m, ADJ ? 1 : 0, a.K, &c);
   if constexpr (sizeof(T) == 4 && SPLIT && V == 8) {
     if (c.packed == 2 && launch_tiled<ADJ>(m, a, st)) return;
+    if (c.packed == 4 && launch_pipelined<ADJ>(m, a, st)) return;
   }
   if constexpr (sizeof(T) == 4 && SPLIT && V == 1) {
     const DevCSR& E = ADJ ? m.adj3 : m.fwd;
@@ -279,7 +309,13 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.ovf_ptr = E.ovf_ptr;
       a.ovf_col = E.ovf_col;
       a.ovf_hl = E.ovf_hl;
-      step3e_kernel<V, ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+      a.order = c.order ? m.row_order : nullptr;
+      if (c.big) {
+        const int64_t bb = (threads + 1023) / 1024;
+        step3e_big_kernel<V, ADJ><<<(unsigned)bb, 1024, 0, st>>>(a);
+      } else {
+        step3e_kernel<V, ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+      }
       return;
     }
   }
@@ -288,7 +324,13 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.hl = (ADJ ? m.adj3.hl : m.fwd.hl);
       a.order = c.order ? m.row_order : nullptr;
       const unsigned nb = (unsigned)blocks;
-      if (c.minb == 6) {
+      if (c.big) {
+        const unsigned bb = (unsigned)((threads + 1023) / 1024);
+        if (c.chunk == 2)
+          step3f_big_kernel<V, 2, ADJ><<<bb, 1024, 0, st>>>(a);
+        else
+          step3f_big_kernel<V, 4, ADJ><<<bb, 1024, 0, st>>>(a);
+      } else if (c.minb == 6) {
         if (c.chunk == 2)
           step3f_occ_kernel<V, 2, ADJ><<<nb, 256, 0, st>>>(a);
         else
@@ -1063,26 +1105,38 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 13; ++variant_id) {
+      for (int variant_id = 0; variant_id < 18; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
         // generic kernels: 7 row metadata staged in shared memory; 8 read directly
         // 9: tile-staged kernel (source rows of 32-row tiles staged by bulk copies);
         // 10, 11: packed, chunks of 2 / 4, rows processed in Z-order
-        // 12: fixed-width (ELL) packed kernel
-        const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11)
+        // 12: fixed-width (ELL) packed kernel; 13: persistent double-buffered tiles
+        // 14, 15: packed chunks of 2 / fixed-width, 1024-thread blocks, Z-order rows;
+        // 16, 17: the same without Z-order
+        const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
+                            variant_id == 16)
                                ? 1
-                               : (variant_id == 9 ? 2 : (variant_id == 12 ? 3 : 0)),
+                               : (variant_id == 9 ? 2
+                                  : (variant_id == 12 || variant_id == 15 || variant_id == 17)
+                                      ? 3
+                                      : (variant_id == 13 ? 4 : 0)),
                   stage = variant_id == 7;
-        const int chunk = (variant_id == 0 || variant_id == 3 || variant_id == 5 || variant_id == 10) ? 2
-                          : (variant_id == 2 ? 8 : 4);
-        const int zorder = variant_id >= 10 ? 1 : 0;
+        const int chunk = (variant_id == 0 || variant_id == 3 || variant_id == 5 || variant_id == 10 ||
+                           variant_id == 14 || variant_id == 16)
+                              ? 2
+                              : (variant_id == 2 ? 8 : 4);
+        const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
+        const int big = variant_id >= 14 ? 1 : 0;
+        if (big && V != 8) continue;
         const int minb = (variant_id == 5 || variant_id == 6) ? 6 : 1;
         const int early = (variant_id == 3 || variant_id == 4) ? 1 : 0;
         if (minb > 1 && V == 8) continue;  // would spill
         if (packed == 1 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8))) continue;
         if (packed == 2 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 8 * 1024 / kTileRows && m.n_tiles > 0))
+          continue;
+        if (packed == 4 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 8 * 512 / kTileRows && m.n_tiles > 0))
           continue;
         if (packed == 3 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8 || (V == 1 && K == 1)) &&
                              m.fwd.ell_col))
@@ -1098,13 +1152,14 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.minb = minb;
         g_force.early = early;
         g_force.order = zorder;
+        g_force.big = big;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
         g_force_on = false;
         if (s) return s;
         if (table && n < 64)
-          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, (double)us};
+          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

@@ -713,6 +713,11 @@ __global__ void __launch_bounds__(256) step3f_kernel(const Step3Args<float> A) {
 
 // the same with at least 6 resident blocks per SM asked of the compiler (<= 40 registers)
 template <int V, int CH, bool ADJ>
+__global__ void __launch_bounds__(1024) step3f_big_kernel(const Step3Args<float> A) {
+  step3f_body<V, CH, ADJ, false>(A, (int64_t)blockIdx.x * blockDim.x);
+}
+
+template <int V, int CH, bool ADJ>
 __global__ void __launch_bounds__(256, 6) step3f_occ_kernel(const Step3Args<float> A) {
   step3f_body<V, CH, ADJ, false>(A, (int64_t)blockIdx.x * blockDim.x);
 }

@@ -245,7 +245,7 @@ __device__ __forceinline__ void ell_entry(const Step3Args<float>& A, int64_t row
 }
 
 template <int V, bool ADJ>
-__global__ void __launch_bounds__(256) step3e_kernel(const Step3Args<float> A) {
+__device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
   constexpr int P = V / 2;
   const int KV = A.K / V;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(256) step3e_kernel(const Step3Args<float> A) {
     gather_obs<V>(A, t - A.row_threads);
     return;
   }
-  const int64_t row = t / KV;
-  const int kv = (int)(t - row * KV);
+  const int64_t rowi = t / KV;
+  const int kv = (int)(t - rowi * KV);
+  const int64_t row = A.order ? (int64_t)A.order[rowi] : rowi;
   const int64_t off = row * A.K + (int64_t)kv * V;
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
@@ -371,6 +372,185 @@ __global__ void __launch_bounds__(256) step3e_kernel(const Step3Args<float> A) {
     xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
   }
   st<float, V>(A.xn + off, xo);
+}
+
+template <int V, bool ADJ>
+__global__ void __launch_bounds__(256) step3e_kernel(const Step3Args<float> A) {
+  step3e_body<V, ADJ>(A);
+}
+
+// the same with 1024-thread blocks: with rows in Z-order a block is a compact
+// brick of the mesh whose neighbour rows stay in its SM's L1
+template <int V, bool ADJ>
+__global__ void __launch_bounds__(1024) step3e_big_kernel(const Step3Args<float> A) {
+  step3e_body<V, ADJ>(A);
+}
+
+// Wait for the given phase parity of an mbarrier, bounded by `cycles`.
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Persistent, double-buffered tile-staged kernel: each block walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; while it computes one tile from one
+// shared-memory buffer, the bulk copies of its next tile fill the other, so
+// the copy latency hides behind compute instead of serialising with it.
+template <bool ADJ>
+__global__ void __launch_bounds__(512) step3p_kernel(const Step3Args<float> A, const TileArgs Tl, int slots_cap) {
+  constexpr int V = 8, P = 4;
+  extern __shared__ __align__(128) unsigned char ptile_smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ptile_smem);
+  float* bufs[2] = {reinterpret_cast<float*>(ptile_smem + 128),
+                    reinterpret_cast<float*>(ptile_smem + 128) + (size_t)slots_cap * A.K};
+  const uint32_t bar_s[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  const int KV = A.K / V;
+  const size_t row_bytes = (size_t)A.K * 4;
+  constexpr long long kWait = 4000000000ll;  // about two seconds at 2 GHz
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s[0]) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s[1]) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int tile, int b) {  // by warp 0
+    const int q0 = Tl.range_ptr[tile], q1 = Tl.range_ptr[tile + 1];
+    if (threadIdx.x == 0) {
+      const uint32_t bytes = (uint32_t)((size_t)Tl.tile_slots[tile] * row_bytes);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_s[b]), "r"(bytes) : "memory");
+    }
+    __syncwarp();
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += 32) {
+      const float* src = A.x + (int64_t)Tl.range_src[q] * A.K;
+      const uint32_t dst = smem_u32(bufs[b] + (size_t)Tl.range_slot[q] * A.K);
+      const uint32_t n = (uint32_t)((size_t)Tl.range_cnt[q] * row_bytes);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+          "l"(src), "r"(n), "r"(bar_s[b])
+          : "memory");
+    }
+  };
+  const int lr = threadIdx.x / KV;
+  const int kv = threadIdx.x - lr * KV;
+  const uint32_t Ku = (uint32_t)A.K;
+  int tile = blockIdx.x;
+  if (tile < Tl.n_tiles && threadIdx.x < 32) issue(tile, 0);
+  for (int it = 0; tile < Tl.n_tiles; ++it, tile += gridDim.x) {
+    const int b = it & 1;
+    const int next = tile + gridDim.x;
+    if (next < Tl.n_tiles && threadIdx.x < 32) issue(next, b ^ 1);
+    const bool ok = mbar_wait_parity(bar_s[b], (uint32_t)((it >> 1) & 1), kWait);
+    if (__syncthreads_or(!ok)) {
+      // a copy never completed: report, let in-flight copies land, stop
+      if (threadIdx.x == 0) atomicExch(Tl.status, (int)PAT_ETIMEOUT);
+      mbar_wait_parity(bar_s[b], (uint32_t)((it >> 1) & 1), kWait);
+      if (next < Tl.n_tiles) mbar_wait_parity(bar_s[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWait);
+      return;
+    }
+    const int64_t r0 = (int64_t)tile * kTileRows;
+    if (r0 + lr < A.N) {
+      const int64_t row = Tl.order[r0 + lr];
+      const int64_t off = row * A.K + (int64_t)kv * V;
+      const int e0 = A.ptr[row], e1 = A.ptr[row + 1];
+      const int ni = ADJ ? (int)A.ninj[row] : 0;
+      const int eA = e1 - ni;
+      const int eB = eA - (int)A.nb[row];
+      Pack<float, V> xpi;
+      if (A.prev_mode == 0) xpi = ld<float, V>(A.xp + off);
+      u64 acc[P], accl[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
+      const float* sk = bufs[b] + kv * V;
+#pragma unroll 4
+      for (int e = e0; e < eA; ++e) {
+        const float2 c = A.hl[e];
+        const float* sp = sk + (size_t)Tl.slot[e] * A.K;
+        const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sp);
+        const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sp + 4);
+        const u64 ch = dup2(c.x), cl = dup2(c.y);
+        acc[0] = ffma2(ch, v0.x, acc[0]);
+        accl[0] = ffma2(cl, v0.x, accl[0]);
+        acc[1] = ffma2(ch, v0.y, acc[1]);
+        accl[1] = ffma2(cl, v0.y, accl[1]);
+        acc[2] = ffma2(ch, v1.x, acc[2]);
+        accl[2] = ffma2(cl, v1.x, accl[2]);
+        acc[3] = ffma2(ch, v1.y, acc[3]);
+        accl[3] = ffma2(cl, v1.y, accl[3]);
+      }
+      if (eB < eA && A.prev_mode != 2) {
+        for (int e = eB; e < eA; ++e) {
+          const float2 c = A.hl[e];
+          u64 x[P];
+          if (A.prev_mode == 0) {
+            ld_pairs<P>(A.xp + (int64_t)kv * V + (A.col[e] & kIdxMask) * Ku, x);
+          } else {
+            const float* sp = sk + (size_t)Tl.slot[e] * A.K;  // xp = x
+            const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sp);
+            const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(sp + 4);
+            x[0] = v0.x;
+            x[1] = v0.y;
+            x[2] = v1.x;
+            x[3] = v1.y;
+          }
+          const u64 ch = dup2(-c.x), cl = dup2(-c.y);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            acc[p] = ffma2(ch, x[p], acc[p]);
+            accl[p] = ffma2(cl, x[p], accl[p]);
+          }
+        }
+      }
+      float src[V];
+#pragma unroll
+      for (int q = 0; q < V; ++q) src[q] = 0.0f;
+      if constexpr (ADJ) {
+        for (int e = eA; e < e1; ++e) {
+          const int64_t j = (int64_t)(A.col[e] & kIdxMask);
+          const float h = A.hl[e].x;
+          if (A.ya) {
+            const Pack<float, V> y = ld<float, V>(A.ya + j * A.K + (int64_t)kv * V);
+#pragma unroll
+            for (int q = 0; q < V; ++q) src[q] = fmaf(h, y.v[q], src[q]);
+          }
+          if (A.yb) {
+            const Pack<float, V> y = ld<float, V>(A.yb + j * A.K + (int64_t)kv * V);
+#pragma unroll
+            for (int q = 0; q < V; ++q) src[q] = fmaf(h, y.v[q], src[q]);
+          }
+        }
+      }
+      const Pack<float, V> xi = ld<float, V>(A.x + off);
+      if (A.prev_mode != 0) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+      }
+      Pack<float, V> xo;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+        const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+        xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+        xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+      }
+      st<float, V>(A.xn + off, xo);
+    }
+    __syncthreads();  // buffer b is refilled by the copies issued in iteration it + 1
+  }
+  // sensor observations of the input state
+  if (!ADJ && A.y_out) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (int64_t)A.n_obs * KV;
+         g += (int64_t)gridDim.x * blockDim.x)
+      gather_obs<V>(A, g);
+  }
 }
 
 // Fixed-width kernel for one sample (K = 1): one thread per row, the row's 8
