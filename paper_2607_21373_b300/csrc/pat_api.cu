@@ -854,7 +854,10 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
                     : v->packed == 3 ? f32s && (v->V == 4 || v->V == 8 || (v->V == 1 && K == 1))
                     : v->packed == 4 ? f32s && v->V == 8 && K <= 8 * 512 / kTileRows
                                      : false;
-  if (!ok_v || !ok_p || (v->staged && K / v->V < 2) || (v->min_blocks != 1 && v->min_blocks != 6)) {
+  const bool ok_pf = v->prefetch == 0 || (v->prefetch >= 1 && v->prefetch <= 4 && (v->packed == 1 || v->packed == 3) &&
+                                          v->V != 1);
+  if (!ok_v || !ok_p || !ok_pf || (v->staged && K / v->V < 2) || (v->min_blocks != 1 && v->min_blocks != 6) ||
+      (v->min_blocks == 6 && v->V == 8)) {
     set_error("pat_select_variant: variant V=%d packed=%d chunk=%d staged=%d is not available for K=%d on this mesh",
               v->V, v->packed, v->chunk, v->staged, K);
     return PAT_EINVAL;
@@ -868,6 +871,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.early = v->early;
   c.order = v->zorder;
   c.big = v->big_blocks && v->V == 8 && (v->packed == 1 || v->packed == 3);
+  c.pf = v->prefetch;
   {
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;

@@ -105,6 +105,7 @@ struct TuneCfg {
   int early = 0;   // packed kernel: load the node's own values before the row walk
   int order = 0;   // packed kernel: process rows in Z-order of the node coordinates
   int big = 0;     // packed kernels: 1024-thread blocks
+  int pf = 0;      // packed kernels: L2 prefetch distance in resident waves (0: off)
 };
 
 struct DeviceMesh {

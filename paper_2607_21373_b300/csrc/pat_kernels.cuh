@@ -33,6 +33,15 @@ __device__ __forceinline__ void st(T* __restrict__ p, const Pack<T, V>& x) {
 // Row blocks update all nodes x samples; the trailing blocks gather the
 // observation of the *input* state (sensors read p = a - w/2 of three nodes).
 // ---------------------------------------------------------------------------
+// q = t / KV for the thread-to-row mapping without a 64-bit division (which
+// the GPU emulates in software): a shift when KV is a power of two, else a
+// 32-bit division while t fits.  Exact for t >= 0, KV >= 1.
+__device__ __forceinline__ int64_t div_kv(int64_t t, int KV) {
+  if ((KV & (KV - 1)) == 0) return t >> (__ffs(KV) - 1);
+  if (t <= 0xffffffffll) return (int64_t)((uint32_t)t / (uint32_t)KV);
+  return t / KV;
+}
+
 template <typename T>
 struct FwdArgs {
   int64_t N;
@@ -59,7 +68,7 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(const FwdArgs<T> A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < A.row_threads) {
     if (A.a_out == nullptr) return;
-    const int64_t row = t / KV;
+    const int64_t row = div_kv(t, KV);
     const int kv = (int)(t - row * KV);
     const int64_t off = row * A.K + (int64_t)kv * V;
     T acc[V], accl[V];
@@ -101,7 +110,7 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(const FwdArgs<T> A) {
   if (A.y_out == nullptr) return;
   const int64_t g = t - A.row_threads;
   if (g >= (int64_t)A.n_obs * KV) return;
-  const int d = (int)(g / KV);
+  const int d = (int)div_kv(g, KV);
   const int kv = (int)(g - (int64_t)d * KV);
   T acc[V];
 #pragma unroll
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(256) adj_step_kernel(const AdjArgs<T> A) {
   const int KV = A.K / V;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.row_threads) return;
-  const int64_t row = t / KV;
+  const int64_t row = div_kv(t, KV);
   const int kv = (int)(t - row * KV);
   const int64_t off = row * A.K + (int64_t)kv * V;
   T ak[V], akl[V], bq[V], bql[V], inj[V];
@@ -254,6 +263,7 @@ struct Step3Args {
   int64_t row_threads;
   int32_t prev_mode;  // 0: xp is a buffer; 1: xp equals x (zero velocity); 2: xp is zero
   int32_t stage_cap;  // shared-memory entries per block (STAGE kernels)
+  int64_t pf_rows;    // > 0: prefetch into L2 the streamed data of the rows this many rows ahead
   const float2* __restrict__ hl;     // (hi, lo) pairs of FP32 split coefficients
   const int32_t* __restrict__ order; // processing order of the rows (nullptr: 0, 1, 2, ...)
   // fixed-width copy of the rows (ELL kernel)
@@ -345,9 +355,9 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
     if (tb0 < A.row_threads) {  // uniform over the block
       C* s_val = reinterpret_cast<C*>(smem);
       uint32_t* s_col = reinterpret_cast<uint32_t*>(smem + ((size_t)A.stage_cap * sizeof(C) + 15) / 16 * 16);
-      const int64_t r0 = tb0 / KV;
+      const int64_t r0 = div_kv(tb0, KV);
       const int64_t tl = (tb0 + (int64_t)blockDim.x < A.row_threads ? tb0 + (int64_t)blockDim.x : A.row_threads) - 1;
-      const int64_t r1 = tl / KV;
+      const int64_t r1 = div_kv(tl, KV);
       base = A.ptr[r0];
       const int n = (int)(A.ptr[r1 + 1] - base);
       for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -360,7 +370,7 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
     }
   }
   if (t < A.row_threads) {
-    const int64_t row = t / KV;
+    const int64_t row = div_kv(t, KV);
     const int kv = (int)(t - row * KV);
     const int64_t off = row * A.K + (int64_t)kv * V;
     T acc[V], accl[V];
@@ -383,7 +393,7 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
 #pragma unroll 4
       for (int e = e0; e < eA; ++e) {
         const uint32_t j = mcol[e] & kIdxMask;
-        const Pack<T, V> xj = ld<T, V>(xk + j * Ku);
+        const Pack<T, V> xj = ld<T, V>(xk + (size_t)j * Ku);
         coef_fma<T, V, SPLIT>(coef(e), xj, acc, accl);
       }
       if (eB < eA && A.prev_mode != 2) {
@@ -392,7 +402,7 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
         const T* pk = (A.prev_mode == 0 ? A.xp : A.x) + (int64_t)kv * V;
         for (int e = eB; e < eA; ++e) {
           const uint32_t j = mcol[e] & kIdxMask;
-          const Pack<T, V> pj = ld<T, V>(pk + j * Ku);
+          const Pack<T, V> pj = ld<T, V>(pk + (size_t)j * Ku);
           Pack<T, V> neg;
 #pragma unroll
           for (int q = 0; q < V; ++q) neg.v[q] = -pj.v[q];
@@ -454,7 +464,7 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
   if (A.y_out == nullptr) return;
   const int64_t g = t - A.row_threads;
   if (g >= (int64_t)A.n_obs * KV) return;
-  const int d = (int)(g / KV);
+  const int d = (int)div_kv(g, KV);
   const int kv = (int)(g - (int64_t)d * KV);
   T acc[V];
 #pragma unroll
@@ -549,17 +559,53 @@ __device__ __forceinline__ void ld_pairs(const float* p, u64 (&out)[P]) {
   }
 }
 
+// Bulk prefetch into L2 (a hint: no data reaches the SM).  Both the address and
+// the size are rounded to the 16-byte granularity the instruction requires.
+__device__ __forceinline__ void l2_prefetch(const void* p, int64_t bytes) {
+  const uintptr_t a = (uintptr_t)p, a16 = (a + 15) & ~(uintptr_t)15;
+  bytes -= (int64_t)(a16 - a);
+  if (bytes < 16) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a16), "r"((uint32_t)(bytes & ~(int64_t)15))
+               : "memory");
+}
+
+// Called by one thread per block: prefetch the data that the block covering
+// rows [r0, r1) + A.pf_rows will stream (its own state rows x_s and x_{s-1} and
+// its row metadata), so that the block which runs on this SM one resident wave
+// later finds them in L2 instead of waiting on DRAM.  Rows in natural order only.
+template <bool ELL>
+__device__ __noinline__ void prefetch_ahead(const Step3Args<float>& A, int64_t r0, int64_t r1) {
+  r0 += A.pf_rows;
+  r1 = min(r1 + A.pf_rows, A.N);
+  if (r0 >= r1) return;
+  const int64_t n = r1 - r0, rb = (int64_t)A.K * 4;
+  if (A.x) l2_prefetch(A.x + r0 * A.K, n * rb);
+  if (A.prev_mode == 0) l2_prefetch(A.xp + r0 * A.K, n * rb);
+  if constexpr (ELL) {
+    l2_prefetch(A.ell_desc + r0, n * 4);
+    l2_prefetch(A.ell_col + r0 * 8, n * 32);
+    l2_prefetch(A.ell_hl + r0 * 8, n * 64);
+  } else {
+    const int64_t e0 = A.ptr[r0], e1 = A.ptr[r1];
+    l2_prefetch(A.ptr + r0, n * 4);
+    l2_prefetch(A.col + e0, (e1 - e0) * 4);
+    l2_prefetch(A.hl + e0, (e1 - e0) * 8);
+  }
+}
+
 template <int V, int CH, bool ADJ, bool EARLY>
 __device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int64_t tb0) {
   constexpr int P = V / 2;  // CH = entries per chunk
   const int KV = A.K / V;
   const int64_t t = tb0 + threadIdx.x;
+  if (A.pf_rows > 0 && threadIdx.x == 0 && tb0 < A.row_threads)
+    prefetch_ahead<false>(A, div_kv(tb0, KV), div_kv(min(tb0 + (int64_t)blockDim.x, A.row_threads), KV) + 1);
   if (t >= A.row_threads) {
     // sensor gather of the input state (forward launches only)
     if (A.y_out == nullptr) return;
     const int64_t g = t - A.row_threads;
     if (g >= (int64_t)A.n_obs * KV) return;
-    const int d = (int)(g / KV);
+    const int d = (int)div_kv(g, KV);
     const int kv = (int)(g - (int64_t)d * KV);
     float acc[V];
 #pragma unroll
@@ -584,7 +630,7 @@ __device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int
     st<float, V>(A.y_out + (int64_t)d * A.K + (int64_t)kv * V, y);
     return;
   }
-  const int64_t rowi = t / KV;
+  const int64_t rowi = div_kv(t, KV);
   const int kv = (int)(t - rowi * KV);
   // rows are independent within a step, so they may be processed in any order;
   // a spatially local order (Z-order of the nodes) keeps a block's neighbour
@@ -634,7 +680,7 @@ __device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int
 #pragma unroll
       for (int q = 0; q < CH; ++q) {
         if (e + q < eA) {
-          ld_pairs<P>(xk + j[q] * Ku, x[q]);
+          ld_pairs<P>(xk + (size_t)j[q] * Ku, x[q]);
         } else {
 #pragma unroll
           for (int p = 0; p < P; ++p) x[q][p] = 0ull;
@@ -665,7 +711,7 @@ __device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int
       for (int e = eB; e < eA; ++e) {
         const float2 c = A.hl[e];
         u64 x[P];
-        ld_pairs<P>(pk + (A.col[e] & kIdxMask) * Ku, x);
+        ld_pairs<P>(pk + (size_t)(A.col[e] & kIdxMask) * Ku, x);
         const u64 ch = dup2(-c.x), cl = dup2(-c.y);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -741,7 +787,7 @@ __global__ void __launch_bounds__(256) adj3_finish_kernel(int64_t row_threads, i
   const int KV = K / V;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= row_threads) return;
-  const int64_t row = t / KV;
+  const int64_t row = div_kv(t, KV);
   const int kv = (int)(t - row * KV);
   const int64_t off = row * K + (int64_t)kv * V;
   T acc[V];

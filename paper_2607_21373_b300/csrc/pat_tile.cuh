@@ -38,7 +38,7 @@ template <int V>
 __device__ __forceinline__ void gather_obs(const Step3Args<float>& A, int64_t g) {
   const int KV = A.K / V;
   if (A.y_out == nullptr || g >= (int64_t)A.n_obs * KV) return;
-  const int d = (int)(g / KV);
+  const int d = (int)div_kv(g, KV);
   const int kv = (int)(g - (int64_t)d * KV);
   float acc[V];
 #pragma unroll
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, 
       const float2 c = A.hl[e];
       u64 x[P];
       if (A.prev_mode == 0) {
-        ld_pairs<P>(A.xp + (int64_t)kv * V + (A.col[e] & kIdxMask) * Ku, x);
+        ld_pairs<P>(A.xp + (int64_t)kv * V + (size_t)(A.col[e] & kIdxMask) * Ku, x);
       } else {
         const float* sp = sk + (size_t)Tl.slot[e] * A.K;  // xp = x
         const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sp);
@@ -244,59 +244,108 @@ __device__ __forceinline__ void ell_entry(const Step3Args<float>& A, int64_t row
   }
 }
 
+// Four consecutive fixed-width entries of a row (columns c, (hi, lo) pairs in
+// ha, hb; only the first n < 4 are used when n < 4): gather the V samples of
+// each source row, then accumulate hi and lo products in entry order.
+template <int P>
+__device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, float4 ha, float4 hb, int n,
+                                         u64 (&acc)[P], u64 (&accl)[P]) {
+  const uint32_t cols[4] = {c.x, c.y, c.z, c.w};
+  const float2 cf[4] = {make_float2(ha.x, ha.y), make_float2(ha.z, ha.w), make_float2(hb.x, hb.y),
+                        make_float2(hb.z, hb.w)};
+  u64 x[4][P];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < n) {
+      ld_pairs<P>(xk + (size_t)cols[q] * Ku, x[q]);
+    } else {
+#pragma unroll
+      for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 cc = q < n ? cf[q] : make_float2(0.0f, 0.0f);
+    const u64 ch = dup2(cc.x), cl = dup2(cc.y);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      acc[p] = ffma2(ch, x[q][p], acc[p]);
+      accl[p] = ffma2(cl, x[q][p], accl[p]);
+    }
+  }
+}
+
 template <int V, bool ADJ>
 __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
   constexpr int P = V / 2;
   const int KV = A.K / V;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (A.pf_rows > 0 && threadIdx.x == 0 && t < A.row_threads)
+    prefetch_ahead<true>(A, div_kv(t, KV), div_kv(min(t + (int64_t)blockDim.x, A.row_threads), KV) + 1);
   if (t >= A.row_threads) {
     gather_obs<V>(A, t - A.row_threads);
     return;
   }
-  const int64_t rowi = t / KV;
+  const int64_t rowi = div_kv(t, KV);
   const int kv = (int)(t - rowi * KV);
   const int64_t row = A.order ? (int64_t)A.order[rowi] : rowi;
   const int64_t off = row * A.K + (int64_t)kv * V;
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;  // stiffness + boundary entries
-  const uint4 c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
-  const uint4 c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
-  const float4 h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
-  const float4 h23 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 2);
-  const float4 h45 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4);
-  const float4 h67 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 6);
-  const uint32_t cols[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-  const float2 cf[8] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
-                        make_float2(h23.z, h23.w), make_float2(h45.x, h45.y), make_float2(h45.z, h45.w),
-                        make_float2(h67.x, h67.y), make_float2(h67.z, h67.w)};
+  // V = 8: all 8 columns and coefficient pairs loaded up front; V = 4: per
+  // half of the row, which needs fewer registers (same arithmetic order)
+  uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = c0;
+  float4 h01 = make_float4(0.f, 0.f, 0.f, 0.f), h23 = h01, h45 = h01, h67 = h01;
+  if constexpr (V == 8) {
+    c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
+    c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
+    h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
+    h23 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 2);
+    h45 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4);
+    h67 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 6);
+  }
   const uint32_t Ku = (uint32_t)A.K;
   u64 acc[P], accl[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
   if (A.x) {
     const float* xk = A.x + (int64_t)kv * V;
+    if constexpr (V == 8) {
+      const uint32_t cols[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+      const float2 cf[8] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
+                            make_float2(h23.z, h23.w), make_float2(h45.x, h45.y), make_float2(h45.z, h45.w),
+                            make_float2(h67.x, h67.y), make_float2(h67.z, h67.w)};
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      u64 x[4][P];
+      for (int h = 0; h < 2; ++h) {
+        u64 x[4][P];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (4 * h + q < eA) {
-          ld_pairs<P>(xk + cols[4 * h + q] * Ku, x[q]);
-        } else {
+        for (int q = 0; q < 4; ++q) {
+          if (4 * h + q < eA) {
+            ld_pairs<P>(xk + (size_t)cols[4 * h + q] * Ku, x[q]);
+          } else {
 #pragma unroll
-          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+            for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 c = (4 * h + q < eA) ? cf[4 * h + q] : make_float2(0.0f, 0.0f);
+          const u64 ch = dup2(c.x), cl = dup2(c.y);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            acc[p] = ffma2(ch, x[q][p], acc[p]);
+            accl[p] = ffma2(cl, x[q][p], accl[p]);
+          }
         }
       }
+    } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 c = (4 * h + q < eA) ? cf[4 * h + q] : make_float2(0.0f, 0.0f);
-        const u64 ch = dup2(c.x), cl = dup2(c.y);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          acc[p] = ffma2(ch, x[q][p], acc[p]);
-          accl[p] = ffma2(cl, x[q][p], accl[p]);
-        }
+      for (int h = 0; h < 2; ++h) {
+        const uint4 cq = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4 * h);
+        const float4 ha = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4 * h);
+        const float4 hb = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4 * h + 2);
+        ell_half<P>(xk, Ku, cq, ha, hb, eA - 4 * h, acc, accl);
       }
     }
     for (int e = 8; e < eA; ++e) {  // overflow of long (boundary) rows
@@ -304,7 +353,7 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
       float2 c;
       ell_entry<V>(A, row, e, &col, &c);
       u64 x[P];
-      ld_pairs<P>(xk + col * Ku, x);
+      ld_pairs<P>(xk + (size_t)col * Ku, x);
       const u64 ch = dup2(c.x), cl = dup2(c.y);
 #pragma unroll
       for (int p = 0; p < P; ++p) {
@@ -320,7 +369,7 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
         float2 c;
         ell_entry<V>(A, row, e, &col, &c);
         u64 x[P];
-        ld_pairs<P>(pk + col * Ku, x);
+        ld_pairs<P>(pk + (size_t)col * Ku, x);
         const u64 ch = dup2(-c.x), cl = dup2(-c.y);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -375,7 +424,14 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
 }
 
 template <int V, bool ADJ>
-__global__ void __launch_bounds__(256) step3e_kernel(const Step3Args<float> A) {
+__global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3Args<float> A) {
+  step3e_body<V, ADJ>(A);
+}
+
+// the same with at least MINB resident 256-thread blocks per SM asked of the
+// compiler: more warps, hence more loads in flight, at the cost of registers
+template <int V, bool ADJ, int MINB>
+__global__ void __launch_bounds__(256, MINB) step3e_occ_kernel(const Step3Args<float> A) {
   step3e_body<V, ADJ>(A);
 }
 
@@ -491,7 +547,7 @@ __global__ void __launch_bounds__(512) step3p_kernel(const Step3Args<float> A, c
           const float2 c = A.hl[e];
           u64 x[P];
           if (A.prev_mode == 0) {
-            ld_pairs<P>(A.xp + (int64_t)kv * V + (A.col[e] & kIdxMask) * Ku, x);
+            ld_pairs<P>(A.xp + (int64_t)kv * V + (size_t)(A.col[e] & kIdxMask) * Ku, x);
           } else {
             const float* sp = sk + (size_t)Tl.slot[e] * A.K;  // xp = x
             const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(sp);
