@@ -213,7 +213,8 @@ def run_ours(a, rank, world, local_rank, dist):
     forced = {"tiled": dict(V=8, packed=2), "v8c2": dict(V=8, packed=1, chunk=2),
               "v4c4": dict(V=4, packed=1, chunk=4), "v8c2z": dict(V=8, packed=1, chunk=2, zorder=True),
               "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3), "pipe": dict(V=8, packed=4),
-              "ell8pf": dict(V=8, packed=3, prefetch=1)}.get(a.variant)
+              "ell8pf": dict(V=8, packed=3, prefetch=1),
+              "ell8p": dict(V=8, packed=3, persistent=True)}.get(a.variant)
     if forced:
         for d in ("fwd", "adj"):
             mesh.select_variant(K, d, **forced)
@@ -298,7 +299,8 @@ def run_ours(a, rank, world, local_rank, dist):
         if e.get("packed") == 4:
             return "step3p_kernel<%s> (persistent double-buffered tiles)" % ("true" if adj else "false")
         if e.get("packed") == 3:
-            return "step3e_kernel<%d,%s>" % (e["V"], "true" if adj else "false")
+            kind = "step3e_persist_kernel" if e.get("persistent") else "step3e_kernel"
+            return "%s<%d,%s>" % (kind, e["V"], "true" if adj else "false")
         if e.get("packed"):
             return "step3f_kernel<%d,%d,%s>%s" % (e["V"], e.get("chunk", 4), "true" if adj else "false",
                                                   " (Z-order rows)" if e.get("zorder") else "")

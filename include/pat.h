@@ -306,16 +306,18 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * >= pat_workspace_bytes(mesh, 2, K); its CGLS state is overwritten), timed
  * with CUDA events on `stream`.  The fastest variant per direction is used by
  * every later call with this K on this mesh.  table (host, may be NULL)
- * receives up to 64 entries {direction 0 fwd / 1 adj, V, staged, packed, chunk,
+ * receives up to 128 entries {direction 0 fwd / 1 adj, V, staged, packed, chunk,
  * min_blocks (resident blocks per SM asked of the compiler), early (own values
  * loaded before the row walk), zorder (rows processed in Z-order of the node
  * coordinates), big_blocks (1024-thread blocks), prefetch (0: off; n: each block
  * first asks L2 to prefetch, by bulk prefetch, the state rows and row metadata
- * of the rows n resident waves ahead), us per step};
+ * of the rows n resident waves ahead), persistent (fixed-width kernel only: a
+ * grid of resident blocks whose warps each walk 32-thread chunks with a stride
+ * of the grid's warps; prefetch then counts strides), us per step};
  * *n_entries the number of variants timed.  Synchronises the stream.
  */
 typedef struct {
-  int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch;
+  int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent;
   double us_per_step;
 } pat_tune_entry;
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,

@@ -106,6 +106,7 @@ struct TuneCfg {
   int order = 0;   // packed kernel: process rows in Z-order of the node coordinates
   int big = 0;     // packed kernels: 1024-thread blocks
   int pf = 0;      // packed kernels: L2 prefetch distance in resident waves (0: off)
+  int persist = 0; // fixed-width kernel: persistent warps walking 32-thread chunks
 };
 
 struct DeviceMesh {

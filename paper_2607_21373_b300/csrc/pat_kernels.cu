@@ -278,26 +278,26 @@ static bool launch_pipelined(const DeviceMesh& m, const Step3Args<float>& a, cud
   return true;
 }
 
+// Resident blocks per SM of kernel `fn` with `bdim`-thread blocks (cached).
+static int resident_blocks(const void* fn, int bdim) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({fn, bdim});
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bdim, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 0;
+  }
+  cache[{fn, bdim}] = per_sm;
+  return per_sm;
+}
+
 // Rows covered by one resident wave of kernel `fn` launched with `bdim`-thread
 // blocks, KV threads per row (the L2 prefetch distance of one wave).
 static int64_t wave_rows(const void* fn, int bdim, int KV) {
-  static std::mutex mu;
-  static std::map<const void*, int> cache;
-  int per_sm = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(fn);
-    if (it != cache.end()) {
-      per_sm = it->second;
-    } else {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bdim, 0) != cudaSuccess) {
-        cudaGetLastError();
-        per_sm = 0;
-      }
-      cache[fn] = per_sm;
-    }
-  }
-  return (int64_t)per_sm * sm_count() * bdim / std::max(KV, 1);
+  return (int64_t)resident_blocks(fn, bdim) * sm_count() * bdim / std::max(KV, 1);
 }
 
 template <typename T, int V, bool SPLIT, bool ADJ>
@@ -332,12 +332,21 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.ovf_col = E.ovf_col;
       a.ovf_hl = E.ovf_hl;
       a.order = c.order ? m.row_order : nullptr;
-      if (c.big) {
+      if (c.persist) {
+        const int64_t n_chunks = (threads + 31) / 32;
+        const int per_sm = std::max(1, resident_blocks((const void*)step3e_persist_kernel<V, ADJ>, 256));
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
+        a.pf_rows = (c.pf && !a.order) ? c.pf : 0;
+        step3e_persist_kernel<V, ADJ><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+      } else if (c.big) {
         const int64_t bb = (threads + 1023) / 1024;
         step3e_big_kernel<V, ADJ><<<(unsigned)bb, 1024, 0, st>>>(a);
       } else if (c.minb == 6 && V == 4) {
-        if (c.pf && !a.order) a.pf_rows = c.pf * wave_rows((const void*)step3e_occ_kernel<V, ADJ, 6>, 256, a.K / V);
-        step3e_occ_kernel<V, ADJ, 6><<<(unsigned)blocks, 256, 0, st>>>(a);
+        if constexpr (V == 4) {
+          if (c.pf && !a.order)
+            a.pf_rows = c.pf * wave_rows((const void*)step3e_occ_kernel<V, ADJ, 6>, 256, a.K / V);
+          step3e_occ_kernel<V, ADJ, 6><<<(unsigned)blocks, 256, 0, st>>>(a);
+        }
       } else {
         if (c.pf && !a.order) a.pf_rows = c.pf * wave_rows((const void*)step3e_kernel<V, ADJ>, 256, a.K / V);
         step3e_kernel<V, ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
@@ -1135,7 +1144,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 23; ++variant_id) {
+      for (int variant_id = 0; variant_id < 26; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1148,12 +1157,13 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 18, 19: fixed-width, L2 prefetch of the rows one / two resident waves ahead;
         // 20, 21: packed chunks of 2 / 4, L2 prefetch one wave ahead
         // 22: fixed-width, >= 6 resident blocks per SM, L2 prefetch one wave ahead
+        // 23, 24, 25: fixed-width, persistent warps, L2 prefetch 1 / 2 / no strides ahead
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
                                : (variant_id == 9 ? 2
                                   : (variant_id == 12 || variant_id == 15 || variant_id == 17 ||
-                                     variant_id == 18 || variant_id == 19 || variant_id == 22)
+                                     variant_id == 18 || variant_id == 19 || variant_id >= 22)
                                       ? 3
                                       : (variant_id == 13 ? 4 : 0)),
                   stage = variant_id == 7;
@@ -1163,9 +1173,11 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
                               : (variant_id == 2 ? 8 : 4);
         const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
         const int big = (variant_id >= 14 && variant_id <= 17) ? 1 : 0;
-        const int pf = variant_id == 19 ? 2 : (variant_id == 18 || variant_id >= 20) ? 1 : 0;
+        const int pf = (variant_id == 19 || variant_id == 24) ? 2
+                       : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23)) ? 1 : 0;
+        const int persist = variant_id >= 23 ? 1 : 0;
         if (variant_id == 22 && V != 4) continue;
-        if (pf && V == 1) continue;
+        if ((pf || persist) && V == 1) continue;
         if (big && V != 8) continue;
         const int minb = (variant_id == 5 || variant_id == 6 || variant_id == 22) ? 6 : 1;
         const int early = (variant_id == 3 || variant_id == 4) ? 1 : 0;
@@ -1191,13 +1203,14 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.order = zorder;
         g_force.big = big;
         g_force.pf = pf;
+        g_force.persist = persist;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
         g_force_on = false;
         if (s) return s;
-        if (table && n < 64)
-          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf, (double)us};
+        if (table && n < 128)
+          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf, persist, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

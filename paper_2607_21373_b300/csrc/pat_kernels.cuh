@@ -569,14 +569,13 @@ __device__ __forceinline__ void l2_prefetch(const void* p, int64_t bytes) {
                : "memory");
 }
 
-// Called by one thread per block: prefetch the data that the block covering
-// rows [r0, r1) + A.pf_rows will stream (its own state rows x_s and x_{s-1} and
-// its row metadata), so that the block which runs on this SM one resident wave
-// later finds them in L2 instead of waiting on DRAM.  Rows in natural order only.
+// Called by one thread: prefetch into L2 the data that the rows [r0, r1) will
+// stream (their own state rows x_s and x_{s-1} and their row metadata), so that
+// the threads which take those rows later find them in L2 instead of waiting
+// on DRAM.  Rows in natural order only.
 template <bool ELL>
 __device__ __noinline__ void prefetch_ahead(const Step3Args<float>& A, int64_t r0, int64_t r1) {
-  r0 += A.pf_rows;
-  r1 = min(r1 + A.pf_rows, A.N);
+  r1 = min(r1, A.N);
   if (r0 >= r1) return;
   const int64_t n = r1 - r0, rb = (int64_t)A.K * 4;
   if (A.x) l2_prefetch(A.x + r0 * A.K, n * rb);
@@ -599,7 +598,8 @@ __device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int
   const int KV = A.K / V;
   const int64_t t = tb0 + threadIdx.x;
   if (A.pf_rows > 0 && threadIdx.x == 0 && tb0 < A.row_threads)
-    prefetch_ahead<false>(A, div_kv(tb0, KV), div_kv(min(tb0 + (int64_t)blockDim.x, A.row_threads), KV) + 1);
+    prefetch_ahead<false>(A, div_kv(tb0, KV) + A.pf_rows,
+                          div_kv(min(tb0 + (int64_t)blockDim.x, A.row_threads), KV) + 1 + A.pf_rows);
   if (t >= A.row_threads) {
     // sensor gather of the input state (forward launches only)
     if (A.y_out == nullptr) return;

@@ -275,13 +275,46 @@ __device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, 
   }
 }
 
+// Sample layout of the fixed-width kernel's threads.  With V = 8 a thread's
+// samples are two runs of 4: kv*4 .. kv*4+3 and K/2 + kv*4 .. K/2 + kv*4+3, so
+// that one 16-byte load per lane covers, across the 8 lanes of a row, one
+// contiguous 128-byte span of a source row (instead of every other 16 bytes of
+// 256); with V = 4 a thread's 4 samples are one run.  Only the assignment of
+// samples to threads changes: every sample's arithmetic is the same.
+template <int V>
+__device__ __forceinline__ void ld_runs(const float* p, int64_t hs, u64 (&out)[V / 2]) {
+  const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(p);
+  out[0] = v0.x;
+  out[1] = v0.y;
+  if constexpr (V == 8) {
+    const ulonglong2 v1 = *reinterpret_cast<const ulonglong2*>(p + hs);
+    out[2] = v1.x;
+    out[3] = v1.y;
+  }
+}
+
+template <int V>
+__device__ __forceinline__ Pack<float, V> ld_run_pack(const float* p, int64_t hs) {
+  Pack<float, V> r;
+  const float4 v0 = *reinterpret_cast<const float4*>(p);
+  r.v[0] = v0.x, r.v[1] = v0.y, r.v[2] = v0.z, r.v[3] = v0.w;
+  if constexpr (V == 8) {
+    const float4 v1 = *reinterpret_cast<const float4*>(p + hs);
+    r.v[4] = v1.x, r.v[5] = v1.y, r.v[6] = v1.z, r.v[7] = v1.w;
+  }
+  return r;
+}
+
+template <int V>
+__device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<float, V>& x) {
+  *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+  if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
+}
+
 template <int V, bool ADJ>
-__device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
+__device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t) {
   constexpr int P = V / 2;
   const int KV = A.K / V;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (A.pf_rows > 0 && threadIdx.x == 0 && t < A.row_threads)
-    prefetch_ahead<true>(A, div_kv(t, KV), div_kv(min(t + (int64_t)blockDim.x, A.row_threads), KV) + 1);
   if (t >= A.row_threads) {
     gather_obs<V>(A, t - A.row_threads);
     return;
@@ -289,7 +322,10 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
   const int64_t rowi = div_kv(t, KV);
   const int kv = (int)(t - rowi * KV);
   const int64_t row = A.order ? (int64_t)A.order[rowi] : rowi;
-  const int64_t off = row * A.K + (int64_t)kv * V;
+  static_assert(V == 4 || V == 8, "fixed-width kernel: V = 4 or 8");
+  const int64_t hs = V == 8 ? A.K / 2 : 0;  // offset of a thread's second run of samples
+  const int64_t base = (int64_t)kv * 4;     // offset of its first run
+  const int64_t off = row * A.K + base;
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;  // stiffness + boundary entries
@@ -310,7 +346,7 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
 #pragma unroll
   for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
   if (A.x) {
-    const float* xk = A.x + (int64_t)kv * V;
+    const float* xk = A.x + base;
     if constexpr (V == 8) {
       const uint32_t cols[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
       const float2 cf[8] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
@@ -322,7 +358,7 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (4 * h + q < eA) {
-            ld_pairs<P>(xk + (size_t)cols[4 * h + q] * Ku, x[q]);
+            ld_runs<V>(xk + (size_t)cols[4 * h + q] * Ku, hs, x[q]);
           } else {
 #pragma unroll
             for (int p = 0; p < P; ++p) x[q][p] = 0ull;
@@ -353,7 +389,7 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
       float2 c;
       ell_entry<V>(A, row, e, &col, &c);
       u64 x[P];
-      ld_pairs<P>(xk + (size_t)col * Ku, x);
+      ld_runs<V>(xk + (size_t)col * Ku, hs, x);
       const u64 ch = dup2(c.x), cl = dup2(c.y);
 #pragma unroll
       for (int p = 0; p < P; ++p) {
@@ -363,13 +399,13 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
     }
     if (nb > 0 && A.prev_mode != 2) {
       // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
-      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + (int64_t)kv * V;
+      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + base;
       for (int e = eA - nb; e < eA; ++e) {
         uint32_t col;
         float2 c;
         ell_entry<V>(A, row, e, &col, &c);
         u64 x[P];
-        ld_pairs<P>(pk + (size_t)col * Ku, x);
+        ld_runs<V>(pk + (size_t)col * Ku, hs, x);
         const u64 ch = dup2(-c.x), cl = dup2(-c.y);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -389,12 +425,12 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
       ell_entry<V>(A, row, e, &col, &c);
       const int64_t j = (int64_t)col;
       if (A.ya) {
-        const Pack<float, V> y = ld<float, V>(A.ya + j * A.K + (int64_t)kv * V);
+        const Pack<float, V> y = ld_run_pack<V>(A.ya + j * A.K + base, hs);
 #pragma unroll
         for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
       }
       if (A.yb) {
-        const Pack<float, V> y = ld<float, V>(A.yb + j * A.K + (int64_t)kv * V);
+        const Pack<float, V> y = ld_run_pack<V>(A.yb + j * A.K + base, hs);
 #pragma unroll
         for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
       }
@@ -402,13 +438,13 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
   }
   Pack<float, V> xi, xpi, xo;
   if (A.x) {
-    xi = ld<float, V>(A.x + off);
+    xi = ld_run_pack<V>(A.x + off, hs);
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
   }
   if (A.prev_mode == 0) {
-    xpi = ld<float, V>(A.xp + off);
+    xpi = ld_run_pack<V>(A.xp + off, hs);
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
@@ -420,12 +456,70 @@ __device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
     xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
     xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
   }
-  st<float, V>(A.xn + off, xo);
+  st_run_pack<V>(A.xn + off, hs, xo);
+}
+
+template <int V, bool ADJ>
+__device__ __forceinline__ void step3e_body(const Step3Args<float>& A) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (A.pf_rows > 0 && threadIdx.x == 0 && t < A.row_threads) {
+    const int KV = A.K / V;
+    prefetch_ahead<true>(A, div_kv(t, KV) + A.pf_rows,
+                         div_kv(min(t + (int64_t)blockDim.x, A.row_threads), KV) + 1 + A.pf_rows);
+  }
+  step3e_row<V, ADJ>(A, t);
 }
 
 template <int V, bool ADJ>
 __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3Args<float> A) {
   step3e_body<V, ADJ>(A);
+}
+
+// The warp's lanes each ask L2 to prefetch one 128-byte line of the data that
+// rows [r0, r1) stream: own state rows x_s and x_{s-1}, then the fixed-width
+// row metadata (descriptor, columns, coefficient pairs).  No divergence: every
+// lane issues at most a few single-line prefetches.
+__device__ __forceinline__ void prefetch_lines(const Step3Args<float>& A, int64_t r0, int64_t r1, int lane) {
+  r1 = min(r1, A.N);
+  if (r0 >= r1) return;
+  const int64_t n = r1 - r0;
+  const char* base[5] = {reinterpret_cast<const char*>(A.x + r0 * A.K),
+                         reinterpret_cast<const char*>(A.xp + r0 * A.K),
+                         reinterpret_cast<const char*>(A.ell_desc + r0),
+                         reinterpret_cast<const char*>(A.ell_col + r0 * 8),
+                         reinterpret_cast<const char*>(A.ell_hl + r0 * 8)};
+  const int64_t bytes[5] = {A.x ? n * A.K * 4 : 0, A.prev_mode == 0 ? n * A.K * 4 : 0, n * 4, n * 32, n * 64};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    if (bytes[s] == 0) continue;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(base[s]);
+    const uintptr_t l0 = a0 >> 7, l1 = (a0 + (uintptr_t)bytes[s] - 1) >> 7;
+    for (uintptr_t l = l0 + (uintptr_t)lane; l <= l1; l += 32) {
+      const uintptr_t a = l == l0 ? a0 : (l << 7);  // inside [a0, a0 + bytes)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+  }
+}
+
+// Persistent form: a grid of resident blocks whose warps each walk 32-thread
+// chunks c, c + S, c + 2S, ... (S = warps in the grid).  A warp takes its next
+// chunk as soon as it is done, instead of idling until every warp of its block
+// has finished; with A.pf_rows = d > 0 it first asks L2 for the rows of the
+// chunk it will take d strides later.
+template <int V, bool ADJ>
+__global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_persist_kernel(const Step3Args<float> A,
+                                                                             int64_t n_chunks) {
+  const int KV = A.K / V;
+  const int lane = threadIdx.x & 31;
+  const int64_t S = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += S) {
+    if (A.pf_rows > 0) {
+      const int64_t t0 = (c + A.pf_rows * S) * 32;
+      if (t0 < A.row_threads)
+        prefetch_lines(A, div_kv(t0, KV), div_kv(min(t0 + 32, A.row_threads) - 1, KV) + 1, lane);
+    }
+    step3e_row<V, ADJ>(A, c * 32 + lane);
+  }
 }
 
 // the same with at least MINB resident 256-thread blocks per SM asked of the
