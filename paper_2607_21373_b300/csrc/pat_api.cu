@@ -873,6 +873,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.big = v->big_blocks && v->V == 8 && (v->packed == 1 || v->packed == 3);
   c.pf = v->prefetch;
   c.persist = v->persistent && v->packed == 3 && v->V != 1;
+  c.pdl = c.persist && v->pdl;
   {
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;

@@ -107,6 +107,7 @@ struct TuneCfg {
   int big = 0;     // packed kernels: 1024-thread blocks
   int pf = 0;      // packed kernels: L2 prefetch distance in resident waves (0: off)
   int persist = 0; // fixed-width kernel: persistent warps walking 32-thread chunks
+  int pdl = 0;     // persistent kernel: programmatic dependent launch
 };
 
 struct DeviceMesh {

@@ -337,7 +337,24 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
         const int per_sm = std::max(1, resident_blocks((const void*)step3e_persist_kernel<V, ADJ>, 256));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
         a.pf_rows = (c.pf && !a.order) ? c.pf : 0;
-        step3e_persist_kernel<V, ADJ><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+        if (c.pdl) {  // programmatic dependent launch: overlap this grid's start with the previous step's drain
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3((unsigned)grid);
+          cfg.blockDim = dim3(256);
+          cfg.dynamicSmemBytes = 0;
+          cfg.stream = st;
+          cudaLaunchAttribute attr[1];
+          attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+          attr[0].val.programmaticStreamSerializationAllowed = 1;
+          cfg.attrs = attr;
+          cfg.numAttrs = 1;
+          if (cudaLaunchKernelEx(&cfg, step3e_persist_kernel<V, ADJ>, a, n_chunks) != cudaSuccess) {
+            cudaGetLastError();  // attribute refused: plain launch
+            step3e_persist_kernel<V, ADJ><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+          }
+        } else {
+          step3e_persist_kernel<V, ADJ><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+        }
       } else if (c.big) {
         const int64_t bb = (threads + 1023) / 1024;
         step3e_big_kernel<V, ADJ><<<(unsigned)bb, 1024, 0, st>>>(a);
@@ -1144,7 +1161,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 26; ++variant_id) {
+      for (int variant_id = 0; variant_id < 28; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1157,7 +1174,8 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 18, 19: fixed-width, L2 prefetch of the rows one / two resident waves ahead;
         // 20, 21: packed chunks of 2 / 4, L2 prefetch one wave ahead
         // 22: fixed-width, >= 6 resident blocks per SM, L2 prefetch one wave ahead
-        // 23, 24, 25: fixed-width, persistent warps, L2 prefetch 1 / 2 / no strides ahead
+        // 23, 24, 25: fixed-width, persistent warps, L2 prefetch 1 / 2 / no strides ahead;
+        // 26, 27: fixed-width, persistent, programmatic dependent launch, no / 1 stride prefetch
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
@@ -1174,8 +1192,9 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
         const int big = (variant_id >= 14 && variant_id <= 17) ? 1 : 0;
         const int pf = (variant_id == 19 || variant_id == 24) ? 2
-                       : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23)) ? 1 : 0;
+                       : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27) ? 1 : 0;
         const int persist = variant_id >= 23 ? 1 : 0;
+        const int pdl = variant_id >= 26 ? 1 : 0;
         if (variant_id == 22 && V != 4) continue;
         if ((pf || persist) && V == 1) continue;
         if (big && V != 8) continue;
@@ -1204,13 +1223,15 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.big = big;
         g_force.pf = pf;
         g_force.persist = persist;
+        g_force.pdl = pdl;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
         g_force_on = false;
         if (s) return s;
         if (table && n < 128)
-          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf, persist, (double)us};
+          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf, persist, pdl,
+                                    (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

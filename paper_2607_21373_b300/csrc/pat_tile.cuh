@@ -475,50 +475,31 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3
   step3e_body<V, ADJ>(A);
 }
 
-// The warp's lanes each ask L2 to prefetch one 128-byte line of the data that
-// rows [r0, r1) stream: own state rows x_s and x_{s-1}, then the fixed-width
-// row metadata (descriptor, columns, coefficient pairs).  No divergence: every
-// lane issues at most a few single-line prefetches.
-__device__ __forceinline__ void prefetch_lines(const Step3Args<float>& A, int64_t r0, int64_t r1, int lane) {
-  r1 = min(r1, A.N);
-  if (r0 >= r1) return;
-  const int64_t n = r1 - r0;
-  const char* base[5] = {reinterpret_cast<const char*>(A.x + r0 * A.K),
-                         reinterpret_cast<const char*>(A.xp + r0 * A.K),
-                         reinterpret_cast<const char*>(A.ell_desc + r0),
-                         reinterpret_cast<const char*>(A.ell_col + r0 * 8),
-                         reinterpret_cast<const char*>(A.ell_hl + r0 * 8)};
-  const int64_t bytes[5] = {A.x ? n * A.K * 4 : 0, A.prev_mode == 0 ? n * A.K * 4 : 0, n * 4, n * 32, n * 64};
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    if (bytes[s] == 0) continue;
-    const uintptr_t a0 = reinterpret_cast<uintptr_t>(base[s]);
-    const uintptr_t l0 = a0 >> 7, l1 = (a0 + (uintptr_t)bytes[s] - 1) >> 7;
-    for (uintptr_t l = l0 + (uintptr_t)lane; l <= l1; l += 32) {
-      const uintptr_t a = l == l0 ? a0 : (l << 7);  // inside [a0, a0 + bytes)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
-    }
-  }
-}
-
 // Persistent form: a grid of resident blocks whose warps each walk 32-thread
 // chunks c, c + S, c + 2S, ... (S = warps in the grid).  A warp takes its next
 // chunk as soon as it is done, instead of idling until every warp of its block
-// has finished; with A.pf_rows = d > 0 it first asks L2 for the rows of the
-// chunk it will take d strides later.
+// has finished.  With A.pf_rows = d > 0, thread 0 asks L2 (bulk prefetch) for
+// the rows of the block's chunks d strides ahead, once per stride.
+// Launched as a programmatic dependent of the previous step, the grid's blocks
+// may become resident while that step drains; griddepcontrol.wait holds them
+// until it has completed and its writes are visible (a no-op otherwise).
 template <int V, bool ADJ>
 __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_persist_kernel(const Step3Args<float> A,
                                                                              int64_t n_chunks) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int KV = A.K / V;
   const int lane = threadIdx.x & 31;
-  const int64_t S = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += S) {
-    if (A.pf_rows > 0) {
-      const int64_t t0 = (c + A.pf_rows * S) * 32;
+  const int wpb = blockDim.x >> 5;
+  const int64_t S = (int64_t)gridDim.x * wpb;
+  for (int64_t cb = (int64_t)blockIdx.x * wpb; cb < n_chunks; cb += S) {
+    if (A.pf_rows > 0 && threadIdx.x == 0) {
+      const int64_t t0 = (cb + A.pf_rows * S) * 32;
       if (t0 < A.row_threads)
-        prefetch_lines(A, div_kv(t0, KV), div_kv(min(t0 + 32, A.row_threads) - 1, KV) + 1, lane);
+        prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(min(t0 + 32 * (int64_t)wpb, A.row_threads) - 1, KV) + 1);
     }
-    step3e_row<V, ADJ>(A, c * 32 + lane);
+    const int64_t c = cb + (threadIdx.x >> 5);
+    if (c < n_chunks) step3e_row<V, ADJ>(A, c * 32 + lane);
   }
 }
 
