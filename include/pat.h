@@ -314,11 +314,14 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * of the rows n resident waves ahead), persistent (fixed-width kernel only: a
  * grid of resident blocks whose warps each walk 32-thread chunks with a stride
  * of the grid's warps; prefetch then counts strides), pdl (persistent only:
- * launched as a programmatic dependent of the previous step), us per step};
+ * launched as a programmatic dependent of the previous step), wide_loads
+ * (persistent, V = 8: each thread's 8 samples read and written by one 256-bit
+ * access), us per step};
  * *n_entries the number of variants timed.  Synchronises the stream.
  */
 typedef struct {
-  int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent, pdl;
+  int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent, pdl,
+      wide_loads;
   double us_per_step;
 } pat_tune_entry;
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,

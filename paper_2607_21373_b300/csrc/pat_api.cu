@@ -874,6 +874,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.pf = v->prefetch;
   c.persist = v->persistent && v->packed == 3 && v->V != 1;
   c.pdl = c.persist && v->pdl;
+  c.wide = c.persist && v->wide_loads && v->V == 8;
   {
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;

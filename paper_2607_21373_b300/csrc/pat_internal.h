@@ -108,6 +108,7 @@ struct TuneCfg {
   int pf = 0;      // packed kernels: L2 prefetch distance in resident waves (0: off)
   int persist = 0; // fixed-width kernel: persistent warps walking 32-thread chunks
   int pdl = 0;     // persistent kernel: programmatic dependent launch
+  int wide = 0;    // persistent kernel, V = 8: 256-bit loads of 8 contiguous samples
 };
 
 struct DeviceMesh {

@@ -300,6 +300,31 @@ static int64_t wave_rows(const void* fn, int bdim, int KV) {
   return (int64_t)resident_blocks(fn, bdim) * sm_count() * bdim / std::max(KV, 1);
 }
 
+// Persistent fixed-width launch: one resident wave of blocks, optionally as a
+// programmatic dependent of the previous kernel on the stream.
+template <int V, bool ADJ, bool W>
+static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
+  const int64_t n_chunks = (threads + 31) / 32;
+  const int per_sm = std::max(1, resident_blocks((const void*)step3e_persist_kernel<V, ADJ, W>, 256));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
+  a.pf_rows = (c.pf && !a.order) ? c.pf : 0;
+  if (c.pdl) {  // overlap this grid's start with the previous step's drain
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, step3e_persist_kernel<V, ADJ, W>, a, n_chunks) == cudaSuccess) return;
+    cudaGetLastError();  // attribute refused: plain launch
+  }
+  step3e_persist_kernel<V, ADJ, W><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+}
+
 template <typename T, int V, bool SPLIT, bool ADJ>
 static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, cudaStream_t st) {
   const int64_t blocks = (threads + 255) / 256;
@@ -333,28 +358,13 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.ovf_hl = E.ovf_hl;
       a.order = c.order ? m.row_order : nullptr;
       if (c.persist) {
-        const int64_t n_chunks = (threads + 31) / 32;
-        const int per_sm = std::max(1, resident_blocks((const void*)step3e_persist_kernel<V, ADJ>, 256));
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
-        a.pf_rows = (c.pf && !a.order) ? c.pf : 0;
-        if (c.pdl) {  // programmatic dependent launch: overlap this grid's start with the previous step's drain
-          cudaLaunchConfig_t cfg = {};
-          cfg.gridDim = dim3((unsigned)grid);
-          cfg.blockDim = dim3(256);
-          cfg.dynamicSmemBytes = 0;
-          cfg.stream = st;
-          cudaLaunchAttribute attr[1];
-          attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-          attr[0].val.programmaticStreamSerializationAllowed = 1;
-          cfg.attrs = attr;
-          cfg.numAttrs = 1;
-          if (cudaLaunchKernelEx(&cfg, step3e_persist_kernel<V, ADJ>, a, n_chunks) != cudaSuccess) {
-            cudaGetLastError();  // attribute refused: plain launch
-            step3e_persist_kernel<V, ADJ><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+        if constexpr (V == 8) {
+          if (c.wide) {
+            launch_persist<V, ADJ, true>(a, c, threads, st);
+            return;
           }
-        } else {
-          step3e_persist_kernel<V, ADJ><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
         }
+        launch_persist<V, ADJ, false>(a, c, threads, st);
       } else if (c.big) {
         const int64_t bb = (threads + 1023) / 1024;
         step3e_big_kernel<V, ADJ><<<(unsigned)bb, 1024, 0, st>>>(a);
@@ -1161,7 +1171,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 28; ++variant_id) {
+      for (int variant_id = 0; variant_id < 30; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1175,7 +1185,8 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 20, 21: packed chunks of 2 / 4, L2 prefetch one wave ahead
         // 22: fixed-width, >= 6 resident blocks per SM, L2 prefetch one wave ahead
         // 23, 24, 25: fixed-width, persistent warps, L2 prefetch 1 / 2 / no strides ahead;
-        // 26, 27: fixed-width, persistent, programmatic dependent launch, no / 1 stride prefetch
+        // 26, 27: fixed-width, persistent, programmatic dependent launch, no / 1 stride prefetch;
+        // 28, 29: the same with 256-bit loads (V = 8)
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
@@ -1192,9 +1203,12 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
         const int big = (variant_id >= 14 && variant_id <= 17) ? 1 : 0;
         const int pf = (variant_id == 19 || variant_id == 24) ? 2
-                       : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27) ? 1 : 0;
+                       : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27 ||
+                          variant_id == 29) ? 1 : 0;
         const int persist = variant_id >= 23 ? 1 : 0;
         const int pdl = variant_id >= 26 ? 1 : 0;
+        const int wide = variant_id >= 28 ? 1 : 0;
+        if (wide && V != 8) continue;
         if (variant_id == 22 && V != 4) continue;
         if ((pf || persist) && V == 1) continue;
         if (big && V != 8) continue;
@@ -1224,14 +1238,15 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.pf = pf;
         g_force.persist = persist;
         g_force.pdl = pdl;
+        g_force.wide = wide;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
         g_force_on = false;
         if (s) return s;
         if (table && n < 128)
-          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf, persist, pdl,
-                                    (double)us};
+          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf,
+                                    persist, pdl, wide, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

@@ -275,14 +275,22 @@ __device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, 
   }
 }
 
-// Sample layout of the fixed-width kernel's threads.  With V = 8 a thread's
+// Sample layout of the fixed-width kernel's threads.  With W (256-bit loads,
+// V = 8) a thread's 8 samples are contiguous, kv*8 .. kv*8+7, read and written
+// by one 32-byte access.  Otherwise, with V = 8 a thread's
 // samples are two runs of 4: kv*4 .. kv*4+3 and K/2 + kv*4 .. K/2 + kv*4+3, so
 // that one 16-byte load per lane covers, across the 8 lanes of a row, one
 // contiguous 128-byte span of a source row (instead of every other 16 bytes of
 // 256); with V = 4 a thread's 4 samples are one run.  Only the assignment of
 // samples to threads changes: every sample's arithmetic is the same.
-template <int V>
+template <int V, bool W = false>
 __device__ __forceinline__ void ld_runs(const float* p, int64_t hs, u64 (&out)[V / 2]) {
+  if constexpr (W) {  // one 256-bit load of 8 contiguous samples
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(out[0]), "=l"(out[1]), "=l"(out[2]), "=l"(out[3])
+                 : "l"(p));
+    return;
+  }
   const ulonglong2 v0 = *reinterpret_cast<const ulonglong2*>(p);
   out[0] = v0.x;
   out[1] = v0.y;
@@ -293,9 +301,16 @@ __device__ __forceinline__ void ld_runs(const float* p, int64_t hs, u64 (&out)[V
   }
 }
 
-template <int V>
+template <int V, bool W = false>
 __device__ __forceinline__ Pack<float, V> ld_run_pack(const float* p, int64_t hs) {
   Pack<float, V> r;
+  if constexpr (W) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]),
+                   "=f"(r.v[6]), "=f"(r.v[7])
+                 : "l"(p));
+    return r;
+  }
   const float4 v0 = *reinterpret_cast<const float4*>(p);
   r.v[0] = v0.x, r.v[1] = v0.y, r.v[2] = v0.z, r.v[3] = v0.w;
   if constexpr (V == 8) {
@@ -305,13 +320,19 @@ __device__ __forceinline__ Pack<float, V> ld_run_pack(const float* p, int64_t hs
   return r;
 }
 
-template <int V>
+template <int V, bool W = false>
 __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<float, V>& x) {
+  if constexpr (W) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]),
+                 "f"(x.v[2]), "f"(x.v[3]), "f"(x.v[4]), "f"(x.v[5]), "f"(x.v[6]), "f"(x.v[7])
+                 : "memory");
+    return;
+  }
   *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
   if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
-template <int V, bool ADJ>
+template <int V, bool ADJ, bool W = false>
 __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t) {
   constexpr int P = V / 2;
   const int KV = A.K / V;
@@ -323,8 +344,9 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
   const int kv = (int)(t - rowi * KV);
   const int64_t row = A.order ? (int64_t)A.order[rowi] : rowi;
   static_assert(V == 4 || V == 8, "fixed-width kernel: V = 4 or 8");
-  const int64_t hs = V == 8 ? A.K / 2 : 0;  // offset of a thread's second run of samples
-  const int64_t base = (int64_t)kv * 4;     // offset of its first run
+  static_assert(!W || V == 8, "256-bit loads: V = 8");
+  const int64_t hs = (V == 8 && !W) ? A.K / 2 : 0;  // offset of a thread's second run of samples
+  const int64_t base = (int64_t)kv * (W ? 8 : 4);   // offset of its first run
   const int64_t off = row * A.K + base;
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
@@ -333,7 +355,19 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
   // half of the row, which needs fewer registers (same arithmetic order)
   uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = c0;
   float4 h01 = make_float4(0.f, 0.f, 0.f, 0.f), h23 = h01, h45 = h01, h67 = h01;
-  if constexpr (V == 8) {
+  if constexpr (W) {
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(c0.x), "=r"(c0.y), "=r"(c0.z), "=r"(c0.w), "=r"(c1.x), "=r"(c1.y), "=r"(c1.z), "=r"(c1.w)
+                 : "l"(A.ell_col + row * 8));
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(h01.x), "=f"(h01.y), "=f"(h01.z), "=f"(h01.w), "=f"(h23.x), "=f"(h23.y), "=f"(h23.z),
+                   "=f"(h23.w)
+                 : "l"(A.ell_hl + row * 8));
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(h45.x), "=f"(h45.y), "=f"(h45.z), "=f"(h45.w), "=f"(h67.x), "=f"(h67.y), "=f"(h67.z),
+                   "=f"(h67.w)
+                 : "l"(A.ell_hl + row * 8 + 4));
+  } else if constexpr (V == 8) {
     c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
     c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
     h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
@@ -358,7 +392,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (4 * h + q < eA) {
-            ld_runs<V>(xk + (size_t)cols[4 * h + q] * Ku, hs, x[q]);
+            ld_runs<V, W>(xk + (size_t)cols[4 * h + q] * Ku, hs, x[q]);
           } else {
 #pragma unroll
             for (int p = 0; p < P; ++p) x[q][p] = 0ull;
@@ -389,7 +423,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
       float2 c;
       ell_entry<V>(A, row, e, &col, &c);
       u64 x[P];
-      ld_runs<V>(xk + (size_t)col * Ku, hs, x);
+      ld_runs<V, W>(xk + (size_t)col * Ku, hs, x);
       const u64 ch = dup2(c.x), cl = dup2(c.y);
 #pragma unroll
       for (int p = 0; p < P; ++p) {
@@ -405,7 +439,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
         float2 c;
         ell_entry<V>(A, row, e, &col, &c);
         u64 x[P];
-        ld_runs<V>(pk + (size_t)col * Ku, hs, x);
+        ld_runs<V, W>(pk + (size_t)col * Ku, hs, x);
         const u64 ch = dup2(-c.x), cl = dup2(-c.y);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -425,12 +459,12 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
       ell_entry<V>(A, row, e, &col, &c);
       const int64_t j = (int64_t)col;
       if (A.ya) {
-        const Pack<float, V> y = ld_run_pack<V>(A.ya + j * A.K + base, hs);
+        const Pack<float, V> y = ld_run_pack<V, W>(A.ya + j * A.K + base, hs);
 #pragma unroll
         for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
       }
       if (A.yb) {
-        const Pack<float, V> y = ld_run_pack<V>(A.yb + j * A.K + base, hs);
+        const Pack<float, V> y = ld_run_pack<V, W>(A.yb + j * A.K + base, hs);
 #pragma unroll
         for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
       }
@@ -438,13 +472,13 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
   }
   Pack<float, V> xi, xpi, xo;
   if (A.x) {
-    xi = ld_run_pack<V>(A.x + off, hs);
+    xi = ld_run_pack<V, W>(A.x + off, hs);
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
   }
   if (A.prev_mode == 0) {
-    xpi = ld_run_pack<V>(A.xp + off, hs);
+    xpi = ld_run_pack<V, W>(A.xp + off, hs);
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
@@ -456,7 +490,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
     xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
     xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
   }
-  st_run_pack<V>(A.xn + off, hs, xo);
+  st_run_pack<V, W>(A.xn + off, hs, xo);
 }
 
 template <int V, bool ADJ>
@@ -483,7 +517,7 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3
 // Launched as a programmatic dependent of the previous step, the grid's blocks
 // may become resident while that step drains; griddepcontrol.wait holds them
 // until it has completed and its writes are visible (a no-op otherwise).
-template <int V, bool ADJ>
+template <int V, bool ADJ, bool W>
 __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_persist_kernel(const Step3Args<float> A,
                                                                              int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -499,7 +533,7 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_persist_kernel(con
         prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(min(t0 + 32 * (int64_t)wpb, A.row_threads) - 1, KV) + 1);
     }
     const int64_t c = cb + (threadIdx.x >> 5);
-    if (c < n_chunks) step3e_row<V, ADJ>(A, c * 32 + lane);
+    if (c < n_chunks) step3e_row<V, ADJ, W>(A, c * 32 + lane);
   }
 }
 

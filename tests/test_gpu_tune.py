@@ -40,7 +40,8 @@ VARIANTS = [dict(V=8, packed=2), dict(V=8, packed=1, chunk=2), dict(V=8, packed=
             dict(V=8, packed=3, prefetch=1), dict(V=4, packed=3, prefetch=2), dict(V=8, packed=1, chunk=2, prefetch=1),
             dict(V=4, packed=3, min_blocks=6, prefetch=1), dict(V=8, packed=3, persistent=True, prefetch=1),
             dict(V=4, packed=3, persistent=True), dict(V=8, packed=3, persistent=True, zorder=True),
-            dict(V=8, packed=3, persistent=True, pdl=True), dict(V=8, packed=3, persistent=True, pdl=True, prefetch=1)]
+            dict(V=8, packed=3, persistent=True, pdl=True), dict(V=8, packed=3, persistent=True, pdl=True, prefetch=1),
+            dict(V=8, packed=3, persistent=True, pdl=True, wide_loads=True)]
 
 
 @pytest.mark.parametrize("K", [16, 64])
