@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
     ap.add_argument("--autotune", type=int, default=1, help="0: keep the library's default step-kernel variant")
-    ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4")
+    ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4 | v8c2z | ell8 | ell4 | pipe | "
+                    "ell8pf | ell8p | ell8pw")
     return ap.parse_args()
 
 
@@ -214,7 +215,8 @@ def run_ours(a, rank, world, local_rank, dist):
               "v4c4": dict(V=4, packed=1, chunk=4), "v8c2z": dict(V=8, packed=1, chunk=2, zorder=True),
               "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3), "pipe": dict(V=8, packed=4),
               "ell8pf": dict(V=8, packed=3, prefetch=1),
-              "ell8p": dict(V=8, packed=3, persistent=True)}.get(a.variant)
+              "ell8p": dict(V=8, packed=3, persistent=True),
+              "ell8pw": dict(V=8, packed=3, persistent=True, pdl=True, wide_loads=True, prefetch=1)}.get(a.variant)
     if forced:
         for d in ("fwd", "adj"):
             mesh.select_variant(K, d, **forced)

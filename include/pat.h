@@ -311,9 +311,11 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * loaded before the row walk), zorder (rows processed in Z-order of the node
  * coordinates), big_blocks (1024-thread blocks), prefetch (0: off; n: each block
  * first asks L2 to prefetch, by bulk prefetch, the state rows and row metadata
- * of the rows n resident waves ahead), persistent (fixed-width kernel only: a
- * grid of resident blocks whose warps each walk 32-thread chunks with a stride
- * of the grid's warps; prefetch then counts strides), pdl (persistent only:
+ * of the rows n resident waves ahead), persistent (fixed-width kernel only:
+ * 1 = a grid of resident blocks whose warps each walk 32-thread chunks with a
+ * stride of the grid's warps, prefetch then counting strides; 2 = each block
+ * walks one contiguous slab of chunks in order, prefetch counting its
+ * iterations), pdl (persistent only:
  * launched as a programmatic dependent of the previous step), wide_loads
  * (persistent, V = 8: each thread's 8 samples read and written by one 256-bit
  * access), us per step};

@@ -209,7 +209,7 @@ class Mesh:
         return [{"direction": ("fwd", "adj")[e.direction], "V": e.V, "staged": bool(e.staged),
                  "packed": int(e.packed), "chunk": e.chunk, "min_blocks": e.min_blocks,
                  "early": bool(e.early), "zorder": bool(e.zorder), "big_blocks": bool(e.big_blocks),
-                 "prefetch": e.prefetch, "persistent": bool(e.persistent), "pdl": bool(e.pdl),
+                 "prefetch": e.prefetch, "persistent": int(e.persistent), "pdl": bool(e.pdl),
                  "wide_loads": bool(e.wide_loads), "us_per_step": e.us_per_step}
                 for e in table[:min(n.value, 128)]]
 

@@ -870,9 +870,9 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.minb = v->min_blocks;
   c.early = v->early;
   c.order = v->zorder;
-  c.big = v->big_blocks && v->V == 8 && (v->packed == 1 || v->packed == 3);
+  c.big = v->big_blocks && v->V == 8 && (v->packed == 1 || v->packed == 3) && v->persistent != 2;
   c.pf = v->prefetch;
-  c.persist = v->persistent && v->packed == 3 && v->V != 1;
+  c.persist = (v->packed == 3 && v->V != 1) ? std::min(std::max(v->persistent, 0), 2) : 0;
   c.pdl = c.persist && v->pdl;
   c.wide = c.persist && v->wide_loads && v->V == 8;
   {

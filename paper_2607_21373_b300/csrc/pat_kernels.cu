@@ -300,18 +300,25 @@ static int64_t wave_rows(const void* fn, int bdim, int KV) {
   return (int64_t)resident_blocks(fn, bdim) * sm_count() * bdim / std::max(KV, 1);
 }
 
-// Persistent fixed-width launch: one resident wave of blocks, optionally as a
-// programmatic dependent of the previous kernel on the stream.
+// Persistent fixed-width launch: one resident wave of blocks (c.persist 1:
+// grid-stride chunks; 2: one contiguous slab of chunks per block), optionally
+// as a programmatic dependent of the previous kernel on the stream.
 template <int V, bool ADJ, bool W>
 static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
   const int64_t n_chunks = (threads + 31) / 32;
-  const int per_sm = std::max(1, resident_blocks((const void*)step3e_persist_kernel<V, ADJ, W>, 256));
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
+  const int bs = (c.big && c.persist == 1) ? 1024 : 256;
+  void (*kern)(const Step3Args<float>, int64_t) =
+      c.persist == 2 ? step3e_slab_kernel<V, ADJ, W>
+      : bs == 1024   ? step3e_persist_kernel<V, ADJ, W, 1024>
+                     : step3e_persist_kernel<V, ADJ, W, 256>;
+  const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
+  const int64_t grid =
+      std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + bs / 32 - 1) / (bs / 32)));
   a.pf_rows = (c.pf && !a.order) ? c.pf : 0;
   if (c.pdl) {  // overlap this grid's start with the previous step's drain
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3((unsigned)bs);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -319,10 +326,10 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, step3e_persist_kernel<V, ADJ, W>, a, n_chunks) == cudaSuccess) return;
+    if (cudaLaunchKernelEx(&cfg, kern, a, n_chunks) == cudaSuccess) return;
     cudaGetLastError();  // attribute refused: plain launch
   }
-  step3e_persist_kernel<V, ADJ, W><<<(unsigned)grid, 256, 0, st>>>(a, n_chunks);
+  kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
 }
 
 template <typename T, int V, bool SPLIT, bool ADJ>
@@ -1171,7 +1178,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 30; ++variant_id) {
+      for (int variant_id = 0; variant_id < 36; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1186,7 +1193,10 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 22: fixed-width, >= 6 resident blocks per SM, L2 prefetch one wave ahead
         // 23, 24, 25: fixed-width, persistent warps, L2 prefetch 1 / 2 / no strides ahead;
         // 26, 27: fixed-width, persistent, programmatic dependent launch, no / 1 stride prefetch;
-        // 28, 29: the same with 256-bit loads (V = 8)
+        // 28, 29: the same with 256-bit loads (V = 8);
+        // 30, 31: slab-walking persistent, PDL, 256-bit loads, no / 1 block-iteration prefetch;
+        // 32, 33: the same with 128-bit loads;
+        // 34, 35: grid-stride persistent, PDL, 1024-thread blocks, 256- / 128-bit loads
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
@@ -1201,13 +1211,13 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
                               ? 2
                               : (variant_id == 2 ? 8 : 4);
         const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
-        const int big = (variant_id >= 14 && variant_id <= 17) ? 1 : 0;
+        const int big = ((variant_id >= 14 && variant_id <= 17) || variant_id >= 34) ? 1 : 0;
         const int pf = (variant_id == 19 || variant_id == 24) ? 2
                        : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27 ||
-                          variant_id == 29) ? 1 : 0;
-        const int persist = variant_id >= 23 ? 1 : 0;
+                          variant_id == 29 || variant_id == 31 || variant_id == 33) ? 1 : 0;
+        const int persist = variant_id >= 34 ? 1 : variant_id >= 30 ? 2 : variant_id >= 23 ? 1 : 0;
         const int pdl = variant_id >= 26 ? 1 : 0;
-        const int wide = variant_id >= 28 ? 1 : 0;
+        const int wide = ((variant_id >= 28 && variant_id <= 31) || variant_id == 34) ? 1 : 0;
         if (wide && V != 8) continue;
         if (variant_id == 22 && V != 4) continue;
         if ((pf || persist) && V == 1) continue;

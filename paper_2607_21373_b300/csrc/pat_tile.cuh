@@ -517,9 +517,9 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3
 // Launched as a programmatic dependent of the previous step, the grid's blocks
 // may become resident while that step drains; griddepcontrol.wait holds them
 // until it has completed and its writes are visible (a no-op otherwise).
-template <int V, bool ADJ, bool W>
-__global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_persist_kernel(const Step3Args<float> A,
-                                                                             int64_t n_chunks) {
+template <int V, bool ADJ, bool W, int BS = 256>
+__global__ void __launch_bounds__(BS, BS == 256 ? (V == 8 ? 4 : 5) : 1) step3e_persist_kernel(const Step3Args<float> A,
+                                                                                              int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int KV = A.K / V;
@@ -534,6 +534,34 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_persist_kernel(con
     }
     const int64_t c = cb + (threadIdx.x >> 5);
     if (c < n_chunks) step3e_row<V, ADJ, W>(A, c * 32 + lane);
+  }
+}
+
+// Persistent slab form: block b owns the contiguous chunk range
+// [b L, (b + 1) L) (L = ceil(chunks / blocks)) and its warps walk it in order,
+// w, w + 8, w + 16, ...  Rows then advance slowly through the block's SM, so
+// the source rows one grid line away (+-(n_x + 1) in a lexicographic node
+// order) are fetched from L2 once and reused from L1 by the rows that follow,
+// instead of once per 32-row group.  Thread 0 bulk-prefetches into L2 the rows
+// of the block's chunks A.pf_rows block-iterations ahead.
+template <int V, bool ADJ, bool W>
+__global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_slab_kernel(const Step3Args<float> A,
+                                                                          int64_t n_chunks) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int KV = A.K / V;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int64_t L = (n_chunks + gridDim.x - 1) / gridDim.x;
+  const int64_t c0 = (int64_t)blockIdx.x * L, c1 = min(c0 + L, n_chunks);
+  for (int64_t cb = c0; cb < c1; cb += wpb) {
+    if (A.pf_rows > 0 && threadIdx.x == 0) {
+      const int64_t t0 = (cb + A.pf_rows * wpb) * 32;
+      const int64_t t1 = min(min(t0 + 32 * (int64_t)wpb, c1 * 32), A.row_threads);
+      if (t0 < t1) prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(t1 - 1, KV) + 1);
+    }
+    const int64_t c = cb + (threadIdx.x >> 5);
+    if (c < c1) step3e_row<V, ADJ, W>(A, c * 32 + lane);
   }
 }
 
