@@ -256,8 +256,13 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
       return PAT_EUNSUPPORTED;
     }
     desc[i] = (uint32_t)n | ((uint32_t)nb[i] << 8) | ((uint32_t)ninj[i] << 16);
+    // slots 0..7: the first stiffness / boundary entries, padded with the row
+    // itself and a zero coefficient; overflow: the remaining stiffness / boundary
+    // entries, then every sensor (injection) entry.  The kernels then walk the
+    // 8 slots without a per-entry test.
+    const int nA = n - (int)ninj[i];
     for (int q = 0; q < 8; ++q) {
-      if (q < n) {
+      if (q < nA) {
         col[i * 8 + q] = R.col[e0 + q] & kIdxMask;
         hl[i * 8 + q] = pair(R.val[e0 + q]);
       } else {
@@ -265,7 +270,7 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
         hl[i * 8 + q] = make_float2(0.0f, 0.0f);
       }
     }
-    for (int q = 8; q < n; ++q) {
+    for (int q = std::min(nA, 8); q < n; ++q) {
       ocol.push_back(R.col[e0 + q] & kIdxMask);
       ohl.push_back(pair(R.val[e0 + q]));
     }

@@ -232,6 +232,8 @@ __global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, 
 // coefficient); longer rows continue in an overflow CSR.  Entries 0..7 are
 // then processed as two chunks of 4 neighbour rows.
 // ---------------------------------------------------------------------------
+// Stiffness / boundary entry e (< the row's count eA) of a fixed-width row:
+// slots 0..7, then the row's overflow list.
 template <int V>
 __device__ __forceinline__ void ell_entry(const Step3Args<float>& A, int64_t row, int e, uint32_t* col, float2* c) {
   if (e < 8) {
@@ -244,28 +246,30 @@ __device__ __forceinline__ void ell_entry(const Step3Args<float>& A, int64_t row
   }
 }
 
-// Four consecutive fixed-width entries of a row (columns c, (hi, lo) pairs in
-// ha, hb; only the first n < 4 are used when n < 4): gather the V samples of
-// each source row, then accumulate hi and lo products in entry order.
+// Sensor (injection) entry j of a fixed-width row with eA stiffness / boundary
+// entries: always in the overflow list, after the stiffness entries beyond 8.
+__device__ __forceinline__ void inj_entry(const Step3Args<float>& A, int64_t row, int j, int eA, uint32_t* col,
+                                          float2* c) {
+  const int64_t o = A.ovf_ptr[row] + max(eA - 8, 0) + j;
+  *col = A.ovf_col[o];
+  *c = A.ovf_hl[o];
+}
+
+// Four consecutive fixed-width slots of a row (columns c, (hi, lo) pairs in
+// ha, hb; padding slots carry a zero coefficient): gather the V samples of
+// each source row, then accumulate hi and lo products in slot order.
 template <int P>
-__device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, float4 ha, float4 hb, int n,
+__device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, float4 ha, float4 hb,
                                          u64 (&acc)[P], u64 (&accl)[P]) {
   const uint32_t cols[4] = {c.x, c.y, c.z, c.w};
   const float2 cf[4] = {make_float2(ha.x, ha.y), make_float2(ha.z, ha.w), make_float2(hb.x, hb.y),
                         make_float2(hb.z, hb.w)};
   u64 x[4][P];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (q < n) {
-      ld_pairs<P>(xk + (size_t)cols[q] * Ku, x[q]);
-    } else {
-#pragma unroll
-      for (int p = 0; p < P; ++p) x[q][p] = 0ull;
-    }
-  }
+  for (int q = 0; q < 4; ++q) ld_pairs<P>(xk + (size_t)cols[q] * Ku, x[q]);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const float2 cc = q < n ? cf[q] : make_float2(0.0f, 0.0f);
+    const float2 cc = cf[q];
     const u64 ch = dup2(cc.x), cl = dup2(cc.y);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -389,18 +393,13 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         u64 x[4][P];
+        // the 8 slots hold only stiffness / boundary entries and padding (the
+        // row itself with a zero coefficient): no per-entry test
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ld_runs<V, W>(xk + (size_t)cols[4 * h + q] * Ku, hs, x[q]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (4 * h + q < eA) {
-            ld_runs<V, W>(xk + (size_t)cols[4 * h + q] * Ku, hs, x[q]);
-          } else {
-#pragma unroll
-            for (int p = 0; p < P; ++p) x[q][p] = 0ull;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 c = (4 * h + q < eA) ? cf[4 * h + q] : make_float2(0.0f, 0.0f);
+          const float2 c = cf[4 * h + q];
           const u64 ch = dup2(c.x), cl = dup2(c.y);
 #pragma unroll
           for (int p = 0; p < P; ++p) {
@@ -415,7 +414,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
         const uint4 cq = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4 * h);
         const float4 ha = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4 * h);
         const float4 hb = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 4 * h + 2);
-        ell_half<P>(xk, Ku, cq, ha, hb, eA - 4 * h, acc, accl);
+        ell_half<P>(xk, Ku, cq, ha, hb, acc, accl);
       }
     }
     for (int e = 8; e < eA; ++e) {  // overflow of long (boundary) rows
@@ -453,10 +452,10 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
 #pragma unroll
   for (int q = 0; q < V; ++q) src[q] = 0.0f;
   if constexpr (ADJ) {
-    for (int e = eA; e < n; ++e) {
+    for (int e = 0; e < ni; ++e) {
       uint32_t col;
       float2 c;
-      ell_entry<V>(A, row, e, &col, &c);
+      inj_entry(A, row, e, eA, &col, &c);
       const int64_t j = (int64_t)col;
       if (A.ya) {
         const Pack<float, V> y = ld_run_pack<V, W>(A.ya + j * A.K + base, hs);
@@ -772,14 +771,14 @@ __global__ void __launch_bounds__(256) step3e1_kernel(const Step3Args<float> A) 
   const float ls[8] = {h01.y, h01.w, h23.y, h23.w, h45.y, h45.w, h67.y, h67.w};
   float acc = 0.0f, accl = 0.0f;
   if (A.x) {
+    // padded slots: the row itself with zero coefficients
     float xv[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) xv[q] = q < eA ? A.x[cols[q]] : 0.0f;
+    for (int q = 0; q < 8; ++q) xv[q] = A.x[cols[q]];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float h = q < eA ? hs[q] : 0.0f, l = q < eA ? ls[q] : 0.0f;
-      acc = fmaf(h, xv[q], acc);
-      accl = fmaf(l, xv[q], accl);
+      acc = fmaf(hs[q], xv[q], acc);
+      accl = fmaf(ls[q], xv[q], accl);
     }
     for (int e = 8; e < eA; ++e) {
       uint32_t col;
@@ -803,10 +802,10 @@ __global__ void __launch_bounds__(256) step3e1_kernel(const Step3Args<float> A) 
   }
   float src = 0.0f;
   if constexpr (ADJ) {
-    for (int e = eA; e < n; ++e) {
+    for (int e = 0; e < ni; ++e) {
       uint32_t col;
       float2 c;
-      ell_entry<1>(A, row, e, &col, &c);
+      inj_entry(A, row, e, eA, &col, &c);
       if (A.ya) src = fmaf(c.x, A.ya[col], src);
       if (A.yb) src = fmaf(c.x, A.yb[col], src);
     }
