@@ -880,6 +880,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.persist = (v->packed == 3 && v->V != 1) ? std::min(std::max(v->persistent, 0), 2) : 0;
   c.pdl = c.persist && v->pdl;
   c.wide = c.persist && v->wide_loads && v->V == 8;
+  c.hint = c.persist == 1 && !c.wide && !c.big && v->l2_hints && v->V == 8;
   {
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;

@@ -109,6 +109,7 @@ struct TuneCfg {
   int persist = 0; // fixed-width kernel: persistent warps walking 32-thread chunks (1: grid-stride, 2: slabs)
   int pdl = 0;     // persistent kernel: programmatic dependent launch
   int wide = 0;    // persistent kernel, V = 8: 256-bit loads of 8 contiguous samples
+  int hint = 0;    // persistent kernel, V = 8: L2 eviction-priority hints
 };
 
 struct DeviceMesh {

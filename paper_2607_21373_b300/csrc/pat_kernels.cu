@@ -311,6 +311,9 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
       c.persist == 2 ? step3e_slab_kernel<V, ADJ, W>
       : bs == 1024   ? step3e_persist_kernel<V, ADJ, W, 1024>
                      : step3e_persist_kernel<V, ADJ, W, 256>;
+  if constexpr (V == 8 && !W) {
+    if (c.hint && c.persist == 1 && bs == 256) kern = step3e_persist_kernel<V, ADJ, false, 256, true>;
+  }
   const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
   const int64_t grid =
       std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + bs / 32 - 1) / (bs / 32)));
@@ -1178,7 +1181,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 36; ++variant_id) {
+      for (int variant_id = 0; variant_id < 38; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1196,7 +1199,8 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 28, 29: the same with 256-bit loads (V = 8);
         // 30, 31: slab-walking persistent, PDL, 256-bit loads, no / 1 block-iteration prefetch;
         // 32, 33: the same with 128-bit loads;
-        // 34, 35: grid-stride persistent, PDL, 1024-thread blocks, 256- / 128-bit loads
+        // 34, 35: grid-stride persistent, PDL, 1024-thread blocks, 256- / 128-bit loads;
+        // 36, 37: grid-stride persistent, PDL, L2 eviction hints, no / 1 stride prefetch
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
@@ -1211,11 +1215,13 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
                               ? 2
                               : (variant_id == 2 ? 8 : 4);
         const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
-        const int big = ((variant_id >= 14 && variant_id <= 17) || variant_id >= 34) ? 1 : 0;
+        const int big = ((variant_id >= 14 && variant_id <= 17) || variant_id == 34 || variant_id == 35) ? 1 : 0;
         const int pf = (variant_id == 19 || variant_id == 24) ? 2
                        : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27 ||
-                          variant_id == 29 || variant_id == 31 || variant_id == 33) ? 1 : 0;
+                          variant_id == 29 || variant_id == 31 || variant_id == 33 || variant_id == 37) ? 1 : 0;
         const int persist = variant_id >= 34 ? 1 : variant_id >= 30 ? 2 : variant_id >= 23 ? 1 : 0;
+        const int hint = variant_id >= 36 ? 1 : 0;
+        if (hint && V != 8) continue;
         const int pdl = variant_id >= 26 ? 1 : 0;
         const int wide = ((variant_id >= 28 && variant_id <= 31) || variant_id == 34) ? 1 : 0;
         if (wide && V != 8) continue;
@@ -1249,6 +1255,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.persist = persist;
         g_force.pdl = pdl;
         g_force.wide = wide;
+        g_force.hint = hint;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1256,7 +1263,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         if (s) return s;
         if (table && n < 128)
           table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf,
-                                    persist, pdl, wide, (double)us};
+                                    persist, pdl, wide, hint, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

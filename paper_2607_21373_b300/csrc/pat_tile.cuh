@@ -279,6 +279,40 @@ __device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, 
   }
 }
 
+// L2 eviction-priority hints (H variants of the fixed-width kernel): the new
+// state x_{s+1} and the row metadata are kept (evict_last), since the next
+// steps read them again; the own rows of x_{s-1}, read for the last time,
+// leave first (evict_first).
+__device__ __forceinline__ uint64_t l2_policy_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_hint_f4(const float* p, uint64_t pol) {
+  float4 v;
+  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_hint_u4(const void* p, uint64_t pol) {
+  uint4 v;
+  asm("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint_f4(float* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
+
 // Sample layout of the fixed-width kernel's threads.  With W (256-bit loads,
 // V = 8) a thread's 8 samples are contiguous, kv*8 .. kv*8+7, read and written
 // by one 32-byte access.  Otherwise, with V = 8 a thread's
@@ -336,8 +370,9 @@ __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<flo
   if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
-template <int V, bool ADJ, bool W = false>
+template <int V, bool ADJ, bool W = false, bool H = false>
 __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t) {
+  static_assert(!H || (V == 8 && !W), "cache-hint variant: V = 8, 128-bit loads");
   constexpr int P = V / 2;
   const int KV = A.K / V;
   if (t >= A.row_threads) {
@@ -371,6 +406,14 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
                  : "=f"(h45.x), "=f"(h45.y), "=f"(h45.z), "=f"(h45.w), "=f"(h67.x), "=f"(h67.y), "=f"(h67.z),
                    "=f"(h67.w)
                  : "l"(A.ell_hl + row * 8 + 4));
+  } else if constexpr (H) {
+    const uint64_t keep = l2_policy_last();
+    c0 = ld_hint_u4(A.ell_col + row * 8, keep);
+    c1 = ld_hint_u4(A.ell_col + row * 8 + 4, keep);
+    h01 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8), keep);
+    h23 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 2), keep);
+    h45 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 4), keep);
+    h67 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 6), keep);
   } else if constexpr (V == 8) {
     c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
     c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
@@ -477,7 +520,14 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
     for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
   }
   if (A.prev_mode == 0) {
-    xpi = ld_run_pack<V, W>(A.xp + off, hs);
+    if constexpr (H) {
+      const uint64_t leave = l2_policy_first();
+      const float4 a = ld_hint_f4(A.xp + off, leave), b = ld_hint_f4(A.xp + off + hs, leave);
+      xpi.v[0] = a.x, xpi.v[1] = a.y, xpi.v[2] = a.z, xpi.v[3] = a.w;
+      xpi.v[4] = b.x, xpi.v[5] = b.y, xpi.v[6] = b.z, xpi.v[7] = b.w;
+    } else {
+      xpi = ld_run_pack<V, W>(A.xp + off, hs);
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
@@ -489,7 +539,13 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
     xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
     xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
   }
-  st_run_pack<V, W>(A.xn + off, hs, xo);
+  if constexpr (H) {
+    const uint64_t keep = l2_policy_last();
+    st_hint_f4(A.xn + off, make_float4(xo.v[0], xo.v[1], xo.v[2], xo.v[3]), keep);
+    st_hint_f4(A.xn + off + hs, make_float4(xo.v[4], xo.v[5], xo.v[6], xo.v[7]), keep);
+  } else {
+    st_run_pack<V, W>(A.xn + off, hs, xo);
+  }
 }
 
 template <int V, bool ADJ>
@@ -516,7 +572,7 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3
 // Launched as a programmatic dependent of the previous step, the grid's blocks
 // may become resident while that step drains; griddepcontrol.wait holds them
 // until it has completed and its writes are visible (a no-op otherwise).
-template <int V, bool ADJ, bool W, int BS = 256>
+template <int V, bool ADJ, bool W, int BS = 256, bool H = false>
 __global__ void __launch_bounds__(BS, BS == 256 ? (V == 8 ? 4 : 5) : 1) step3e_persist_kernel(const Step3Args<float> A,
                                                                                               int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -532,7 +588,7 @@ __global__ void __launch_bounds__(BS, BS == 256 ? (V == 8 ? 4 : 5) : 1) step3e_p
         prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(min(t0 + 32 * (int64_t)wpb, A.row_threads) - 1, KV) + 1);
     }
     const int64_t c = cb + (threadIdx.x >> 5);
-    if (c < n_chunks) step3e_row<V, ADJ, W>(A, c * 32 + lane);
+    if (c < n_chunks) step3e_row<V, ADJ, W, H>(A, c * 32 + lane);
   }
 }
 
