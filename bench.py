@@ -34,6 +34,14 @@ import numpy as np  # noqa: E402
 import synthetic as S  # noqa: E402
 
 METRIC = "rto_samples_per_s"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step launch, from
+# one ncu capture of that kernel variant on the default workload (cube58, K = 64,
+# 1024 sensors); see profiles/step3e_persist_kernel_cube58_K64.md.  Used for the
+# roofline's "traffic" only when the timed run uses the same variant and workload.
+PROFILED_TRAFFIC = {
+    "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)": 160.878336e6,
+    "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)": 159.663104e6,
+}
 UNIT = "samples/s"
 
 
@@ -54,7 +62,7 @@ def parse():
     ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
     ap.add_argument("--autotune", type=int, default=1, help="0: keep the library's default step-kernel variant")
     ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4 | v8c2z | ell8 | ell4 | pipe | "
-                    "ell8pf | ell8p | ell8pw")
+                    "ell8pf | ell8p | ell8pw | ell8pp")
     return ap.parse_args()
 
 
@@ -216,7 +224,8 @@ def run_ours(a, rank, world, local_rank, dist):
               "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3), "pipe": dict(V=8, packed=4),
               "ell8pf": dict(V=8, packed=3, prefetch=1),
               "ell8p": dict(V=8, packed=3, persistent=True),
-              "ell8pw": dict(V=8, packed=3, persistent=True, pdl=True, wide_loads=True, prefetch=1)}.get(a.variant)
+              "ell8pw": dict(V=8, packed=3, persistent=True, pdl=True, wide_loads=True, prefetch=1),
+              "ell8pp": dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1)}.get(a.variant)
     if forced:
         for d in ("fwd", "adj"):
             mesh.select_variant(K, d, **forced)
@@ -301,21 +310,40 @@ def run_ours(a, rank, world, local_rank, dist):
         if e.get("packed") == 4:
             return "step3p_kernel<%s> (persistent double-buffered tiles)" % ("true" if adj else "false")
         if e.get("packed") == 3:
-            kind = "step3e_persist_kernel" if e.get("persistent") else "step3e_kernel"
-            return "%s<%d,%s>" % (kind, e["V"], "true" if adj else "false")
+            p = int(e.get("persistent") or 0)
+            kind = {0: "step3e_kernel", 1: "step3e_persist_kernel", 2: "step3e_slab_kernel"}[p]
+            flags = []
+            if p:
+                flags.append("1024-thread blocks" if e.get("big_blocks") else "256-thread blocks")
+            if e.get("pdl"):
+                flags.append("PDL")
+            if e.get("prefetch"):
+                flags.append("L2 prefetch %d" % e["prefetch"])
+            if e.get("wide_loads"):
+                flags.append("256-bit loads")
+            if e.get("l2_hints"):
+                flags.append("L2 hints")
+            if e.get("min_blocks", 1) > 1:
+                flags.append(">=%d blocks/SM" % e["min_blocks"])
+            return "%s<%d,%s>%s" % (kind, e["V"], "true" if adj else "false",
+                                    " (%s)" % ", ".join(flags) if flags else "")
         if e.get("packed"):
             return "step3f_kernel<%d,%d,%s>%s" % (e["V"], e.get("chunk", 4), "true" if adj else "false",
                                                   " (Z-order rows)" if e.get("zorder") else "")
         return "step3_kernel<float,%d,split,%s,staged=%d>" % (e["V"], "adj" if adj else "fwd", e["staged"])
     bf, ba = best("fwd"), best("adj")
+    default_workload = (a.cells, a.K, a.n_obs, a.mesh_flags) == (58, 64, 1024, 0)
     kname = "fwd_step_kernel<float,4,true>" if two_level else kernel_name(bf, False)
     aname = "adj_step_kernel<float,4,true>" if two_level else kernel_name(ba, True)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak,
+            "traffic": PROFILED_TRAFFIC.get(kname) if default_workload else None,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
             "bytes_per_launch": fwd_bytes_per_launch, "avg_launch_us": 1e3 * fwd_avg_ms,
+            "traffic_source": "ncu capture of the same variant, profiles/step3e_persist_kernel_cube58_K64.md",
             "adjoint": {"kernel": aname, "achieved": adj_achieved,
-                        "frac": adj_achieved / peak, "avg_launch_us": 1e3 * adj_avg_ms}}
+                        "frac": adj_achieved / peak, "avg_launch_us": 1e3 * adj_avg_ms,
+                        "traffic": PROFILED_TRAFFIC.get(aname) if default_workload else None}}
 
     # plain one-sample form on the same library and workload
     plain = None

@@ -95,15 +95,49 @@ def test_single_coefficient_storage_is_less_accurate():
 def test_full_size_batched_forward_sampled_columns():
     """205,379 nodes, 1000 steps, 1024 sensors, K = 64 in one launch sequence:
     two of the 64 columns against single-column oracle runs."""
+    """The benchmark's workload and launch configuration: 205,379 nodes, 1000 steps,
+    1024 sensors, K = 64, step kernels chosen by the autotuner as bench.py does;
+    forward and transposed solves against the oracle on sampled columns."""
     P = cube_problem(58, 1024, 1000, faces=S.LIMITED_VIEW_FACES, seed=1003, phantom="blobs20+vessels")
     m = gpu_mesh(P, "f32")
-    N = P["xyz"].shape[0]
+    m.autotune(64, n_probe=10)
     rng = np.random.default_rng(0)
     p0 = as_precision(P["p0"][:, None] * rng.uniform(0.5, 1.5, size=(1, 64)), "f32")
     Y = m.forward(to_dev(p0, "f32"))
+    yh = as_precision(S.standard_normal((P["n_steps"], 1024, 64), 31), "f32")
+    g = m.adjoint(to_dev(yh, "f32"))
     for k in (0, 63):
         ref = wave.forward(P["ops"], p0[:, k], P["dt"], P["n_steps"])
         assert rel_l2(Y[..., k].cpu().numpy(), ref) < 1e-5
+    for k in (5,):
+        ref = wave.adjoint(P["ops"], yh[..., k], P["dt"])
+        assert rel_l2(g[:, k].cpu().numpy(), ref) < 1e-5
+
+
+# the persistent fixed-width variants the autotuner picks on the benchmark mesh
+BENCH_VARIANTS = [dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1),
+                  dict(V=8, packed=3, persistent=1, pdl=True, big_blocks=True),
+                  dict(V=8, packed=3, persistent=1, pdl=True, wide_loads=True)]
+
+
+@pytest.mark.parametrize("K", [8, 24])
+@pytest.mark.parametrize("vi", range(len(BENCH_VARIANTS)))
+def test_persistent_variants_match_oracle(K, vi):
+    """Forward, transpose and dot test of the persistent kernels against the oracle
+    on a mesh with boundary rows longer than 8 entries and sensor rows."""
+    P = cube_problem(8, 32, 200)
+    m = gpu_mesh(P, "f32")
+    for d in ("fwd", "adj"):
+        m.select_variant(K, d, **BENCH_VARIANTS[vi])
+    p0 = as_precision(S.standard_normal((P["xyz"].shape[0], K), 40 + K), "f32")
+    yh = as_precision(S.standard_normal((P["n_steps"], 32, K), 41 + K), "f32")
+    Y = m.forward(to_dev(p0, "f32"))
+    g = m.adjoint(to_dev(yh, "f32"))
+    assert rel_l2(Y.cpu().numpy(), wave.forward(P["ops"], p0, P["dt"], P["n_steps"])) < 1e-5
+    assert rel_l2(g.cpu().numpy(), wave.adjoint(P["ops"], yh, P["dt"])) < 1e-5
+    lhs = (Y.double() * to_dev(yh, "f32").double()).sum(dim=(0, 1))
+    rhs = (to_dev(p0, "f32").double() * g.double()).sum(dim=0)
+    assert torch.all((lhs - rhs).abs() <= 1e-6 * lhs.abs())
 
 
 def test_gpu_sensor_map_matches_oracle():
