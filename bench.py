@@ -39,8 +39,8 @@ METRIC = "rto_samples_per_s"
 # 1024 sensors); see profiles/step3e_persist_kernel_cube58_K64.md.  Used for the
 # roofline's "traffic" only when the timed run uses the same variant and workload.
 PROFILED_TRAFFIC = {
-    "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)": 160.878336e6,
-    "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)": 159.663104e6,
+    "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)": 160.643584e6,
+    "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)": 159.604480e6,
 }
 UNIT = "samples/s"
 
