@@ -315,7 +315,9 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * 1 = a grid of resident blocks whose warps each walk 32-thread chunks with a
  * stride of the grid's warps, prefetch then counting strides; 2 = each block
  * walks one contiguous slab of chunks in order, prefetch counting its
- * iterations), pdl (persistent only:
+ * iterations; 3 = as 1, with each warp's next chunk's row metadata copied
+ * into shared memory by cp.async while it processes the current one, V = 8
+ * and K / V >= 4 only, else 1), pdl (persistent only:
  * launched as a programmatic dependent of the previous step), wide_loads
  * (persistent, V = 8: each thread's 8 samples read and written by one 256-bit
  * access), l2_hints (persistent grid-stride, V = 8, 128-bit: the new state

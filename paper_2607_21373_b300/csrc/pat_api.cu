@@ -877,7 +877,8 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.order = v->zorder;
   c.big = v->big_blocks && v->V == 8 && (v->packed == 1 || v->packed == 3) && v->persistent != 2;
   c.pf = v->prefetch;
-  c.persist = (v->packed == 3 && v->V != 1) ? std::min(std::max(v->persistent, 0), 2) : 0;
+  c.persist = (v->packed == 3 && v->V != 1) ? std::min(std::max(v->persistent, 0), 3) : 0;
+  if (c.persist == 3 && (v->V != 8 || K / v->V < 4)) c.persist = 1;
   c.pdl = c.persist && v->pdl;
   c.wide = c.persist && v->wide_loads && v->V == 8;
   c.hint = c.persist == 1 && !c.wide && !c.big && v->l2_hints && v->V == 8;

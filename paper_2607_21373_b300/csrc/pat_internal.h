@@ -106,7 +106,8 @@ struct TuneCfg {
   int order = 0;   // packed kernel: process rows in Z-order of the node coordinates
   int big = 0;     // packed kernels: 1024-thread blocks
   int pf = 0;      // packed kernels: L2 prefetch distance in resident waves (0: off)
-  int persist = 0; // fixed-width kernel: persistent warps walking 32-thread chunks (1: grid-stride, 2: slabs)
+  int persist = 0; // fixed-width kernel: persistent warps walking 32-thread chunks (1: grid-stride, 2: slabs,
+                   // 3: grid-stride with the row metadata staged through shared memory)
   int pdl = 0;     // persistent kernel: programmatic dependent launch
   int wide = 0;    // persistent kernel, V = 8: 256-bit loads of 8 contiguous samples
   int hint = 0;    // persistent kernel, V = 8: L2 eviction-priority hints

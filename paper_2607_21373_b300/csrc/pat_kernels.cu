@@ -301,7 +301,8 @@ static int64_t wave_rows(const void* fn, int bdim, int KV) {
 }
 
 // Persistent fixed-width launch: one resident wave of blocks (c.persist 1:
-// grid-stride chunks; 2: one contiguous slab of chunks per block), optionally
+// grid-stride chunks; 2: one contiguous slab of chunks per block; 3: grid-stride
+// with staged row metadata), optionally
 // as a programmatic dependent of the previous kernel on the stream.
 template <int V, bool ADJ, bool W>
 static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
@@ -313,6 +314,8 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
                      : step3e_persist_kernel<V, ADJ, W, 256>;
   if constexpr (V == 8 && !W) {
     if (c.hint && c.persist == 1 && bs == 256) kern = step3e_persist_kernel<V, ADJ, false, 256, true>;
+    // metadata staged through shared memory: at most kStageRows rows per 32-thread chunk
+    if (c.persist == 3 && a.K / V >= 4 && !a.order) kern = step3e_stage_kernel<ADJ>;
   }
   const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
   const int64_t grid =
@@ -1181,7 +1184,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 38; ++variant_id) {
+      for (int variant_id = 0; variant_id < 41; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1200,7 +1203,9 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 30, 31: slab-walking persistent, PDL, 256-bit loads, no / 1 block-iteration prefetch;
         // 32, 33: the same with 128-bit loads;
         // 34, 35: grid-stride persistent, PDL, 1024-thread blocks, 256- / 128-bit loads;
-        // 36, 37: grid-stride persistent, PDL, L2 eviction hints, no / 1 stride prefetch
+        // 36, 37: grid-stride persistent, PDL, L2 eviction hints, no / 1 stride prefetch;
+        // 38, 39, 40: grid-stride persistent, row metadata staged through shared memory by
+        // cp.async one chunk ahead, PDL / PDL + 1 stride prefetch / neither
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
@@ -1218,11 +1223,13 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         const int big = ((variant_id >= 14 && variant_id <= 17) || variant_id == 34 || variant_id == 35) ? 1 : 0;
         const int pf = (variant_id == 19 || variant_id == 24) ? 2
                        : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27 ||
-                          variant_id == 29 || variant_id == 31 || variant_id == 33 || variant_id == 37) ? 1 : 0;
-        const int persist = variant_id >= 34 ? 1 : variant_id >= 30 ? 2 : variant_id >= 23 ? 1 : 0;
-        const int hint = variant_id >= 36 ? 1 : 0;
+                          variant_id == 29 || variant_id == 31 || variant_id == 33 || variant_id == 37 ||
+                          variant_id == 39) ? 1 : 0;
+        const int persist = variant_id >= 38 ? 3 : variant_id >= 34 ? 1 : variant_id >= 30 ? 2 : variant_id >= 23 ? 1 : 0;
+        if (persist == 3 && (V != 8 || K / V < 4)) continue;
+        const int hint = (variant_id == 36 || variant_id == 37) ? 1 : 0;
         if (hint && V != 8) continue;
-        const int pdl = variant_id >= 26 ? 1 : 0;
+        const int pdl = (variant_id >= 26 && variant_id != 40) ? 1 : 0;
         const int wide = ((variant_id >= 28 && variant_id <= 31) || variant_id == 34) ? 1 : 0;
         if (wide && V != 8) continue;
         if (variant_id == 22 && V != 4) continue;

@@ -279,6 +279,22 @@ __device__ __forceinline__ void ell_half(const float* xk, uint32_t Ku, uint4 c, 
   }
 }
 
+// Row metadata of one 32-thread chunk (at most kStageRows rows, so K / V >= 4),
+// staged in shared memory by the warp that will process it.
+constexpr int kStageRows = 9;
+struct alignas(16) EllStage {
+  uint32_t desc[12];
+  uint4 col[2 * kStageRows];
+  float4 hl[4 * kStageRows];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+
 // L2 eviction-priority hints (H variants of the fixed-width kernel): the new
 // state x_{s+1} and the row metadata are kept (evict_last), since the next
 // steps read them again; the own rows of x_{s-1}, read for the last time,
@@ -370,9 +386,11 @@ __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<flo
   if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
-template <int V, bool ADJ, bool W = false, bool H = false>
-__device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t) {
+template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false>
+__device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t,
+                                           const EllStage* sm = nullptr, int64_t r0 = 0) {
   static_assert(!H || (V == 8 && !W), "cache-hint variant: V = 8, 128-bit loads");
+  static_assert(!SMD || (V == 8 && !W && !H), "staged-metadata variant: V = 8, 128-bit loads");
   constexpr int P = V / 2;
   const int KV = A.K / V;
   if (t >= A.row_threads) {
@@ -387,7 +405,8 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
   const int64_t hs = (V == 8 && !W) ? A.K / 2 : 0;  // offset of a thread's second run of samples
   const int64_t base = (int64_t)kv * (W ? 8 : 4);   // offset of its first run
   const int64_t off = row * A.K + base;
-  const uint32_t desc = A.ell_desc[row];
+  const int lr = SMD ? (int)(row - r0) : 0;  // row within the staged chunk
+  const uint32_t desc = SMD ? sm->desc[lr] : A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;  // stiffness + boundary entries
   // V = 8: all 8 columns and coefficient pairs loaded up front; V = 4: per
@@ -406,6 +425,13 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
                  : "=f"(h45.x), "=f"(h45.y), "=f"(h45.z), "=f"(h45.w), "=f"(h67.x), "=f"(h67.y), "=f"(h67.z),
                    "=f"(h67.w)
                  : "l"(A.ell_hl + row * 8 + 4));
+  } else if constexpr (SMD) {
+    c0 = sm->col[2 * lr];
+    c1 = sm->col[2 * lr + 1];
+    h01 = sm->hl[4 * lr];
+    h23 = sm->hl[4 * lr + 1];
+    h45 = sm->hl[4 * lr + 2];
+    h67 = sm->hl[4 * lr + 3];
   } else if constexpr (H) {
     const uint64_t keep = l2_policy_last();
     c0 = ld_hint_u4(A.ell_col + row * 8, keep);
@@ -590,6 +616,63 @@ __global__ void __launch_bounds__(BS, BS == 256 ? (V == 8 ? 4 : 5) : 1) step3e_p
     const int64_t c = cb + (threadIdx.x >> 5);
     if (c < n_chunks) step3e_row<V, ADJ, W, H>(A, c * 32 + lane);
   }
+}
+
+// Persistent grid-stride kernel with the row metadata software-pipelined
+// through shared memory: while a warp processes chunk c, its lanes have
+// cp.async copies of chunk c + S's descriptors, columns and coefficient pairs
+// in flight into the warp's other stage buffer, so a chunk's critical path
+// starts with shared-memory reads instead of an L2 round trip before the
+// neighbour gather.  V = 8, K / V >= 4 (at most kStageRows rows per chunk),
+// rows in natural order.  Optional L2 bulk prefetch as in the persistent kernel.
+template <bool ADJ>
+__global__ void __launch_bounds__(256, 4) step3e_stage_kernel(const Step3Args<float> A, int64_t n_chunks) {
+  constexpr int V = 8, WPB = 8;
+  __shared__ EllStage stage[WPB][2];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int KV = A.K / V;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t S = (int64_t)gridDim.x * WPB;
+  // copies of chunk c's metadata into dst: per row one 4-byte descriptor,
+  // two 16-byte column pieces, four 16-byte coefficient pieces
+  auto issue = [&](int64_t c, EllStage* dst) {
+    const int64_t t0 = c * 32;
+    if (t0 < A.row_threads) {
+      const int64_t q0 = div_kv(t0, KV), q1 = div_kv(min(t0 + 32, A.row_threads) - 1, KV);
+      const int total = (int)(q1 - q0 + 1) * 7;
+      for (int i = lane; i < total; i += 32) {
+        const int r = i / 7, part = i - 7 * r;
+        const int64_t row = q0 + r;
+        if (part == 0)
+          cp_async4(&dst->desc[r], A.ell_desc + row);
+        else if (part < 3)
+          cp_async16(&dst->col[2 * r + part - 1], A.ell_col + row * 8 + 4 * (part - 1));
+        else
+          cp_async16(&dst->hl[4 * r + part - 3], A.ell_hl + row * 8 + 2 * (part - 3));
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int64_t c = (int64_t)blockIdx.x * WPB + w;
+  int s = 0;
+  issue(c, &stage[w][0]);
+  for (; c < n_chunks; c += S) {
+    if (A.pf_rows > 0 && threadIdx.x == 0) {
+      const int64_t cb = c - w, t0 = (cb + A.pf_rows * S) * 32;
+      if (t0 < A.row_threads)
+        prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(min(t0 + 32 * (int64_t)WPB, A.row_threads) - 1, KV) + 1);
+    }
+    issue(c + S, &stage[w][s ^ 1]);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp();
+    const int64_t t0 = c * 32;
+    const int64_t r0 = t0 < A.row_threads ? div_kv(t0, KV) : 0;
+    step3e_row<V, ADJ, false, false, true>(A, t0 + lane, &stage[w][s], r0);
+    __syncwarp();
+    s ^= 1;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Persistent slab form: block b owns the contiguous chunk range

@@ -117,7 +117,8 @@ def test_full_size_batched_forward_sampled_columns():
 # the persistent fixed-width variants the autotuner picks on the benchmark mesh
 BENCH_VARIANTS = [dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1),
                   dict(V=8, packed=3, persistent=1, pdl=True, big_blocks=True),
-                  dict(V=8, packed=3, persistent=1, pdl=True, wide_loads=True)]
+                  dict(V=8, packed=3, persistent=1, pdl=True, wide_loads=True),
+                  dict(V=8, packed=3, persistent=3, pdl=True)]
 
 
 @pytest.mark.parametrize("K", [8, 24])
