@@ -322,12 +322,14 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * (persistent, V = 8: each thread's 8 samples read and written by one 256-bit
  * access), l2_hints (persistent grid-stride, V = 8, 128-bit: the new state
  * and the row metadata stored / loaded with L2 evict_last priority, the last
- * read of x_{s-1} with evict_first), us per step};
+ * read of x_{s-1} with evict_first), gather_batch (persistent grid-stride,
+ * V = 8, 128-bit: source rows loaded per batch before any is used, 0 = 4;
+ * 8 runs at 2 blocks per SM, 2 at min_blocks 5 or 6), us per step};
  * *n_entries the number of variants timed.  Synchronises the stream.
  */
 typedef struct {
   int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent, pdl,
-      wide_loads, l2_hints;
+      wide_loads, l2_hints, gather_batch;
   double us_per_step;
 } pat_tune_entry;
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,

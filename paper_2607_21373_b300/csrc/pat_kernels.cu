@@ -316,6 +316,14 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
     if (c.hint && c.persist == 1 && bs == 256) kern = step3e_persist_kernel<V, ADJ, false, 256, true>;
     // metadata staged through shared memory: at most kStageRows rows per 32-thread chunk
     if (c.persist == 3 && a.K / V >= 4 && !a.order) kern = step3e_stage_kernel<ADJ>;
+    if (c.batch && c.persist == 1 && bs == 256 && !c.hint) {
+      if (c.batch == 8)
+        kern = step3e_persist_kernel<V, ADJ, false, 256, false, 8, 2>;
+      else if (c.batch == 2 && c.minb == 6)
+        kern = step3e_persist_kernel<V, ADJ, false, 256, false, 2, 6>;
+      else if (c.batch == 2)
+        kern = step3e_persist_kernel<V, ADJ, false, 256, false, 2, 5>;
+    }
   }
   const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
   const int64_t grid =
@@ -1184,7 +1192,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 41; ++variant_id) {
+      for (int variant_id = 0; variant_id < 45; ++variant_id) {
         // packed f32x2 kernels (FP32 split, V = 4 or 8):
         //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
         //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
@@ -1205,7 +1213,9 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         // 34, 35: grid-stride persistent, PDL, 1024-thread blocks, 256- / 128-bit loads;
         // 36, 37: grid-stride persistent, PDL, L2 eviction hints, no / 1 stride prefetch;
         // 38, 39, 40: grid-stride persistent, row metadata staged through shared memory by
-        // cp.async one chunk ahead, PDL / PDL + 1 stride prefetch / neither
+        // cp.async one chunk ahead, PDL / PDL + 1 stride prefetch / neither;
+        // 41, 42: grid-stride persistent, PDL, all 8 source rows in flight (2 blocks per SM),
+        // no / 1 stride prefetch; 43, 44: source rows in batches of 2 at >= 5 / >= 6 blocks per SM
         const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
                             variant_id == 16 || variant_id == 20 || variant_id == 21)
                                ? 1
@@ -1224,8 +1234,11 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         const int pf = (variant_id == 19 || variant_id == 24) ? 2
                        : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27 ||
                           variant_id == 29 || variant_id == 31 || variant_id == 33 || variant_id == 37 ||
-                          variant_id == 39) ? 1 : 0;
-        const int persist = variant_id >= 38 ? 3 : variant_id >= 34 ? 1 : variant_id >= 30 ? 2 : variant_id >= 23 ? 1 : 0;
+                          variant_id == 39 || variant_id == 42) ? 1 : 0;
+        const int persist = variant_id >= 41 ? 1 : variant_id >= 38 ? 3 : variant_id >= 34 ? 1 : variant_id >= 30 ? 2
+                            : variant_id >= 23 ? 1 : 0;
+        const int batch = variant_id >= 43 ? 2 : variant_id >= 41 ? 8 : 0;
+        if (batch && V != 8) continue;
         if (persist == 3 && (V != 8 || K / V < 4)) continue;
         const int hint = (variant_id == 36 || variant_id == 37) ? 1 : 0;
         if (hint && V != 8) continue;
@@ -1235,9 +1248,9 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         if (variant_id == 22 && V != 4) continue;
         if ((pf || persist) && V == 1) continue;
         if (big && V != 8) continue;
-        const int minb = (variant_id == 5 || variant_id == 6 || variant_id == 22) ? 6 : 1;
+        const int minb = (variant_id == 5 || variant_id == 6 || variant_id == 22 || variant_id == 44) ? 6 : 1;
         const int early = (variant_id == 3 || variant_id == 4) ? 1 : 0;
-        if (minb > 1 && V == 8) continue;  // would spill
+        if (minb > 1 && V == 8 && batch != 2) continue;  // would spill
         if (packed == 1 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8))) continue;
         if (packed == 2 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 8 * 1024 / kTileRows && m.n_tiles > 0))
           continue;
@@ -1263,6 +1276,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.pdl = pdl;
         g_force.wide = wide;
         g_force.hint = hint;
+        g_force.batch = batch;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1270,7 +1284,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         if (s) return s;
         if (table && n < 128)
           table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf,
-                                    persist, pdl, wide, hint, (double)us};
+                                    persist, pdl, wide, hint, batch, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

@@ -386,7 +386,7 @@ __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<flo
   if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
-template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false>
+template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false, int NB = 4>
 __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t,
                                            const EllStage* sm = nullptr, int64_t r0 = 0) {
   static_assert(!H || (V == 8 && !W), "cache-hint variant: V = 8, 128-bit loads");
@@ -440,7 +440,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
     h23 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 2), keep);
     h45 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 4), keep);
     h67 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 6), keep);
-  } else if constexpr (V == 8) {
+  } else if constexpr (V == 8 && NB != 2) {
     c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
     c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
     h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
@@ -454,21 +454,45 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
   for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
   if (A.x) {
     const float* xk = A.x + base;
-    if constexpr (V == 8) {
+    if constexpr (V == 8 && NB == 2) {
+      // batches of 2 source rows, each batch's 2 columns and coefficient pairs
+      // loaded with it (L1 hits after the first): fewest live registers
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const uint2 cq = *reinterpret_cast<const uint2*>(A.ell_col + row * 8 + 2 * h);
+        u64 x[2][P];
+        ld_runs<V, W>(xk + (size_t)cq.x * Ku, hs, x[0]);
+        ld_runs<V, W>(xk + (size_t)cq.y * Ku, hs, x[1]);
+        const float4 hq = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 2 * h);
+        const float2 cf[2] = {make_float2(hq.x, hq.y), make_float2(hq.z, hq.w)};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const u64 ch = dup2(cf[q].x), cl = dup2(cf[q].y);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            acc[p] = ffma2(ch, x[q][p], acc[p]);
+            accl[p] = ffma2(cl, x[q][p], accl[p]);
+          }
+        }
+      }
+    } else if constexpr (V == 8) {
       const uint32_t cols[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
       const float2 cf[8] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
                             make_float2(h23.z, h23.w), make_float2(h45.x, h45.y), make_float2(h45.z, h45.w),
                             make_float2(h67.x, h67.y), make_float2(h67.z, h67.w)};
+      // NB source rows in flight per batch: 8 (one gather latency per row,
+      // more registers), 4 (default) or 2 (fewer registers, more warps)
+      static_assert(NB == 2 || NB == 4 || NB == 8, "batch of 2, 4 or 8 source rows");
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        u64 x[4][P];
+      for (int h = 0; h < 8 / NB; ++h) {
+        u64 x[NB][P];
         // the 8 slots hold only stiffness / boundary entries and padding (the
         // row itself with a zero coefficient): no per-entry test
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ld_runs<V, W>(xk + (size_t)cols[4 * h + q] * Ku, hs, x[q]);
+        for (int q = 0; q < NB; ++q) ld_runs<V, W>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 c = cf[4 * h + q];
+        for (int q = 0; q < NB; ++q) {
+          const float2 c = cf[NB * h + q];
           const u64 ch = dup2(c.x), cl = dup2(c.y);
 #pragma unroll
           for (int p = 0; p < P; ++p) {
@@ -538,6 +562,27 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
       }
     }
   }
+  if constexpr (V == 8 && NB == 2) {
+    // the update one run of 4 samples at a time (fewer live registers)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int64_t o = off + r * hs;
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 xv = A.x ? *reinterpret_cast<const float4*>(A.x + o) : z;
+      const float4 pv = A.prev_mode == 0 ? *reinterpret_cast<const float4*>(A.xp + o) : (A.prev_mode == 1 ? xv : z);
+      const float xs[4] = {xv.x, xv.y, xv.z, xv.w}, ps[4] = {pv.x, pv.y, pv.z, pv.w};
+      float out[4];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const float2 a = unpack2(acc[2 * r + p]), al = unpack2(accl[2 * r + p]);
+        const float w0 = xs[2 * p] - ps[2 * p], w1 = xs[2 * p + 1] - ps[2 * p + 1];
+        out[2 * p] = xs[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[4 * r + 2 * p]);
+        out[2 * p + 1] = xs[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[4 * r + 2 * p + 1]);
+      }
+      *reinterpret_cast<float4*>(A.xn + o) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    return;
+  }
   Pack<float, V> xi, xpi, xo;
   if (A.x) {
     xi = ld_run_pack<V, W>(A.x + off, hs);
@@ -598,9 +643,9 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3
 // Launched as a programmatic dependent of the previous step, the grid's blocks
 // may become resident while that step drains; griddepcontrol.wait holds them
 // until it has completed and its writes are visible (a no-op otherwise).
-template <int V, bool ADJ, bool W, int BS = 256, bool H = false>
-__global__ void __launch_bounds__(BS, BS == 256 ? (V == 8 ? 4 : 5) : 1) step3e_persist_kernel(const Step3Args<float> A,
-                                                                                              int64_t n_chunks) {
+template <int V, bool ADJ, bool W, int BS = 256, bool H = false, int NB = 4,
+          int MINB = (BS == 256 ? (V == 8 ? 4 : 5) : 1)>
+__global__ void __launch_bounds__(BS, MINB) step3e_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int KV = A.K / V;
@@ -614,7 +659,7 @@ __global__ void __launch_bounds__(BS, BS == 256 ? (V == 8 ? 4 : 5) : 1) step3e_p
         prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(min(t0 + 32 * (int64_t)wpb, A.row_threads) - 1, KV) + 1);
     }
     const int64_t c = cb + (threadIdx.x >> 5);
-    if (c < n_chunks) step3e_row<V, ADJ, W, H>(A, c * 32 + lane);
+    if (c < n_chunks) step3e_row<V, ADJ, W, H, false, NB>(A, c * 32 + lane);
   }
 }
 

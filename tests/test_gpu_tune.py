@@ -46,7 +46,9 @@ VARIANTS = [dict(V=8, packed=2), dict(V=8, packed=1, chunk=2), dict(V=8, packed=
             dict(V=4, packed=3, persistent=2, prefetch=1),
             dict(V=8, packed=3, persistent=1, pdl=True, wide_loads=True, big_blocks=True),
             dict(V=8, packed=3, persistent=1, pdl=True, l2_hints=True, prefetch=1),
-            dict(V=8, packed=3, persistent=3, pdl=True), dict(V=8, packed=3, persistent=3, prefetch=1)]
+            dict(V=8, packed=3, persistent=3, pdl=True), dict(V=8, packed=3, persistent=3, prefetch=1),
+            dict(V=8, packed=3, persistent=1, pdl=True, gather_batch=8),
+            dict(V=8, packed=3, persistent=1, pdl=True, gather_batch=2, min_blocks=6)]
 
 
 @pytest.mark.parametrize("K", [16, 64])
