@@ -1177,6 +1177,89 @@ static pat_status probe_t(const DeviceMesh& m, int K, char* ws, int n_probe, int
   return s;
 }
 
+// Step-kernel variants timed by pat_autotune (fields as in TuneCfg; only_v: the
+// one V a variant is written for, 0 = any).  The packed f32x2 CSR, generic,
+// tile-staged and fixed-width (ELL) families and their options; the persistent
+// fixed-width ones are the fastest on large meshes.
+struct TuneVariant {
+  int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v;
+};
+static const TuneVariant kTuneVariants[] = {
+    // packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v
+    {1, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  //  0 packed f32x2, chunks of 2
+    {1, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  //  1 packed, chunks of 4
+    {1, 0, 8, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  //  2 packed, chunks of 8
+    {1, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 0},  //  3 packed, chunks of 2, own values first
+    {1, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 0},  //  4 packed, chunks of 4, own values first
+    {1, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 6, 0, 0},  //  5 packed, chunks of 2, >= 6 blocks/SM
+    {1, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 6, 0, 0},  //  6 packed, chunks of 4, >= 6 blocks/SM
+    {0, 1, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  //  7 generic, metadata staged in shared memory
+    {0, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  //  8 generic
+    {2, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  //  9 tile-staged (bulk copies of 32-row tiles' source rows)
+    {1, 0, 2, 1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 10 packed, chunks of 2, Z-order rows
+    {1, 0, 4, 1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 11 packed, chunks of 4, Z-order rows
+    {3, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 12 fixed-width (ELL)
+    {4, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 13 persistent double-buffered tiles
+    {1, 0, 2, 1, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 14 packed, chunks of 2, 1024-thread blocks, Z-order
+    {3, 0, 4, 1, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 15 fixed-width, 1024-thread blocks, Z-order
+    {1, 0, 2, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 16 packed, chunks of 2, 1024-thread blocks
+    {3, 0, 4, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 17 fixed-width, 1024-thread blocks
+    {3, 0, 4, 0, 0, 1, 0, 0, 0, 0, 0, 1, 0, 0},  // 18 fixed-width, L2 prefetch 1 wave
+    {3, 0, 4, 0, 0, 2, 0, 0, 0, 0, 0, 1, 0, 0},  // 19 fixed-width, L2 prefetch 2 waves
+    {1, 0, 2, 0, 0, 1, 0, 0, 0, 0, 0, 1, 0, 0},  // 20 packed, chunks of 2, L2 prefetch 1 wave
+    {1, 0, 4, 0, 0, 1, 0, 0, 0, 0, 0, 1, 0, 0},  // 21 packed, chunks of 4, L2 prefetch 1 wave
+    {3, 0, 4, 0, 0, 1, 0, 0, 0, 0, 0, 6, 0, 4},  // 22 fixed-width, >= 6 blocks/SM, L2 prefetch (V = 4)
+    {3, 0, 4, 0, 0, 1, 1, 0, 0, 0, 0, 1, 0, 0},  // 23 persistent, prefetch 1 stride
+    {3, 0, 4, 0, 0, 2, 1, 0, 0, 0, 0, 1, 0, 0},  // 24 persistent, prefetch 2 strides
+    {3, 0, 4, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0},  // 25 persistent
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 0, 1, 0, 0},  // 26 persistent, PDL
+    {3, 0, 4, 0, 0, 1, 1, 1, 0, 0, 0, 1, 0, 0},  // 27 persistent, PDL, prefetch 1
+    {3, 0, 4, 0, 0, 0, 1, 1, 1, 0, 0, 1, 0, 0},  // 28 persistent, PDL, 256-bit loads
+    {3, 0, 4, 0, 0, 1, 1, 1, 1, 0, 0, 1, 0, 0},  // 29 persistent, PDL, 256-bit loads, prefetch 1
+    {3, 0, 4, 0, 0, 0, 2, 1, 1, 0, 0, 1, 0, 0},  // 30 slabs, PDL, 256-bit loads
+    {3, 0, 4, 0, 0, 1, 2, 1, 1, 0, 0, 1, 0, 0},  // 31 slabs, PDL, 256-bit loads, prefetch 1
+    {3, 0, 4, 0, 0, 0, 2, 1, 0, 0, 0, 1, 0, 0},  // 32 slabs, PDL
+    {3, 0, 4, 0, 0, 1, 2, 1, 0, 0, 0, 1, 0, 0},  // 33 slabs, PDL, prefetch 1
+    {3, 0, 4, 0, 1, 0, 1, 1, 1, 0, 0, 1, 0, 0},  // 34 persistent, PDL, 1024-thread blocks, 256-bit loads
+    {3, 0, 4, 0, 1, 0, 1, 1, 0, 0, 0, 1, 0, 0},  // 35 persistent, PDL, 1024-thread blocks
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 1, 0, 1, 0, 0},  // 36 persistent, PDL, L2 eviction hints
+    {3, 0, 4, 0, 0, 1, 1, 1, 0, 1, 0, 1, 0, 0},  // 37 persistent, PDL, L2 eviction hints, prefetch 1
+    {3, 0, 4, 0, 0, 0, 3, 1, 0, 0, 0, 1, 0, 0},  // 38 persistent, staged metadata, PDL
+    {3, 0, 4, 0, 0, 1, 3, 1, 0, 0, 0, 1, 0, 0},  // 39 persistent, staged metadata, PDL, prefetch 1
+    {3, 0, 4, 0, 0, 0, 3, 0, 0, 0, 0, 1, 0, 0},  // 40 persistent, staged metadata
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 8, 1, 0, 0},  // 41 persistent, PDL, batches of 8 source rows
+    {3, 0, 4, 0, 0, 1, 1, 1, 0, 0, 8, 1, 0, 0},  // 42 persistent, PDL, batches of 8, prefetch 1
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 2, 1, 0, 0},  // 43 persistent, PDL, batches of 2
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 2, 6, 0, 0},  // 44 persistent, PDL, batches of 2, >= 6 blocks/SM
+};
+
+// Whether variant t exists for V samples per thread and K samples on mesh m.
+static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, int K) {
+  if (t.only_v && V != t.only_v) return false;
+  if ((t.batch || t.hint || t.wide || t.big) && V != 8) return false;
+  if (t.persist == 3 && (V != 8 || K / V < 4)) return false;  // staged metadata: <= kStageRows rows per chunk
+  if ((t.pf || t.persist) && V == 1) return false;
+  if (t.minb > 1 && V == 8 && t.batch != 2) return false;  // would spill
+  const bool f32s = m.prec == PAT_F32 && m.split;
+  switch (t.packed) {
+    case 1:
+      if (!(f32s && (V == 4 || V == 8)) || (t.chunk == 8 && V == 8)) return false;
+      break;
+    case 2:
+      if (!(f32s && V == 8 && K <= 8 * 1024 / kTileRows && m.n_tiles > 0)) return false;
+      break;
+    case 3:
+      if (!(f32s && (V == 4 || V == 8 || (V == 1 && K == 1)) && m.fwd.ell_col)) return false;
+      break;
+    case 4:
+      if (!(f32s && V == 8 && K <= 8 * 512 / kTileRows && m.n_tiles > 0)) return false;
+      break;
+    default:
+      if (V == 8) return false;
+  }
+  return !(t.stage && K / V < 2);
+}
+
 pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_entry* table, int* n_entries,
                     cudaStream_t st) {
   const RtoLayout L = rto_layout(m, K);
@@ -1192,99 +1275,32 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
     float best_us = 1e30f;
     for (int V = vmax; V >= 1; V /= 2) {
       if (K % V) continue;
-      for (int variant_id = 0; variant_id < 45; ++variant_id) {
-        // packed f32x2 kernels (FP32 split, V = 4 or 8):
-        //   0, 1, 2: chunks of 2 / 4 / 8 row entries; 3, 4: chunks of 2 / 4, own values loaded
-        //   before the row walk; 5, 6: chunks of 2 / 4, >= 6 resident blocks per SM;
-        // generic kernels: 7 row metadata staged in shared memory; 8 read directly
-        // 9: tile-staged kernel (source rows of 32-row tiles staged by bulk copies);
-        // 10, 11: packed, chunks of 2 / 4, rows processed in Z-order
-        // 12: fixed-width (ELL) packed kernel; 13: persistent double-buffered tiles
-        // 14, 15: packed chunks of 2 / fixed-width, 1024-thread blocks, Z-order rows;
-        // 16, 17: the same without Z-order
-        // 18, 19: fixed-width, L2 prefetch of the rows one / two resident waves ahead;
-        // 20, 21: packed chunks of 2 / 4, L2 prefetch one wave ahead
-        // 22: fixed-width, >= 6 resident blocks per SM, L2 prefetch one wave ahead
-        // 23, 24, 25: fixed-width, persistent warps, L2 prefetch 1 / 2 / no strides ahead;
-        // 26, 27: fixed-width, persistent, programmatic dependent launch, no / 1 stride prefetch;
-        // 28, 29: the same with 256-bit loads (V = 8);
-        // 30, 31: slab-walking persistent, PDL, 256-bit loads, no / 1 block-iteration prefetch;
-        // 32, 33: the same with 128-bit loads;
-        // 34, 35: grid-stride persistent, PDL, 1024-thread blocks, 256- / 128-bit loads;
-        // 36, 37: grid-stride persistent, PDL, L2 eviction hints, no / 1 stride prefetch;
-        // 38, 39, 40: grid-stride persistent, row metadata staged through shared memory by
-        // cp.async one chunk ahead, PDL / PDL + 1 stride prefetch / neither;
-        // 41, 42: grid-stride persistent, PDL, all 8 source rows in flight (2 blocks per SM),
-        // no / 1 stride prefetch; 43, 44: source rows in batches of 2 at >= 5 / >= 6 blocks per SM
-        const int packed = (variant_id <= 6 || variant_id == 10 || variant_id == 11 || variant_id == 14 ||
-                            variant_id == 16 || variant_id == 20 || variant_id == 21)
-                               ? 1
-                               : (variant_id == 9 ? 2
-                                  : (variant_id == 12 || variant_id == 15 || variant_id == 17 ||
-                                     variant_id == 18 || variant_id == 19 || variant_id >= 22)
-                                      ? 3
-                                      : (variant_id == 13 ? 4 : 0)),
-                  stage = variant_id == 7;
-        const int chunk = (variant_id == 0 || variant_id == 3 || variant_id == 5 || variant_id == 10 ||
-                           variant_id == 14 || variant_id == 16 || variant_id == 20)
-                              ? 2
-                              : (variant_id == 2 ? 8 : 4);
-        const int zorder = (variant_id == 10 || variant_id == 11 || variant_id == 14 || variant_id == 15) ? 1 : 0;
-        const int big = ((variant_id >= 14 && variant_id <= 17) || variant_id == 34 || variant_id == 35) ? 1 : 0;
-        const int pf = (variant_id == 19 || variant_id == 24) ? 2
-                       : (variant_id == 18 || (variant_id >= 20 && variant_id <= 23) || variant_id == 27 ||
-                          variant_id == 29 || variant_id == 31 || variant_id == 33 || variant_id == 37 ||
-                          variant_id == 39 || variant_id == 42) ? 1 : 0;
-        const int persist = variant_id >= 41 ? 1 : variant_id >= 38 ? 3 : variant_id >= 34 ? 1 : variant_id >= 30 ? 2
-                            : variant_id >= 23 ? 1 : 0;
-        const int batch = variant_id >= 43 ? 2 : variant_id >= 41 ? 8 : 0;
-        if (batch && V != 8) continue;
-        if (persist == 3 && (V != 8 || K / V < 4)) continue;
-        const int hint = (variant_id == 36 || variant_id == 37) ? 1 : 0;
-        if (hint && V != 8) continue;
-        const int pdl = (variant_id >= 26 && variant_id != 40) ? 1 : 0;
-        const int wide = ((variant_id >= 28 && variant_id <= 31) || variant_id == 34) ? 1 : 0;
-        if (wide && V != 8) continue;
-        if (variant_id == 22 && V != 4) continue;
-        if ((pf || persist) && V == 1) continue;
-        if (big && V != 8) continue;
-        const int minb = (variant_id == 5 || variant_id == 6 || variant_id == 22 || variant_id == 44) ? 6 : 1;
-        const int early = (variant_id == 3 || variant_id == 4) ? 1 : 0;
-        if (minb > 1 && V == 8 && batch != 2) continue;  // would spill
-        if (packed == 1 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8))) continue;
-        if (packed == 2 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 8 * 1024 / kTileRows && m.n_tiles > 0))
-          continue;
-        if (packed == 4 && !(m.prec == PAT_F32 && m.split && V == 8 && K <= 8 * 512 / kTileRows && m.n_tiles > 0))
-          continue;
-        if (packed == 3 && !(m.prec == PAT_F32 && m.split && (V == 4 || V == 8 || (V == 1 && K == 1)) &&
-                             m.fwd.ell_col))
-          continue;
-        if (packed == 1 && chunk == 8 && V == 8) continue;
-        if (!packed && V == 8) continue;
-        if (stage && K / V < 2) continue;
+      for (const TuneVariant& t : kTuneVariants) {
+        if (!tune_applicable(t, m, V, K)) continue;
         g_force_on = true;
         g_force.V = V;
-        g_force.stage = stage;
-        g_force.packed = packed;
-        g_force.chunk = chunk;
-        g_force.minb = minb;
-        g_force.early = early;
-        g_force.order = zorder;
-        g_force.big = big;
-        g_force.pf = pf;
-        g_force.persist = persist;
-        g_force.pdl = pdl;
-        g_force.wide = wide;
-        g_force.hint = hint;
-        g_force.batch = batch;
+        g_force.stage = t.stage;
+        g_force.packed = t.packed;
+        g_force.chunk = t.chunk;
+        g_force.minb = t.minb;
+        g_force.early = t.early;
+        g_force.order = t.zorder;
+        g_force.big = t.big;
+        g_force.pf = t.pf;
+        g_force.persist = t.persist;
+        g_force.pdl = t.pdl;
+        g_force.wide = t.wide;
+        g_force.hint = t.hint;
+        g_force.batch = t.batch;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
         g_force_on = false;
         if (s) return s;
         if (table && n < 128)
-          table[n] = pat_tune_entry{dir, V, stage, packed, packed ? chunk : 0, minb, early, zorder, big, pf,
-                                    persist, pdl, wide, hint, batch, (double)us};
+          table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
+                                    t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
+                                    t.wide, t.hint,  t.batch, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;
