@@ -323,8 +323,10 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * access), l2_hints (persistent grid-stride, V = 8, 128-bit: the new state
  * and the row metadata stored / loaded with L2 evict_last priority, the last
  * read of x_{s-1} with evict_first), gather_batch (persistent grid-stride,
- * V = 8, 128-bit: source rows loaded per batch before any is used, 0 = 4;
- * 8 runs at 2 blocks per SM, 2 at min_blocks 5 or 6), us per step};
+ * V = 8, 128-bit: source rows loaded per batch before any is used; 0 = 4
+ * with the row's metadata loaded up front; 8 runs at 2 blocks per SM; 2 or 4
+ * load each batch's metadata with it, with min_blocks 1 (4 per SM), 5 or 6),
+ * us per step};
  * *n_entries the number of variants timed.  Synchronises the stream.
  */
 typedef struct {

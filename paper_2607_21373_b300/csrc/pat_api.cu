@@ -861,8 +861,12 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
                                      : false;
   const bool ok_pf = v->prefetch == 0 || (v->prefetch >= 1 && v->prefetch <= 4 && (v->packed == 1 || v->packed == 3) &&
                                           v->V != 1);
-  if (!ok_v || !ok_p || !ok_pf || (v->staged && K / v->V < 2) || (v->min_blocks != 1 && v->min_blocks != 6) ||
-      (v->min_blocks == 6 && v->V == 8 && !(v->packed == 3 && v->persistent == 1 && v->gather_batch == 2))) {
+  // min_blocks 5 or 6 with V = 8 only for the persistent kernels whose source rows and
+  // metadata come per batch (2 or 4 rows); otherwise they would spill
+  const bool batched8 = v->packed == 3 && v->persistent == 1 && (v->gather_batch == 2 || v->gather_batch == 4);
+  if (!ok_v || !ok_p || !ok_pf || (v->staged && K / v->V < 2) ||
+      (v->min_blocks != 1 && v->min_blocks != 6 && !(v->min_blocks == 5 && batched8)) ||
+      (v->min_blocks > 1 && v->V == 8 && !batched8)) {
     set_error("pat_select_variant: variant V=%d packed=%d chunk=%d staged=%d is not available for K=%d on this mesh",
               v->V, v->packed, v->chunk, v->staged, K);
     return PAT_EINVAL;
@@ -883,7 +887,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   c.wide = c.persist && v->wide_loads && v->V == 8;
   c.hint = c.persist == 1 && !c.wide && !c.big && v->l2_hints && v->V == 8;
   c.batch = (c.persist == 1 && !c.wide && !c.big && !c.hint && v->V == 8 &&
-             (v->gather_batch == 2 || v->gather_batch == 8))
+             (v->gather_batch == 2 || v->gather_batch == 4 || v->gather_batch == 8))
                 ? v->gather_batch
                 : 0;
   {

@@ -111,7 +111,8 @@ struct TuneCfg {
   int pdl = 0;     // persistent kernel: programmatic dependent launch
   int wide = 0;    // persistent kernel, V = 8: 256-bit loads of 8 contiguous samples
   int hint = 0;    // persistent kernel, V = 8: L2 eviction-priority hints
-  int batch = 0;   // persistent kernel, V = 8: source rows in flight per batch (0: 4; 8; 2)
+  int batch = 0;   // persistent kernel, V = 8: source rows in flight per batch (0: 4 with the row's
+                   // metadata loaded up front; 8; 2 or 4 with each batch's metadata loaded with it)
 };
 
 struct DeviceMesh {

@@ -323,6 +323,10 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
         kern = step3e_persist_kernel<V, ADJ, false, 256, false, 2, 6>;
       else if (c.batch == 2)
         kern = step3e_persist_kernel<V, ADJ, false, 256, false, 2, 5>;
+      else if (c.batch == 4 && c.minb == 5)
+        kern = step3e_persist_kernel<V, ADJ, false, 256, false, 4, 5, true>;
+      else if (c.batch == 4)
+        kern = step3e_persist_kernel<V, ADJ, false, 256, false, 4, 4, true>;
     }
   }
   const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
@@ -1231,6 +1235,8 @@ static const TuneVariant kTuneVariants[] = {
     {3, 0, 4, 0, 0, 1, 1, 1, 0, 0, 8, 1, 0, 0},  // 42 persistent, PDL, batches of 8, prefetch 1
     {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 2, 1, 0, 0},  // 43 persistent, PDL, batches of 2
     {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 2, 6, 0, 0},  // 44 persistent, PDL, batches of 2, >= 6 blocks/SM
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 0},  // 45 persistent, PDL, batches of 4, metadata per batch
+    {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 5, 0, 0},  // 46 the same, >= 5 blocks/SM
 };
 
 // Whether variant t exists for V samples per thread and K samples on mesh m.
@@ -1239,7 +1245,7 @@ static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, in
   if ((t.batch || t.hint || t.wide || t.big) && V != 8) return false;
   if (t.persist == 3 && (V != 8 || K / V < 4)) return false;  // staged metadata: <= kStageRows rows per chunk
   if ((t.pf || t.persist) && V == 1) return false;
-  if (t.minb > 1 && V == 8 && t.batch != 2) return false;  // would spill
+  if (t.minb > 1 && V == 8 && t.batch == 0) return false;  // would spill
   const bool f32s = m.prec == PAT_F32 && m.split;
   switch (t.packed) {
     case 1:

@@ -386,7 +386,7 @@ __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<flo
   if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
-template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false, int NB = 4>
+template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false, int NB = 4, bool PB = (NB == 2)>
 __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t,
                                            const EllStage* sm = nullptr, int64_t r0 = 0) {
   static_assert(!H || (V == 8 && !W), "cache-hint variant: V = 8, 128-bit loads");
@@ -440,7 +440,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
     h23 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 2), keep);
     h45 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 4), keep);
     h67 = ld_hint_f4(reinterpret_cast<const float*>(A.ell_hl + row * 8 + 6), keep);
-  } else if constexpr (V == 8 && NB != 2) {
+  } else if constexpr (V == 8 && !PB) {
     c0 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8);
     c1 = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4);
     h01 = *reinterpret_cast<const float4*>(A.ell_hl + row * 8);
@@ -454,19 +454,33 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
   for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
   if (A.x) {
     const float* xk = A.x + base;
-    if constexpr (V == 8 && NB == 2) {
-      // batches of 2 source rows, each batch's 2 columns and coefficient pairs
-      // loaded with it (L1 hits after the first): fewest live registers
+    if constexpr (V == 8 && PB) {
+      // batches of NB (2 or 4) source rows, each batch's columns and
+      // coefficient pairs loaded with it (L1 hits after the first): fewer live
+      // registers than loading all 8 up front
+      static_assert(NB == 2 || NB == 4, "per-batch metadata: batches of 2 or 4");
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const uint2 cq = *reinterpret_cast<const uint2*>(A.ell_col + row * 8 + 2 * h);
-        u64 x[2][P];
-        ld_runs<V, W>(xk + (size_t)cq.x * Ku, hs, x[0]);
-        ld_runs<V, W>(xk + (size_t)cq.y * Ku, hs, x[1]);
-        const float4 hq = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + 2 * h);
-        const float2 cf[2] = {make_float2(hq.x, hq.y), make_float2(hq.z, hq.w)};
+      for (int h = 0; h < 8 / NB; ++h) {
+        uint32_t cq[NB];
+        if constexpr (NB == 2) {
+          const uint2 c = *reinterpret_cast<const uint2*>(A.ell_col + row * 8 + 2 * h);
+          cq[0] = c.x, cq[1] = c.y;
+        } else {
+          const uint4 c = *reinterpret_cast<const uint4*>(A.ell_col + row * 8 + 4 * h);
+          cq[0] = c.x, cq[1] = c.y, cq[2] = c.z, cq[3] = c.w;
+        }
+        u64 x[NB][P];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < NB; ++q) ld_runs<V, W>(xk + (size_t)cq[q] * Ku, hs, x[q]);
+        float2 cf[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q += 2) {
+          const float4 hq = *reinterpret_cast<const float4*>(A.ell_hl + row * 8 + NB * h + q);
+          cf[q] = make_float2(hq.x, hq.y);
+          cf[q + 1] = make_float2(hq.z, hq.w);
+        }
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
           const u64 ch = dup2(cf[q].x), cl = dup2(cf[q].y);
 #pragma unroll
           for (int p = 0; p < P; ++p) {
@@ -562,7 +576,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
       }
     }
   }
-  if constexpr (V == 8 && NB == 2) {
+  if constexpr (V == 8 && PB) {
     // the update one run of 4 samples at a time (fewer live registers)
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -644,7 +658,7 @@ __global__ void __launch_bounds__(256, V == 8 ? 4 : 5) step3e_kernel(const Step3
 // may become resident while that step drains; griddepcontrol.wait holds them
 // until it has completed and its writes are visible (a no-op otherwise).
 template <int V, bool ADJ, bool W, int BS = 256, bool H = false, int NB = 4,
-          int MINB = (BS == 256 ? (V == 8 ? 4 : 5) : 1)>
+          int MINB = (BS == 256 ? (V == 8 ? 4 : 5) : 1), bool PB = (NB == 2)>
 __global__ void __launch_bounds__(BS, MINB) step3e_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -659,7 +673,7 @@ __global__ void __launch_bounds__(BS, MINB) step3e_persist_kernel(const Step3Arg
         prefetch_ahead<true>(A, div_kv(t0, KV), div_kv(min(t0 + 32 * (int64_t)wpb, A.row_threads) - 1, KV) + 1);
     }
     const int64_t c = cb + (threadIdx.x >> 5);
-    if (c < n_chunks) step3e_row<V, ADJ, W, H, false, NB>(A, c * 32 + lane);
+    if (c < n_chunks) step3e_row<V, ADJ, W, H, false, NB, PB>(A, c * 32 + lane);
   }
 }
 

@@ -48,7 +48,8 @@ VARIANTS = [dict(V=8, packed=2), dict(V=8, packed=1, chunk=2), dict(V=8, packed=
             dict(V=8, packed=3, persistent=1, pdl=True, l2_hints=True, prefetch=1),
             dict(V=8, packed=3, persistent=3, pdl=True), dict(V=8, packed=3, persistent=3, prefetch=1),
             dict(V=8, packed=3, persistent=1, pdl=True, gather_batch=8),
-            dict(V=8, packed=3, persistent=1, pdl=True, gather_batch=2, min_blocks=6)]
+            dict(V=8, packed=3, persistent=1, pdl=True, gather_batch=2, min_blocks=6),
+            dict(V=8, packed=3, persistent=1, pdl=True, gather_batch=4, min_blocks=5)]
 
 
 @pytest.mark.parametrize("K", [16, 64])
