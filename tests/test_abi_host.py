@@ -111,3 +111,34 @@ def test_compute_on_host_only_mesh_is_refused():
     import ctypes as C
     st = L.pat_forward(m._h, C.c_void_p(16), 1, C.c_void_p(16), 1.0, C.c_void_p(256), 1 << 30, None)
     assert st == 1 and b"HOST_ONLY" in L.pat_last_error()
+
+
+def test_variant_selection_validates_combinations():
+    """pat_select_variant is pure host logic: it accepts the documented step-kernel
+    variants and refuses combinations that do not exist (PAT_EINVAL), without a GPU."""
+    from paper_2607_21373_b300 import PatError
+    n = 2
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(4, S.ALL_FACES, 1)
+    from paper_2607_21373_b300 import Mesh
+    m = Mesh(xyz, tets, det, 0.3 / n, 5, "f32", flags=0x8)
+    good = [dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1),
+            dict(V=8, packed=3, persistent=1, pdl=True, big_blocks=True),
+            dict(V=8, packed=3, persistent=3), dict(V=8, packed=3, persistent=2),
+            dict(V=8, packed=3, persistent=1, gather_batch=2, min_blocks=6),
+            dict(V=8, packed=3, persistent=1, gather_batch=4, min_blocks=5),
+            dict(V=4, packed=1, chunk=8), dict(V=4, packed=0, staged=True), dict(V=8, packed=2)]
+    for v in good:
+        for d in ("fwd", "adj"):
+            m.select_variant(64, d, **v)
+    bad = [(64, dict(V=8, packed=1, chunk=8)),                     # chunk 8 only with V = 4
+           (64, dict(V=8, packed=0)),                               # the generic kernel has no V = 8
+           (64, dict(V=8, packed=3, min_blocks=6)),                 # would spill
+           (64, dict(V=8, packed=3, persistent=1, min_blocks=5)),   # min_blocks 5 needs a per-batch gather
+           (12, dict(V=8, packed=3)),                               # V must divide K
+           (64, dict(V=4, packed=3, prefetch=9)),                   # prefetch distance 0..4
+           (1, dict(V=1, packed=3, prefetch=1)),                    # no prefetch for K = 1
+           (0, dict(V=1, packed=0))]                                # K out of range
+    for K, v in bad:
+        with pytest.raises(PatError, match="PAT_EINVAL"):
+            m.select_variant(K, "fwd", **v)
