@@ -41,6 +41,8 @@ METRIC = "rto_samples_per_s"
 PROFILED_TRAFFIC = {
     "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)": 160.643584e6,
     "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)": 159.604480e6,
+    "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)": 159.210752e6,
+    "step3e_persist_kernel<8,true> (1024-thread blocks, PDL)": 158.733312e6,
 }
 UNIT = "samples/s"
 
@@ -62,7 +64,7 @@ def parse():
     ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
     ap.add_argument("--autotune", type=int, default=1, help="0: keep the library's default step-kernel variant")
     ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4 | v8c2z | ell8 | ell4 | pipe | "
-                    "ell8pf | ell8p | ell8pw | ell8pp")
+                    "ell8pf | ell8p | ell8pw | ell8pp | ell8pb")
     return ap.parse_args()
 
 
@@ -225,7 +227,8 @@ def run_ours(a, rank, world, local_rank, dist):
               "ell8pf": dict(V=8, packed=3, prefetch=1),
               "ell8p": dict(V=8, packed=3, persistent=True),
               "ell8pw": dict(V=8, packed=3, persistent=True, pdl=True, wide_loads=True, prefetch=1),
-              "ell8pp": dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1)}.get(a.variant)
+              "ell8pp": dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1),
+              "ell8pb": dict(V=8, packed=3, persistent=1, pdl=True, big_blocks=True)}.get(a.variant)
     if forced:
         for d in ("fwd", "adj"):
             mesh.select_variant(K, d, **forced)
