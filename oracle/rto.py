@@ -10,9 +10,12 @@ the least-squares solution of G_ext p = b with
     G_ext = [sigma^{-1} G ; M_L^{1/2}],
     b     = [sigma^{-1}(y_obs + sigma eta) ; M_L^{1/2} p_prior],
     p_prior = C^{1/2} xi = M_L^{-1/2} xi,  eta, xi ~ N(0, I).
-The least-squares problem is solved by CGLS (the paper allows LSQR or CGLS,
-eq. normal-equations) started from x = 0 with a fixed number of iterations (the
-paper uses fixed iteration limits, Section 6.1), Algorithm 1.  The data-space
+The least-squares problem is solved by CGLS or by LSQR (Paige & Saunders 1982,
+the paper's solver; the paper allows either, eq. normal-equations) started from
+x = 0 with a fixed number of iterations (the paper uses fixed iteration limits,
+Section 6.1), Algorithm 1.  In exact arithmetic both produce the same iterates
+(the minimiser of ||A x - b|| over the k-th Krylov space of A^T A and A^T b).
+MAP (eq. MAP) is the same problem with zero perturbations.  The data-space
 norm is the plain Euclidean one (the dt of the L2(0,T) norm cancels in sigma).
 
 Statistics: eq. ergodic (mean, and std with 1/(N_sample - 1)).
@@ -87,6 +90,62 @@ def cgls(apply_A, apply_AT, b, n_iter, x_shape, batched):
     return st["x"], np.array(hist)
 
 
+def _div(a, b):
+    """a / b per column, 0 where b == 0 (a Golub-Kahan vector of norm 0 stays 0)."""
+    b = np.asarray(b, dtype=np.float64)
+    return np.where(b != 0.0, a / np.where(b != 0.0, b, 1.0), 0.0)
+
+
+def lsqr_begin(apply_AT, b, x_shape, batched):
+    """LSQR start (Paige & Saunders 1982, the paper's solver, Section 5.1):
+    beta_1 u_1 = b, alpha_1 v_1 = A^T u_1, w_1 = v_1, x_0 = 0,
+    phibar_1 = beta_1, rhobar_1 = alpha_1."""
+    beta = np.sqrt(_sq(b, batched))
+    u = tuple(_div(np.asarray(ui, dtype=np.float64), beta) for ui in b)
+    vh = apply_AT(u)
+    alpha = np.sqrt(_sq((vh,), batched))
+    v = _div(vh, alpha)
+    return {"x": np.zeros(x_shape), "u": u, "v": v, "w": v.copy(), "alpha": alpha,
+            "phibar": beta, "rhobar": alpha}
+
+
+def lsqr_step(apply_A, apply_AT, st, batched):
+    """One LSQR iteration: Golub-Kahan bidiagonalization
+        beta u' = A v - alpha u,   alpha' v' = A^T u' - beta v,
+    the plane rotation that eliminates beta from the lower bidiagonal
+        rho = (rhobar^2 + beta^2)^{1/2}, c = rhobar / rho, s = beta / rho,
+        theta = s alpha', rhobar' = -c alpha', phi = c phibar, phibar' = s phibar,
+    and the updates x += (phi / rho) w, w = v' - (theta / rho) w.
+    phibar' is the norm of the residual b - A x of the new iterate."""
+    Av = apply_A(st["v"])
+    uh = tuple(a - st["alpha"] * u for a, u in zip(Av, st["u"]))
+    beta = np.sqrt(_sq(uh, batched))
+    u = tuple(_div(x, beta) for x in uh)
+    vh = apply_AT(u) - beta * st["v"]
+    alpha = np.sqrt(_sq((vh,), batched))
+    v = _div(vh, alpha)
+    rho = np.sqrt(st["rhobar"] ** 2 + beta ** 2)
+    c, s = _div(st["rhobar"], rho), _div(beta, rho)
+    theta, rhobar = s * alpha, -c * alpha
+    phi, phibar = c * st["phibar"], s * st["phibar"]
+    x = st["x"] + _div(phi, rho) * st["w"]
+    w = v - _div(theta, rho) * st["w"]
+    return {"x": x, "u": u, "v": v, "w": w, "alpha": alpha, "phibar": phibar, "rhobar": rhobar}
+
+
+def lsqr(apply_A, apply_AT, b, n_iter, x_shape, batched):
+    """LSQR for min ||A x - b||_2 from x = 0, exactly n_iter iterations (the
+    paper's fixed iteration limits, Section 6.1).  Same block / batched
+    conventions as cgls.  Returns x and the history of phibar = ||b - A x||
+    (one entry per iterate, starting with ||b||)."""
+    st = lsqr_begin(apply_AT, b, x_shape, batched)
+    hist = [st["phibar"]]
+    for _ in range(n_iter):
+        st = lsqr_step(apply_A, apply_AT, st, batched)
+        hist.append(st["phibar"])
+    return st["x"], np.array(hist)
+
+
 def extended_operator(ops, dt, n_steps, sigma):
     """Actions of G_ext and G_ext^T (eq. lsqr-residual, eq. lsqr-transpose-action)."""
     ML = ops["ML"]
@@ -126,6 +185,33 @@ def rto_samples(ops, dt, n_steps, y_obs, sigma, eta, xi, n_iter):
     b = rto_rhs(ops, y_obs, sigma, eta, xi)
     batched = np.ndim(xi) == 2
     return cgls(apply_A, apply_AT, b, n_iter, np.shape(xi), batched)
+
+
+def rto_samples_lsqr(ops, dt, n_steps, y_obs, sigma, eta, xi, n_iter):
+    """RTO samples as Algorithm 1 states them, with LSQR.  Returns samples and
+    the phibar history (n_iter + 1, K)."""
+    apply_A, apply_AT = extended_operator(ops, dt, n_steps, sigma)
+    b = rto_rhs(ops, y_obs, sigma, eta, xi)
+    return lsqr(apply_A, apply_AT, b, n_iter, np.shape(xi), np.ndim(xi) == 2)
+
+
+def map_estimate(ops, dt, n_steps, y_obs, sigma, n_iter, solver="lsqr"):
+    """MAP estimate (eq. MAP): the extended least-squares problem with zero
+    perturbations, b = (y_obs / sigma, 0); returns x and the residual history."""
+    apply_A, apply_AT = extended_operator(ops, dt, n_steps, sigma)
+    b = (np.asarray(y_obs, dtype=np.float64) / sigma, np.zeros(len(ops["ML"])))
+    f = lsqr if solver == "lsqr" else cgls
+    return f(apply_A, apply_AT, b, n_iter, (len(ops["ML"]),), False)
+
+
+def whitened_misfit(ops, dt, n_steps, p, y_obs, sigma):
+    """Discrepancy-principle diagnostic (Section 6.1): ||G p - y_obs|| / (sigma
+    sqrt(N_T N_obs)), about 1 when the data are fitted to the noise level."""
+    r = wave.forward(ops, p, dt, n_steps) - (y_obs if np.ndim(p) == 1 else np.asarray(y_obs)[..., None])
+    n = np.prod(np.shape(y_obs))
+    if np.ndim(p) == 1:
+        return np.sqrt(np.sum(r * r)) / (sigma * np.sqrt(n))
+    return np.sqrt(_colsum(r * r)) / (sigma * np.sqrt(n))
 
 
 def ergodic_mean_std(samples):

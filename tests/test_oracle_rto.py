@@ -106,3 +106,98 @@ def test_normal_draws_are_standard_normal():
     assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
     # a sample's draws do not depend on the batch size
     assert np.array_equal(rng.normals(7, 1, 100, 8)[:, 3], rng.normals(7, 1, 100, 4)[:, 3])
+
+
+# ---------------------------------------------------------------------------
+# LSQR (Paige & Saunders 1982), MAP and the discrepancy diagnostic
+# ---------------------------------------------------------------------------
+def _dense_ext(ops, dt, nt, sigma):
+    """The extended matrix [G / sigma; M_L^{1/2}] formed densely (tiny meshes only)."""
+    G = wave.forward_matrix_dense(ops, dt, nt)
+    return np.vstack([G / sigma, np.diag(np.sqrt(ops["ML"]))]), G
+
+
+def test_lsqr_iterates_equal_scipy_lsqr():
+    """SciPy's LSQR (the same published algorithm, run on the dense extended
+    matrix with every stopping test disabled) gives the same k-th iterate, while
+    the rounding difference of the two operator evaluations is not yet amplified
+    by the Krylov recurrences (it is by ~1e10 at k = 12 on this mesh, as for CGLS)."""
+    from scipy.sparse.linalg import lsqr as sp_lsqr
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    A, _ = _dense_ext(ops, dt, nt, sigma)
+    eta = S.standard_normal((nt, 8), 21)
+    xi = S.standard_normal(N, 22)
+    b = rto.rto_rhs(ops, y_obs, sigma, eta, xi)
+    bv = np.concatenate([np.ravel(b[0]), b[1]])
+    for k in (1, 2, 3, 5):
+        x, hist = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta, xi, k)
+        ref = sp_lsqr(A, bv, atol=0.0, btol=0.0, conlim=0.0, iter_lim=k)[0]
+        assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+def test_lsqr_phibar_is_the_residual_norm_and_matches_cgls_iterates():
+    """phibar_{k+1} = ||b - A x_k|| (Paige & Saunders' residual estimate is exact
+    in exact arithmetic); LSQR and CGLS iterates coincide (both minimise over
+    the same Krylov space) while rounding is small (first iterations)."""
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    A, _ = _dense_ext(ops, dt, nt, sigma)
+    eta = S.standard_normal((nt, 8), 23)
+    xi = S.standard_normal(N, 24)
+    b = rto.rto_rhs(ops, y_obs, sigma, eta, xi)
+    bv = np.concatenate([np.ravel(b[0]), b[1]])
+    for k in (1, 2, 3, 4):
+        xl, hist = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta, xi, k)
+        xc, _ = rto.rto_samples(ops, dt, nt, y_obs, sigma, eta, xi, k)
+        assert np.linalg.norm(xl - xc) <= 1e-9 * np.linalg.norm(xc)
+        assert abs(hist[-1] - np.linalg.norm(bv - A @ xl)) <= 1e-10 * np.linalg.norm(bv)
+    assert abs(hist[0] - np.linalg.norm(bv)) <= 1e-14 * np.linalg.norm(bv)
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])           # the residual never grows
+
+
+def test_batched_lsqr_equals_columnwise():
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    eta = S.standard_normal((nt, 8, 3), 25)
+    xi = S.standard_normal((N, 3), 26)
+    X, H = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta, xi, 5)
+    for k in range(3):
+        x, h = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta[..., k], xi[:, k], 5)
+        assert np.abs(X[:, k] - x).max() <= 1e-9 * np.abs(x).max()
+        assert np.abs(H[:, k] - h).max() <= 1e-12 * h[0]
+
+
+def test_converged_lsqr_is_the_closed_form_sample_and_map_is_the_posterior_mean():
+    """Appendix A closed forms: the converged RTO sample, and with zero
+    perturbations (eq. MAP) the posterior mean mu_post."""
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    G = wave.forward_matrix_dense(ops, dt, nt)
+    eta = S.standard_normal((nt, 8), 27)
+    xi = S.standard_normal(N, 28)
+    x, _ = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta, xi, 400)
+    ref = rto.exact_sample(G, ops["ML"], y_obs, sigma, eta, xi)
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+    _, mu = rto.dense_posterior(G, ops["ML"], y_obs, sigma)
+    for solver in ("lsqr", "cgls"):
+        xm, _ = rto.map_estimate(ops, dt, nt, y_obs, sigma, 400, solver)
+        assert np.linalg.norm(xm - mu) <= 1e-8 * np.linalg.norm(mu)
+
+
+def test_whitened_misfit_of_the_true_initial_pressure_is_about_one():
+    """The noise is sigma eta0 with eta0 ~ N(0, I) (eq. noise-model), so the true p0
+    misfits the data by ||sigma eta0|| ~ sigma sqrt(N_T N_obs): the discrepancy level."""
+    xyz, tets = S.cube_mesh(3)
+    det = S.detector_points(16, S.ALL_FACES, 3)
+    ops = fem.build(xyz, tets, det, 3)
+    dt, nt = 0.1, 400
+    p0 = S.gaussian_blobs(xyz, 2, 4)
+    Y = wave.forward(ops, p0, dt, nt)
+    eta0 = S.standard_normal(Y.shape, 5)
+    y_obs, sigma = rto.add_noise(Y, eta0, 0.05, dt)
+    m = rto.whitened_misfit(ops, dt, nt, p0, y_obs, sigma)
+    assert abs(m - np.linalg.norm(eta0) / np.sqrt(eta0.size)) <= 1e-10
+    assert 0.95 < m < 1.05
+    M2 = rto.whitened_misfit(ops, dt, nt, np.stack([p0, 0 * p0], axis=1), y_obs, sigma)
+    assert abs(M2[0] - m) <= 1e-12 and M2[1] > m
