@@ -263,6 +263,64 @@ pat_status pat_cgls_finish(const pat_mesh* mesh, int32_t K, double* samples, dou
                            double* stdev, void* workspace, size_t workspace_bytes, void* stream);
 pat_status pat_cgls_layout(const pat_mesh* mesh, int32_t K, size_t* offsets /* [7] */);
 
+/*
+ * LSQR (Paige & Saunders, ACM TOMS 8, 1982; the solver the paper uses,
+ * Section 5.1 and Algorithm 1) on the same extended system, workspace and
+ * precision rules as the CGLS calls: the Golub-Kahan bidiagonalisation of
+ * G_ext, one plane rotation per iteration and the x, w updates, every scalar
+ * and x in FP64.  In exact arithmetic its iterates equal CGLS's; it is the
+ * more robust of the two in finite precision.  The left vectors are kept
+ * unnormalised (beta_i u_i) in the r_d / r_p fields, v in d, w in an extra
+ * field; x sits where CGLS keeps it, so pat_cgls_finish (or
+ * pat_whitened_misfit) also serves an LSQR solve.
+ *   pat_lsqr_begin    beta_1 u_1 = b, alpha_1 v_1 = A^T u_1, w_1 = v_1, x = 0;
+ *   pat_lsqr_iterate  n_iter iterations; resid (device [n_iter][K] double, or
+ *                     NULL) receives phibar^2 = ||b - A x||^2 of each new
+ *                     iterate (the residual identity of the algorithm).
+ * Same arguments and errors as pat_cgls_begin / pat_cgls_iterate.
+ */
+pat_status pat_lsqr_begin(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K,
+                          const void* eta, const void* xi, uint64_t seed, void* workspace,
+                          size_t workspace_bytes, void* stream);
+pat_status pat_lsqr_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32_t n_iter,
+                            double* resid, void* workspace, size_t workspace_bytes, void* stream);
+/* Byte offsets of the LSQR state in the workspace: off[0] x [N][K] double,
+ * off[1] beta u data block [N_T][N_obs][K] real, off[2] beta u prior block
+ * [N][K] real, off[3] v [N][K] real, off[4] w [N][K] real, off[5] per-sample
+ * scalars [12][K] double (rows: alpha, beta, rhobar, phibar, then temporaries
+ * of the last iteration), off[6] status word. */
+pat_status pat_lsqr_layout(const pat_mesh* mesh, int32_t K, size_t* offsets /* [7] */);
+
+/* pat_rto_sample with LSQR instead of CGLS (Algorithm 1 as the paper states it);
+ * resid [n_iter+1][K] receives ||r_j||^2 of each iterate, starting with ||b||^2. */
+pat_status pat_rto_sample_lsqr(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K,
+                               int32_t n_iter, const void* eta, const void* xi, uint64_t seed,
+                               double* samples, double* mean, double* stdev, double* resid,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * MAP estimate (eq. MAP): the extended least-squares problem with zero
+ * perturbations, b = (y_obs / sigma, 0), from x = 0 with n_iter iterations of
+ * CGLS (solver 0) or LSQR (solver 1).  x_map device [N] double; resid device
+ * [n_iter+1] double or NULL (||r_j||^2).  Workspace >= pat_workspace_bytes(mesh, 2, 1).
+ */
+pat_status pat_map_estimate(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t n_iter,
+                            int32_t solver, double* x_map, double* resid, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/*
+ * Discrepancy-principle diagnostic (Section 6.1): out[k] = ||G x_k - y_obs|| /
+ * (sigma sqrt(N_T N_obs)) for each column of x (device [N][K] double), about 1
+ * when the data are fitted to the noise level.  Euclidean data norm, as sigma
+ * scales the noise vector (eq. noise-model).  out device [K] double.  Runs one
+ * forward solve in the solver's workspace (>= pat_workspace_bytes(mesh, 2, K)):
+ * it overwrites the d, q_d and time-stepping fields, so call it between solves,
+ * not between the iterations of one.
+ */
+pat_status pat_whitened_misfit(const pat_mesh* mesh, const double* x, const void* y_obs, double sigma,
+                               int32_t K, double* out, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
 /* Synchronise `stream` and read the workspace's status word (PAT_OK, PAT_ENUMERIC ...). */
 pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* workspace, void* stream);
 

@@ -157,8 +157,11 @@ class Mesh:
 
     # -- RTO -------------------------------------------------------------
     def rto_sample(self, y_obs, sigma, K, n_iter, eta=None, xi=None, seed=0, samples=True, resid=False,
-                   mean=True, stdev=None):
-        """K RTO posterior samples by n_iter CGLS iterations (pat_rto_sample)."""
+                   mean=True, stdev=None, solver="cgls"):
+        """K RTO posterior samples by n_iter CGLS (pat_rto_sample) or LSQR
+        (pat_rto_sample_lsqr) iterations."""
+        if solver not in ("cgls", "lsqr"):
+            raise ValueError("solver must be 'cgls' or 'lsqr'")
         self._check_field(y_obs, (self.n_steps, self.n_obs), "y_obs")
         if eta is not None:
             self._check_field(eta, (self.n_steps, self.n_obs, K), "eta")
@@ -172,10 +175,36 @@ class Mesh:
         out["std"] = torch.empty(self.N, dtype=torch.float64, device=dev) if stdev else None
         out["resid"] = torch.empty((n_iter + 1, K), dtype=torch.float64, device=dev) if resid else None
         ws = self.workspace(2, K)
-        _lib.check(lib().pat_rto_sample(
+        fn = lib().pat_rto_sample if solver == "cgls" else lib().pat_rto_sample_lsqr
+        _lib.check(fn(
             self._h, _ptr(y_obs), float(sigma), K, n_iter, _ptr(eta), _ptr(xi), C.c_uint64(seed),
             _ptr(out["samples"]), _ptr(out["mean"]), _ptr(out["std"]), _ptr(out["resid"]), _ptr(ws),
             ws.numel(), _stream()))
+        return out
+
+    def map_estimate(self, y_obs, sigma, n_iter, solver="lsqr", resid=False):
+        """MAP estimate (eq. MAP) by n_iter LSQR or CGLS iterations from zero
+        (pat_map_estimate); returns x [N] float64 and, with resid, ||r_j||^2."""
+        self._check_field(y_obs, (self.n_steps, self.n_obs), "y_obs")
+        x = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        r = torch.empty(n_iter + 1, dtype=torch.float64, device=self.device) if resid else None
+        ws = self.workspace(2, 1)
+        _lib.check(lib().pat_map_estimate(self._h, _ptr(y_obs), float(sigma), n_iter,
+                                          {"cgls": 0, "lsqr": 1}[solver], _ptr(x), _ptr(r), _ptr(ws), ws.numel(),
+                                          _stream()))
+        return (x, r) if resid else x
+
+    def whitened_misfit(self, x, y_obs, sigma):
+        """||G x_k - y_obs|| / (sigma sqrt(N_T N_obs)) per column of x [N] or [N, K]
+        float64 (pat_whitened_misfit; the discrepancy-principle diagnostic)."""
+        K = 1 if x.dim() == 1 else x.shape[1]
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+            raise TypeError("x must be a contiguous CUDA float64 tensor")
+        self._check_field(y_obs, (self.n_steps, self.n_obs), "y_obs")
+        out = torch.empty(K, dtype=torch.float64, device=self.device)
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_whitened_misfit(self._h, _ptr(x), _ptr(y_obs), float(sigma), K, _ptr(out), _ptr(ws),
+                                             ws.numel(), _stream()))
         return out
 
     def set_c2(self, c2):
@@ -242,6 +271,35 @@ class Mesh:
         ws = self.workspace(2, K)
         _lib.check(lib().pat_cgls_begin(self._h, _ptr(y_obs), float(sigma), K, _ptr(eta), _ptr(xi),
                                         C.c_uint64(seed), _ptr(ws), ws.numel(), _stream()))
+
+    def lsqr_begin(self, y_obs, sigma, K, eta=None, xi=None, seed=0):
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_lsqr_begin(self._h, _ptr(y_obs), float(sigma), K, _ptr(eta), _ptr(xi),
+                                        C.c_uint64(seed), _ptr(ws), ws.numel(), _stream()))
+
+    def lsqr_iterate(self, sigma, K, n_iter, resid=None):
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_lsqr_iterate(self._h, float(sigma), K, n_iter, _ptr(resid), _ptr(ws), ws.numel(),
+                                          _stream()))
+
+    def lsqr_state(self, K):
+        """Views of the LSQR state in the workspace: x, ub_d, ub_p (beta u), v, w,
+        alpha, beta, rhobar, phibar [K], status."""
+        off = (C.c_size_t * 7)()
+        _lib.check(lib().pat_lsqr_layout(self._h, K, off))
+        ws = self.workspace(2, K)
+        N, D = self.N, self.n_steps * self.n_obs
+
+        def view(o, n, dtype, shape):
+            return ws[o:o + n * (8 if dtype == torch.float64 else 4)].view(dtype).view(shape)
+
+        lsq = view(off[5], 12 * K, torch.float64, (12, K))
+        return {"x": view(off[0], N * K, torch.float64, (N, K)),
+                "ub_d": view(off[1], D * K, self.dtype, (self.n_steps, self.n_obs, K)),
+                "ub_p": view(off[2], N * K, self.dtype, (N, K)),
+                "v": view(off[3], N * K, self.dtype, (N, K)), "w": view(off[4], N * K, self.dtype, (N, K)),
+                "alpha": lsq[0], "beta": lsq[1], "rhobar": lsq[2], "phibar": lsq[3],
+                "status": ws[off[6]:off[6] + 4].view(torch.int32)}
 
     def cgls_iterate(self, sigma, K, n_iter, resid=None):
         ws = self.workspace(2, K)

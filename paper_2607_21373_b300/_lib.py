@@ -63,6 +63,17 @@ SIGNATURES = {
                                  C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_size_t, C.c_void_p]),
     "pat_rto_sample_multi": (C.c_int, [C.c_int32, C.POINTER(RtoJob), C.c_int32, C.c_void_p]),
+    "pat_rto_sample_lsqr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p,
+                                      C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_lsqr_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_lsqr_iterate": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                   C.c_size_t, C.c_void_p]),
+    "pat_map_estimate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_whitened_misfit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                      C.c_void_p, C.c_size_t, C.c_void_p]),
     "pat_cgls_begin": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_uint64, C.c_void_p, C.c_size_t, C.c_void_p]),
     "pat_cgls_iterate": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
@@ -70,6 +81,7 @@ SIGNATURES = {
     "pat_cgls_finish": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_size_t, C.c_void_p]),
     "pat_cgls_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
+    "pat_lsqr_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
     "pat_rto_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_draw_normals": (C.c_int, [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(TuneEntry),

@@ -699,6 +699,24 @@ pat_status pat_cgls_layout(const pat_mesh* mesh, int32_t K, size_t* off) {
   return PAT_OK;
 }
 
+pat_status pat_lsqr_layout(const pat_mesh* mesh, int32_t K, size_t* off) {
+  clear_error();
+  if (!mesh || !off) {
+    set_error("pat_lsqr_layout: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_lsqr_layout")) return PAT_EINVAL;
+  const RtoLayout L = rto_layout(mesh->d, K);
+  off[0] = L.x;
+  off[1] = L.r_d;
+  off[2] = L.r_p;
+  off[3] = L.d;
+  off[4] = L.w;
+  off[5] = L.lsq;
+  off[6] = L.status;
+  return PAT_OK;
+}
+
 pat_status pat_cgls_begin(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, const void* eta,
                           const void* xi, uint64_t seed, void* ws, size_t ws_bytes, void* stream) {
   clear_error();
@@ -758,6 +776,113 @@ pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma,
   s = pat_cgls_iterate(mesh, sigma, K, n_iter, resid ? resid + K : nullptr, ws, ws_bytes, stream);
   if (s) return s;
   return pat_cgls_finish(mesh, K, samples, mean, stdev, ws, ws_bytes, stream);
+}
+
+static pat_status lsqr_begin_checked(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K,
+                                     const void* eta, const void* xi, uint64_t seed, bool zero_draws, void* ws,
+                                     size_t ws_bytes, void* stream, const char* fn) {
+  if (!mesh || !y_obs) {
+    set_error("%s: NULL argument", fn);
+    return PAT_EINVAL;
+  }
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) {
+    set_error("%s: sigma must be finite and > 0 (got %g)", fn, sigma);
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, fn) || !check_device(mesh, fn)) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, fn);
+  if (s) return s;
+  return lsqr_begin(mesh->d, y_obs, sigma, K, eta, xi, seed, zero_draws, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_lsqr_begin(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, const void* eta,
+                          const void* xi, uint64_t seed, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  return lsqr_begin_checked(mesh, y_obs, sigma, K, eta, xi, seed, false, ws, ws_bytes, stream, "pat_lsqr_begin");
+}
+
+pat_status pat_lsqr_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32_t n_iter, double* resid, void* ws,
+                            size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || n_iter < 0) {
+    set_error("pat_lsqr_iterate: NULL mesh or n_iter < 0");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_lsqr_iterate") || !check_device(mesh, "pat_lsqr_iterate")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_lsqr_iterate");
+  if (s) return s;
+  return lsqr_iterate(mesh->d, sigma, K, n_iter, resid, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_rto_sample_lsqr(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, int32_t n_iter,
+                               const void* eta, const void* xi, uint64_t seed, double* samples, double* mean,
+                               double* stdev, double* resid, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (n_iter < 0 || (stdev && K < 2)) {
+    set_error("pat_rto_sample_lsqr: n_iter < 0, or stdev asked with K < 2");
+    return PAT_EINVAL;
+  }
+  pat_status s =
+      lsqr_begin_checked(mesh, y_obs, sigma, K, eta, xi, seed, false, ws, ws_bytes, stream, "pat_rto_sample_lsqr");
+  if (s) return s;
+  if (resid) {
+    s = lsqr_residual(mesh->d, K, resid, (char*)ws, (cudaStream_t)stream);
+    if (s) return s;
+  }
+  s = lsqr_iterate(mesh->d, sigma, K, n_iter, resid ? resid + K : nullptr, (char*)ws, (cudaStream_t)stream);
+  if (s) return s;
+  return cgls_finish(mesh->d, K, samples, mean, stdev, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_map_estimate(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t n_iter, int32_t solver,
+                            double* x_map, double* resid, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (n_iter < 0 || (solver != 0 && solver != 1) || !x_map) {
+    set_error("pat_map_estimate: n_iter < 0, solver not 0 (CGLS) or 1 (LSQR), or NULL x_map");
+    return PAT_EINVAL;
+  }
+  const char* fn = "pat_map_estimate";
+  cudaStream_t st = (cudaStream_t)stream;
+  pat_status s;
+  if (solver == 1) {
+    s = lsqr_begin_checked(mesh, y_obs, sigma, 1, nullptr, nullptr, 0, true, ws, ws_bytes, stream, fn);
+    if (s) return s;
+    if (resid) {
+      s = lsqr_residual(mesh->d, 1, resid, (char*)ws, st);
+      if (s) return s;
+    }
+    s = lsqr_iterate(mesh->d, sigma, 1, n_iter, resid ? resid + 1 : nullptr, (char*)ws, st);
+  } else {
+    if (!mesh || !y_obs || !(sigma > 0.0) || !std::isfinite(sigma)) {
+      set_error("%s: NULL argument or sigma not finite and > 0", fn);
+      return PAT_EINVAL;
+    }
+    if (!check_device(mesh, fn)) return PAT_EINVAL;
+    s = check_ws(mesh, 2, 1, ws, ws_bytes, fn);
+    if (s) return s;
+    s = cgls_begin(mesh->d, y_obs, sigma, 1, nullptr, nullptr, 0, (char*)ws, st, true);
+    if (s) return s;
+    if (resid) {
+      s = residual_norms(mesh->d, 1, resid, (char*)ws, st);
+      if (s) return s;
+    }
+    s = cgls_iterate(mesh->d, sigma, 1, n_iter, resid ? resid + 1 : nullptr, (char*)ws, st);
+  }
+  if (s) return s;
+  return cgls_finish(mesh->d, 1, x_map, nullptr, nullptr, (char*)ws, st);
+}
+
+pat_status pat_whitened_misfit(const pat_mesh* mesh, const double* x, const void* y_obs, double sigma, int32_t K,
+                               double* out, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || !x || !y_obs || !out || !(sigma > 0.0) || !std::isfinite(sigma)) {
+    set_error("pat_whitened_misfit: NULL argument or sigma not finite and > 0");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_whitened_misfit") || !check_device(mesh, "pat_whitened_misfit")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_whitened_misfit");
+  if (s) return s;
+  return whitened_misfit(mesh->d, x, y_obs, sigma, K, out, (char*)ws, (cudaStream_t)stream);
 }
 
 pat_status pat_rto_sample_multi(int32_t n_jobs, const pat_rto_job* jobs, int32_t n_iter, void* stream) {

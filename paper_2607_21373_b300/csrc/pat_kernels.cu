@@ -669,22 +669,23 @@ __global__ void draw_normals_kernel(uint64_t seed, int stream, int64_t n_elem, i
 }
 
 // r_d = y_obs / sigma + eta, r_p = xi  (b of eq. extended-matrices with C = M_L^{-1})
+// With zero_draws (the MAP problem, eq. MAP) eta = 0 and xi = 0.
 template <typename T>
 __global__ void rhs_kernel(int64_t n_data, int64_t N, int K, const T* __restrict__ y_obs, const T* __restrict__ eta,
                            const T* __restrict__ xi, uint64_t seed, double inv_sigma, T* __restrict__ r_d,
-                           T* __restrict__ r_p) {
+                           T* __restrict__ r_p, int zero_draws) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nd = n_data * K;
   if (t < nd) {
     const int64_t e = t / K;
     const int k = (int)(t - e * K);
-    const double et = eta ? (double)eta[t] : normal_draw(seed, 0, (uint64_t)k, (uint64_t)e);
+    const double et = zero_draws ? 0.0 : eta ? (double)eta[t] : normal_draw(seed, 0, (uint64_t)k, (uint64_t)e);
     r_d[t] = (T)((double)y_obs[e] * inv_sigma + et);
   } else if (t < nd + N * K) {
     const int64_t u = t - nd;
     const int64_t i = u / K;
     const int k = (int)(u - i * K);
-    r_p[u] = xi ? xi[u] : (T)normal_draw(seed, 1, (uint64_t)k, (uint64_t)i);
+    r_p[u] = zero_draws ? T(0) : xi ? xi[u] : (T)normal_draw(seed, 1, (uint64_t)k, (uint64_t)i);
   }
 }
 
@@ -876,6 +877,8 @@ RtoLayout rto_layout(const DeviceMesh& m, int K) {
   L.sigma = o; o = align256(o + 8);
   L.partial = o; o = align256(o + (size_t)4 * L.n_part * K * 8);
   L.status = o; o = align256(o + 4);
+  L.w = o; o = align256(o + NK * rs);
+  L.lsq = o; o = align256(o + (size_t)kLsq * K * 8);
   L.total = o;
   return L;
 }
@@ -944,14 +947,14 @@ static pat_status cgls_solve(const DeviceMesh& m, int dir, int K, double sigma, 
 // by the grouped multi-mesh driver).
 template <typename T>
 pat_status begin_pre(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
-                     uint64_t seed, char* ws, cudaStream_t st) {
+                     uint64_t seed, char* ws, cudaStream_t st, bool zero_draws) {
   const RtoLayout L = rto_layout(m, K);
   const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
   PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.status, 0, 4, st), "cgls_begin memset"));
   set_double_kernel<<<1, 1, 0, st>>>((double*)(ws + L.sigma), sigma);
   PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.x, 0, (size_t)m.N * K * 8, st), "cgls_begin memset x"));
   rhs_kernel<T><<<nblocks((ndata + m.N) * K), 256, 0, st>>>(ndata, m.N, K, y_obs, eta, xi, seed, 1.0 / sigma,
-                                                            (T*)(ws + L.r_d), (T*)(ws + L.r_p));
+                                                            (T*)(ws + L.r_d), (T*)(ws + L.r_p), zero_draws ? 1 : 0);
   count(m, 2);
   return cuda_check(cudaGetLastError(), "cgls_begin launch");
 }
@@ -1014,9 +1017,8 @@ pat_status iter_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
 
 template <typename T>
 static pat_status begin_t(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
-                          uint64_t seed, char* ws, cudaStream_t st) {
-  const RtoLayout L = rto_layout(m, K);
-  PAT_TRY(begin_pre<T>(m, y_obs, sigma, K, eta, xi, seed, ws, st));
+                          uint64_t seed, char* ws, cudaStream_t st, bool zero_draws) {
+  PAT_TRY(begin_pre<T>(m, y_obs, sigma, K, eta, xi, seed, ws, st, zero_draws));
   // s = A^T r, d = s, gamma = ||s||^2 (the transpose lands in s, combined in place)
   PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
   return begin_post<T>(m, K, ws, st);
@@ -1061,10 +1063,12 @@ static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter
 }
 
 pat_status cgls_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta, const void* xi,
-                      uint64_t seed, char* ws, cudaStream_t st) {
+                      uint64_t seed, char* ws, cudaStream_t st, bool zero_draws) {
   if (m.prec == PAT_F64)
-    return begin_t<double>(m, (const double*)y_obs, sigma, K, (const double*)eta, (const double*)xi, seed, ws, st);
-  return begin_t<float>(m, (const float*)y_obs, sigma, K, (const float*)eta, (const float*)xi, seed, ws, st);
+    return begin_t<double>(m, (const double*)y_obs, sigma, K, (const double*)eta, (const double*)xi, seed, ws, st,
+                           zero_draws);
+  return begin_t<float>(m, (const float*)y_obs, sigma, K, (const float*)eta, (const float*)xi, seed, ws, st,
+                        zero_draws);
 }
 
 pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
@@ -1092,6 +1096,323 @@ pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean
   return cuda_check(cudaGetLastError(), "cgls_finish launch");
 }
 
+// ---------------------------------------------------------------------------
+// LSQR (Paige & Saunders 1982, the paper's solver) on the extended system.
+// The left Golub-Kahan vectors are kept unnormalised, ub_i = beta_i u_i, so no
+// pass over the data-space fields is spent on normalising them:
+//   ub_{i+1} = A v_i - (alpha_i / beta_i) ub_i,        beta_{i+1} = ||ub_{i+1}||,
+//   t = A^T ub_{i+1} / beta_{i+1} - beta_{i+1} v_i,    alpha_{i+1} = ||t||, v_{i+1} = t / alpha_{i+1},
+// then the plane rotation and the x, w updates of the published algorithm.
+// Fields: ub = (r_d, r_p), v = d, A v data block = q_d, A^T ub data part = s,
+// w = w, x = x (FP64); per-sample FP64 scalars in lsq [kLsq][K].
+// ---------------------------------------------------------------------------
+enum LsqSlot { kAlpha = 0, kBeta, kRhoBar, kPhiBar, kC, kS, kRho, kPhi, kFx, kFw, kIa, kIb };
+
+// ub = A v - c ub on one block with c = alpha / beta per sample (P: prior block,
+// A v = sqrt(M_L) v; else data block, A v = q), and the partial sums of ub^2.
+template <typename T, bool P>
+__global__ void lsqr_u_kernel(const T* __restrict__ q, const double* __restrict__ sqml, T* ub, int64_t rows, int K,
+                              int rpb, const double* __restrict__ lsq, double* __restrict__ partial) {
+  extern __shared__ double sh[];
+  const int k = threadIdx.x % K;
+  const int r0 = threadIdx.x / K;
+  const double b = lsq[kBeta * K + k];
+  const double c = b != 0.0 ? lsq[kAlpha * K + k] / b : 0.0;
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * rpb + r0; r < rows; r += (int64_t)gridDim.x * rpb) {
+    const int64_t i = r * K + k;
+    const double av = P ? sqml[r] * (double)q[i] : (double)q[i];
+    const T u = (T)(av - c * (double)ub[i]);
+    ub[i] = u;
+    acc += (double)u * (double)u;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (r0 == 0) {
+    double t = 0.0;
+    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
+    partial[(int64_t)blockIdx.x * K + k] = t;
+  }
+}
+
+// t = (ah + sqrt(M_L) ub_p) / beta - beta v (v NULL at the start) into out, and sum t^2
+template <typename T>
+__global__ void lsqr_t_kernel(const T* ah, const T* __restrict__ ub_p, const double* __restrict__ sqml,
+                              const T* __restrict__ v, int64_t rows, int K, int rpb, const double* __restrict__ lsq,
+                              T* out, double* __restrict__ partial) {
+  extern __shared__ double sh[];
+  const int k = threadIdx.x % K;
+  const int r0 = threadIdx.x / K;
+  const double b = lsq[kBeta * K + k], ib = lsq[kIb * K + k];
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * rpb + r0; r < rows; r += (int64_t)gridDim.x * rpb) {
+    const int64_t i = r * K + k;
+    double t = ((double)ah[i] + sqml[r] * (double)ub_p[i]) * ib;
+    if (v) t -= b * (double)v[i];
+    const T tv = (T)t;
+    out[i] = tv;
+    acc += (double)tv * (double)tv;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (r0 == 0) {
+    double t = 0.0;
+    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
+    partial[(int64_t)blockIdx.x * K + k] = t;
+  }
+}
+
+__device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
+
+// beta_1 = ||b||: phibar = beta, 1 / beta
+__global__ void lsqr_beta0_kernel(const double* pa, int na, const double* pb, int nb, int K, double* lsq,
+                                  int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  for (int b = 0; b < nb; ++b) s += pb[(int64_t)b * K + k];
+  if (!isfinite(s)) flag(status, PAT_ENUMERIC);
+  const double beta = sqrt(s);
+  lsq[kBeta * K + k] = beta;
+  lsq[kPhiBar * K + k] = beta;
+  lsq[kIb * K + k] = safe_div(1.0, beta);
+}
+
+// alpha_1 = ||A^T u_1||: rhobar = alpha, 1 / alpha
+__global__ void lsqr_alpha0_kernel(const double* pa, int na, int K, double* lsq, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  if (!isfinite(s)) flag(status, PAT_ENUMERIC);
+  const double alpha = sqrt(s);
+  lsq[kAlpha * K + k] = alpha;
+  lsq[kRhoBar * K + k] = alpha;
+  lsq[kIa * K + k] = safe_div(1.0, alpha);
+}
+
+// beta_{i+1} = ||ub_{i+1}||, then the rotation quantities that need it:
+// rho = (rhobar^2 + beta^2)^{1/2}, c = rhobar / rho, s = beta / rho, phi = c phibar, phibar = s phibar
+__global__ void lsqr_beta_kernel(const double* pa, int na, const double* pb, int nb, int K, double* lsq,
+                                 int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s2 = 0.0;
+  for (int b = 0; b < na; ++b) s2 += pa[(int64_t)b * K + k];
+  for (int b = 0; b < nb; ++b) s2 += pb[(int64_t)b * K + k];
+  if (!isfinite(s2)) flag(status, PAT_ENUMERIC);
+  const double beta = sqrt(s2), rhobar = lsq[kRhoBar * K + k], phibar = lsq[kPhiBar * K + k];
+  const double rho = sqrt(rhobar * rhobar + beta * beta);
+  const double c = safe_div(rhobar, rho), s = safe_div(beta, rho);
+  lsq[kBeta * K + k] = beta;
+  lsq[kIb * K + k] = safe_div(1.0, beta);
+  lsq[kRho * K + k] = rho;
+  lsq[kC * K + k] = c;
+  lsq[kS * K + k] = s;
+  lsq[kPhi * K + k] = c * phibar;
+  lsq[kPhiBar * K + k] = s * phibar;
+}
+
+// alpha_{i+1} = ||t||, theta = s alpha, rhobar = -c alpha, x / w coefficients phi / rho, theta / rho
+__global__ void lsqr_alpha_kernel(const double* pa, int na, int K, double* lsq, int* status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s2 = 0.0;
+  for (int b = 0; b < na; ++b) s2 += pa[(int64_t)b * K + k];
+  if (!isfinite(s2)) flag(status, PAT_ENUMERIC);
+  const double alpha = sqrt(s2), rho = lsq[kRho * K + k];
+  const double theta = lsq[kS * K + k] * alpha;
+  lsq[kAlpha * K + k] = alpha;
+  lsq[kIa * K + k] = safe_div(1.0, alpha);
+  lsq[kRhoBar * K + k] = -lsq[kC * K + k] * alpha;
+  lsq[kFx * K + k] = safe_div(lsq[kPhi * K + k], rho);
+  lsq[kFw * K + k] = safe_div(theta, rho);
+}
+
+// v = t / alpha; with W: x += (phi / rho) w, w = v - (theta / rho) w; else (start) w = v
+template <typename T, bool W>
+__global__ void lsqr_vxw_kernel(int64_t N, int K, const T* __restrict__ t, const double* __restrict__ lsq, T* v,
+                                T* w, double* x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N * K) return;
+  const int k = (int)(i % K);
+  const T vn = (T)((double)t[i] * lsq[kIa * K + k]);
+  v[i] = vn;
+  if constexpr (W) {
+    const double wo = (double)w[i];
+    x[i] += lsq[kFx * K + k] * wo;
+    w[i] = (T)((double)vn - lsq[kFw * K + k] * wo);
+  } else {
+    w[i] = vn;
+  }
+}
+
+// out[k] = phibar^2 (the squared residual norm of the current iterate)
+__global__ void lsqr_resid_kernel(int K, const double* __restrict__ lsq, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const double p = lsq[kPhiBar * K + k];
+  out[k] = p * p;
+}
+
+template <typename T>
+static pat_status lsqr_begin_t(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
+                               uint64_t seed, bool zero_draws, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  // ub_1 = b (r_d, r_p), x = 0
+  PAT_TRY(begin_pre<T>(m, y_obs, sigma, K, eta, xi, seed, ws, st, zero_draws));
+  double* lsq = (double*)(ws + L.lsq);
+  double* pa = (double*)(ws + L.partial);
+  double* pb = pa + (size_t)L.n_part * K;
+  const RedShape rsD = red_shape(K, ndata, L.n_part);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  int* status = (int*)(ws + L.status);
+  sumsq_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>((T*)(ws + L.r_d), nullptr, ndata, K,
+                                                                                 rsD.rpb, pa);
+  sumsq_kernel<T, false><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>((T*)(ws + L.r_p), nullptr, m.N, K,
+                                                                                 rsN.rpb, pb);
+  lsqr_beta0_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, lsq, status);
+  // t = A^T ub_1 / beta_1; alpha_1 = ||t||; v_1 = t / alpha_1; w_1 = v_1
+  PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
+  T* s = (T*)(ws + L.s);
+  lsqr_t_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
+      s, (T*)(ws + L.r_p), m.sqrt_ml, nullptr, m.N, K, rsN.rpb, lsq, s, pa);
+  lsqr_alpha0_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, lsq, status);
+  lsqr_vxw_kernel<T, false><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, s, lsq, (T*)(ws + L.d), (T*)(ws + L.w),
+                                                              (double*)(ws + L.x));
+  count(m, 6);
+  return cuda_check(cudaGetLastError(), "lsqr_begin launch");
+}
+
+template <typename T>
+static pat_status lsqr_iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
+                                 cudaStream_t st) {
+  if (!(sigma > 0.0)) {
+    set_error("pat_lsqr_iterate: sigma must be > 0 (got %g)", sigma);
+    return PAT_EINVAL;
+  }
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  double* lsq = (double*)(ws + L.lsq);
+  double* pa = (double*)(ws + L.partial);
+  double* pb = pa + (size_t)L.n_part * K;
+  const RedShape rsD = red_shape(K, ndata, L.n_part);
+  const RedShape rsN = red_shape(K, m.N, L.n_part);
+  int* status = (int*)(ws + L.status);
+  T* v = (T*)(ws + L.d);
+  T* s = (T*)(ws + L.s);
+  for (int it = 0; it < n_iter; ++it) {
+    // ub = A v - (alpha / beta) ub: data block from q_d = G v / sigma, prior block sqrt(M_L) v
+    PAT_TRY(cgls_solve(m, 0, K, sigma, ws, st));
+    lsqr_u_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>(
+        (T*)(ws + L.q_d), nullptr, (T*)(ws + L.r_d), ndata, K, rsD.rpb, lsq, pa);
+    lsqr_u_kernel<T, true><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
+        v, m.sqrt_ml, (T*)(ws + L.r_p), m.N, K, rsN.rpb, lsq, pb);
+    lsqr_beta_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, lsq, status);
+    // t = A^T ub / beta - beta v, alpha = ||t||, v = t / alpha, x and w updates
+    PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
+    lsqr_t_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
+        s, (T*)(ws + L.r_p), m.sqrt_ml, v, m.N, K, rsN.rpb, lsq, s, pa);
+    lsqr_alpha_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, lsq, status);
+    lsqr_vxw_kernel<T, true><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, s, lsq, v, (T*)(ws + L.w),
+                                                               (double*)(ws + L.x));
+    count(m, 6);
+    if (resid) {
+      lsqr_resid_kernel<<<nblocks(K, 128), 128, 0, st>>>(K, lsq, resid + (int64_t)it * K);
+      count(m, 1);
+    }
+  }
+  return cuda_check(cudaGetLastError(), "lsqr_iterate launch");
+}
+
+pat_status lsqr_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta, const void* xi,
+                      uint64_t seed, bool zero_draws, char* ws, cudaStream_t st) {
+  if (m.prec == PAT_F64)
+    return lsqr_begin_t<double>(m, (const double*)y_obs, sigma, K, (const double*)eta, (const double*)xi, seed,
+                                zero_draws, ws, st);
+  return lsqr_begin_t<float>(m, (const float*)y_obs, sigma, K, (const float*)eta, (const float*)xi, seed, zero_draws,
+                             ws, st);
+}
+
+pat_status lsqr_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
+                        cudaStream_t st) {
+  if (m.prec == PAT_F64) return lsqr_iterate_t<double>(m, sigma, K, n_iter, resid, ws, st);
+  return lsqr_iterate_t<float>(m, sigma, K, n_iter, resid, ws, st);
+}
+
+pat_status lsqr_residual(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  lsqr_resid_kernel<<<nblocks(K, 128), 128, 0, st>>>(K, (const double*)(ws + L.lsq), out);
+  count(m, 1);
+  return cuda_check(cudaGetLastError(), "lsqr residual launch");
+}
+
+// ---------------------------------------------------------------------------
+// Discrepancy diagnostic (Section 6.1): ||G x_k - y_obs|| / (sigma sqrt(N_T N_obs))
+// for each sample column of the FP64 iterate x [N][K].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void to_real_kernel(int64_t n, const double* __restrict__ x, T* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)x[i];
+}
+
+template <typename T>
+__global__ void misfit_kernel(const T* __restrict__ Y, const T* __restrict__ y_obs, int64_t rows, int K, int rpb,
+                              double* __restrict__ partial) {
+  extern __shared__ double sh[];
+  const int k = threadIdx.x % K;
+  const int r0 = threadIdx.x / K;
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * rpb + r0; r < rows; r += (int64_t)gridDim.x * rpb) {
+    const double d = (double)Y[r * K + k] - (double)y_obs[r];
+    acc += d * d;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (r0 == 0) {
+    double t = 0.0;
+    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
+    partial[(int64_t)blockIdx.x * K + k] = t;
+  }
+}
+
+__global__ void misfit_finish_kernel(const double* pa, int na, int K, double scale, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  out[k] = sqrt(s) * scale;
+}
+
+template <typename T>
+static pat_status misfit_t(const DeviceMesh& m, const double* x, const T* y_obs, double sigma, int K, double* out,
+                           char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
+  T* xr = (T*)(ws + L.d);
+  T* Y = (T*)(ws + L.q_d);
+  to_real_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N * K, x, xr);
+  count(m, 1);
+  PAT_TRY(cuda_check(cudaGetLastError(), "misfit launch"));
+  PAT_TRY(forward(m, xr, K, Y, 1.0, ws + L.state, st));
+  double* pa = (double*)(ws + L.partial);
+  const RedShape rsD = red_shape(K, ndata, L.n_part);
+  misfit_kernel<T><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>(Y, y_obs, ndata, K, rsD.rpb, pa);
+  misfit_finish_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, K, 1.0 / (sigma * std::sqrt((double)ndata)),
+                                                         out);
+  count(m, 2);
+  return cuda_check(cudaGetLastError(), "misfit launch");
+}
+
+pat_status whitened_misfit(const DeviceMesh& m, const double* x, const void* y_obs, double sigma, int K,
+                           double* out, char* ws, cudaStream_t st) {
+  if (m.prec == PAT_F64) return misfit_t<double>(m, x, (const double*)y_obs, sigma, K, out, ws, st);
+  return misfit_t<float>(m, x, (const float*)y_obs, sigma, K, out, ws, st);
+}
+
 template Step3Args<float> fwd3_args<float>(const DeviceMesh&, int, int, const float*, float*, float, float* const[3],
                                            int, int64_t*);
 template Step3Args<double> fwd3_args<double>(const DeviceMesh&, int, int, const double*, double*, double,
@@ -1101,9 +1422,9 @@ template Step3Args<float> adj3_args<float>(const DeviceMesh&, int, int, const fl
 template Step3Args<double> adj3_args<double>(const DeviceMesh&, int, int, const double*, double, double* const[3],
                                              int, int64_t*);
 template pat_status begin_pre<float>(const DeviceMesh&, const float*, double, int, const float*, const float*, uint64_t,
-                                     char*, cudaStream_t);
+                                     char*, cudaStream_t, bool);
 template pat_status begin_pre<double>(const DeviceMesh&, const double*, double, int, const double*, const double*,
-                                      uint64_t, char*, cudaStream_t);
+                                      uint64_t, char*, cudaStream_t, bool);
 template pat_status begin_post<float>(const DeviceMesh&, int, char*, cudaStream_t);
 template pat_status begin_post<double>(const DeviceMesh&, int, char*, cudaStream_t);
 template pat_status iter_mid<float>(const DeviceMesh&, int, char*, cudaStream_t);

@@ -12,11 +12,13 @@ namespace pat {
 
 // Workspace layout of one RTO solve with K stacked samples (byte offsets,
 // 256-aligned).  Fields: x, d, r_d, q_d, r_p, s, state (a0, w0, a1, w1),
-// per-sample scalars, reduction partials, status word.
+// per-sample scalars, reduction partials, status word; w and the LSQR
+// scalars lsq [kLsq][K] are used by the LSQR driver only.
 struct RtoLayout {
-  size_t x, d, r_d, q_d, r_p, s, state, gamma, alpha, beta, sigma, partial, status, total;
+  size_t x, d, r_d, q_d, r_p, s, state, gamma, alpha, beta, sigma, partial, status, w, lsq, total;
   int n_part;  // reduction blocks per partial slot
 };
+constexpr int kLsq = 12;
 
 size_t state_bytes(const DeviceMesh& m, int K);   // 4 N K real
 RtoLayout rto_layout(const DeviceMesh& m, int K);
@@ -27,12 +29,22 @@ pat_status adjoint(const DeviceMesh& m, const void* Yhat, int K, void* out, doub
                    cudaStream_t st);
 
 pat_status cgls_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta,
-                      const void* xi, uint64_t seed, char* ws, cudaStream_t st);
+                      const void* xi, uint64_t seed, char* ws, cudaStream_t st, bool zero_draws = false);
 pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
                         cudaStream_t st);
 pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean, double* stdev, char* ws,
                        cudaStream_t st);
 pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st);
+
+// LSQR (Paige & Saunders) on the same extended system and workspace; the
+// iterate x sits where CGLS keeps it, so cgls_finish also finishes LSQR.
+pat_status lsqr_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta,
+                      const void* xi, uint64_t seed, bool zero_draws, char* ws, cudaStream_t st);
+pat_status lsqr_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
+                        cudaStream_t st);
+pat_status lsqr_residual(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st);
+pat_status whitened_misfit(const DeviceMesh& m, const double* x, const void* y_obs, double sigma, int K,
+                           double* out, char* ws, cudaStream_t st);
 
 // Building blocks of the grouped (multi-mesh) driver, pat_multi.cu.
 template <typename T>
@@ -45,7 +57,7 @@ Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale
                        int64_t* threads);
 template <typename T>
 pat_status begin_pre(const DeviceMesh& m, const T* y_obs, double sigma, int K, const T* eta, const T* xi,
-                     uint64_t seed, char* ws, cudaStream_t st);
+                     uint64_t seed, char* ws, cudaStream_t st, bool zero_draws = false);
 template <typename T>
 pat_status begin_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st);
 template <typename T>
