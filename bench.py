@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
     ap.add_argument("--autotune", type=int, default=1, help="0: keep the library's default step-kernel variant")
+    ap.add_argument("--solver", default="cgls", choices=["cgls", "lsqr"],
+                    help="least-squares solver of every RTO sample (the configured workload names CGLS)")
     ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4 | v8c2z | ell8 | ell4 | pipe | "
                     "ell8pf | ell8p | ell8pw | ell8pp | ell8pb")
     return ap.parse_args()
@@ -73,9 +75,10 @@ def workload_config(a):
     return {
         "workload": f"cube{a.cells}_rto: unit cube {a.cells}^3 cells x 6 Kuhn tets, {(a.cells + 1) ** 3} nodes, "
                     f"N_T={a.n_steps}, dt=0.3h, {a.n_obs} sensors on 5 faces, K={a.K} samples per batch, "
-                    f"CGLS k={a.k_iter}, white-noise prior N(0, M_L^-1), 1% noise",
+                    f"{a.solver.upper()} k={a.k_iter}, white-noise prior N(0, M_L^-1), 1% noise",
         "n_nodes": (a.cells + 1) ** 3, "n_tets": 6 * a.cells ** 3, "n_steps": a.n_steps, "n_obs": a.n_obs,
-        "K": a.K, "cgls_iters": a.k_iter, "noise": w.noise,
+        "K": a.K, "solver": a.solver, "cgls_iters" if a.solver == "cgls" else "lsqr_iters": a.k_iter,
+        "noise": w.noise,
         "node_steps_per_sample": (2 * a.k_iter + 1) * a.n_steps * (a.cells + 1) ** 3,
         "l2": "inputs larger than L2: the K-stacked state is 4*N*K*4 B = %.0f MB per buffer set"
               % (4 * (a.cells + 1) ** 3 * a.K * 4 / 1e6),
@@ -240,7 +243,8 @@ def run_ours(a, rank, world, local_rank, dist):
             tune["K1"] = mesh.autotune(1, n_probe=30)
 
     def batch(K_, seed):
-        return mesh.rto_sample(y_obs, sigma, K_, k, seed=seed, samples=False, mean=True, stdev=K_ >= 2)
+        return mesh.rto_sample(y_obs, sigma, K_, k, seed=seed, samples=False, mean=True, stdev=K_ >= 2,
+                               solver=a.solver)
 
     def barrier():
         if dist is not None:
@@ -375,7 +379,7 @@ def run_ours(a, rank, world, local_rank, dist):
         t0.record(st)
         for i in range(a.e2e_steps):
             y_dev.copy_(y_host, non_blocking=True)
-            out = mesh.rto_sample(y_dev, sigma, K, k, seed=5000 + i, samples=False)
+            out = mesh.rto_sample(y_dev, sigma, K, k, seed=5000 + i, samples=False, solver=a.solver)
             mean_h.copy_(out["mean"], non_blocking=True)
             std_h.copy_(out["std"], non_blocking=True)
         t1.record(st)
