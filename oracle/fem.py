@@ -118,11 +118,38 @@ def sensor_weights_cube(n, det_xyz):
     return nodes, w
 
 
+def sensor_weights_nodes(xyz, det_xyz):
+    """Node-coincident sensors: each sensor position equals a mesh node's
+    coordinates (to 1e-12 of the mesh size); its observation is that node's
+    value.  Returns nodes (N_obs, 1) int64 and weights (N_obs, 1)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    det_xyz = np.asarray(det_xyz, dtype=np.float64)
+    scale = np.ptp(xyz, axis=0).max()
+    nodes = np.empty((len(det_xyz), 1), dtype=np.int64)
+    for d, x in enumerate(det_xyz):
+        dist = np.abs(xyz - x).max(axis=1)
+        i = int(np.argmin(dist))
+        if dist[i] > 1e-12 * scale:
+            raise ValueError(f"sensor {d} does not coincide with a node")
+        nodes[d, 0] = i
+    return nodes, np.ones((len(det_xyz), 1))
+
+
 def observation_matrix(N, nodes, weights):
     """Pi as a sparse (N_obs, N) matrix: row d holds the sensor's P1 weights."""
     n_obs = len(nodes)
     rows = np.repeat(np.arange(n_obs), nodes.shape[1])
     return sp.csr_matrix((weights.ravel(), (rows, nodes.ravel())), shape=(n_obs, N))
+
+
+def build_node_sensors(xyz, tets, det_xyz, c2_elem=None):
+    """All oracle operators for any tetrahedral mesh with node-coincident sensors."""
+    ops = assemble(xyz, tets, c2_elem)
+    nodes, w = sensor_weights_nodes(xyz, det_xyz)
+    ops["det_nodes"] = nodes
+    ops["det_w"] = w
+    ops["Pi"] = observation_matrix(len(xyz), nodes, w)
+    return ops
 
 
 def build(xyz, tets, det_xyz, n, c2_elem=None):

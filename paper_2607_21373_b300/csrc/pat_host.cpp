@@ -275,8 +275,47 @@ pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
   m.n_obs = n_obs;
   m.det_node.assign(3 * (size_t)n_obs, 0);
   m.det_w.assign(3 * (size_t)n_obs, 0.0);
+  // node-coincident sensors (any node, interior ones included): nodes hashed by
+  // their coordinates quantised to q = 1e-9 of the mesh's extent; a sensor
+  // within 1e-12 of the extent of a node observes that node's value alone
+  double ext = 0.0, nlo[3] = {1e300, 1e300, 1e300};
+  for (int64_t i = 0; i < m.N; ++i)
+    for (int c = 0; c < 3; ++c) nlo[c] = std::min(nlo[c], X[3 * i + c]);
+  for (int64_t i = 0; i < m.N; ++i)
+    for (int c = 0; c < 3; ++c) ext = std::max(ext, X[3 * i + c] - nlo[c]);
+  const double q = std::max(ext, 1e-300) * 1e-9;
+  auto qkey = [&](const double* p, int di, int dj, int dk) {
+    const int64_t a = (int64_t)std::floor((p[0] - nlo[0]) / q) + di, b = (int64_t)std::floor((p[1] - nlo[1]) / q) + dj,
+                  c = (int64_t)std::floor((p[2] - nlo[2]) / q) + dk;
+    return (uint64_t)(a * 73856093LL) ^ (uint64_t)(b * 19349663LL) ^ (uint64_t)(c * 83492791LL);
+  };
+  std::unordered_multimap<uint64_t, int32_t> node_hash;
+  node_hash.reserve((size_t)m.N);
+  for (int64_t i = 0; i < m.N; ++i) node_hash.emplace(qkey(X + 3 * i, 0, 0, 0), (int32_t)i);
+  auto node_at = [&](const double* p) -> int32_t {
+    for (int di = -1; di <= 1; ++di)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int dk = -1; dk <= 1; ++dk) {
+          auto range = node_hash.equal_range(qkey(p, di, dj, dk));
+          for (auto it = range.first; it != range.second; ++it) {
+            const double* y = X + 3 * (int64_t)it->second;
+            if (std::fabs(y[0] - p[0]) <= 1e-12 * ext && std::fabs(y[1] - p[1]) <= 1e-12 * ext &&
+                std::fabs(y[2] - p[2]) <= 1e-12 * ext)
+              return it->second;
+          }
+        }
+    return -1;
+  };
   for (int32_t d = 0; d < n_obs; ++d) {
     const double* x = det + 3 * d;
+    const int32_t at = node_at(x);
+    if (at >= 0) {
+      for (int a = 0; a < 3; ++a) {
+        m.det_node[3 * d + a] = at;
+        m.det_w[3 * d + a] = a == 0 ? 1.0 : 0.0;
+      }
+      continue;
+    }
     int64_t c0[3];
     cell_of(x, c0);
     int64_t best = -1;
@@ -323,7 +362,8 @@ pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
           }
         }
     if (best < 0) {
-      set_error("pat_mesh_create: sensor %d at (%g, %g, %g) is not on a boundary triangle", d, x[0], x[1], x[2]);
+      set_error("pat_mesh_create: sensor %d at (%g, %g, %g) is neither a mesh node nor on a boundary triangle", d,
+                x[0], x[1], x[2]);
       return PAT_EINVAL;
     }
     double s = 0.0;

@@ -59,6 +59,36 @@ def cube_mesh(n: int):
     return xyz, tets.reshape(-1, 4).astype(np.int32)
 
 
+def sphere_mesh(n: int, radius: float):
+    """A ball of the given radius carved from the Kuhn mesh of [-radius, radius]^3
+    with n cells per side: the tetrahedra whose centroid lies inside the ball,
+    the nodes they use renumbered in their lexicographic order.  A stand-in for
+    the paper's unstructured sphere mesh (Section 6.4), whose mesher and mesh
+    are not available: a stair-cased boundary, interior nodes of graph degree
+    up to 14.  Returns (xyz, tets) as cube_mesh does."""
+    xyz, tets = cube_mesh(n)
+    xyz = (2.0 * xyz - 1.0) * radius
+    cent = xyz[tets].mean(axis=1)
+    keep = np.einsum("ij,ij->i", cent, cent) < radius * radius
+    tets = tets[keep]
+    used = np.unique(tets)
+    new = -np.ones(len(xyz), dtype=np.int64)
+    new[used] = np.arange(len(used))
+    return xyz[used], new[tets].astype(np.int32)
+
+
+def octant_node_sensors(xyz, n_obs: int, r_phys: float, h: float, seed: int):
+    """Node-coincident detectors on the physical sphere of radius r_phys, first
+    octant (Section 6.4): n_obs seeded picks among the nodes with x, y, z >= 0
+    whose radius is within h / 2 of r_phys.  Returns their coordinates (n_obs, 3)."""
+    r = np.linalg.norm(xyz, axis=1)
+    cand = np.nonzero((np.abs(r - r_phys) <= 0.5 * h) & np.all(xyz >= 0.0, axis=1))[0]
+    if len(cand) < n_obs:
+        raise ValueError(f"only {len(cand)} candidate nodes for {n_obs} detectors")
+    pick = np.random.default_rng(seed).choice(cand, size=n_obs, replace=False)
+    return xyz[np.sort(pick)]
+
+
 # ----------------------------------------------------------------------------
 # Detectors
 # ----------------------------------------------------------------------------

@@ -142,3 +142,40 @@ def test_variant_selection_validates_combinations():
     for K, v in bad:
         with pytest.raises(PatError, match="PAT_EINVAL"):
             m.select_variant(K, "fwd", **v)
+
+
+def test_host_assembly_of_a_carved_sphere_with_node_sensors_matches_oracle():
+    """A non-cube mesh (ball carved from the Kuhn mesh) and interior node-coincident
+    sensors: the library's FP64 assembly and sensor map equal the oracle's."""
+    from paper_2607_21373_b300 import Mesh
+    n, R = 8, 2.0
+    xyz, tets = S.sphere_mesh(n, R)
+    det = S.octant_node_sensors(xyz, 10, 1.0, 2 * R / n, 7)
+    m = Mesh(xyz, tets, det, 0.3 * 2 * R / n, 10, precision="f64", flags=0x8 | 0x1)
+    ops = fem.build_node_sensors(xyz, tets, det)
+    ex = m.export()
+    assert np.abs(ex["ML"] - ops["ML"]).max() < 1e-15 * ops["ML"].max()
+    for which, A in ((0, ops["K"]), (1, ops["B"])):
+        rp, col, val = m.export_csr(which)
+        A = A.tocsr()
+        A.sort_indices()
+        assert np.array_equal(rp, A.indptr) and np.array_equal(col, A.indices)
+        assert np.abs(val - A.data).max() < 1e-14 * np.abs(A.data).max()
+    for d in range(len(det)):
+        a = {int(k): w for k, w in zip(ex["det_nodes"][d], ex["det_w"][d]) if w > 0}
+        assert a == {int(ops["det_nodes"][d, 0]): 1.0}
+
+
+def test_rcm_renumbering_is_a_permutation_that_narrows_the_band():
+    from paper_2607_21373_b300.reorder import bandwidth, rcm_permutation, renumber
+    xyz, tets = S.sphere_mesh(10, 2.0)
+    N = len(xyz)
+    rng = np.random.default_rng(0)
+    shuffled = rng.permutation(N)
+    xs, ts = renumber(xyz, tets, shuffled)
+    perm = rcm_permutation(ts, N)
+    assert np.array_equal(np.sort(perm), np.arange(N))
+    xr, tr = renumber(xs, ts, perm)
+    assert bandwidth(tr, N) < bandwidth(ts, N) / 4
+    # the same mesh: every tetrahedron's vertex coordinates are unchanged
+    assert np.array_equal(xr[tr], xs[ts])

@@ -1,0 +1,77 @@
+"""The forward map, its transpose and LSQR sampling on a non-cube mesh: a ball of
+radius 2 carved from the Kuhn mesh (stand-in for the paper's sphere, Section
+6.4) with node-coincident detectors on the physical unit sphere's first octant,
+against the FP64 oracle; and invariance under an RCM renumbering of the nodes.
+
+The carved ball's stair-cased corners (nodes of a single tetrahedron) carry a
+large explicit absorbing term: the growth check refuses dt = 0.25 h there, so
+these meshes use dt = 0.2 h.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import fem, rto, wave
+from problems import as_precision, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def sphere(n=10, n_obs=12, nt=150, seed=5):
+    xyz, tets = S.sphere_mesh(n, 2.0)
+    h = 4.0 / n
+    det = S.octant_node_sensors(xyz, n_obs, 1.0, h, seed)
+    ops = fem.build_node_sensors(xyz, tets, det)
+    p0 = S.gaussian_blobs(xyz, 3, seed + 1, sigma=(0.2, 0.4), centre=(-0.5, 0.8))
+    return xyz, tets, det, ops, 0.2 * h, nt, p0
+
+
+def dev(a, prec):
+    return torch.tensor(np.asarray(a), dtype=torch.float64 if prec == "f64" else torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_forward_adjoint_and_dot_test_on_a_carved_sphere(prec, tol):
+    from paper_2607_21373_b300 import Mesh
+    xyz, tets, det, ops, dt, nt, p0 = sphere()
+    m = Mesh(xyz, tets, det, dt, nt, precision=prec)
+    K = 4
+    P = as_precision(np.stack([p0 * (1 + 0.25 * k) for k in range(K)], axis=1)
+                     + 0.05 * S.standard_normal((len(xyz), K), 8), prec)
+    Y = m.forward(dev(P, prec))
+    assert rel_l2(Y.cpu().numpy(), wave.forward(ops, P, dt, nt)) < tol
+    yh = as_precision(S.standard_normal((nt, len(det), K), 9), prec)
+    g = m.adjoint(dev(yh, prec))
+    assert rel_l2(g.cpu().numpy(), wave.adjoint(ops, yh, dt)) < tol
+    lhs = (Y.double() * dev(yh, prec).double()).sum(dim=(0, 1))
+    rhs = (dev(P, prec).double() * g.double()).sum(dim=0)
+    scale = Y.double().pow(2).sum(dim=(0, 1)).sqrt() * dev(yh, prec).double().pow(2).sum(dim=(0, 1)).sqrt()
+    assert torch.all((lhs - rhs).abs() <= (1e-13 if prec == "f64" else 1e-6) * scale)
+
+
+def test_rcm_renumbering_leaves_the_observations_unchanged():
+    from paper_2607_21373_b300 import Mesh
+    from paper_2607_21373_b300.reorder import rcm_permutation, renumber
+    xyz, tets, det, ops, dt, nt, p0 = sphere()
+    perm = rcm_permutation(tets, len(xyz))
+    xr, tr = renumber(xyz, tets, perm)
+    a = Mesh(xyz, tets, det, dt, nt, precision="f64").forward(dev(p0, "f64"))
+    b = Mesh(xr, tr, det, dt, nt, precision="f64").forward(dev(p0[perm], "f64"))
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-12
+
+
+def test_lsqr_sampling_on_a_carved_sphere_matches_oracle():
+    from paper_2607_21373_b300 import Mesh
+    xyz, tets, det, ops, dt, nt, p0 = sphere()
+    Y = wave.forward(ops, p0, dt, nt)
+    y_obs, sigma = rto.add_noise(Y, S.standard_normal(Y.shape, 10), 0.02, dt)
+    K = 3
+    eta = S.standard_normal((nt, len(det), K), 11)
+    xi = S.standard_normal((len(xyz), K), 12)
+    m = Mesh(xyz, tets, det, dt, nt, precision="f64")
+    out = m.rto_sample(dev(y_obs, "f64"), sigma, K, 3, eta=dev(eta, "f64"), xi=dev(xi, "f64"), solver="lsqr",
+                       resid=True)
+    X, hist = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta, xi, 3)
+    assert rel_l2(out["samples"].cpu().numpy(), X) < 1e-9
+    assert rel_l2(out["resid"].cpu().numpy(), hist ** 2) < 1e-9

@@ -122,3 +122,43 @@ def test_sensor_interpolation(n):
         keys = {k for k in set(a) | set(b) if max(a.get(k, 0), b.get(k, 0)) > 1e-12}
         for k in keys:
             assert abs(a.get(k, 0.0) - b.get(k, 0.0)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# A non-cube mesh: the ball carved from the Kuhn mesh, node-coincident sensors
+# ---------------------------------------------------------------------------
+def _boundary_faces_independent(tets):
+    """Faces belonging to exactly one tetrahedron, found by counting sorted triples."""
+    faces = np.sort(np.concatenate([tets[:, [0, 1, 2]], tets[:, [0, 1, 3]], tets[:, [0, 2, 3]],
+                                    tets[:, [1, 2, 3]]]), axis=1)
+    uniq, cnt = np.unique(faces, axis=0, return_counts=True)
+    return uniq[cnt == 1]
+
+
+def test_carved_sphere_operators_have_their_closed_form_sums():
+    """Every Kuhn tetrahedron of cell size h has volume h^3/6, so sum M_L = E h^3/6;
+    K annihilates constants; 1^T B 1 is the boundary area (B_f = A_f/12 (1 + delta_ab))."""
+    n, R = 10, 2.0
+    xyz, tets = S.sphere_mesh(n, R)
+    h = 2 * R / n
+    ops = fem.assemble(xyz, tets)
+    assert abs(ops["ML"].sum() - len(tets) * h ** 3 / 6) <= 1e-12 * len(tets) * h ** 3
+    assert np.abs(ops["K"] @ np.ones(len(xyz))).max() <= 1e-13 * np.abs(ops["K"]).max()
+    bf = _boundary_faces_independent(tets)
+    P = xyz[bf]
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1).sum()
+    one = np.ones(len(xyz))
+    assert abs(one @ (ops["B"] @ one) - area) <= 1e-12 * area
+    assert 4 * np.pi * R * R < area < 4 * np.pi * R * R * 2.0       # a stair-cased sphere: larger than 4 pi R^2
+    r = np.linalg.norm(xyz, axis=1)
+    assert r.max() <= R + np.sqrt(3) * h and len(np.unique(tets)) == len(xyz)
+
+
+def test_node_sensors_observe_the_node_values():
+    n, R = 10, 2.0
+    xyz, tets = S.sphere_mesh(n, R)
+    det = S.octant_node_sensors(xyz, 12, 1.0, 2 * R / n, 5)
+    ops = fem.build_node_sensors(xyz, tets, det)
+    f = xyz @ np.array([0.3, -1.2, 0.7]) + 0.25                 # any nodal field
+    assert np.abs(ops["Pi"] @ f - (det @ np.array([0.3, -1.2, 0.7]) + 0.25)).max() < 1e-14
+    assert np.all(det >= 0.0) and np.all(np.abs(np.linalg.norm(det, axis=1) - 1.0) <= R / n)
