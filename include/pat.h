@@ -81,10 +81,13 @@ typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_prec;
  *            for c = 1.  It scales the element stiffness only; the absorbing
  *            boundary matrix is assembled at c = 1 (the paper's nondimensional
  *            setting).
- *   det_xyz  host, [n_obs][3] double: sensor positions; each must lie on a
+ *   det_xyz  host, [n_obs][3] double: sensor positions, read by P1
+ *            interpolation (the general Pi of Section 5.1): a position within
+ *            1e-12 of the mesh extent of a node reads that node; one on a
  *            boundary triangle (a tetrahedron face not shared with another
- *            tetrahedron), within 1e-9 of the mesh size.  A sensor is read by P1
- *            interpolation in that triangle (general Pi of Section 5.1).
+ *            tetrahedron, within 1e-9 of the mesh size) interpolates in that
+ *            triangle; any other position inside the mesh interpolates in the
+ *            tetrahedron that holds it.
  *   dt       time step; n_steps = N_T observation times t_n = n dt, n = 1..N_T.
  *   prec     state precision of all compute calls on this mesh.
  *   flags    PAT_MESH_* bits.
@@ -95,8 +98,8 @@ typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_prec;
  * triangle.  Unless PAT_MESH_SKIP_STABILITY is given, the call runs the
  * propagator for 300 steps in FP64 on the host from a seeded random state and
  * returns PAT_EUNSTABLE when the last 100 steps grow faster than 1e-3 per step.
- * Errors: PAT_EINVAL (index out of range, degenerate tetrahedron, sensor off the
- * boundary, dt <= 0, n_steps < 1), PAT_EUNSTABLE, PAT_ENOMEM, PAT_ECUDA.
+ * Errors: PAT_EINVAL (index out of range, degenerate tetrahedron, sensor outside
+ * the mesh, dt <= 0, n_steps < 1), PAT_EUNSTABLE, PAT_ENOMEM, PAT_ECUDA.
  */
 pat_status pat_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                            const double* c2_elem, const double* det_xyz, int32_t n_obs, double dt,
@@ -130,8 +133,10 @@ pat_status pat_mesh_query(const pat_mesh* mesh, pat_mesh_info* info);
 
 /*
  * Copy assembly results to host buffers (each may be NULL):
- *   lumped_mass [N] double; det_nodes [n_obs][3] int32 and det_w [n_obs][3]
- *   double (the boundary triangle and P1 weights of each sensor, weights >= 0);
+ *   lumped_mass [N] double; det_nodes [n_obs][4] int32 and det_w [n_obs][4]
+ *   double (the nodes and P1 weights of each sensor, weights >= 0: one node
+ *   for a node-coincident sensor, a boundary triangle's three, a
+ *   tetrahedron's four; unused entries repeat a node with weight 0);
  *   boundary_faces [F][3] int32 (sorted vertex triples, lexicographic order).
  */
 pat_status pat_mesh_export(const pat_mesh* mesh, double* lumped_mass, int32_t* det_nodes,

@@ -142,6 +142,41 @@ def observation_matrix(N, nodes, weights):
     return sp.csr_matrix((weights.ravel(), (rows, nodes.ravel())), shape=(n_obs, N))
 
 
+def sensor_weights_points(xyz, tets, det_xyz):
+    """Sensors anywhere in a tetrahedral mesh, by brute force (small meshes): the
+    tetrahedron that holds the point and its barycentric coordinates, i.e. the
+    P1 interpolation weights of its four vertices (eq. lagrange).  A point on a
+    shared face or edge takes the holding tetrahedron of smallest index."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    tets = np.asarray(tets, dtype=np.int64)
+    P0 = xyz[tets[:, 0]]
+    J = np.stack([xyz[tets[:, v]] - P0 for v in (1, 2, 3)], axis=2)     # (E, 3, 3), edges as columns
+    Jinv = np.linalg.inv(J)
+    nodes = np.empty((len(det_xyz), 4), dtype=np.int64)
+    w = np.empty((len(det_xyz), 4))
+    for d, x in enumerate(np.asarray(det_xyz, dtype=np.float64)):
+        l123 = np.einsum("eij,ej->ei", Jinv, x - P0)
+        lam = np.concatenate([1.0 - l123.sum(axis=1)[:, None], l123], axis=1)
+        inside = np.nonzero(lam.min(axis=1) >= -1e-12)[0]
+        if len(inside) == 0:
+            raise ValueError(f"sensor {d} is outside the mesh")
+        e = inside[0]
+        lm = np.maximum(lam[e], 0.0)
+        nodes[d] = tets[e]
+        w[d] = lm / lm.sum()
+    return nodes, w
+
+
+def build_point_sensors(xyz, tets, det_xyz, c2_elem=None):
+    """All oracle operators for any tetrahedral mesh with sensors anywhere inside it."""
+    ops = assemble(xyz, tets, c2_elem)
+    nodes, w = sensor_weights_points(xyz, tets, det_xyz)
+    ops["det_nodes"] = nodes
+    ops["det_w"] = w
+    ops["Pi"] = observation_matrix(len(xyz), nodes, w)
+    return ops
+
+
 def build_node_sensors(xyz, tets, det_xyz, c2_elem=None):
     """All oracle operators for any tetrahedral mesh with node-coincident sensors."""
     ops = assemble(xyz, tets, c2_elem)

@@ -84,10 +84,11 @@ class Mesh:
 
     # -- host exports ------------------------------------------------------
     def export(self):
-        """Lumped mass, sensor triangles and weights, boundary faces (host numpy)."""
+        """Lumped mass, sensor nodes and P1 weights (4 per sensor, unused ones with
+        weight 0), boundary faces (host numpy)."""
         ml = np.empty(self.N)
-        dn = np.empty((self.n_obs, 3), dtype=np.int32)
-        dw = np.empty((self.n_obs, 3))
+        dn = np.empty((self.n_obs, 4), dtype=np.int32)
+        dw = np.empty((self.n_obs, 4))
         bf = np.empty((self.info["n_boundary_faces"], 3), dtype=np.int32)
         _lib.check(lib().pat_mesh_export(self._h, ml.ctypes.data, dn.ctypes.data, dw.ctypes.data,
                                          bf.ctypes.data))

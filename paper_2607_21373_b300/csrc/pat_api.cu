@@ -313,7 +313,8 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
   // sensor lists per node (for the adjoint's injection entries)
   std::vector<std::vector<std::pair<int32_t, double>>> inj(N);
   for (int32_t d = 0; d < n_obs; ++d)
-    for (int a = 0; a < 3; ++a) inj[h.det_node[3 * d + a]].push_back({d, h.det_w[3 * d + a]});
+    for (int a = 0; a < kDetPts; ++a)
+      if (h.det_w[kDetPts * d + a] != 0.0) inj[h.det_node[kDetPts * d + a]].push_back({d, h.det_w[kDetPts * d + a]});
 
   m.three_level = !(flags & PAT_MESH_TWO_LEVEL);
   HostRows F, A, A3;

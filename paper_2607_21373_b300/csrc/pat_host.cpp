@@ -228,7 +228,123 @@ pat_status assemble_host(const double* xyz, int64_t N, const int32_t* tets, int6
 // is below 1e-9 of the triangle size and all barycentric coordinates are
 // >= -1e-12; among several, the largest minimum coordinate wins (lowest
 // triangle index on ties).
+// Sensors inside the mesh (neither a node nor on a boundary triangle): the
+// tetrahedron that holds the point and its four barycentric coordinates (P1
+// interpolation).  Tetrahedra are hashed by their bounding boxes on a uniform
+// grid of the largest tetrahedron extent, built on the first such sensor.
+struct TetGrid {
+  bool built = false;
+  double lo[3] = {0, 0, 0}, cell = 1.0;
+  int64_t dims[3] = {1, 1, 1};
+  std::unordered_map<int64_t, std::vector<int32_t>> cells;
+};
+
+static void build_tet_grid(const HostMesh& m, TetGrid& g) {
+  const double* X = m.xyz.data();
+  double hi[3] = {-1e300, -1e300, -1e300}, hmax = 0.0;
+  for (int c = 0; c < 3; ++c) g.lo[c] = 1e300;
+  for (int64_t i = 0; i < m.N; ++i)
+    for (int c = 0; c < 3; ++c) {
+      g.lo[c] = std::min(g.lo[c], X[3 * i + c]);
+      hi[c] = std::max(hi[c], X[3 * i + c]);
+    }
+  for (int64_t e = 0; e < m.E; ++e)
+    for (int c = 0; c < 3; ++c) {
+      double a = 1e300, b = -1e300;
+      for (int v = 0; v < 4; ++v) {
+        const double t = X[3 * (int64_t)m.tets[4 * e + v] + c];
+        a = std::min(a, t);
+        b = std::max(b, t);
+      }
+      hmax = std::max(hmax, b - a);
+    }
+  g.cell = std::max(hmax, 1e-300);
+  for (int c = 0; c < 3; ++c) g.dims[c] = std::max<int64_t>(1, (int64_t)std::ceil((hi[c] - g.lo[c]) / g.cell) + 1);
+  for (int64_t e = 0; e < m.E; ++e) {
+    int64_t a0[3], a1[3];
+    for (int c = 0; c < 3; ++c) {
+      double a = 1e300, b = -1e300;
+      for (int v = 0; v < 4; ++v) {
+        const double t = X[3 * (int64_t)m.tets[4 * e + v] + c];
+        a = std::min(a, t);
+        b = std::max(b, t);
+      }
+      a0[c] = std::min(std::max<int64_t>((int64_t)std::floor((a - g.lo[c]) / g.cell), 0), g.dims[c] - 1);
+      a1[c] = std::min(std::max<int64_t>((int64_t)std::floor((b - g.lo[c]) / g.cell), 0), g.dims[c] - 1);
+    }
+    for (int64_t i = a0[0]; i <= a1[0]; ++i)
+      for (int64_t j = a0[1]; j <= a1[1]; ++j)
+        for (int64_t k = a0[2]; k <= a1[2]; ++k)
+          g.cells[(i * g.dims[1] + j) * g.dims[2] + k].push_back((int32_t)e);
+  }
+  g.built = true;
+}
+
+static pat_status locate_in_tets(const double* x, int32_t d, HostMesh& m, TetGrid& g) {
+  if (!g.built) build_tet_grid(m, g);
+  const double* X = m.xyz.data();
+  int64_t ijk[3];
+  for (int c = 0; c < 3; ++c) {
+    const int64_t v = (int64_t)std::floor((x[c] - g.lo[c]) / g.cell);
+    if (v < 0 || v >= g.dims[c]) {
+      set_error("pat_mesh_create: sensor %d at (%g, %g, %g) is outside the mesh", d, x[0], x[1], x[2]);
+      return PAT_EINVAL;
+    }
+    ijk[c] = v;
+  }
+  auto it = g.cells.find((ijk[0] * g.dims[1] + ijk[1]) * g.dims[2] + ijk[2]);
+  int64_t best = -1;
+  double best_min = -1e300, best_l[4] = {0, 0, 0, 0};
+  if (it != g.cells.end())
+    for (int32_t e : it->second) {
+      const int32_t* t = &m.tets[4 * (int64_t)e];
+      const double* P0 = X + 3 * (int64_t)t[0];
+      double J[3][3], r[3];
+      for (int c = 0; c < 3; ++c) {
+        for (int v = 0; v < 3; ++v) J[c][v] = X[3 * (int64_t)t[v + 1] + c] - P0[c];
+        r[c] = x[c] - P0[c];
+      }
+      // solve J l = r by Cramer's rule (J's columns are the edges from vertex 0)
+      const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                         J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+      if (det == 0.0) continue;
+      double l[4];
+      for (int v = 0; v < 3; ++v) {
+        double A[3][3];
+        for (int c = 0; c < 3; ++c)
+          for (int u = 0; u < 3; ++u) A[c][u] = (u == v) ? r[c] : J[c][u];
+        l[v + 1] = (A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                    A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) /
+                   det;
+      }
+      l[0] = 1.0 - l[1] - l[2] - l[3];
+      const double mn = std::min(std::min(l[0], l[1]), std::min(l[2], l[3]));
+      if (mn < -1e-12) continue;
+      if (mn > best_min || (mn == best_min && e < best)) {
+        best = e;
+        best_min = mn;
+        for (int v = 0; v < 4; ++v) best_l[v] = l[v];
+      }
+    }
+  if (best < 0) {
+    set_error("pat_mesh_create: sensor %d at (%g, %g, %g) is not inside the mesh", d, x[0], x[1], x[2]);
+    return PAT_EINVAL;
+  }
+  double s = 0.0;
+  for (int v = 0; v < 4; ++v) {
+    best_l[v] = std::max(best_l[v], 0.0);
+    s += best_l[v];
+  }
+  for (int v = 0; v < 4; ++v) {
+    m.det_node[kDetPts * d + v] = m.tets[4 * best + v];
+    m.det_w[kDetPts * d + v] = best_l[v] / s;
+  }
+  return PAT_OK;
+}
+
 pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
+  TetGrid tet_grid;
   const int64_t F = (int64_t)m.bfaces.size() / 3;
   const double* X = m.xyz.data();
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -273,8 +389,8 @@ pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
         for (int64_t k = a0[2]; k <= a1[2]; ++k) grid[(i * dims[1] + j) * dims[2] + k].push_back((int32_t)f);
   }
   m.n_obs = n_obs;
-  m.det_node.assign(3 * (size_t)n_obs, 0);
-  m.det_w.assign(3 * (size_t)n_obs, 0.0);
+  m.det_node.assign(kDetPts * (size_t)n_obs, 0);
+  m.det_w.assign(kDetPts * (size_t)n_obs, 0.0);
   // node-coincident sensors (any node, interior ones included): nodes hashed by
   // their coordinates quantised to q = 1e-9 of the mesh's extent; a sensor
   // within 1e-12 of the extent of a node observes that node's value alone
@@ -310,9 +426,9 @@ pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
     const double* x = det + 3 * d;
     const int32_t at = node_at(x);
     if (at >= 0) {
-      for (int a = 0; a < 3; ++a) {
-        m.det_node[3 * d + a] = at;
-        m.det_w[3 * d + a] = a == 0 ? 1.0 : 0.0;
+      for (int a = 0; a < kDetPts; ++a) {
+        m.det_node[kDetPts * d + a] = at;
+        m.det_w[kDetPts * d + a] = a == 0 ? 1.0 : 0.0;
       }
       continue;
     }
@@ -362,9 +478,9 @@ pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
           }
         }
     if (best < 0) {
-      set_error("pat_mesh_create: sensor %d at (%g, %g, %g) is neither a mesh node nor on a boundary triangle", d,
-                x[0], x[1], x[2]);
-      return PAT_EINVAL;
+      const pat_status si = locate_in_tets(x, d, m, tet_grid);
+      if (si) return si;
+      continue;
     }
     double s = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -372,9 +488,10 @@ pat_status locate_sensors(const double* det, int32_t n_obs, HostMesh& m) {
       s += best_l[a];
     }
     for (int a = 0; a < 3; ++a) {
-      m.det_node[3 * d + a] = m.bfaces[3 * best + a];
-      m.det_w[3 * d + a] = best_l[a] / s;
+      m.det_node[kDetPts * d + a] = m.bfaces[3 * best + a];
+      m.det_w[kDetPts * d + a] = best_l[a] / s;
     }
+    m.det_node[kDetPts * d + 3] = m.bfaces[3 * best];  // unused fourth point: weight 0
   }
   return PAT_OK;
 }

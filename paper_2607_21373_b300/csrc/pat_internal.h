@@ -56,6 +56,9 @@ void assemble_stiffness(HostMesh& m);
 pat_status assemble_host(const double* xyz, int64_t N, const int32_t* tets, int64_t E,
                          const double* c2, HostMesh& m);
 // Locates sensors on boundary triangles.
+// Nodes and P1 weights per sensor: a node-coincident sensor uses 1, one on a
+// boundary triangle 3, one inside a tetrahedron 4 (unused points weigh 0).
+constexpr int kDetPts = 4;
 pat_status locate_sensors(const double* det_xyz, int32_t n_obs, HostMesh& m);
 // Growth check of the propagator (FP64, host).  Returns PAT_OK or PAT_EUNSTABLE.
 pat_status check_stability(const HostMesh& m, double* growth_out);

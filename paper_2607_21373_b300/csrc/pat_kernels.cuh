@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(const FwdArgs<T> A) {
 #pragma unroll
   for (int q = 0; q < V; ++q) acc[q] = T(0);
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const int64_t node = A.det_node[3 * d + s];
-    const T wt = A.det_w[3 * d + s];
+  for (int s = 0; s < kDetPts; ++s) {
+    const int64_t node = A.det_node[kDetPts * d + s];
+    const T wt = A.det_w[kDetPts * d + s];
     const Pack<T, V> a = ld<T, V>(A.a_in + node * A.K + (int64_t)kv * V);
     if (A.w_in) {
       const Pack<T, V> w = ld<T, V>(A.w_in + node * A.K + (int64_t)kv * V);
@@ -470,9 +470,9 @@ __device__ __forceinline__ void step3_body(const Step3Args<T>& A, const int64_t 
 #pragma unroll
   for (int q = 0; q < V; ++q) acc[q] = T(0);
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const int64_t node = A.det_node[3 * d + s];
-    const T wt = A.det_w[3 * d + s];
+  for (int s = 0; s < kDetPts; ++s) {
+    const int64_t node = A.det_node[kDetPts * d + s];
+    const T wt = A.det_w[kDetPts * d + s];
     const Pack<T, V> a = ld<T, V>(A.x + node * A.K + (int64_t)kv * V);
     if (A.prev_mode == 0) {
       const Pack<T, V> b = ld<T, V>(A.xp + node * A.K + (int64_t)kv * V);
@@ -611,9 +611,9 @@ __device__ __forceinline__ void step3f_body(const Step3Args<float>& A, const int
 #pragma unroll
     for (int q = 0; q < V; ++q) acc[q] = 0.0f;
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const int64_t node = A.det_node[3 * d + s];
-      const float wt = A.det_w[3 * d + s];
+    for (int s = 0; s < kDetPts; ++s) {
+      const int64_t node = A.det_node[kDetPts * d + s];
+      const float wt = A.det_w[kDetPts * d + s];
       const Pack<float, V> a = ld<float, V>(A.x + node * A.K + (int64_t)kv * V);
       if (A.prev_mode == 0) {
         const Pack<float, V> b = ld<float, V>(A.xp + node * A.K + (int64_t)kv * V);

@@ -44,9 +44,9 @@ __device__ __forceinline__ void gather_obs(const Step3Args<float>& A, int64_t g)
 #pragma unroll
   for (int q = 0; q < V; ++q) acc[q] = 0.0f;
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const int64_t node = A.det_node[3 * d + s];
-    const float wt = A.det_w[3 * d + s];
+  for (int s = 0; s < kDetPts; ++s) {
+    const int64_t node = A.det_node[kDetPts * d + s];
+    const float wt = A.det_w[kDetPts * d + s];
     const Pack<float, V> a = ld<float, V>(A.x + node * A.K + (int64_t)kv * V);
     if (A.prev_mode == 0) {
       const Pack<float, V> b = ld<float, V>(A.xp + node * A.K + (int64_t)kv * V);

@@ -89,6 +89,15 @@ def octant_node_sensors(xyz, n_obs: int, r_phys: float, h: float, seed: int):
     return xyz[np.sort(pick)]
 
 
+def octant_sphere_points(n_obs: int, r_phys: float, seed: int):
+    """Detectors on the physical sphere of radius r_phys, first octant (Section
+    6.4), uniform on that spherical triangle (seeded): generally inside a
+    tetrahedron of the mesh, not at a node."""
+    rng = np.random.default_rng(seed)
+    v = np.abs(rng.standard_normal((n_obs, 3)))
+    return r_phys * v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
 # ----------------------------------------------------------------------------
 # Detectors
 # ----------------------------------------------------------------------------

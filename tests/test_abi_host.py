@@ -89,8 +89,11 @@ def test_bad_inputs_are_rejected():
     from paper_2607_21373_b300 import Mesh, PatError
     xyz, tets = S.cube_mesh(2)
     det = S.detector_points(4, S.ALL_FACES, 1)
-    with pytest.raises(PatError, match="PAT_EINVAL"):        # sensor off the boundary
-        Mesh(xyz, tets, det + np.array([0.0, 0.0, 1e-3]) * (det[:, 2:3] < 1), 0.1, 5, "f64", flags=0x8)
+    with pytest.raises(PatError, match="PAT_EINVAL"):        # sensor outside the mesh
+        Mesh(xyz, tets, det + np.array([0.0, 0.0, 1.5]), 0.1, 5, "f64", flags=0x8)
+    # a sensor just inside the mesh is read by interpolation in its tetrahedron
+    Mesh(xyz, tets, det + np.array([0.0, 0.0, 1e-3]) * (det[:, 2:3] < 1) - np.array([0.0, 0.0, 1e-3]) * (det[:, 2:3] == 1),
+         0.1, 5, "f64", flags=0x8)
     bad = tets.copy()
     bad[3, 2] = 10_000
     with pytest.raises(PatError, match="PAT_EINVAL"):        # vertex index out of range
@@ -179,3 +182,27 @@ def test_rcm_renumbering_is_a_permutation_that_narrows_the_band():
     assert bandwidth(tr, N) < bandwidth(ts, N) / 4
     # the same mesh: every tetrahedron's vertex coordinates are unchanged
     assert np.array_equal(xr[tr], xs[ts])
+
+
+def test_sensors_inside_tetrahedra_match_the_oracle():
+    """Detectors on the physical unit sphere inside the carved ball: the library's
+    holding tetrahedron and weights equal the oracle's brute-force search; a point
+    outside the mesh is refused."""
+    from paper_2607_21373_b300 import Mesh, PatError
+    n, R = 8, 2.0
+    xyz, tets = S.sphere_mesh(n, R)
+    det = S.octant_sphere_points(16, 1.0, 4)
+    m = Mesh(xyz, tets, det, 0.2 * 2 * R / n, 10, precision="f64", flags=0x8 | 0x1)
+    nodes, w = fem.sensor_weights_points(xyz, tets, det)
+    ex = m.export()
+    for d in range(len(det)):
+        a = {}
+        for k, wt in zip(ex["det_nodes"][d], ex["det_w"][d]):
+            if wt > 1e-12:
+                a[int(k)] = a.get(int(k), 0.0) + wt
+        b = {int(k): wt for k, wt in zip(nodes[d], w[d]) if wt > 1e-12}
+        assert set(a) == set(b)
+        for k in a:
+            assert abs(a[k] - b[k]) < 1e-13
+    with pytest.raises(PatError, match="PAT_EINVAL"):
+        Mesh(xyz, tets, np.array([[5.0, 0.0, 0.0]]), 0.1, 10, precision="f64", flags=0x8 | 0x1)

@@ -75,3 +75,21 @@ def test_lsqr_sampling_on_a_carved_sphere_matches_oracle():
     X, hist = rto.rto_samples_lsqr(ops, dt, nt, y_obs, sigma, eta, xi, 3)
     assert rel_l2(out["samples"].cpu().numpy(), X) < 1e-9
     assert rel_l2(out["resid"].cpu().numpy(), hist ** 2) < 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_detectors_inside_tetrahedra(prec, tol):
+    """Detectors on the physical unit sphere (first octant), generally inside a
+    tetrahedron: P1 interpolation over its four vertices, and the transpose
+    spreads each residual over the same four nodes."""
+    from paper_2607_21373_b300 import Mesh
+    xyz, tets, _, _, dt, nt, p0 = sphere()
+    det = S.octant_sphere_points(14, 1.0, 21)
+    ops = fem.build_point_sensors(xyz, tets, det)
+    m = Mesh(xyz, tets, det, dt, nt, precision=prec)
+    P = as_precision(np.stack([p0, 0.5 * p0 + 0.1], axis=1), prec)
+    Y = m.forward(dev(P, prec))
+    assert rel_l2(Y.cpu().numpy(), wave.forward(ops, P, dt, nt)) < tol
+    yh = as_precision(S.standard_normal((nt, len(det), 2), 22), prec)
+    g = m.adjoint(dev(yh, prec))
+    assert rel_l2(g.cpu().numpy(), wave.adjoint(ops, yh, dt)) < tol

@@ -162,3 +162,17 @@ def test_node_sensors_observe_the_node_values():
     f = xyz @ np.array([0.3, -1.2, 0.7]) + 0.25                 # any nodal field
     assert np.abs(ops["Pi"] @ f - (det @ np.array([0.3, -1.2, 0.7]) + 0.25)).max() < 1e-14
     assert np.all(det >= 0.0) and np.all(np.abs(np.linalg.norm(det, axis=1) - 1.0) <= R / n)
+
+
+def test_point_sensors_interpolate_linear_fields_exactly():
+    """P1 interpolation inside a tetrahedron reproduces linear fields (eq. lagrange),
+    and the weights are a partition of unity over the holding tetrahedron."""
+    xyz, tets = S.sphere_mesh(8, 2.0)
+    det = S.octant_sphere_points(20, 1.0, 3)
+    nodes, w = fem.sensor_weights_points(xyz, tets, det)
+    a, b = np.array([0.3, -1.2, 0.7]), 0.25
+    f = xyz @ a + b
+    assert np.abs((w * f[nodes]).sum(axis=1) - (det @ a + b)).max() < 1e-13
+    assert np.all(w >= 0.0) and np.abs(w.sum(axis=1) - 1.0).max() < 1e-14
+    with pytest.raises(ValueError):
+        fem.sensor_weights_points(xyz, tets, np.array([[5.0, 0.0, 0.0]]))
