@@ -202,6 +202,41 @@ def run_reference(a, rank, world):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def kernel_name(e, adj):
+    """Readable name of the step-kernel variant an autotune entry describes."""
+    tf = "true" if adj else "false"
+    packed = e.get("packed")
+    if packed == 2:
+        return "step3t_kernel<8,%s>" % tf
+    if packed == 4:
+        return "step3p_kernel<%s> (persistent double-buffered tiles)" % tf
+    if packed == 3:
+        p = int(e.get("persistent") or 0)
+        kind = {0: "step3e_kernel", 1: "step3e_persist_kernel", 2: "step3e_slab_kernel",
+                3: "step3e_stage_kernel"}.get(p, "step3e_persistent(%d)" % p)
+        flags = []
+        if p:
+            flags.append("1024-thread blocks" if e.get("big_blocks") else "256-thread blocks")
+        if e.get("pdl"):
+            flags.append("PDL")
+        if e.get("prefetch"):
+            flags.append("L2 prefetch %d" % e["prefetch"])
+        if e.get("wide_loads"):
+            flags.append("256-bit loads")
+        if e.get("l2_hints"):
+            flags.append("L2 hints")
+        if e.get("gather_batch"):
+            flags.append("batches of %d" % e["gather_batch"])
+        if e.get("min_blocks", 1) > 1:
+            flags.append(">=%d blocks/SM" % e["min_blocks"])
+        return "%s<%d,%s>%s" % (kind, e.get("V", 0), tf, " (%s)" % ", ".join(flags) if flags else "")
+    if packed:
+        return "step3f_kernel<%d,%d,%s>%s" % (e.get("V", 0), e.get("chunk", 4), tf,
+                                              " (Z-order rows)" if e.get("zorder") else "")
+    return "step3_kernel<float,%d,split,%s,staged=%d>" % (e.get("V", 0), "adj" if adj else "fwd",
+                                                          int(bool(e.get("staged"))))
+
+
 def run_ours(a, rank, world, local_rank, dist):
     import torch
 
@@ -311,33 +346,6 @@ def run_ours(a, rank, world, local_rank, dist):
         rows = [e for e in tune.get("K%d" % K, []) if e["direction"] == direction]
         return min(rows, key=lambda e: e["us_per_step"]) if rows else {"V": 4, "staged": False, "packed": True}
 
-    def kernel_name(e, adj):
-        if e.get("packed") == 2:
-            return "step3t_kernel<8,%s>" % ("true" if adj else "false")
-        if e.get("packed") == 4:
-            return "step3p_kernel<%s> (persistent double-buffered tiles)" % ("true" if adj else "false")
-        if e.get("packed") == 3:
-            p = int(e.get("persistent") or 0)
-            kind = {0: "step3e_kernel", 1: "step3e_persist_kernel", 2: "step3e_slab_kernel"}[p]
-            flags = []
-            if p:
-                flags.append("1024-thread blocks" if e.get("big_blocks") else "256-thread blocks")
-            if e.get("pdl"):
-                flags.append("PDL")
-            if e.get("prefetch"):
-                flags.append("L2 prefetch %d" % e["prefetch"])
-            if e.get("wide_loads"):
-                flags.append("256-bit loads")
-            if e.get("l2_hints"):
-                flags.append("L2 hints")
-            if e.get("min_blocks", 1) > 1:
-                flags.append(">=%d blocks/SM" % e["min_blocks"])
-            return "%s<%d,%s>%s" % (kind, e["V"], "true" if adj else "false",
-                                    " (%s)" % ", ".join(flags) if flags else "")
-        if e.get("packed"):
-            return "step3f_kernel<%d,%d,%s>%s" % (e["V"], e.get("chunk", 4), "true" if adj else "false",
-                                                  " (Z-order rows)" if e.get("zorder") else "")
-        return "step3_kernel<float,%d,split,%s,staged=%d>" % (e["V"], "adj" if adj else "fwd", e["staged"])
     bf, ba = best("fwd"), best("adj")
     default_workload = (a.cells, a.K, a.n_obs, a.mesh_flags) == (58, 64, 1024, 0)
     kname = "fwd_step_kernel<float,4,true>" if two_level else kernel_name(bf, False)
