@@ -16,11 +16,12 @@ Readings (the paper gives the construction in words only):
     is sigma^2 (the normalisation Z);  the covariance of T z is then
     F^{-1} diag(S) F, whose continuum limit for s = 3/2, d = 3 is the Matern
     function sigma^2 (1 + r/l) e^{-r/l};
-    (the text's SPDE "(1/l^2 - Delta)^3 p0 = W" would square that operator; the
-    covariance operator of eq. matern-cov-op is followed);
-  * P is trilinear interpolation from the grid to the nodes (the text says the
-    field is "projected onto the finite element space"; nodal interpolation is
-    the plain reading for a P1 space);
+    (the SPDE written in Section 6.4 applies the cubed operator to p0, which
+    would square that covariance; the covariance operator of eq. matern-cov-op
+    is followed);
+  * P is trilinear interpolation from the grid to the nodes (the paper carries
+    the grid field to the finite element space without naming the operator;
+    nodal interpolation is the plain reading for a P1 space);
   * latent RTO: min || (G P T z - y_obs) / sigma_n - eta ||^2 + || z - xi ||^2,
     the extended system A = [G P T / sigma_n ; I], b = (y_obs / sigma_n + eta, xi).
 """
