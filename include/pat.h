@@ -11,8 +11,12 @@
  *   - its exact algebraic transpose G^T (Section 5.1: eq. backward-recursion
  *     with the transposed step eq. adjoint-verlet);
  *   - batched least-squares solves of the extended RTO system
- *     (eq. extended-matrices, eq. normal-equations, Algorithm 1), K posterior
- *     samples at a time, and their pointwise mean / std (eq. ergodic).
+ *     (eq. extended-matrices, eq. normal-equations, Algorithm 1) by CGLS or
+ *     LSQR, K posterior samples at a time, and their pointwise mean / std
+ *     (eq. ergodic); the MAP estimate (eq. MAP) and the discrepancy-principle
+ *     diagnostic (Section 6.1).
+ * Meshes are any tetrahedral meshes; sensors may sit at nodes, on boundary
+ * triangles or inside tetrahedra (P1 interpolation, eq. lagrange).
  *
  * Conventions (all entry points):
  *   - Every call returns a pat_status; PAT_OK == 0.  On failure,
