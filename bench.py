@@ -6,19 +6,26 @@ extended least-squares system with k iterations (2k+1 wave solves of N_T steps
 per sample), on a seeded synthetic workload shaped like the paper's 3D problem
 (Section 6.4: ~2e5 unknowns): unit cube 58^3 cells x 6 tets (205,379 nodes),
 N_T = 1000, 1024 sensors on five faces, K = 64, k = 100, FP32 state with FP64
-CGLS scalars.  The timed region holds the whole batch (data perturbations and
-prior draws come from the library's counter-based generator on the device).
+CGLS scalars.  The stiffness operator is the full P1 graph (15 entries per
+interior row, the entries that cancel on the regular lattice kept, as on an
+unstructured mesh); --mesh pruned drops those exact zeros, --mesh jitter moves
+the interior nodes so that nothing cancels.  The timed region holds the whole
+batch (data perturbations and prior draws come from the library's
+counter-based generator on the device).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--mesh cube|pruned|jitter] [--tune-log FILE]
 
 Under torchrun every rank runs its own K samples (sample parallelism, no data
 collective; weak scaling); rank 0 prints the line.  --impl reference times the
-FP64 CPU oracle on the same workload (a bounded, extrapolated sample).
+FP64 CPU oracle on the same workload (a bounded, extrapolated sample, one
+oracle process per host core).
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -34,20 +41,22 @@ import numpy as np  # noqa: E402
 import synthetic as S  # noqa: E402
 
 METRIC = "rto_samples_per_s"
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step launch, from
-# one ncu capture of that kernel variant on the default workload (cube58, K = 64,
-# 1024 sensors); see profiles/step3e_persist_kernel_cube58_K64.md.  Used for the
-# roofline's "traffic" only when the timed run uses the same variant and workload.
-PROFILED_TRAFFIC = {
-    "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)": 160.643584e6,
-    "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)": 159.604480e6,
-    "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)": 159.210752e6,
-    "step3e_persist_kernel<8,true> (1024-thread blocks, PDL)": 158.733312e6,
-}
 UNIT = "samples/s"
+MESH_KEEP_ZEROS = 0x2
+MESH_TWO_LEVEL = 0x10
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step launch of a
+# kernel variant, from one ncu capture on the named workload (K = 64, 1024 sensors,
+# profiles/).  Used for the roofline's "traffic" only when the timed run uses that
+# variant on that workload; null otherwise.
+PROFILED_TRAFFIC = {
+    ("pruned", "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)"): 160.643584e6,
+    ("pruned", "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)"): 159.604480e6,
+    ("pruned", "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)"): 159.210752e6,
+    ("pruned", "step3e_persist_kernel<8,true> (1024-thread blocks, PDL)"): 158.733312e6,
+}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -58,35 +67,63 @@ def parse():
     ap.add_argument("--n-obs", type=int, default=1024)
     ap.add_argument("--K", type=int, default=64)
     ap.add_argument("--k-iter", type=int, default=100)
-    ap.add_argument("--plain-steps", type=int, default=1, help="timed K=1 batches (0: skip the plain form)")
+    ap.add_argument("--mesh", default="cube", choices=["cube", "pruned", "jitter"],
+                    help="cube: full P1 graph (default); pruned: exact-zero entries of the lattice dropped; "
+                         "jitter: interior nodes moved by up to 0.15 h per axis (nothing cancels)")
+    ap.add_argument("--plain-steps", type=int, default=3, help="timed K=1 samples (0: skip the plain form)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
-    ap.add_argument("--mesh-flags", type=int, default=0, help="pat_mesh_create flags (e.g. 16: two-level form)")
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0: one per host core, at most 64)")
+    ap.add_argument("--mesh-flags", type=int, default=0, help="extra pat_mesh_create flags (e.g. 16: two-level form)")
     ap.add_argument("--autotune", type=int, default=1, help="0: keep the library's default step-kernel variant")
+    ap.add_argument("--tune-log", default="", help="write the autotuner's full timing table (JSON) to this file")
     ap.add_argument("--solver", default="cgls", choices=["cgls", "lsqr"],
                     help="least-squares solver of every RTO sample (the configured workload names CGLS)")
-    ap.add_argument("--variant", default="", help="force a step-kernel variant for K: tiled | v8c2 | v4c4 | v8c2z | ell8 | ell4 | pipe | "
-                    "ell8pf | ell8p | ell8pw | ell8pp | ell8pb")
-    return ap.parse_args()
+    ap.add_argument("--variant", default="", help="force a step-kernel variant for K: " + " | ".join(sorted(FORCED)))
+    return ap.parse_args(argv)
+
+
+# step-kernel variants that --variant can force (fields of pat_select_variant)
+FORCED = {
+    "tiled": dict(V=8, packed=2), "v8c2": dict(V=8, packed=1, chunk=2), "v4c4": dict(V=4, packed=1, chunk=4),
+    "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3), "pipe": dict(V=8, packed=4),
+    "ell8pp": dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1),
+    "ell8pb": dict(V=8, packed=3, persistent=1, pdl=True, big_blocks=True),
+    "w16": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4),
+    "w16c": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True),
+    "w16b8": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8),
+    "w16b8c": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8, early=True),
+    "w16big": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, big_blocks=True),
+}
+
+
+def mesh_flags(a):
+    return (0 if a.mesh == "pruned" else MESH_KEEP_ZEROS) | a.mesh_flags
 
 
 def workload_config(a):
     w = S.BATCHED
+    n = a.cells
+    kind = {"cube": "Kuhn tets, full P1 graph (15 entries per interior row, lattice zeros kept)",
+            "pruned": "Kuhn tets, exact-zero entries dropped (7-point interior rows)",
+            "jitter": "Kuhn connectivity, interior nodes jittered by U[-0.15h, 0.15h]^3 (15 nonzeros per row)"}[a.mesh]
     return {
-        "workload": f"cube{a.cells}_rto: unit cube {a.cells}^3 cells x 6 Kuhn tets, {(a.cells + 1) ** 3} nodes, "
+        "workload": f"cube{n}_rto_{a.mesh}: unit cube {n}^3 cells x 6 tets ({kind}), {(n + 1) ** 3} nodes, "
                     f"N_T={a.n_steps}, dt=0.3h, {a.n_obs} sensors on 5 faces, K={a.K} samples per batch, "
                     f"{a.solver.upper()} k={a.k_iter}, white-noise prior N(0, M_L^-1), 1% noise",
-        "n_nodes": (a.cells + 1) ** 3, "n_tets": 6 * a.cells ** 3, "n_steps": a.n_steps, "n_obs": a.n_obs,
-        "K": a.K, "solver": a.solver, "cgls_iters" if a.solver == "cgls" else "lsqr_iters": a.k_iter,
-        "noise": w.noise,
-        "node_steps_per_sample": (2 * a.k_iter + 1) * a.n_steps * (a.cells + 1) ** 3,
-        "l2": "inputs larger than L2: the K-stacked state is 4*N*K*4 B = %.0f MB per buffer set"
-              % (4 * (a.cells + 1) ** 3 * a.K * 4 / 1e6),
+        "n_nodes": (n + 1) ** 3, "n_tets": 6 * n ** 3, "n_steps": a.n_steps, "n_obs": a.n_obs,
+        "K": a.K, "solver": a.solver, "iters": a.k_iter, "noise": w.noise, "mesh": a.mesh,
+        "node_steps_per_sample": (2 * a.k_iter + 1) * a.n_steps * (n + 1) ** 3,
+        "l2": "inputs larger than L2: the state buffers hold 3*N*K*4 B = %.0f MB (L2 126 MB)"
+              % (3 * (n + 1) ** 3 * a.K * 4 / 1e6),
     }
 
 
 def problem(a):
-    xyz, tets = S.cube_mesh(a.cells)
+    if a.mesh == "jitter":
+        xyz, tets = S.jittered_cube_mesh(a.cells, 0.15, S.BATCHED.seed + 200)
+    else:
+        xyz, tets = S.cube_mesh(a.cells)
     det = S.detector_points(a.n_obs, S.LIMITED_VIEW_FACES, S.BATCHED.seed)
     p0 = S.phantom(xyz, "blobs20+vessels", S.BATCHED.seed + 100, a.cells)
     return xyz, tets, det, p0, 0.3 / a.cells
@@ -148,19 +185,65 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle timing (reported baseline and the reference arm)
 # --------------------------------------------------------------------------
-def oracle_rate(a, n_solve_steps, xyz=None, tets=None, det=None, p0=None):
-    """Oracle node-steps/s over one forward and one transposed solve of
-    n_solve_steps steps each (K = 1), single-threaded SciPy."""
-    from oracle import fem, wave
-    if xyz is None:
-        xyz, tets, det, p0, _ = problem(a)
-    dt = 0.3 / a.cells
-    ops = fem.build(xyz, tets, det, a.cells)
+_W = {}
+
+
+def _oracle_init(ops, p0, dt):
+    _W.update(ops=ops, p0=p0, dt=dt)
+
+
+def _oracle_solve(n_solve):
+    """One oracle forward and one transposed solve of n_solve steps (K = 1);
+    returns its wall time."""
+    from oracle import wave
     t0 = time.perf_counter()
-    Y = wave.forward(ops, p0, dt, n_solve_steps)
-    wave.adjoint(ops, Y, dt)
-    sec = time.perf_counter() - t0
-    return 2 * n_solve_steps * len(xyz) / sec, sec
+    Y = wave.forward(_W["ops"], _W["p0"], _W["dt"], n_solve)
+    wave.adjoint(_W["ops"], Y, _W["dt"])
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The FP64 oracle (SciPy, single-threaded) in `procs` spawned processes,
+    one RTO sample's wave solves per process (the paper's sample parallelism,
+    Section 6.4).  Spawned, not forked, so the children hold no CUDA state."""
+
+    def __init__(self, a, procs, problem_data=None):
+        from oracle import fem
+        xyz, tets, det, p0, dt = problem_data if problem_data else problem(a)
+        ops = fem.build(xyz, tets, det, a.cells)
+        self.N = len(xyz)
+        self.procs = max(1, procs)
+        lean = {k: ops[k] for k in ("K", "B", "ML", "Pi")}
+        _oracle_init(lean, p0, dt)
+        self.pool = None
+        if self.procs > 1:
+            for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+                os.environ[var] = "1"
+            self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_init, initargs=(lean, p0, dt))
+
+    def rate(self, n_solve, reps=1):
+        """Aggregate node-steps/s of `procs` concurrent forward + transposed
+        solves of n_solve steps, repeated reps times; and the wall time."""
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            if self.pool is None:
+                _oracle_solve(n_solve)
+            else:
+                self.pool.map(_oracle_solve, [n_solve] * self.procs, chunksize=1)
+        sec = time.perf_counter() - t0
+        return reps * self.procs * 2 * n_solve * self.N / sec, sec
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
 
 
 def run_reference(a, rank, world):
@@ -168,35 +251,48 @@ def run_reference(a, rank, world):
         return
     cfg = workload_config(a)
     nsps = cfg["node_steps_per_sample"]
-    xyz, tets, det, p0, _ = problem(a)
-    from oracle import fem, wave
-    ops = fem.build(xyz, tets, det, a.cells)
-    dt = 0.3 / a.cells
-    n_solve = 50      # one step = one forward + one transposed solve of 50 time steps
-
-    def one():
-        Y = wave.forward(ops, p0, dt, n_solve)
-        wave.adjoint(ops, Y, dt)
-
+    procs = a.cpu_procs or min(host_cores(), 64)
+    pool = OraclePool(a, procs)
+    n_solve = 50      # one step = one forward + one transposed solve of 50 time steps per process
+    pool.rate(2)      # warm-up of every process (imports, first touch)
     for _ in range(a.warmup):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        one()
-    sec = time.perf_counter() - t0
-    node_steps = a.steps * 2 * n_solve * len(xyz)
-    value = node_steps / sec / nsps
-    sample = (f"per step: one FP64 oracle forward and one transposed solve of {n_solve} of the {a.n_steps} time "
-              f"steps (K=1); samples/s extrapolated by node-steps: {nsps:.3e} node-steps per sample")
+        pool.rate(n_solve)
+    rate, sec = pool.rate(n_solve, reps=a.steps)
+    pool.close()
+    value = rate / nsps
+    sample = (f"per step: {procs} oracle processes (one per host core), each one FP64 forward and one transposed "
+              f"solve of {n_solve} of the {a.n_steps} time steps (K=1); samples/s extrapolated by node-steps: "
+              f"{nsps:.3e} node-steps per sample")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": 1e3 * sec / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "node_steps_per_s": node_steps / sec,
+        "node_steps_per_s": rate,
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(a, data, nsps):
+    """The oracle on the host cores: all cores (one process each), and one
+    thread, on a bounded sample of the workload's wave solves."""
+    procs = a.cpu_procs or min(host_cores(), 64)
+    pool = OraclePool(a, procs, data)
+    pool.rate(2)
+    n_all = 100
+    rate_all, sec_all = pool.rate(n_all)
+    pool.close()
+    one = OraclePool(a, 1, data)
+    n_one = 200
+    rate_one, sec_one = one.rate(n_one)
+    return {"value": rate_all / nsps, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} concurrent oracle processes (FP64 SciPy, one thread each), each one forward and one "
+                      f"transposed solve of {n_all} of the {a.n_steps} steps on the same mesh (K=1), {sec_all:.1f} s; "
+                      f"samples/s extrapolated by node-steps ({nsps:.3e} per sample)",
+            "node_steps_per_s": rate_all,
+            "one_thread": {"value": rate_one / nsps, "node_steps_per_s": rate_one,
+                           "sample": f"one process, {n_one}-step forward + transposed solve, {sec_one:.1f} s"}}
 
 
 # --------------------------------------------------------------------------
@@ -206,11 +302,21 @@ def kernel_name(e, adj):
     """Readable name of the step-kernel variant an autotune entry describes."""
     tf = "true" if adj else "false"
     packed = e.get("packed")
+    if packed == 5:
+        if e.get("V") == 1:
+            return "step3w1_kernel<%s> (16 slots, one sample)" % tf
+        nb = e.get("gather_batch") or 4
+        big = bool(e.get("big_blocks"))
+        return "step3w_persist_kernel<%s> (16 slots, rounds of %d%s%s)" % (
+            tf, nb, ", columns per round" if e.get("early") else "",
+            ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""))
     if packed == 2:
         return "step3t_kernel<8,%s>" % tf
     if packed == 4:
         return "step3p_kernel<%s> (persistent double-buffered tiles)" % tf
     if packed == 3:
+        if e.get("V") == 1:
+            return "step3e1_kernel<%s> (8 slots, one sample)" % tf
         p = int(e.get("persistent") or 0)
         kind = {0: "step3e_kernel", 1: "step3e_persist_kernel", 2: "step3e_slab_kernel",
                 3: "step3e_stage_kernel"}.get(p, "step3e_persistent(%d)" % p)
@@ -237,16 +343,26 @@ def kernel_name(e, adj):
                                                           int(bool(e.get("staged"))))
 
 
+def graph_operator_bytes(info, N):
+    """Operator bytes per step on the full FEM graph as the scope table counts
+    them: 4-byte column + 4-byte value per stiffness and boundary entry, row
+    pointers and lumped mass of K (4 B each per node), row pointers of B."""
+    return (info["nnz_K_graph"] * 8 + (N + 1) * 4 + N * 4 + info["nnz_B"] * 8
+            + (info["n_boundary_nodes"] + 1) * 4)
+
+
 def run_ours(a, rank, world, local_rank, dist):
     import torch
 
     from paper_2607_21373_b300 import Mesh
+    from paper_2607_21373_b300.dist import allreduce_moments, sample_seed
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     cfg = workload_config(a)
-    xyz, tets, det, p0, dt = problem(a)
-    mesh = Mesh(xyz, tets, det, dt, a.n_steps, precision="f32", flags=a.mesh_flags)
+    data = problem(a)
+    xyz, tets, det, p0, dt = data
+    mesh = Mesh(xyz, tets, det, dt, a.n_steps, precision="f32", flags=mesh_flags(a))
     N = mesh.N
     # synthetic observations: Y = G p0 (our forward map), 1% relative noise (eq. noise-model)
     p0_d = torch.tensor(p0, dtype=torch.float32, device=dev)
@@ -257,25 +373,21 @@ def run_ours(a, rank, world, local_rank, dist):
     sigma = float(S.BATCHED.noise * torch.linalg.vector_norm(Y.double()) / torch.linalg.vector_norm(eta0.double()))
     y_obs = (Y + sigma * eta0).contiguous()
     K, k = a.K, a.k_iter
+    two_level = bool(mesh_flags(a) & MESH_TWO_LEVEL)
     # pick the step-kernel variant per direction for both sample counts (not timed)
     tune = {}
-    forced = {"tiled": dict(V=8, packed=2), "v8c2": dict(V=8, packed=1, chunk=2),
-              "v4c4": dict(V=4, packed=1, chunk=4), "v8c2z": dict(V=8, packed=1, chunk=2, zorder=True),
-              "ell8": dict(V=8, packed=3), "ell4": dict(V=4, packed=3), "pipe": dict(V=8, packed=4),
-              "ell8pf": dict(V=8, packed=3, prefetch=1),
-              "ell8p": dict(V=8, packed=3, persistent=True),
-              "ell8pw": dict(V=8, packed=3, persistent=True, pdl=True, wide_loads=True, prefetch=1),
-              "ell8pp": dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1),
-              "ell8pb": dict(V=8, packed=3, persistent=1, pdl=True, big_blocks=True)}.get(a.variant)
+    forced = FORCED.get(a.variant)
     if forced:
         for d in ("fwd", "adj"):
             mesh.select_variant(K, d, **forced)
-        tune["K%d" % K] = [dict(dict(direction=d, us_per_step=0.0, staged=False, chunk=0), **forced)
-                           for d in ("fwd", "adj")]
-    elif a.autotune and not (a.mesh_flags & 0x10):
+        tune["K%d" % K] = [dict(dict(direction=d, us_per_step=0.0), **forced) for d in ("fwd", "adj")]
+    elif a.autotune and not two_level:
         tune["K%d" % K] = mesh.autotune(K, n_probe=30)
-        if a.plain_steps > 0:
-            tune["K1"] = mesh.autotune(1, n_probe=30)
+    if a.autotune and not two_level and a.plain_steps > 0:
+        tune["K1"] = mesh.autotune(1, n_probe=30)
+    if a.tune_log and rank == 0:
+        with open(a.tune_log, "w") as f:
+            json.dump(tune, f)
 
     def batch(K_, seed):
         return mesh.rto_sample(y_obs, sigma, K_, k, seed=seed, samples=False, mean=True, stdev=K_ >= 2,
@@ -285,7 +397,6 @@ def run_ours(a, rank, world, local_rank, dist):
         if dist is not None:
             dist.barrier()
 
-    from paper_2607_21373_b300.dist import allreduce_moments, sample_seed
     for i in range(a.warmup):
         batch(K, sample_seed(i, rank))
     mesh.status(K)
@@ -318,47 +429,49 @@ def run_ours(a, rank, world, local_rank, dist):
     value = world * K * a.steps / sec
     nsps = cfg["node_steps_per_sample"]
 
-    # roofline of the dominant kernel (forward step; the transposed step is reported beside it)
+    # roofline of the dominant kernel: the forward step (the transposed step beside it)
     info = mesh.info
     n_obs, NT = a.n_obs, a.n_steps
-    two_level = bool(a.mesh_flags & 0x10)
-    # per node and sample: two-level reads a, w and writes a, w (16 B); three-level reads
-    # x_s, x_{s-1} and writes x_{s+1} (12 B)
+    # bytes per step as the scope table counts them: 16 B of state per node and
+    # sample (read p, v; write p, v) + the full-graph operator; sensor I/O ignored
+    alg_step = 16.0 * N * K + graph_operator_bytes(info, N)
+    # bytes this library's step moves: 12 B of state (three-level form: read x_s,
+    # x_{s-1}, write x_{s+1}; 16 B for the two-level form), its stored operator,
+    # and the sensor reads / writes
     state_b = (16.0 if two_level else 12.0) * N * K
-    gather_b = n_obs * K * (3 * 8 + 4.0)         # sensor reads of two fields at 3 nodes + the observation write
-    fwd_loop_bytes = NT * (state_b + info["operator_bytes"]) + NT * gather_b
-    fwd_launch_per_loop = NT + 1
-    fwd_avg_ms = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
-    fwd_bytes_per_launch = fwd_loop_bytes / fwd_launch_per_loop
-    if two_level:
-        adj_op_b = info["operator_bytes"] + 8.0 * N + n_obs * 3 * 12.0
-        adj_loop_bytes = NT * (state_b + adj_op_b) + NT * n_obs * K * 4.0
-    else:
-        adj_op_b = info["operator_bytes"] + n_obs * 3 * 12.0
-        adj_loop_bytes = NT * (state_b + adj_op_b) + NT * 2 * n_obs * K * 4.0
-    adj_avg_ms = prof["adj_ms"] / max(prof["adj_launches"], 1)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    fwd_moved = state_b + info["operator_bytes"] + n_obs * K * (3 * 8 + 4.0)
+    adj_moved = state_b + info["operator_bytes"] + n_obs * 3 * 12.0 + 2 * n_obs * K * 4.0
+    fwd_ms_launch = prof["fwd_ms"] / max(prof["fwd_launches"], 1)
+    adj_ms_launch = prof["adj_ms"] / max(prof["adj_launches"], 1)
+    per_launch = NT / (NT + 1.0)       # a forward solve: N_T steps + the final observation launch
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else None
     peak = peaks["hbm_gbs"] if peaks else 6400.0
-    achieved = fwd_bytes_per_launch / (fwd_avg_ms * 1e-3) / 1e9
-    adj_achieved = (adj_loop_bytes / (NT + 1)) / (adj_avg_ms * 1e-3) / 1e9
+
+    def gbs(b, ms_):
+        return b * per_launch / (ms_ * 1e-3) / 1e9
+
     def best(direction):
         rows = [e for e in tune.get("K%d" % K, []) if e["direction"] == direction]
-        return min(rows, key=lambda e: e["us_per_step"]) if rows else {"V": 4, "staged": False, "packed": True}
+        return min(rows, key=lambda e: e["us_per_step"]) if rows else {}
 
     bf, ba = best("fwd"), best("adj")
-    default_workload = (a.cells, a.K, a.n_obs, a.mesh_flags) == (58, 64, 1024, 0)
     kname = "fwd_step_kernel<float,4,true>" if two_level else kernel_name(bf, False)
     aname = "adj_step_kernel<float,4,true>" if two_level else kernel_name(ba, True)
-    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak,
-            "traffic": PROFILED_TRAFFIC.get(kname) if default_workload else None,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-            "bytes_per_launch": fwd_bytes_per_launch, "avg_launch_us": 1e3 * fwd_avg_ms,
-            "traffic_source": "ncu capture of the same variant, profiles/step3e_persist_kernel_cube58_K64.md",
-            "adjoint": {"kernel": aname, "achieved": adj_achieved,
-                        "frac": adj_achieved / peak, "avg_launch_us": 1e3 * adj_avg_ms,
-                        "traffic": PROFILED_TRAFFIC.get(aname) if default_workload else None}}
+    default_shape = (a.cells, a.K, a.n_obs, a.mesh_flags) == (58, 64, 1024, 0)
+    traffic = PROFILED_TRAFFIC.get((a.mesh, kname)) if default_shape else None
+    ach = gbs(alg_step, fwd_ms_launch)
+    roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": traffic,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6400 GB/s",
+            "bytes_per_launch": alg_step * per_launch, "avg_launch_us": 1e3 * fwd_ms_launch,
+            "bytes_rule": "16 B/node/sample of state + full-graph operator (nnz*8 + 8N + nnz_B*8 + 4N_b)",
+            "moved": {"bytes_per_launch": fwd_moved * per_launch, "achieved": gbs(fwd_moved, fwd_ms_launch),
+                      "frac": gbs(fwd_moved, fwd_ms_launch) / peak,
+                      "rule": "12 B/node/sample (three-level state) + stored operator + sensor I/O"},
+            "adjoint": {"kernel": aname, "avg_launch_us": 1e3 * adj_ms_launch,
+                        "achieved": gbs(alg_step, adj_ms_launch), "frac": gbs(alg_step, adj_ms_launch) / peak,
+                        "moved_frac": gbs(adj_moved, adj_ms_launch) / peak}}
 
     # plain one-sample form on the same library and workload
     plain = None
@@ -372,8 +485,10 @@ def run_ours(a, rank, world, local_rank, dist):
         p1e.record(st)
         torch.cuda.synchronize()
         psec = p0e.elapsed_time(p1e) / 1e3
-        plain = {"K": 1, "samples_per_s": a.plain_steps / psec, "node_steps_per_s": a.plain_steps * nsps / psec,
-                 "ms_per_sample": 1e3 * psec / a.plain_steps}
+        k1 = [e for e in tune.get("K1", []) if e["direction"] == "fwd"]
+        plain = {"K": 1, "samples": a.plain_steps, "samples_per_s": a.plain_steps / psec,
+                 "node_steps_per_s": a.plain_steps * nsps / psec, "ms_per_sample": 1e3 * psec / a.plain_steps,
+                 "fwd_kernel": kernel_name(min(k1, key=lambda e: e["us_per_step"]), False) if k1 else None}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -398,23 +513,21 @@ def run_ours(a, rank, world, local_rank, dist):
 
     cpu = None
     if rank == 0 and world == 1 and a.cpu_baseline:
-        n_solve = a.n_steps
-        rate, csec = oracle_rate(a, n_solve, xyz, tets, det, p0)
-        cpu = {"value": rate / nsps, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle forward and one transposed solve of {n_solve} steps on the same mesh "
-                         f"(K=1, single-threaded SciPy, {csec:.1f} s); samples/s extrapolated by node-steps "
-                         f"({nsps:.3e} per sample)", "node_steps_per_s": rate}
+        cpu = cpu_baseline(a, data, nsps)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 state, f64 CGLS scalars", "data": "synthetic (seeded cube mesh, phantom, noise, draws)",
+            "dtype": "f32", "precision": "f32 state and stepping, f64 CGLS scalars, norms and iterate",
+            "data": "synthetic (seeded mesh, phantom, noise, device draws)",
             "config": cfg, "node_steps_per_s": world * K * a.steps * nsps / sec,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": prof["total_launches"],
             "gpu_launches_per_step": prof["total_launches"] / a.steps, "clocks": clk, "plain": plain,
             "batched_over_plain": (value / world) / plain["samples_per_s"] if plain else None,
-            "autotune": tune,
+            "variants": {"fwd": kname, "adj": aname,
+                         "fwd_us": bf.get("us_per_step"), "adj_us": ba.get("us_per_step"),
+                         "timed": sum(len(v) for v in tune.values())},
         }
         print(json.dumps(line), flush=True)
 

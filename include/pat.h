@@ -373,7 +373,7 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  * >= pat_workspace_bytes(mesh, 2, K); its CGLS state is overwritten), timed
  * with CUDA events on `stream`.  The fastest variant per direction is used by
  * every later call with this K on this mesh.  table (host, may be NULL)
- * receives up to 128 entries {direction 0 fwd / 1 adj, V, staged, packed, chunk,
+ * receives up to 256 entries {direction 0 fwd / 1 adj, V, staged, packed, chunk,
  * min_blocks (resident blocks per SM asked of the compiler), early (own values
  * loaded before the row walk), zorder (rows processed in Z-order of the node
  * coordinates), big_blocks (1024-thread blocks), prefetch (0: off; n: each block
@@ -407,7 +407,11 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
 /* Use the given variant (fields as in pat_tune_entry; packed 2 = the
  * tile-staged kernel, which stages each 32-row tile's source rows in shared
  * memory by bulk asynchronous copies; packed 3 = the fixed-width kernel, whose
- * rows' first 8 entries sit at fixed positions) for direction 0 (forward) or 1
+ * rows' first 8 entries sit at fixed positions; packed 5 = the 16-slot
+ * fixed-width kernel for meshes with rows wider than 8 entries (the full P1
+ * graph), persistent, V = 8 (or V = 1 for K = 1), gather_batch 4 or 8 source
+ * rows per round, early = each round's columns loaded with it, big_blocks =
+ * 1024-thread blocks, min_blocks 3 with rounds of 8) for direction 0 (forward) or 1
  * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not
  * exist for this K and precision.  Every variant gives bit-identical results. */
 pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* variant);

@@ -232,7 +232,7 @@ class Mesh:
         """Time every step-kernel variant for K samples and keep the fastest (pat_autotune).
         Returns the timing table as a list of dicts."""
         ws = self.workspace(2, K)
-        table = (_lib.TuneEntry * 128)()
+        table = (_lib.TuneEntry * 256)()
         n = C.c_int32()
         _lib.check(lib().pat_autotune(self._h, K, _ptr(ws), ws.numel(), int(n_probe), table, C.byref(n),
                                       _stream()))
@@ -242,7 +242,7 @@ class Mesh:
                  "prefetch": e.prefetch, "persistent": int(e.persistent), "pdl": bool(e.pdl),
                  "wide_loads": bool(e.wide_loads), "l2_hints": bool(e.l2_hints), "gather_batch": int(e.gather_batch),
                  "us_per_step": e.us_per_step}
-                for e in table[:min(n.value, 128)]]
+                for e in table[:min(n.value, 256)]]
 
     def select_variant(self, K, direction, V, packed=1, chunk=4, staged=False, min_blocks=1, early=False,
                        zorder=False, big_blocks=False, prefetch=0, persistent=False, pdl=False, wide_loads=False,

@@ -52,6 +52,10 @@ void free_device(DeviceMesh& m) {
                  (void**)&m.fwd.ell_col, (void**)&m.fwd.ell_hl, (void**)&m.fwd.ell_desc, (void**)&m.fwd.ovf_ptr,
                  (void**)&m.fwd.ovf_col, (void**)&m.fwd.ovf_hl, (void**)&m.adj3.ell_col, (void**)&m.adj3.ell_hl,
                  (void**)&m.adj3.ell_desc, (void**)&m.adj3.ovf_ptr, (void**)&m.adj3.ovf_col, (void**)&m.adj3.ovf_hl,
+                 (void**)&m.fwd.w16_col, (void**)&m.fwd.w16_hl, (void**)&m.fwd.w16_ovf_ptr,
+                 (void**)&m.fwd.w16_ovf_col, (void**)&m.fwd.w16_ovf_hl, (void**)&m.adj3.w16_col,
+                 (void**)&m.adj3.w16_hl, (void**)&m.adj3.w16_ovf_ptr, (void**)&m.adj3.w16_ovf_col,
+                 (void**)&m.adj3.w16_ovf_hl,
                  &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
                  &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
                  (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
@@ -236,12 +240,14 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
   return s;
 }
 
-// Fixed-width (8) copy of a three-level CSR for the ELL kernel (FP32 split only).
+// Fixed-width copy of a three-level CSR for the ELL kernels (FP32 split only):
+// W = 8 or 16 slots per row.  The descriptor word is written with the 8-slot
+// copy and shared by both.
 pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const std::vector<uint8_t>& ninj,
-                     DevCSR& d) {
+                     DevCSR& d, int W) {
   const int64_t N = (int64_t)R.ptr.size() - 1;
-  std::vector<uint32_t> col(N * 8), desc(N);
-  std::vector<float2> hl(N * 8);
+  std::vector<uint32_t> col(N * W), desc(N);
+  std::vector<float2> hl(N * W);
   std::vector<int32_t> optr(N + 1, 0);
   std::vector<uint32_t> ocol;
   std::vector<float2> ohl;
@@ -256,21 +262,21 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
       return PAT_EUNSUPPORTED;
     }
     desc[i] = (uint32_t)n | ((uint32_t)nb[i] << 8) | ((uint32_t)ninj[i] << 16);
-    // slots 0..7: the first stiffness / boundary entries, padded with the row
+    // slots 0..W-1: the first stiffness / boundary entries, padded with the row
     // itself and a zero coefficient; overflow: the remaining stiffness / boundary
     // entries, then every sensor (injection) entry.  The kernels then walk the
-    // 8 slots without a per-entry test.
+    // W slots without a per-entry test.
     const int nA = n - (int)ninj[i];
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < W; ++q) {
       if (q < nA) {
-        col[i * 8 + q] = R.col[e0 + q] & kIdxMask;
-        hl[i * 8 + q] = pair(R.val[e0 + q]);
+        col[i * W + q] = R.col[e0 + q] & kIdxMask;
+        hl[i * W + q] = pair(R.val[e0 + q]);
       } else {
-        col[i * 8 + q] = (uint32_t)i;  // padding reads the row itself with a zero coefficient
-        hl[i * 8 + q] = make_float2(0.0f, 0.0f);
+        col[i * W + q] = (uint32_t)i;  // padding reads the row itself with a zero coefficient
+        hl[i * W + q] = make_float2(0.0f, 0.0f);
       }
     }
-    for (int q = std::min(nA, 8); q < n; ++q) {
+    for (int q = std::min(nA, W); q < n; ++q) {
       ocol.push_back(R.col[e0 + q] & kIdxMask);
       ohl.push_back(pair(R.val[e0 + q]));
     }
@@ -280,13 +286,29 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
     ocol.push_back(0);
     ohl.push_back(make_float2(0.0f, 0.0f));
   }
-  pat_status s = upload(col, &d.ell_col);
-  if (!s) s = upload(hl, &d.ell_hl);
-  if (!s) s = upload(desc, &d.ell_desc);
-  if (!s) s = upload(optr, &d.ovf_ptr);
-  if (!s) s = upload(ocol, &d.ovf_col);
-  if (!s) s = upload(ohl, &d.ovf_hl);
+  pat_status s = PAT_OK;
+  if (W == 8) {
+    s = upload(col, &d.ell_col);
+    if (!s) s = upload(hl, &d.ell_hl);
+    if (!s) s = upload(desc, &d.ell_desc);
+    if (!s) s = upload(optr, &d.ovf_ptr);
+    if (!s) s = upload(ocol, &d.ovf_col);
+    if (!s) s = upload(ohl, &d.ovf_hl);
+  } else {
+    s = upload(col, &d.w16_col);
+    if (!s) s = upload(hl, &d.w16_hl);
+    if (!s) s = upload(optr, &d.w16_ovf_ptr);
+    if (!s) s = upload(ocol, &d.w16_ovf_col);
+    if (!s) s = upload(ohl, &d.w16_ovf_hl);
+  }
   return s;
+}
+
+// Most stiffness / boundary entries of any row of a three-level CSR.
+static int widest_row(const HostRows& R, const std::vector<uint8_t>& ninj) {
+  int w = 0;
+  for (size_t i = 0; i + 1 < R.ptr.size(); ++i) w = std::max(w, R.ptr[i + 1] - R.ptr[i] - (int)ninj[i]);
+  return w;
 }
 
 // Device copies of the operators from the host assembly (also used after
@@ -445,8 +467,11 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
   if (!s) s = build_tiles(m, F, A3, row_ninj, order, !m.host_only);
   if (!s && !m.host_only && prec == PAT_F32 && m.split) {
     std::vector<uint8_t> no_inj(N, 0);
-    s = build_ell(F, row_nb, no_inj, m.fwd);
-    if (!s) s = build_ell(A3, row_nb, row_ninj, m.adj3);
+    s = build_ell(F, row_nb, no_inj, m.fwd, 8);
+    if (!s) s = build_ell(A3, row_nb, row_ninj, m.adj3, 8);
+    // 16-slot copies where some row spills out of 8 slots (the full P1 graph)
+    if (!s && widest_row(F, no_inj) > 8) s = build_ell(F, row_nb, no_inj, m.fwd, kEllWide);
+    if (!s && widest_row(A3, row_ninj) > 8) s = build_ell(A3, row_nb, row_ninj, m.adj3, kEllWide);
   }
   if (!s && !m.host_only) {
     cudaStream_t cs = nullptr;
@@ -976,6 +1001,32 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   }
   if (bad_K(K, "pat_select_variant")) return PAT_EINVAL;
   const bool f32s = mesh->d.prec == PAT_F32 && mesh->d.split;
+  if (v->packed == 5) {  // 16-slot fixed-width rows
+    const bool ok = f32s && mesh->d.fwd.w16_col && K % 8 == 0 ? v->V == 8 : (f32s && mesh->d.fwd.w16_col && K == 1 && v->V == 1);
+    const int nb = v->gather_batch ? v->gather_batch : 4;
+    if (!ok || (nb != 4 && nb != 8) || (v->min_blocks != 1 && !(v->min_blocks == 3 && nb == 8))) {
+      set_error("pat_select_variant: 16-slot variant V=%d gather_batch=%d min_blocks=%d is not available for K=%d on "
+                "this mesh (it needs rows wider than 8 slots, FP32 split coefficients, V = 8 or K = V = 1)",
+                v->V, v->gather_batch, v->min_blocks, K);
+      return PAT_EINVAL;
+    }
+    TuneCfg c;
+    c.V = v->V;
+    c.packed = 5;
+    c.persist = 1;
+    c.pdl = v->pdl;
+    c.batch = nb;
+    c.early = v->early;
+    c.big = v->big_blocks && nb == 4;
+    c.minb = v->min_blocks;
+    std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
+    mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
+    std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);
+    for (auto& kv : mesh->d.graphs)
+      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+    mesh->d.graphs.clear();
+    return PAT_OK;
+  }
   const bool ok_v = (v->V == 1 || v->V == 2 || v->V == 4 || v->V == 8) && K % v->V == 0 &&
                     (mesh->d.prec == PAT_F32 || v->V <= 2);
   const bool ok_p = v->packed == 0 ? v->V != 8 && !(v->V == 1 && v->packed)

@@ -87,7 +87,16 @@ struct DevCSR {
   int32_t* ovf_ptr = nullptr;
   uint32_t* ovf_col = nullptr;
   float2* ovf_hl = nullptr;
+  // the same with 16 fixed slots per row (built when some row has more than 8
+  // stiffness / boundary entries: the full P1 graph, unstructured meshes)
+  uint32_t* w16_col = nullptr;
+  float2* w16_hl = nullptr;
+  int32_t* w16_ovf_ptr = nullptr;
+  uint32_t* w16_ovf_col = nullptr;
+  float2* w16_ovf_hl = nullptr;
 };
+
+constexpr int kEllWide = 16;  // slots of the wide fixed-width copy
 
 // Event-based loop timing and launch counting (pat_profile_*).
 struct Profiler {

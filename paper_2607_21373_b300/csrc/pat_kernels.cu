@@ -8,6 +8,7 @@
 
 #include "pat_kernels.cuh"
 #include "pat_tile.cuh"
+#include "pat_wide.cuh"
 #include "pat_solver.cuh"
 
 namespace pat {
@@ -350,6 +351,44 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
   kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
 }
 
+// 16-slot fixed-width launch (variant packed == 5): persistent grid-stride
+// blocks as a programmatic dependent of the previous step.  c.batch: source
+// rows per gather round (4 or 8); c.early: each round's columns loaded with
+// it; c.big: 1024-thread blocks; c.minb: 3 asks for 3 resident blocks of 256.
+template <bool ADJ>
+static void launch_wide(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
+  const int64_t n_chunks = (threads + 31) / 32;
+  int bs = 256;
+  void (*kern)(const Step3Args<float>, int64_t) = step3w_persist_kernel<ADJ, 4, false, 256, 4>;
+  if (c.big) {
+    bs = 1024;
+    kern = step3w_persist_kernel<ADJ, 4, true, 1024, 1>;
+  } else if (c.batch == 8) {
+    kern = c.minb == 3 ? step3w_persist_kernel<ADJ, 8, true, 256, 3>
+           : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2>
+                       : step3w_persist_kernel<ADJ, 8, false, 256, 2>;
+  } else if (c.early) {
+    kern = step3w_persist_kernel<ADJ, 4, true, 256, 4>;
+  }
+  const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
+  const int64_t grid =
+      std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + bs / 32 - 1) / (bs / 32)));
+  a.pf_rows = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)bs);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = c.pdl ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, kern, a, n_chunks) == cudaSuccess) return;
+  cudaGetLastError();  // attribute refused: plain launch
+  kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
+}
+
 template <typename T, int V, bool SPLIT, bool ADJ>
 static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, cudaStream_t st) {
   const int64_t blocks = (threads + 255) / 256;
@@ -358,6 +397,22 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
   if constexpr (sizeof(T) == 4 && SPLIT && V == 8) {
     if (c.packed == 2 && launch_tiled<ADJ>(m, a, st)) return;
     if (c.packed == 4 && launch_pipelined<ADJ>(m, a, st)) return;
+  }
+  if constexpr (sizeof(T) == 4 && SPLIT && (V == 1 || V == 8)) {
+    const DevCSR& E = ADJ ? m.adj3 : m.fwd;
+    if (c.packed == 5 && E.w16_col && (V == 8 || a.K == 1)) {  // 16-slot fixed-width rows
+      a.ell_col = E.w16_col;
+      a.ell_hl = E.w16_hl;
+      a.ell_desc = E.ell_desc;
+      a.ovf_ptr = E.w16_ovf_ptr;
+      a.ovf_col = E.w16_ovf_col;
+      a.ovf_hl = E.w16_ovf_hl;
+      if constexpr (V == 1)
+        step3w1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+      else
+        launch_wide<ADJ>(a, c, threads, st);
+      return;
+    }
   }
   if constexpr (sizeof(T) == 4 && SPLIT && V == 1) {
     const DevCSR& E = ADJ ? m.adj3 : m.fwd;
@@ -1506,6 +1561,8 @@ static pat_status probe_t(const DeviceMesh& m, int K, char* ws, int n_probe, int
 // one V a variant is written for, 0 = any).  The packed f32x2 CSR, generic,
 // tile-staged and fixed-width (ELL) families and their options; the persistent
 // fixed-width ones are the fastest on large meshes.
+constexpr int kTuneTableMax = 256;  // entries pat_autotune writes at most
+
 struct TuneVariant {
   int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v;
 };
@@ -1558,11 +1615,20 @@ static const TuneVariant kTuneVariants[] = {
     {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 2, 6, 0, 0},  // 44 persistent, PDL, batches of 2, >= 6 blocks/SM
     {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 0},  // 45 persistent, PDL, batches of 4, metadata per batch
     {3, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 5, 0, 0},  // 46 the same, >= 5 blocks/SM
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 0},  // 47 16 slots, persistent, PDL, rounds of 4
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 0},  // 48 16 slots, rounds of 4, columns per round
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 8, 1, 0, 0},  // 49 16 slots, rounds of 8 (2 blocks/SM)
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 8, 1, 1, 0},  // 50 16 slots, rounds of 8, columns per round
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 8, 3, 1, 0},  // 51 the same, 3 blocks/SM
+    {5, 0, 4, 0, 1, 0, 1, 1, 0, 0, 4, 1, 1, 0},  // 52 16 slots, 1024-thread blocks, rounds of 4
 };
 
 // Whether variant t exists for V samples per thread and K samples on mesh m.
 static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, int K) {
   if (t.only_v && V != t.only_v) return false;
+  if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1
+    return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (V == 8 || (V == 1 && K == 1 && t.batch == 4 &&
+                                                                         !t.early && !t.big));
   if ((t.batch || t.hint || t.wide || t.big) && V != 8) return false;
   if (t.persist == 3 && (V != 8 || K / V < 4)) return false;  // staged metadata: <= kStageRows rows per chunk
   if ((t.pf || t.persist) && V == 1) return false;
@@ -1624,7 +1690,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
         g_force_on = false;
         if (s) return s;
-        if (table && n < 128)
+        if (table && n < kTuneTableMax)
           table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
                                     t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
                                     t.wide, t.hint,  t.batch, (double)us};

@@ -1,0 +1,273 @@
+// Sixteen-slot fixed-width rows: the three-level step (Section 3, eq.
+// fully-discrete in the scaled three-level form) for meshes whose rows carry
+// more than 8 stiffness / boundary entries.  A P1 tetrahedral mesh couples a
+// node to every node it shares a tetrahedron with: 15 entries per interior row
+// of the Kuhn cube's full graph (its diagonal edges assemble to exact zeros,
+// which this layout keeps), about 15 on an unstructured mesh.  With 8 slots
+// the remaining entries went through the overflow list one dependent load at
+// a time; here the first 16 sit at fixed positions, so a row's columns and
+// coefficient pairs arrive in one round of broadcast loads and its source rows
+// in two to four rounds of independent gathers.
+//
+// Layout (per direction): col [N][16] uint32, hl [N][16] float2 (hi, lo), the
+// descriptor word of the 8-slot layout, and an overflow CSR holding the
+// stiffness / boundary entries beyond 16 followed by every sensor entry.  A
+// slot past the row's count reads the row itself with a zero coefficient.
+// Entries are visited in the row's CSR order, hi and lo products accumulated
+// separately, so every variant gives the same bits as the 8-slot and CSR
+// kernels.
+#pragma once
+
+#include "pat_tile.cuh"
+
+namespace pat {
+
+constexpr int kWide = 16;
+
+// Stiffness / boundary entry e (< the row's count eA) of a 16-slot row.
+__device__ __forceinline__ void wide_entry(const Step3Args<float>& A, int64_t row, int e, uint32_t* col,
+                                           float2* c) {
+  if (e < kWide) {
+    *col = A.ell_col[row * kWide + e];
+    *c = A.ell_hl[row * kWide + e];
+  } else {
+    const int64_t o = A.ovf_ptr[row] + (e - kWide);
+    *col = A.ovf_col[o];
+    *c = A.ovf_hl[o];
+  }
+}
+
+// Sensor entry j of a 16-slot row with eA stiffness / boundary entries.
+__device__ __forceinline__ void wide_inj(const Step3Args<float>& A, int64_t row, int j, int eA, uint32_t* col,
+                                         float2* c) {
+  const int64_t o = A.ovf_ptr[row] + max(eA - kWide, 0) + j;
+  *col = A.ovf_col[o];
+  *c = A.ovf_hl[o];
+}
+
+// Thread t of the row threads: 8 samples of one row (two runs of 4, as in the
+// 8-slot kernel), NB source rows gathered per round.  PB: each round's columns
+// and coefficient pairs are loaded with it (fewer live registers); otherwise
+// all 16 columns arrive up front and the coefficient pairs per round.
+template <bool ADJ, int NB, bool PB>
+__device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t) {
+  constexpr int V = 8, P = 4;
+  static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
+  const int KV = A.K / V;
+  if (t >= A.row_threads) {
+    gather_obs<V>(A, t - A.row_threads);
+    return;
+  }
+  const int64_t row = div_kv(t, KV);
+  const int kv = (int)(t - row * KV);
+  const int64_t hs = A.K / 2;
+  const int64_t base = (int64_t)kv * 4;
+  const int64_t off = row * A.K + base;
+  const uint32_t desc = A.ell_desc[row];
+  const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
+  const int eA = n - ni;
+  const uint32_t Ku = (uint32_t)A.K;
+  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col + row * kWide);
+  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl + row * kWide);
+  u64 acc[P], accl[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
+  if (A.x) {
+    const float* xk = A.x + base;
+    uint32_t cols[kWide];
+    if constexpr (!PB) {
+#pragma unroll
+      for (int q = 0; q < kWide / 4; ++q) {
+        const uint4 c = cp[q];
+        cols[4 * q] = c.x, cols[4 * q + 1] = c.y, cols[4 * q + 2] = c.z, cols[4 * q + 3] = c.w;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kWide / NB; ++h) {
+      if constexpr (PB) {
+#pragma unroll
+        for (int q = 0; q < NB / 4; ++q) {
+          const uint4 c = cp[h * (NB / 4) + q];
+          cols[NB * h + 4 * q] = c.x, cols[NB * h + 4 * q + 1] = c.y;
+          cols[NB * h + 4 * q + 2] = c.z, cols[NB * h + 4 * q + 3] = c.w;
+        }
+      }
+      u64 x[NB][P];
+#pragma unroll
+      for (int q = 0; q < NB; ++q) ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
+      float2 cf[NB];
+#pragma unroll
+      for (int q = 0; q < NB; q += 2) {
+        const float4 hq = hp[(NB * h + q) / 2];
+        cf[q] = make_float2(hq.x, hq.y);
+        cf[q + 1] = make_float2(hq.z, hq.w);
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        const u64 ch = dup2(cf[q].x), cl = dup2(cf[q].y);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          acc[p] = ffma2(ch, x[q][p], acc[p]);
+          accl[p] = ffma2(cl, x[q][p], accl[p]);
+        }
+      }
+    }
+    for (int e = kWide; e < eA; ++e) {  // overflow of long (boundary) rows
+      uint32_t col;
+      float2 c;
+      wide_entry(A, row, e, &col, &c);
+      u64 x[P];
+      ld_runs<V>(xk + (size_t)col * Ku, hs, x);
+      const u64 ch = dup2(c.x), cl = dup2(c.y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        acc[p] = ffma2(ch, x[p], acc[p]);
+        accl[p] = ffma2(cl, x[p], accl[p]);
+      }
+    }
+    if (nb > 0 && A.prev_mode != 2) {
+      // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
+      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + base;
+      for (int e = eA - nb; e < eA; ++e) {
+        uint32_t col;
+        float2 c;
+        wide_entry(A, row, e, &col, &c);
+        u64 x[P];
+        ld_runs<V>(pk + (size_t)col * Ku, hs, x);
+        const u64 ch = dup2(-c.x), cl = dup2(-c.y);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          acc[p] = ffma2(ch, x[p], acc[p]);
+          accl[p] = ffma2(cl, x[p], accl[p]);
+        }
+      }
+    }
+  }
+  float src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = 0; e < ni; ++e) {
+      uint32_t col;
+      float2 c;
+      wide_inj(A, row, e, eA, &col, &c);
+      const int64_t j = (int64_t)col;
+      if (A.ya) {
+        const Pack<float, V> y = ld_run_pack<V>(A.ya + j * A.K + base, hs);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+      }
+      if (A.yb) {
+        const Pack<float, V> y = ld_run_pack<V>(A.yb + j * A.K + base, hs);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+      }
+    }
+  }
+  Pack<float, V> xi, xpi, xo;
+  if (A.x) {
+    xi = ld_run_pack<V>(A.x + off, hs);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
+  }
+  if (A.prev_mode == 0) {
+    xpi = ld_run_pack<V>(A.xp + off, hs);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+    const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+    xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+    xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+  }
+  st_run_pack<V>(A.xn + off, hs, xo);
+}
+
+// Persistent grid-stride form (as the 8-slot persistent kernel): a resident
+// wave of blocks whose warps walk 32-thread chunks with the grid's stride,
+// launched as a programmatic dependent of the previous step.
+template <bool ADJ, int NB, bool PB, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int wpb = BS >> 5;
+  const int64_t S = (int64_t)gridDim.x * wpb;
+  for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S)
+    step3w_row<ADJ, NB, PB>(A, c * 32 + lane);
+}
+
+// One sample (K = 1): one thread per row, 16 fixed slots.
+template <bool ADJ>
+__global__ void __launch_bounds__(256) step3w1_kernel(const Step3Args<float> A) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= A.row_threads) {
+    gather_obs<1>(A, t - A.row_threads);
+    return;
+  }
+  const int64_t row = t;
+  const uint32_t desc = A.ell_desc[row];
+  const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
+  const int eA = n - ni;
+  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col + row * kWide);
+  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl + row * kWide);
+  float acc = 0.0f, accl = 0.0f;
+  if (A.x) {
+    uint32_t cols[kWide];
+#pragma unroll
+    for (int q = 0; q < kWide / 4; ++q) {
+      const uint4 c = cp[q];
+      cols[4 * q] = c.x, cols[4 * q + 1] = c.y, cols[4 * q + 2] = c.z, cols[4 * q + 3] = c.w;
+    }
+    float xv[kWide];
+#pragma unroll
+    for (int q = 0; q < kWide; ++q) xv[q] = A.x[cols[q]];
+#pragma unroll
+    for (int q = 0; q < kWide; q += 2) {
+      const float4 h = hp[q / 2];
+      acc = fmaf(h.x, xv[q], acc);
+      accl = fmaf(h.y, xv[q], accl);
+      acc = fmaf(h.z, xv[q + 1], acc);
+      accl = fmaf(h.w, xv[q + 1], accl);
+    }
+    for (int e = kWide; e < eA; ++e) {
+      uint32_t col;
+      float2 c;
+      wide_entry(A, row, e, &col, &c);
+      const float x = A.x[col];
+      acc = fmaf(c.x, x, acc);
+      accl = fmaf(c.y, x, accl);
+    }
+    if (nb > 0 && A.prev_mode != 2) {
+      const float* pk = A.prev_mode == 0 ? A.xp : A.x;
+      for (int e = eA - nb; e < eA; ++e) {
+        uint32_t col;
+        float2 c;
+        wide_entry(A, row, e, &col, &c);
+        const float x = pk[col];
+        acc = fmaf(-c.x, x, acc);
+        accl = fmaf(-c.y, x, accl);
+      }
+    }
+  }
+  float src = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = 0; e < ni; ++e) {
+      uint32_t col;
+      float2 c;
+      wide_inj(A, row, e, eA, &col, &c);
+      if (A.ya) src = fmaf(c.x, A.ya[col], src);
+      if (A.yb) src = fmaf(c.x, A.yb[col], src);
+    }
+  }
+  const float xi = A.x ? A.x[row] : 0.0f;
+  const float xpi = A.prev_mode == 0 ? A.xp[row] : (A.prev_mode == 1 ? xi : 0.0f);
+  const float w = xi - xpi;
+  A.xn[row] = xi + (w - (acc + accl) + A.inj_scale * src);
+}
+
+}  // namespace pat

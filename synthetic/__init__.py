@@ -59,6 +59,30 @@ def cube_mesh(n: int):
     return xyz, tets.reshape(-1, 4).astype(np.int32)
 
 
+def jittered_cube_mesh(n: int, amp: float, seed: int):
+    """cube_mesh(n) with every interior node moved by amp * h * U[-1, 1] per
+    coordinate (h = 1 / n; seeded), boundary nodes left on the lattice so the
+    faces stay planar.  The connectivity is the Kuhn one, but no stiffness entry
+    cancels any more: an interior row couples its node to all 14 graph
+    neighbours, as on the paper's unstructured meshes (Section 6.4).  amp <= 0.15
+    keeps every tetrahedron's orientation (checked).  Returns (xyz, tets)."""
+    if not 0.0 <= amp <= 0.15:
+        raise ValueError("amp must be in [0, 0.15]")
+    xyz, tets = cube_mesh(n)
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-1.0, 1.0, size=xyz.shape) * (amp / n)
+    interior = np.all((xyz > 0.5 / n) & (xyz < 1.0 - 0.5 / n), axis=1)
+    def orient(p):
+        X = p[tets]
+        return np.einsum("ei,ei->e", np.cross(X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]), X[:, 3] - X[:, 0])
+
+    before = orient(xyz)
+    xyz = xyz + d * interior[:, None]
+    if not np.all(orient(xyz) * before > 0.0):
+        raise ValueError("jitter inverted a tetrahedron")
+    return xyz, tets
+
+
 def sphere_mesh(n: int, radius: float):
     """A ball of the given radius carved from the Kuhn mesh of [-radius, radius]^3
     with n cells per side: the tetrahedra whose centroid lies inside the ball,

@@ -1,0 +1,139 @@
+"""The full P1 graph and unstructured-like rows on the GPU.
+
+A P1 mesh couples each node to every node of its tetrahedra: 15 entries per
+interior row.  On the regular Kuhn lattice 8 of them assemble to exactly 0.0
+(the 7-point stencil remains); kept (PAT_MESH_KEEP_ZEROS) they are the rows an
+unstructured mesh has, and moving the interior nodes (the jittered cube) makes
+every one of them nonzero.  Such rows overflow the 8-slot fixed-width layout,
+so the library builds a 16-slot copy; its kernels must give the same bits as
+every other variant (same entries, same order, same arithmetic) and match the
+FP64 oracle at the FP32 tolerances (1e-5 relative L2, dot test 1e-6).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import fem, wave
+from problems import as_precision, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+WIDE_VARIANTS = [dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4),
+                 dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True),
+                 dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8),
+                 dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8, early=True),
+                 dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8, early=True, min_blocks=3),
+                 dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, big_blocks=True),
+                 dict(V=8, packed=5, persistent=1, pdl=False, gather_batch=4)]
+OTHER_VARIANTS = [dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1), dict(V=8, packed=1, chunk=2),
+                  dict(V=4, packed=0)]
+
+
+def jitter_problem(n, n_obs, n_steps, seed):
+    xyz, tets = S.jittered_cube_mesh(n, 0.15, seed)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, seed)
+    return xyz, tets, det, fem.build(xyz, tets, det, n), 0.3 / n
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("mesh_kind", ["cube_full_graph", "jitter"])
+@pytest.mark.parametrize("K", [8, 64])
+def test_wide_variants_are_bit_identical(mesh_kind, K):
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
+    n, n_obs, nt = 10, 48, 60
+    if mesh_kind == "jitter":
+        xyz, tets = S.jittered_cube_mesh(n, 0.15, 11)
+    else:
+        xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, 6)
+    m = Mesh(xyz, tets, det, 0.3 / n, nt, precision="f32", flags=MESH_KEEP_ZEROS)
+    assert m.info["nnz_K"] == m.info["nnz_K_graph"]
+    p0 = dev(S.standard_normal((len(xyz), K), 3))
+    yh = dev(S.standard_normal((nt, n_obs, K), 4))
+    Y0, g0 = m.forward(p0).clone(), m.adjoint(yh).clone()
+    for v in WIDE_VARIANTS + OTHER_VARIANTS:
+        for d in ("fwd", "adj"):
+            m.select_variant(K, d, **v)
+        assert torch.equal(m.forward(p0), Y0), v
+        assert torch.equal(m.adjoint(yh), g0), v
+
+
+def test_wide_single_sample_kernel_is_bit_identical():
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
+    n, n_obs, nt = 10, 48, 60
+    xyz, tets = S.jittered_cube_mesh(n, 0.15, 12)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, 7)
+    m = Mesh(xyz, tets, det, 0.3 / n, nt, precision="f32", flags=MESH_KEEP_ZEROS)
+    p0 = dev(S.standard_normal(len(xyz), 5))
+    yh = dev(S.standard_normal((nt, n_obs), 6))
+    Y0, g0 = m.forward(p0).clone(), m.adjoint(yh).clone()
+    for v in (dict(V=1, packed=5, gather_batch=4), dict(V=1, packed=3), dict(V=1, packed=0)):
+        for d in ("fwd", "adj"):
+            m.select_variant(1, d, **v)
+        assert torch.equal(m.forward(p0), Y0), v
+        assert torch.equal(m.adjoint(yh), g0), v
+
+
+def test_wide_variant_refused_on_pruned_lattice():
+    """The pruned Kuhn lattice has no row wider than 8 slots: no 16-slot copy."""
+    from paper_2607_21373_b300 import Mesh, PatError
+    xyz, tets = S.cube_mesh(6)
+    m = Mesh(xyz, tets, S.detector_points(8, S.ALL_FACES, 1), 0.05, 10, precision="f32")
+    with pytest.raises(PatError):
+        m.select_variant(8, "fwd", **WIDE_VARIANTS[0])
+
+
+@pytest.mark.parametrize("K", [1, 16])
+def test_jittered_mesh_matches_oracle(K):
+    """Forward, transpose and dot test on a jittered 12^3 mesh (every graph entry
+    nonzero) with the 16-slot kernels, against the FP64 oracle."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
+    n, n_obs, nt = 12, 40, 150
+    xyz, tets, det, ops, dt = jitter_problem(n, n_obs, nt, 21)
+    m = Mesh(xyz, tets, det, dt, nt, precision="f32", flags=MESH_KEEP_ZEROS)
+    v = dict(V=1, packed=5, gather_batch=4) if K == 1 else WIDE_VARIANTS[1]
+    for d in ("fwd", "adj"):
+        m.select_variant(K, d, **v)
+    shape = (len(xyz),) if K == 1 else (len(xyz), K)
+    p0 = as_precision(S.standard_normal(shape, 50 + K), "f32")
+    yh = as_precision(S.standard_normal((nt, n_obs) + shape[1:], 51 + K), "f32")
+    Y = m.forward(dev(p0))
+    g = m.adjoint(dev(yh))
+    assert rel_l2(Y.cpu().numpy(), wave.forward(ops, p0, dt, nt)) < 1e-5
+    assert rel_l2(g.cpu().numpy(), wave.adjoint(ops, yh, dt)) < 1e-5
+    lhs = float((Y.double() * dev(yh).double()).sum())
+    rhs = float((dev(p0).double() * g.double()).sum())
+    scale = float(Y.double().norm() * dev(yh).double().norm())
+    assert abs(lhs - rhs) <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("mesh_kind", ["cube_full_graph", "jitter"])
+def test_full_size_wide_forward_and_transpose_sampled_columns(mesh_kind):
+    """The benchmark's size and launch configuration on the full graph: 205,379
+    nodes, 1000 steps, 1024 sensors, K = 64, kernels chosen by the autotuner as
+    bench.py does; forward and transposed solves against single-column oracle
+    solves on sampled columns."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
+    n, n_obs, nt, seed = 58, 1024, 1000, 1003
+    if mesh_kind == "jitter":
+        xyz, tets = S.jittered_cube_mesh(n, 0.15, seed + 200)
+    else:
+        xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, seed)
+    ops = fem.build(xyz, tets, det, n)
+    dt = 0.3 / n
+    m = Mesh(xyz, tets, det, dt, nt, precision="f32", flags=MESH_KEEP_ZEROS)
+    m.autotune(64, n_probe=10)
+    p = S.phantom(xyz, "blobs20+vessels", seed + 100, n)
+    rng = np.random.default_rng(1)
+    p0 = as_precision(p[:, None] * rng.uniform(0.5, 1.5, size=(1, 64)), "f32")
+    Y = m.forward(dev(p0))
+    yh = as_precision(S.standard_normal((nt, n_obs, 64), 32), "f32")
+    g = m.adjoint(dev(yh))
+    for k in (0, 63):
+        assert rel_l2(Y[..., k].cpu().numpy(), wave.forward(ops, p0[:, k], dt, nt)) < 1e-5
+    assert rel_l2(g[:, 7].cpu().numpy(), wave.adjoint(ops, yh[..., 7], dt)) < 1e-5

@@ -93,8 +93,6 @@ def test_single_coefficient_storage_is_less_accurate():
 
 
 def test_full_size_batched_forward_sampled_columns():
-    """205,379 nodes, 1000 steps, 1024 sensors, K = 64 in one launch sequence:
-    two of the 64 columns against single-column oracle runs."""
     """The benchmark's workload and launch configuration: 205,379 nodes, 1000 steps,
     1024 sensors, K = 64, step kernels chosen by the autotuner as bench.py does;
     forward and transposed solves against the oracle on sampled columns."""
