@@ -330,8 +330,23 @@ pat_status pat_whitened_misfit(const pat_mesh* mesh, const double* x, const void
                                int32_t K, double* out, void* workspace, size_t workspace_bytes,
                                void* stream);
 
-/* Synchronise `stream` and read the workspace's status word (PAT_OK, PAT_ENUMERIC ...). */
+/* Synchronise `stream` and read the workspace's status word (PAT_OK, PAT_ENUMERIC ...),
+ * then the mesh's time-step status word: PAT_ETIMEOUT when a tile-staged step
+ * kernel gave up waiting for its shared-memory copies (the rows of that tile
+ * were then not updated).  The mesh's word is cleared once reported. */
 pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* workspace, void* stream);
+
+/*
+ * Failure-detection hook: the number of SM clock cycles a block of the
+ * tile-staged step kernels (variants packed 2 and 4) waits for its bulk copies
+ * before it records PAT_ETIMEOUT in the mesh's status word and gives up on its
+ * tile (it still waits for the copies in flight to land before it exits, so
+ * no copy outlives its shared memory).  cycles <= 0 restores the default of
+ * 4e9 cycles (about two seconds).  A tiny budget makes every wait run out: a
+ * test of the timeout path that neither hangs nor faults the GPU.  Drops the
+ * mesh's captured CUDA graphs (they hold the previous budget).
+ */
+pat_status pat_mesh_set_wait_cycles(pat_mesh* mesh, int64_t cycles);
 
 /*
  * Counter-based N(0,1) draws used when pat_cgls_begin / pat_rto_sample get NULL

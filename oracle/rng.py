@@ -33,10 +33,12 @@ def splitmix64_output(seed, i):
         return z ^ (z >> np.uint64(31))
 
 
-def normals(seed, stream, n_elem, K):
-    """Draws for elements e < n_elem and samples k < K, shape (n_elem, K)."""
+def normals(seed, stream, n_elem, K, samples=None):
+    """Draws for elements e < n_elem and samples k < K, shape (n_elem, K); or,
+    with ``samples`` (a list of sample indices), only those columns."""
     e = np.arange(n_elem, dtype=np.uint64)[:, None]
-    k = np.arange(K, dtype=np.uint64)[None, :]
+    ks = np.arange(K) if samples is None else np.asarray(samples)
+    k = ks.astype(np.uint64)[None, :]
     c = (((k << np.uint64(1)) | np.uint64(stream)) << np.uint64(40)) | e
     with np.errstate(over="ignore"):
         h1 = splitmix64_output(seed, np.uint64(2) * c + np.uint64(1))

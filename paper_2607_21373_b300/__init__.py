@@ -263,6 +263,11 @@ class Mesh:
         _lib.check(lib().pat_profile_read(self._h, C.byref(p)))
         return {k: getattr(p, k) for k, _ in _lib.Profile._fields_}
 
+    def set_wait_cycles(self, cycles):
+        """Copy-wait budget of the tile-staged step kernels in SM cycles (<= 0: the
+        default); a tiny budget exercises the PAT_ETIMEOUT path (pat_mesh_set_wait_cycles)."""
+        _lib.check(lib().pat_mesh_set_wait_cycles(self._h, int(cycles)))
+
     def status(self, K):
         ws = self.workspace(2, K)
         _lib.check(lib().pat_rto_status(self._h, K, _ptr(ws), _stream()))

@@ -83,6 +83,7 @@ SIGNATURES = {
     "pat_cgls_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
     "pat_lsqr_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
     "pat_rto_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pat_mesh_set_wait_cycles": (C.c_int, [C.c_void_p, C.c_int64]),
     "pat_draw_normals": (C.c_int, [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(TuneEntry),
                                C.POINTER(C.c_int32), C.c_void_p]),

@@ -974,9 +974,27 @@ pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* ws, void*
     if (s) return s;
     if (word != 0) {
       set_error("a time-step kernel gave up waiting for its shared-memory copies (status %d)", word);
+      // reported once: clear the word so that later calls on the mesh start clean
+      s = cuda_check(cudaMemset(mesh->d.d_status, 0, 4), "pat_rto_status clear");
+      if (s) return s;
       return (pat_status)word;
     }
   }
+  return PAT_OK;
+}
+
+pat_status pat_mesh_set_wait_cycles(pat_mesh* mesh, int64_t cycles) {
+  clear_error();
+  if (!mesh) {
+    set_error("pat_mesh_set_wait_cycles: NULL mesh");
+    return PAT_EINVAL;
+  }
+  mesh->d.tile_wait_cycles = cycles > 0 ? (long long)cycles : 4000000000ll;
+  // captured solves carry the previous budget in their kernel arguments
+  std::lock_guard<std::mutex> lock(mesh->d.graph_mutex);
+  for (auto& kv : mesh->d.graphs)
+    if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+  mesh->d.graphs.clear();
   return PAT_OK;
 }
 

@@ -148,6 +148,7 @@ struct DeviceMesh {
           *tile_range_slot = nullptr, *tile_slots = nullptr;
   uint16_t *tile_slot_fwd = nullptr, *tile_slot_adj = nullptr;
   int32_t* d_status = nullptr;  // device status word of the tile kernels (PAT_ETIMEOUT)
+  long long tile_wait_cycles = 4000000000ll;  // copy-wait budget of the tile kernels (pat_mesh_set_wait_cycles)
   int32_t* row_order = nullptr;  // [N] rows sorted by the Z-order (Morton) key of their coordinates
   int32_t* etets = nullptr;  // [E][4] element vertices (c^2 gradient)
   void* eK0 = nullptr;       // [E][10] real: upper triangle of V grad(l_a).grad(l_b) (c = 1)

@@ -240,7 +240,7 @@ static bool launch_tiled(const DeviceMesh& m, const Step3Args<float>& a, cudaStr
     cudaFuncSetAttribute(step3t_kernel<8, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   });
   TileArgs Tl{m.tile_range_ptr, m.tile_range_src, m.tile_range_cnt, m.tile_range_slot, m.tile_slots,
-              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles, m.row_order};
+              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles, m.row_order, m.tile_wait_cycles};
   Step3Args<float> A = a;
   A.hl = ADJ ? m.adj3.hl : m.fwd.hl;
   const int bdim = kTileRows * (a.K / 8);
@@ -271,7 +271,7 @@ static bool launch_pipelined(const DeviceMesh& m, const Step3Args<float>& a, cud
     return false;
   }
   TileArgs Tl{m.tile_range_ptr, m.tile_range_src, m.tile_range_cnt, m.tile_range_slot, m.tile_slots,
-              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles, m.row_order};
+              ADJ ? m.tile_slot_adj : m.tile_slot_fwd, m.d_status, m.n_tiles, m.row_order, m.tile_wait_cycles};
   Step3Args<float> A = a;
   A.hl = ADJ ? m.adj3.hl : m.fwd.hl;
   const int blocks = std::min(m.n_tiles, per_sm * sm_count());

@@ -31,7 +31,14 @@ struct TileArgs {
   int32_t* status;                        // device status word (PAT_ETIMEOUT on a stuck copy)
   int32_t n_tiles;                        // blocks beyond the tiles gather the sensor observations
   const int32_t* __restrict__ order;      // rows of tile t: order[t*R .. t*R+R)
+  long long wait_cycles;                  // SM cycles a block waits for its copies before it reports
+                                          // PAT_ETIMEOUT and gives up on the tile
 };
+
+// Cycles a block that gave up still waits for its copies in flight to land
+// before it exits (its shared memory must outlive them): about two seconds at
+// 2 GHz, far beyond any copy.
+constexpr long long kDrainWait = 4000000000ll;
 
 // observation of the input state by thread g of the gather blocks
 template <int V>
@@ -132,11 +139,9 @@ __global__ void __launch_bounds__(1024) step3t_kernel(const Step3Args<float> A, 
   // the node's previous value comes from global memory while the copies run
   Pack<float, V> xpi;
   if (active && A.prev_mode == 0) xpi = ld<float, V>(A.xp + off);
-  // about two seconds at 2 GHz: far beyond any copy, short enough to report a stuck one
-  constexpr long long kWait = 4000000000ll;
-  if (!mbar_wait(bar_s, kWait)) {
+  if (!mbar_wait(bar_s, Tl.wait_cycles)) {
     atomicExch(Tl.status, (int)PAT_ETIMEOUT);
-    mbar_wait(bar_s, kWait);  // let the copies land before the block's memory is released
+    mbar_wait(bar_s, kDrainWait);  // let the copies land before the block's memory is released
     return;
   }
   if (!active) return;
@@ -805,7 +810,6 @@ __global__ void __launch_bounds__(512) step3p_kernel(const Step3Args<float> A, c
   const uint32_t bar_s[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
   const int KV = A.K / V;
   const size_t row_bytes = (size_t)A.K * 4;
-  constexpr long long kWait = 4000000000ll;  // about two seconds at 2 GHz
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s[0]) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s[1]) : "memory");
@@ -838,12 +842,12 @@ __global__ void __launch_bounds__(512) step3p_kernel(const Step3Args<float> A, c
     const int b = it & 1;
     const int next = tile + gridDim.x;
     if (next < Tl.n_tiles && threadIdx.x < 32) issue(next, b ^ 1);
-    const bool ok = mbar_wait_parity(bar_s[b], (uint32_t)((it >> 1) & 1), kWait);
+    const bool ok = mbar_wait_parity(bar_s[b], (uint32_t)((it >> 1) & 1), Tl.wait_cycles);
     if (__syncthreads_or(!ok)) {
-      // a copy never completed: report, let in-flight copies land, stop
+      // a copy did not complete in time: report, let in-flight copies land, stop
       if (threadIdx.x == 0) atomicExch(Tl.status, (int)PAT_ETIMEOUT);
-      mbar_wait_parity(bar_s[b], (uint32_t)((it >> 1) & 1), kWait);
-      if (next < Tl.n_tiles) mbar_wait_parity(bar_s[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWait);
+      mbar_wait_parity(bar_s[b], (uint32_t)((it >> 1) & 1), kDrainWait);
+      if (next < Tl.n_tiles) mbar_wait_parity(bar_s[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kDrainWait);
       return;
     }
     const int64_t r0 = (int64_t)tile * kTileRows;

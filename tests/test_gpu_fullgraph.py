@@ -78,13 +78,19 @@ def test_wide_single_sample_kernel_is_bit_identical():
         assert torch.equal(m.adjoint(yh), g0), v
 
 
-def test_wide_variant_refused_on_pruned_lattice():
-    """The pruned Kuhn lattice has no row wider than 8 slots: no 16-slot copy."""
-    from paper_2607_21373_b300 import Mesh, PatError
+def test_wide_variant_refused_where_it_does_not_exist():
+    """16-slot rows exist for FP32 split-coefficient meshes only, with 8 samples
+    per thread (K a multiple of 8) or one thread per row (K = 1)."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh, PatError
     xyz, tets = S.cube_mesh(6)
-    m = Mesh(xyz, tets, S.detector_points(8, S.ALL_FACES, 1), 0.05, 10, precision="f32")
+    det = S.detector_points(8, S.ALL_FACES, 1)
+    m64 = Mesh(xyz, tets, det, 0.05, 10, precision="f64", flags=MESH_KEEP_ZEROS)
     with pytest.raises(PatError):
-        m.select_variant(8, "fwd", **WIDE_VARIANTS[0])
+        m64.select_variant(8, "fwd", **WIDE_VARIANTS[0])
+    m32 = Mesh(xyz, tets, det, 0.05, 10, precision="f32", flags=MESH_KEEP_ZEROS)
+    with pytest.raises(PatError):
+        m32.select_variant(4, "fwd", **WIDE_VARIANTS[0])
+    m32.select_variant(8, "fwd", **WIDE_VARIANTS[0])
 
 
 @pytest.mark.parametrize("K", [1, 16])
