@@ -212,7 +212,11 @@ pat_status pat_adjoint(const pat_mesh* mesh, const void* Yhat, int32_t K, void* 
  *   xi      device [N][K] real, N(0,1) prior draws, or NULL (drawn from `seed`).
  *   samples device [N][K] double or NULL; mean, stdev device [N] double or NULL
  *           (stdev needs K >= 2; estimator of eq. ergodic with 1/(K-1)).
- *   resid   device [n_iter+1][K] double or NULL: ||r_j||^2 of each iterate.
+ *   resid   device [n_iter+1][K][2] double or NULL: the squared norms of the
+ *           data block and the prior block of the residual r_j = b - A x_j of
+ *           each iterate, ||r_d||^2 and ||r_p||^2 (the data misfit and prior
+ *           terms of the convergence diagnostics of Section 6.1; their sum is
+ *           ||r_j||^2).
  *   workspace >= pat_workspace_bytes(mesh, 2, K).
  * Each wave solve of the CGLS loop is captured once into a CUDA graph (per
  * workspace, K and sigma, cached on the mesh) and replayed, unless the stream
@@ -257,6 +261,8 @@ pat_status pat_rto_sample_multi(int32_t n_jobs, const pat_rto_job* jobs, int32_t
  * held in the workspace:
  *   pat_cgls_begin    r = b, s = A^T r, d = s, gamma = ||s||^2, x = 0;
  *   pat_cgls_iterate  n_iter CGLS iterations (q = A d, alpha, x, r, s, beta, d);
+ *                     resid (device [n_iter][K][2] double, or NULL) receives
+ *                     the data and prior blocks of ||r||^2 of each new iterate;
  *   pat_cgls_finish   copy x to samples and form mean / stdev.
  * pat_cgls_layout returns byte offsets into the workspace of the state fields:
  *   off[0] x [N][K] double, off[1] d [N][K] real, off[2] r_d [N_T][N_obs][K] real,
@@ -347,6 +353,35 @@ pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* workspace
  * mesh's captured CUDA graphs (they hold the previous budget).
  */
 pat_status pat_mesh_set_wait_cycles(pat_mesh* mesh, int64_t cycles);
+
+/*
+ * Sample parallelism across processes (Section 6.4 runs one sample per process;
+ * the paper has no multi-GPU code).  Each process holds a mesh and solves its
+ * own K samples; the only exchange is the pointwise posterior statistics of
+ * eq. ergodic over all processes' samples, in two passes of sums that the
+ * caller adds up across processes (e.g. an NCCL all-reduce of the [N] buffers):
+ *
+ *   pat_mesh_set_first_sample  library-drawn perturbations (eta, xi NULL) of
+ *       sample k of later calls on this mesh use the draw index
+ *       first_sample + k (default 0): with first_sample = rank * K the
+ *       processes' draws are those of one K_total-sample run, disjoint by
+ *       construction.  0 <= first_sample <= 2^23 - 1024, else PAT_EINVAL.
+ *   pat_rto_moments  from the iterate x of the last CGLS / LSQR solve held in
+ *       `workspace` (K samples): center NULL -> out[i] = sum_k x_ik; center
+ *       (device [N] double) -> out[i] = sum_k (x_ik - center_i)^2.  out device
+ *       [N] double.  Workspace as pat_rto_sample's.
+ *   pat_moments_finish  in place on v (device [n_nodes] double), n_samples
+ *       the total over all processes: which 0: v /= n_samples (the mean from
+ *       the summed first pass); which 1: v = sqrt(v / (n_samples - 1)) (the
+ *       std from the summed second pass, centred on that mean).
+ *
+ * Order: moments (center NULL) -> sum across processes -> finish 0 = mean ->
+ * moments (center = mean) -> sum across processes -> finish 1 = std.
+ */
+pat_status pat_mesh_set_first_sample(pat_mesh* mesh, int64_t first_sample);
+pat_status pat_rto_moments(const pat_mesh* mesh, int32_t K, const double* center, double* out, void* workspace,
+                           size_t workspace_bytes, void* stream);
+pat_status pat_moments_finish(int64_t n_nodes, double n_samples, int32_t which, double* v, void* stream);
 
 /*
  * Counter-based N(0,1) draws used when pat_cgls_begin / pat_rto_sample get NULL

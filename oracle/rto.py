@@ -73,21 +73,27 @@ def cgls_step(apply_A, apply_AT, st, batched):
     return {"x": x, "r": r, "s": s, "d": s + beta * st["d"], "gamma": gamma}
 
 
-def cgls(apply_A, apply_AT, b, n_iter, x_shape, batched):
+def cgls(apply_A, apply_AT, b, n_iter, x_shape, batched, block_hist=False):
     """CGLS for min ||A x - b||_2 from x = 0, exactly n_iter iterations.
 
     Textbook form (Hestenes-Stiefel CG on the normal equations, as in Hansen,
     Rank-Deficient and Discrete Ill-Posed Problems, 1998).  ``b`` and ``q`` are
     tuples of blocks; with ``batched`` every array carries K independent
     problems in its last axis and the scalars are per column.
-    Returns x and the history of ||r||^2 (one entry per iterate).
+    Returns x and the history of ||r||^2 (one entry per iterate); with
+    ``block_hist`` the squared norm of each block of r separately, stacked in
+    a last axis (the data misfit and prior terms of the Section 6.1 diagnostics).
     """
+    def record(r):
+        return [_sq((u,), batched) for u in r] if block_hist else _sq(r, batched)
+
     st = cgls_begin(apply_AT, b, x_shape, batched)
-    hist = [_sq(st["r"], batched)]
+    hist = [record(st["r"])]
     for _ in range(n_iter):
         st = cgls_step(apply_A, apply_AT, st, batched)
-        hist.append(_sq(st["r"], batched))
-    return st["x"], np.array(hist)
+        hist.append(record(st["r"]))
+    h = np.array(hist)
+    return st["x"], (np.moveaxis(h, 1, -1) if block_hist and batched else h)
 
 
 def _div(a, b):
@@ -176,15 +182,16 @@ def rto_rhs(ops, y_obs, sigma, eta, xi):
     return ((yo + sigma * eta) / sigma, np.sqrt(mlc) * p_prior)
 
 
-def rto_samples(ops, dt, n_steps, y_obs, sigma, eta, xi, n_iter):
+def rto_samples(ops, dt, n_steps, y_obs, sigma, eta, xi, n_iter, block_hist=False):
     """RTO posterior samples (Algorithm 1) for K draws stacked in the last axis.
 
-    Returns samples (N, K) and the CGLS residual history (n_iter+1, K).
+    Returns samples (N, K) and the CGLS residual history (n_iter+1, K), or with
+    ``block_hist`` its data and prior blocks (n_iter+1, K, 2).
     """
     apply_A, apply_AT = extended_operator(ops, dt, n_steps, sigma)
     b = rto_rhs(ops, y_obs, sigma, eta, xi)
     batched = np.ndim(xi) == 2
-    return cgls(apply_A, apply_AT, b, n_iter, np.shape(xi), batched)
+    return cgls(apply_A, apply_AT, b, n_iter, np.shape(xi), batched, block_hist)
 
 
 def rto_samples_lsqr(ops, dt, n_steps, y_obs, sigma, eta, xi, n_iter):

@@ -160,7 +160,9 @@ class Mesh:
     def rto_sample(self, y_obs, sigma, K, n_iter, eta=None, xi=None, seed=0, samples=True, resid=False,
                    mean=True, stdev=None, solver="cgls"):
         """K RTO posterior samples by n_iter CGLS (pat_rto_sample) or LSQR
-        (pat_rto_sample_lsqr) iterations."""
+        (pat_rto_sample_lsqr) iterations.  With resid: CGLS gives the data and
+        prior blocks of ||r_j||^2 per iterate, shape (n_iter + 1, K, 2); LSQR gives
+        phibar_j^2 = ||r_j||^2, shape (n_iter + 1, K)."""
         if solver not in ("cgls", "lsqr"):
             raise ValueError("solver must be 'cgls' or 'lsqr'")
         self._check_field(y_obs, (self.n_steps, self.n_obs), "y_obs")
@@ -174,7 +176,8 @@ class Mesh:
         out["samples"] = torch.empty((self.N, K), dtype=torch.float64, device=dev) if samples else None
         out["mean"] = torch.empty(self.N, dtype=torch.float64, device=dev) if mean else None
         out["std"] = torch.empty(self.N, dtype=torch.float64, device=dev) if stdev else None
-        out["resid"] = torch.empty((n_iter + 1, K), dtype=torch.float64, device=dev) if resid else None
+        rshape = (n_iter + 1, K, 2) if solver == "cgls" else (n_iter + 1, K)
+        out["resid"] = torch.empty(rshape, dtype=torch.float64, device=dev) if resid else None
         ws = self.workspace(2, K)
         fn = lib().pat_rto_sample if solver == "cgls" else lib().pat_rto_sample_lsqr
         _lib.check(fn(
@@ -267,6 +270,24 @@ class Mesh:
         """Copy-wait budget of the tile-staged step kernels in SM cycles (<= 0: the
         default); a tiny budget exercises the PAT_ETIMEOUT path (pat_mesh_set_wait_cycles)."""
         _lib.check(lib().pat_mesh_set_wait_cycles(self._h, int(cycles)))
+
+    def set_first_sample(self, first):
+        """Library-drawn perturbations of sample k use the draw index first + k
+        (pat_mesh_set_first_sample): rank r of a sample-parallel run sets r * K."""
+        _lib.check(lib().pat_mesh_set_first_sample(self._h, int(first)))
+
+    def rto_moments(self, K, center=None):
+        """Sum over the K samples of the last solve held in the workspace of x
+        (center None) or of (x - center)^2, [N] float64 (pat_rto_moments)."""
+        out = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        ws = self.workspace(2, K)
+        _lib.check(lib().pat_rto_moments(self._h, K, _ptr(center), _ptr(out), _ptr(ws), ws.numel(), _stream()))
+        return out
+
+    def moments_finish(self, v, n_samples, which):
+        """In place: which 0, v / n (mean); which 1, sqrt(v / (n - 1)) (std) (pat_moments_finish)."""
+        _lib.check(lib().pat_moments_finish(v.numel(), float(n_samples), int(which), _ptr(v), _stream()))
+        return v
 
     def status(self, K):
         ws = self.workspace(2, K)

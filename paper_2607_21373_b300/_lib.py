@@ -84,6 +84,10 @@ SIGNATURES = {
     "pat_lsqr_layout": (C.c_int, [C.c_void_p, C.c_int32, c_size_p]),
     "pat_rto_status": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_mesh_set_wait_cycles": (C.c_int, [C.c_void_p, C.c_int64]),
+    "pat_mesh_set_first_sample": (C.c_int, [C.c_void_p, C.c_int64]),
+    "pat_rto_moments": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
+    "pat_moments_finish": (C.c_int, [C.c_int64, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_draw_normals": (C.c_int, [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(TuneEntry),
                                C.POINTER(C.c_int32), C.c_void_p]),

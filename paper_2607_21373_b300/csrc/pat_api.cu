@@ -770,7 +770,7 @@ pat_status pat_cgls_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32
   if (bad_K(K, "pat_cgls_iterate") || !check_device(mesh, "pat_cgls_iterate")) return PAT_EINVAL;
   pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_cgls_iterate");
   if (s) return s;
-  return cgls_iterate(mesh->d, sigma, K, n_iter, resid, (char*)ws, (cudaStream_t)stream);
+  return cgls_iterate(mesh->d, sigma, K, n_iter, resid, (char*)ws, (cudaStream_t)stream, true);
 }
 
 pat_status pat_cgls_finish(const pat_mesh* mesh, int32_t K, double* samples, double* mean, double* stdev, void* ws,
@@ -796,10 +796,10 @@ pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma,
   pat_status s = pat_cgls_begin(mesh, y_obs, sigma, K, eta, xi, seed, ws, ws_bytes, stream);
   if (s) return s;
   if (resid) {
-    s = residual_norms(mesh->d, K, resid, (char*)ws, (cudaStream_t)stream);
+    s = residual_norms(mesh->d, K, resid, (char*)ws, (cudaStream_t)stream, true);
     if (s) return s;
   }
-  s = pat_cgls_iterate(mesh, sigma, K, n_iter, resid ? resid + K : nullptr, ws, ws_bytes, stream);
+  s = pat_cgls_iterate(mesh, sigma, K, n_iter, resid ? resid + 2 * (int64_t)K : nullptr, ws, ws_bytes, stream);
   if (s) return s;
   return pat_cgls_finish(mesh, K, samples, mean, stdev, ws, ws_bytes, stream);
 }
@@ -889,10 +889,10 @@ pat_status pat_map_estimate(const pat_mesh* mesh, const void* y_obs, double sigm
     s = cgls_begin(mesh->d, y_obs, sigma, 1, nullptr, nullptr, 0, (char*)ws, st, true);
     if (s) return s;
     if (resid) {
-      s = residual_norms(mesh->d, 1, resid, (char*)ws, st);
+      s = residual_norms(mesh->d, 1, resid, (char*)ws, st, false);
       if (s) return s;
     }
-    s = cgls_iterate(mesh->d, sigma, 1, n_iter, resid ? resid + 1 : nullptr, (char*)ws, st);
+    s = cgls_iterate(mesh->d, sigma, 1, n_iter, resid ? resid + 1 : nullptr, (char*)ws, st, false);
   }
   if (s) return s;
   return cgls_finish(mesh->d, 1, x_map, nullptr, nullptr, (char*)ws, st);
@@ -981,6 +981,40 @@ pat_status pat_rto_status(const pat_mesh* mesh, int32_t K, const void* ws, void*
     }
   }
   return PAT_OK;
+}
+
+pat_status pat_mesh_set_first_sample(pat_mesh* mesh, int64_t first_sample) {
+  clear_error();
+  // with K <= 1024 the largest draw index first_sample + K - 1 stays below 2^23
+  if (!mesh || first_sample < 0 || first_sample > kMaxDrawSample - 1024) {
+    set_error("pat_mesh_set_first_sample: NULL mesh or first_sample outside [0, %lld]",
+              (long long)(kMaxDrawSample - 1024));
+    return PAT_EINVAL;
+  }
+  mesh->d.first_sample = first_sample;
+  return PAT_OK;
+}
+
+pat_status pat_rto_moments(const pat_mesh* mesh, int32_t K, const double* center, double* out, void* ws,
+                           size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!mesh || !out) {
+    set_error("pat_rto_moments: NULL argument");
+    return PAT_EINVAL;
+  }
+  if (bad_K(K, "pat_rto_moments") || !check_device(mesh, "pat_rto_moments")) return PAT_EINVAL;
+  pat_status s = check_ws(mesh, 2, K, ws, ws_bytes, "pat_rto_moments");
+  if (s) return s;
+  return rto_moments(mesh->d, K, center, out, (char*)ws, (cudaStream_t)stream);
+}
+
+pat_status pat_moments_finish(int64_t n_nodes, double n_samples, int32_t which, double* v, void* stream) {
+  clear_error();
+  if (!v || n_nodes < 1 || (which != 0 && which != 1) || !(n_samples >= (which == 0 ? 1.0 : 2.0))) {
+    set_error("pat_moments_finish: NULL buffer, n_nodes < 1, which not 0 or 1, or too few samples (%g)", n_samples);
+    return PAT_EINVAL;
+  }
+  return moments_finish(n_nodes, n_samples, which, v, (cudaStream_t)stream);
 }
 
 pat_status pat_mesh_set_wait_cycles(pat_mesh* mesh, int64_t cycles) {

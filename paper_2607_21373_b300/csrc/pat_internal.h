@@ -98,6 +98,10 @@ struct DevCSR {
 
 constexpr int kEllWide = 16;  // slots of the wide fixed-width copy
 
+// The draw counter c = ((k << 1 | stream) << 40) | e leaves 23 bits for the
+// sample index k: first_sample + K must stay below 2^23.
+constexpr int64_t kMaxDrawSample = int64_t(1) << 23;
+
 // Event-based loop timing and launch counting (pat_profile_*).
 struct Profiler {
   bool on = false;
@@ -149,6 +153,7 @@ struct DeviceMesh {
   uint16_t *tile_slot_fwd = nullptr, *tile_slot_adj = nullptr;
   int32_t* d_status = nullptr;  // device status word of the tile kernels (PAT_ETIMEOUT)
   long long tile_wait_cycles = 4000000000ll;  // copy-wait budget of the tile kernels (pat_mesh_set_wait_cycles)
+  int64_t first_sample = 0;  // draw index of sample 0 of library-drawn perturbations (pat_mesh_set_first_sample)
   int32_t* row_order = nullptr;  // [N] rows sorted by the Z-order (Morton) key of their coordinates
   int32_t* etets = nullptr;  // [E][4] element vertices (c^2 gradient)
   void* eK0 = nullptr;       // [E][10] real: upper triangle of V grad(l_a).grad(l_b) (c = 1)

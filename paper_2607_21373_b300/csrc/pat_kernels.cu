@@ -725,22 +725,23 @@ __global__ void draw_normals_kernel(uint64_t seed, int stream, int64_t n_elem, i
 
 // r_d = y_obs / sigma + eta, r_p = xi  (b of eq. extended-matrices with C = M_L^{-1})
 // With zero_draws (the MAP problem, eq. MAP) eta = 0 and xi = 0.
+// Library draws of sample k use the draw index first + k.
 template <typename T>
 __global__ void rhs_kernel(int64_t n_data, int64_t N, int K, const T* __restrict__ y_obs, const T* __restrict__ eta,
                            const T* __restrict__ xi, uint64_t seed, double inv_sigma, T* __restrict__ r_d,
-                           T* __restrict__ r_p, int zero_draws) {
+                           T* __restrict__ r_p, int zero_draws, uint64_t first) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nd = n_data * K;
   if (t < nd) {
     const int64_t e = t / K;
     const int k = (int)(t - e * K);
-    const double et = zero_draws ? 0.0 : eta ? (double)eta[t] : normal_draw(seed, 0, (uint64_t)k, (uint64_t)e);
+    const double et = zero_draws ? 0.0 : eta ? (double)eta[t] : normal_draw(seed, 0, first + k, (uint64_t)e);
     r_d[t] = (T)((double)y_obs[e] * inv_sigma + et);
   } else if (t < nd + N * K) {
     const int64_t u = t - nd;
     const int64_t i = u / K;
     const int k = (int)(u - i * K);
-    r_p[u] = zero_draws ? T(0) : xi ? xi[u] : (T)normal_draw(seed, 1, (uint64_t)k, (uint64_t)i);
+    r_p[u] = zero_draws ? T(0) : xi ? xi[u] : (T)normal_draw(seed, 1, first + k, (uint64_t)i);
   }
 }
 
@@ -852,6 +853,18 @@ __global__ void finalize_beta_kernel(const double* pa, int na, int K, double* ga
   gamma[k] = s;
 }
 
+// out[2k] = sum of the data-block partials, out[2k+1] = sum of the prior-block
+// partials of sample k (the two blocks of ||r||^2 separately)
+__global__ void finalize_blocks_kernel(const double* pa, int na, const double* pb, int nb, int K, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double sa = 0.0, sb = 0.0;
+  for (int b = 0; b < na; ++b) sa += pa[(int64_t)b * K + k];
+  for (int b = 0; b < nb; ++b) sb += pb[(int64_t)b * K + k];
+  out[2 * k] = sa;
+  out[2 * k + 1] = sb;
+}
+
 __global__ void finalize_sum2_kernel(const double* pa, int na, const double* pb, int nb, int K, double* out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
@@ -910,6 +923,33 @@ __global__ void mean_std_kernel(int64_t N, int K, const double* __restrict__ x, 
     for (int k = 0; k < K; ++k) v += (r[k] - m) * (r[k] - m);
     stdev[i] = K > 1 ? sqrt(v / (K - 1)) : 0.0;
   }
+}
+
+// Pooled statistics of eq. ergodic over samples held by several processes, in
+// two passes so that no variance is formed by cancellation: pass 0 writes
+// out[i] = sum_k x_ik, pass 1 writes out[i] = sum_k (x_ik - center_i)^2; the
+// caller sums out over the processes between the passes and after pass 1.
+__global__ void moments_kernel(int64_t N, int K, const double* __restrict__ x, const double* __restrict__ center,
+                               double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* r = x + i * K;
+  double s = 0.0;
+  if (center == nullptr) {
+    for (int k = 0; k < K; ++k) s += r[k];
+  } else {
+    const double c = center[i];
+    for (int k = 0; k < K; ++k) s += (r[k] - c) * (r[k] - c);
+  }
+  out[i] = s;
+}
+
+// In place: which 0, v = v / n (the mean from the pooled sum); which 1,
+// v = sqrt(v / (n - 1)) (the std from the pooled squared deviations).
+__global__ void moments_finish_kernel(int64_t N, double n, int which, double* __restrict__ v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  v[i] = which == 0 ? v[i] / n : sqrt(v[i] / (n - 1.0));
 }
 
 RtoLayout rto_layout(const DeviceMesh& m, int K) {
@@ -1009,7 +1049,8 @@ pat_status begin_pre(const DeviceMesh& m, const T* y_obs, double sigma, int K, c
   set_double_kernel<<<1, 1, 0, st>>>((double*)(ws + L.sigma), sigma);
   PAT_TRY(cuda_check(cudaMemsetAsync(ws + L.x, 0, (size_t)m.N * K * 8, st), "cgls_begin memset x"));
   rhs_kernel<T><<<nblocks((ndata + m.N) * K), 256, 0, st>>>(ndata, m.N, K, y_obs, eta, xi, seed, 1.0 / sigma,
-                                                            (T*)(ws + L.r_d), (T*)(ws + L.r_p), zero_draws ? 1 : 0);
+                                                            (T*)(ws + L.r_d), (T*)(ws + L.r_p), zero_draws ? 1 : 0,
+                                                            (uint64_t)m.first_sample);
   count(m, 2);
   return cuda_check(cudaGetLastError(), "cgls_begin launch");
 }
@@ -1079,8 +1120,10 @@ static pat_status begin_t(const DeviceMesh& m, const T* y_obs, double sigma, int
   return begin_post<T>(m, K, ws, st);
 }
 
+// ||r||^2 per sample of the current CGLS residual (blocks = false: out[K]), or
+// its data and prior blocks separately (blocks = true: out[K][2])
 template <typename T>
-static pat_status residual_t(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st) {
+static pat_status residual_t(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st, bool blocks) {
   const RtoLayout L = rto_layout(m, K);
   const int64_t ndata = (int64_t)m.n_steps * m.n_obs;
   double* part = (double*)(ws + L.partial);
@@ -1092,14 +1135,17 @@ static pat_status residual_t(const DeviceMesh& m, int K, double* out, char* ws, 
                                                                                  rsD.rpb, pa);
   sumsq_kernel<T, false><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>((T*)(ws + L.r_p), nullptr, m.N, K,
                                                                                  rsN.rpb, pb);
-  finalize_sum2_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
+  if (blocks)
+    finalize_blocks_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
+  else
+    finalize_sum2_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
   count(m, 3);
   return cuda_check(cudaGetLastError(), "residual launch");
 }
 
 template <typename T>
 static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool blocks) {
   const RtoLayout L = rto_layout(m, K);
   if (!(sigma > 0.0)) {
     set_error("pat_cgls_iterate: sigma must be > 0 (got %g)", sigma);
@@ -1112,7 +1158,7 @@ static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter
     // s = A^T r = G^T r_d / sigma + M^{1/2} r_p
     PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
     PAT_TRY(iter_post<T>(m, K, ws, st));
-    if (resid) PAT_TRY(residual_t<T>(m, K, resid + (int64_t)it * K, ws, st));
+    if (resid) PAT_TRY(residual_t<T>(m, K, resid + (int64_t)it * (blocks ? 2 : 1) * K, ws, st, blocks));
   }
   return PAT_OK;
 }
@@ -1127,14 +1173,26 @@ pat_status cgls_begin(const DeviceMesh& m, const void* y_obs, double sigma, int 
 }
 
 pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
-                        cudaStream_t st) {
-  if (m.prec == PAT_F64) return iterate_t<double>(m, sigma, K, n_iter, resid, ws, st);
-  return iterate_t<float>(m, sigma, K, n_iter, resid, ws, st);
+                        cudaStream_t st, bool blocks) {
+  if (m.prec == PAT_F64) return iterate_t<double>(m, sigma, K, n_iter, resid, ws, st, blocks);
+  return iterate_t<float>(m, sigma, K, n_iter, resid, ws, st, blocks);
 }
 
-pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st) {
-  if (m.prec == PAT_F64) return residual_t<double>(m, K, out, ws, st);
-  return residual_t<float>(m, K, out, ws, st);
+pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st, bool blocks) {
+  if (m.prec == PAT_F64) return residual_t<double>(m, K, out, ws, st, blocks);
+  return residual_t<float>(m, K, out, ws, st, blocks);
+}
+
+pat_status rto_moments(const DeviceMesh& m, int K, const double* center, double* out, char* ws, cudaStream_t st) {
+  const RtoLayout L = rto_layout(m, K);
+  moments_kernel<<<nblocks(m.N), 256, 0, st>>>(m.N, K, (const double*)(ws + L.x), center, out);
+  count(m, 1);
+  return cuda_check(cudaGetLastError(), "rto_moments launch");
+}
+
+pat_status moments_finish(int64_t N, double n, int which, double* v, cudaStream_t st) {
+  moments_finish_kernel<<<nblocks(N), 256, 0, st>>>(N, n, which, v);
+  return cuda_check(cudaGetLastError(), "moments_finish launch");
 }
 
 pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean, double* stdev, char* ws,

@@ -31,10 +31,14 @@ pat_status adjoint(const DeviceMesh& m, const void* Yhat, int K, void* out, doub
 pat_status cgls_begin(const DeviceMesh& m, const void* y_obs, double sigma, int K, const void* eta,
                       const void* xi, uint64_t seed, char* ws, cudaStream_t st, bool zero_draws = false);
 pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, double* resid, char* ws,
-                        cudaStream_t st);
+                        cudaStream_t st, bool blocks);
 pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean, double* stdev, char* ws,
                        cudaStream_t st);
-pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st);
+pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st, bool blocks);
+// Pooled-statistics passes over the CGLS / LSQR iterate x held in ws (moments_kernel)
+// and their in-place finish (moments_finish_kernel).
+pat_status rto_moments(const DeviceMesh& m, int K, const double* center, double* out, char* ws, cudaStream_t st);
+pat_status moments_finish(int64_t N, double n, int which, double* v, cudaStream_t st);
 
 // LSQR (Paige & Saunders) on the same extended system and workspace; the
 // iterate x sits where CGLS keeps it, so cgls_finish also finishes LSQR.

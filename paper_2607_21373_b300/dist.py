@@ -1,11 +1,14 @@
 """Sample-parallel RTO across processes (one GPU per rank).
 
 RTO samples are independent (Section 5: every perturbed problem is solved on
-its own), so ranks draw disjoint sample sets and never exchange data while
-solving.  The one exchange is the pointwise posterior statistics of
-eq. ergodic over all ranks' samples, combined here from each rank's count,
-mean and std with two FP64 all-reduces (sums of K_r m_r, then of the
-within-rank and between-rank squared deviations).
+its own), so each rank solves its own K samples and never exchanges data while
+solving; rank r's library draws are keyed by the global sample indices
+r*K .. r*K + K - 1 (pat_mesh_set_first_sample), so the ranks together draw
+exactly the perturbations of one K_total-sample run.  The one exchange is the
+pointwise posterior statistics of eq. ergodic over all ranks' samples: the
+library forms each rank's sums (pat_rto_moments) and finishes mean and std
+(pat_moments_finish); this module only adds the [N] FP64 buffers across ranks
+(two all-reduces, plus one of the sample count).
 """
 from __future__ import annotations
 
@@ -13,25 +16,23 @@ import torch
 import torch.distributed as dist
 
 
-def sample_seed(base_seed: int, rank: int) -> int:
-    """Seed of a rank's batch: disjoint counter streams per rank."""
-    return (int(base_seed) * 1_000_003 + int(rank)) & 0xFFFFFFFFFFFFFFFF
+def first_sample(rank: int, K: int) -> int:
+    """Global index of rank's first sample when every rank solves K samples."""
+    return int(rank) * int(K)
 
 
-def allreduce_moments(mean: torch.Tensor, std: torch.Tensor, K: int, group=None):
-    """Global pointwise mean and std (1/(K_total - 1)) from per-rank statistics.
-
-    mean, std: this rank's [N] float64 mean and std over its K samples (std may
-    be None when K == 1).  Returns (mean, std, K_total) on every rank.
-    """
-    dev = mean.device
-    k = torch.tensor([float(K)], dtype=torch.float64, device=dev)
-    dist.all_reduce(k, group=group)
-    k_tot = float(k.item())
-    s1 = (mean.double() * K).clone()
-    dist.all_reduce(s1, group=group)
-    mu = s1 / k_tot
-    m2 = (std.double() ** 2) * (K - 1) if (std is not None and K > 1) else torch.zeros_like(mu)
-    m2 = m2 + K * (mean.double() - mu) ** 2
-    dist.all_reduce(m2, group=group)
-    return mu, torch.sqrt(m2 / (k_tot - 1)), int(round(k_tot))
+def allreduce_moments(mesh, K: int, group=None):
+    """Global pointwise mean and std (1/(K_total - 1)) of the samples of the last
+    RTO solve of every rank on `mesh` (K samples on this rank), on every rank.
+    Returns (mean, std, K_total); std is None when K_total < 2."""
+    s = mesh.rto_moments(K)                        # sum_k x_ik over this rank's samples
+    n = torch.tensor([float(K)], dtype=torch.float64, device=s.device)
+    dist.all_reduce(n, group=group)
+    dist.all_reduce(s, group=group)
+    k_tot = float(n.item())
+    mean = mesh.moments_finish(s, k_tot, 0)
+    if k_tot < 2:
+        return mean, None, int(round(k_tot))
+    q = mesh.rto_moments(K, center=mean)           # sum_k (x_ik - mean_i)^2
+    dist.all_reduce(q, group=group)
+    return mean, mesh.moments_finish(q, k_tot, 1), int(round(k_tot))

@@ -252,3 +252,24 @@ def test_krylov_amplification_of_one_rounding_sized_perturbation():
         ma, _ = rto.ergodic_mean_std(a[k])
         mp, _ = rto.ergodic_mean_std(p[k])
         assert rel(p[k], a[k]) > 1e-3 and rel(mp, ma) > 1e-3
+
+
+def test_residual_blocks_are_the_direct_residual_blocks():
+    """The recursively updated residual's two blocks (data misfit and prior term,
+    Section 6.1) equal the blocks of b - A x_k formed directly from the iterate,
+    and sum to the total history."""
+    ops, dt, nt, y_obs, sigma, _ = small_problem()
+    N = ops["K"].shape[0]
+    eta = S.standard_normal((nt, 8, 2), 15)
+    xi = S.standard_normal((N, 2), 16)
+    A, AT = rto.extended_operator(ops, dt, nt, sigma)
+    b = rto.rto_rhs(ops, y_obs, sigma, eta, xi)
+    for k in (0, 3, 6):
+        x, hb = rto.rto_samples(ops, dt, nt, y_obs, sigma, eta, xi, k, block_hist=True)
+        _, ht = rto.rto_samples(ops, dt, nt, y_obs, sigma, eta, xi, k)
+        assert hb.shape == (k + 1, 2, 2)
+        assert np.allclose(hb.sum(axis=-1), ht, rtol=1e-13, atol=0)
+        q = A(x)
+        for j in range(2):
+            direct = np.sum((b[j] - q[j]).reshape(-1, 2) ** 2, axis=0)
+            assert np.allclose(hb[-1, :, j], direct, rtol=1e-8, atol=1e-12 * np.sum(b[0] ** 2))
