@@ -80,6 +80,9 @@ def parse(argv=None):
     ap.add_argument("--solver", default="cgls", choices=["cgls", "lsqr"],
                     help="least-squares solver of every RTO sample (the configured workload names CGLS)")
     ap.add_argument("--variant", default="", help="force a step-kernel variant for K: " + " | ".join(sorted(FORCED)))
+    ap.add_argument("--workload", default="rto", choices=["rto", "uneven"],
+                    help="rto: one mesh, K samples per batch (default); uneven: six cubes 16^3..58^3 cells with "
+                         "K 256..8 and N_T 276..1000 in one grouped solve per step (k = 50)")
     return ap.parse_args(argv)
 
 
@@ -533,6 +536,81 @@ def run_ours(a, rank, world, local_rank, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_uneven(a, rank, world, local_rank, dist):
+    """Uneven batch: the six jobs of S.UNEVEN (cubes of 16^3..58^3 cells, N_T =
+    1000 n / 58, sensors 1024 (n / 58)^2 on five faces, K = 256..8, noise 1-4 %,
+    CGLS k = 50) in one grouped solve (pat_rto_sample_multi) per step."""
+    import torch
+
+    from paper_2607_21373_b300 import Mesh, rto_sample_multi
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    jobs, info = [], []
+    for w in S.UNEVEN:
+        xyz, tets = S.cube_mesh(w.n)
+        det = S.detector_points(w.n_obs, w.faces, w.seed)
+        p0 = S.phantom(xyz, w.phantom, w.seed + 100, w.n)
+        m = Mesh(xyz, tets, det, w.dt_factor / w.n, w.n_steps, precision="f32", flags=mesh_flags(a))
+        m.set_first_sample(rank * w.K)
+        Y = m.forward(torch.tensor(p0, dtype=torch.float32, device=dev))
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(w.seed + 2)
+        eta0 = torch.randn(Y.shape, generator=gen, device=dev, dtype=torch.float32)
+        sigma = float(w.noise * torch.linalg.vector_norm(Y.double()) / torch.linalg.vector_norm(eta0.double()))
+        jobs.append({"mesh": m, "y_obs": (Y + sigma * eta0).contiguous(), "sigma": sigma, "K": w.K, "seed": w.seed})
+        info.append({"n": w.n, "N": m.N, "N_T": w.n_steps, "n_obs": w.n_obs, "K": w.K, "noise": w.noise,
+                     "op_bytes": graph_operator_bytes(m.info, m.N)})
+    k = S.UNEVEN[0].n_iter
+    for i in range(a.warmup):
+        rto_sample_multi(jobs, k, samples=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    e0.record(st)
+    for i in range(a.steps):
+        rto_sample_multi(jobs, k, samples=False)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    for j in jobs:
+        j["mesh"].status(j["K"])
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    ksum = sum(w["K"] for w in info)
+    node_steps = sum((2 * k + 1) * w["N_T"] * w["N"] * w["K"] for w in info)
+    alg_bytes = sum((2 * k + 1) * w["N_T"] * (16.0 * w["N"] * w["K"] + w["op_bytes"]) for w in info)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(peaks_path))["hbm_gbs"] if os.path.exists(peaks_path) else 6400.0
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * ksum * a.steps / sec, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded meshes, phantoms, noise, device draws)",
+            "config": {"workload": "uneven batch: six cubes %s^3 cells, K %s, one grouped CGLS k=%d solve per step, "
+                                   "mesh %s" % ("/".join(str(w["n"]) for w in info),
+                                                "/".join(str(w["K"]) for w in info), k, a.mesh),
+                       "jobs": [{kk: w[kk] for kk in ("n", "N", "N_T", "n_obs", "K", "noise")} for w in info]},
+            "node_steps_per_s": world * node_steps * a.steps / sec,
+            "per_job_samples_per_s": [w["K"] * a.steps / sec for w in info],
+            "roofline": {"bound": "hbm", "kernel": "step3g_persist_kernel (grouped fixed-width steps)",
+                         "achieved": alg_bytes * a.steps / sec / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg_bytes * a.steps / sec / 1e9 / peak, "traffic": None,
+                         "note": "whole-step average (vector kernels and launch gaps included): a lower bound "
+                                 "on the step kernels' own rate"},
+            "cpu_baseline": None, "e2e": None, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -549,6 +627,8 @@ def main():
         dist = tdist
     if a.impl == "reference":
         run_reference(a, rank, world)
+    elif a.workload == "uneven":
+        run_uneven(a, rank, world, local_rank, dist)
     else:
         run_ours(a, rank, world, local_rank, dist)
     if dist is not None:

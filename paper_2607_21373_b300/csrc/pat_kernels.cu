@@ -19,11 +19,6 @@ pat_status cuda_check(cudaError_t e, const char* what) {
   return PAT_ECUDA;
 }
 
-#define PAT_TRY(expr)                       \
-  do {                                      \
-    pat_status _s = (expr);                 \
-    if (_s != PAT_OK) return _s;            \
-  } while (0)
 
 int sm_count() {
   int dev = 0, n = 148;

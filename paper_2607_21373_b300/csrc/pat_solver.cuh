@@ -8,6 +8,13 @@
 
 #include "pat_internal.h"
 
+// Return the status of `expr` from the enclosing function unless it is PAT_OK.
+#define PAT_TRY(expr)            \
+  do {                           \
+    pat_status _s = (expr);      \
+    if (_s != PAT_OK) return _s; \
+  } while (0)
+
 namespace pat {
 
 // Workspace layout of one RTO solve with K stacked samples (byte offsets,

@@ -201,6 +201,31 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
     step3w_row<ADJ, NB, PB>(A, c * 32 + lane);
 }
 
+// Uneven batch: one persistent grid over the 32-thread chunks of several jobs
+// (meshes with their own sizes, sensor sets, time-step counts and K).  Job g
+// owns chunks block_off[g] <= c < block_off[g + 1] (each job's row threads and
+// sensor-gather threads rounded up to whole chunks), so a warp never mixes
+// jobs; a warp's chunks increase, so its job index only moves forward.  Every
+// job's rows run the single-mesh fixed-width row code (16 slots with WIDE,
+// else 8) on that job's arguments.
+template <bool ADJ, bool WIDE>
+__global__ void __launch_bounds__(256, 4) step3g_persist_kernel(const __grid_constant__ Step3Group<float> G,
+                                                                 int64_t n_chunks) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int64_t S = (int64_t)gridDim.x * 8;
+  int g = 0;
+  for (int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); c < n_chunks; c += S) {
+    while (g + 1 < G.n && c >= G.block_off[g + 1]) ++g;
+    const int64_t t = (c - G.block_off[g]) * 32 + lane;
+    if constexpr (WIDE)
+      step3w_row<ADJ, 4, true>(G.a[g], t);
+    else
+      step3e_row<8, ADJ>(G.a[g], t);
+  }
+}
+
 // One sample (K = 1): one thread per row, 16 fixed slots.
 template <bool ADJ>
 __global__ void __launch_bounds__(256) step3w1_kernel(const Step3Args<float> A) {

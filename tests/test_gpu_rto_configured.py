@@ -91,8 +91,8 @@ def test_cube32_single_sample_k100_against_oracle_floor():
     P = cube_problem(32, 256, 600, faces=S.LIMITED_VIEW_FACES, seed=1002, phantom="blobs20+vessels", data=True)
     N, k = P["xyz"].shape[0], 100
     y = as_precision(P["y_obs"], "f32")
-    eta = as_precision(S.standard_normal((600, 256), 1007), "f32")
-    xi = as_precision(S.standard_normal(N, 1008), "f32")
+    eta = as_precision(S.standard_normal((600, 256, 1), 1007), "f32")
+    xi = as_precision(S.standard_normal((N, 1), 1008), "f32")
     m = Mesh(P["xyz"], P["tets"], P["det"], P["dt"], 600, precision="f32")
     out = m.rto_sample(dev(y, "f32"), P["sigma"], 1, k, eta=dev(eta, "f32"), xi=dev(xi, "f32"))
     m.status(1)
