@@ -180,8 +180,10 @@ pat_status pat_forward(const pat_mesh* mesh, const void* p0, int32_t K, void* Y,
  *     PAT_F64 meshes; larger requests return PAT_EINVAL with a message naming
  *     the limit.  The call never allocates or frees device memory.
  *   - The first call on a device looks up that array's device address (with the
- *     device current) and caches it; make that first call before any stream
- *     capture.
+ *     device current) and caches it for the rest of the process; make that first
+ *     call before any stream capture.  The cached address does not survive
+ *     cudaDeviceReset (the library's module is reloaded and the array may
+ *     move): do not call this entry point after resetting the device.
  *   - All calls on a device share the one array: calls that overlap on the GPU
  *     (other streams, other host threads) race and corrupt each other's
  *     results; serialise them.  A call never reads what an earlier call left
@@ -395,6 +397,51 @@ pat_status pat_moments_finish(int64_t n_nodes, double n_samples, int32_t which, 
  */
 pat_status pat_draw_normals(uint64_t seed, int32_t stream_id, int64_t n_elem, int32_t K, double* out,
                             void* stream);
+
+/*
+ * Whittle-Matern prior (Section 4.1.2, eq. matern-cov-op; Section 6.4) for FP32
+ * meshes: the prior field p0 = P T z with z ~ N(0, I) on a periodic box grid of
+ * n_grid^3 points, T = F^{-1} diag(sqrt(S)) F (F the unitary 3D DFT),
+ * S(k) = (1/ell^2 + |2 pi k|^2)^{-(s + 3/2)} at the DFT frequencies scaled so
+ * that the grid field's marginal variance is sigma^2 (the normalisation Z), and
+ * P trilinear interpolation from the grid to the mesh nodes.  The box is
+ * [box_lo[c], box_lo[c] + box_len) on every axis c, grid point j at
+ * box_lo + j box_len / n_grid; every node must lie inside.  The paper's
+ * covariance operator is followed (its Section 6.4 SPDE applies the cubed
+ * operator to p0, which would square it).  Grid fields are K-stacked [G][K],
+ * G = n_grid^3, grid point (ix, iy, iz) at (ix n_grid + iy) n_grid + iz.
+ *
+ *   pat_matern_create   builds sqrt(S) (FP32), P (8 grid points and FP32
+ *       weights per node) and P^T as a grid -> node list of the same weights.
+ *       n_grid a power of two in [8, 256].  Errors: PAT_EINVAL (arguments, a
+ *       node outside the box), PAT_EUNSUPPORTED (FP64 mesh), PAT_ENOMEM.
+ *   pat_matern_workspace_bytes  device workspace of the calls below for K
+ *       samples: an RTO workspace of the mesh followed by the latent fields.
+ *   pat_matern_apply  op 0: out = T in (grid -> grid); 1: out = P in (grid ->
+ *       nodes [N][K]); 2: out = P^T in (nodes -> grid); 3: out = P T in (grid ->
+ *       nodes).  FP32 device fields.
+ *   pat_rto_sample_matern  K RTO samples in the latent space (Section 6.4):
+ *       n_iter CGLS iterations from z = 0 on min ||(G P T z - y_obs)/sigma -
+ *       eta||^2 + ||z - xi||^2, every inner product, norm, scalar and the
+ *       iterate z in FP64.  eta device [N_T][N_obs][K] float or NULL (library
+ *       draws, stream 0); xi device [G][K] float or NULL (library draws of
+ *       stream 1 at element = grid point); both keyed by the mesh's first
+ *       sample index as in pat_rto_sample.  Outputs (device double, each may be
+ *       NULL): z_samples [G][K]; p_samples [N][K] = P T z; mean, stdev [N] of
+ *       the nodal samples (eq. ergodic).  PAT_ENUMERIC is reported by
+ *       pat_rto_status(mesh, K, workspace, stream) as for the other solvers.
+ */
+typedef struct pat_matern pat_matern;
+pat_status pat_matern_create(const pat_mesh* mesh, int32_t n_grid, const double* box_lo /* [3] */, double box_len,
+                             double ell, double s, double sigma, pat_matern** out);
+pat_status pat_matern_destroy(pat_matern* prior);
+pat_status pat_matern_workspace_bytes(const pat_mesh* mesh, const pat_matern* prior, int32_t K, size_t* bytes);
+pat_status pat_matern_apply(const pat_mesh* mesh, const pat_matern* prior, int32_t op, const float* in, int32_t K,
+                            float* out, void* workspace, size_t workspace_bytes, void* stream);
+pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* prior, const void* y_obs, double sigma,
+                                 int32_t K, int32_t n_iter, const void* eta, const float* xi, uint64_t seed,
+                                 double* z_samples, double* p_samples, double* mean, double* stdev, void* workspace,
+                                 size_t workspace_bytes, void* stream);
 
 /*
  * Derivatives of a data misfit L(p0, theta) whose cotangent with respect to

@@ -20,7 +20,7 @@ import torch
 from . import _lib
 from ._lib import PatError
 
-__all__ = ["Mesh", "PatError", "draw_normals", "rto_sample_multi", "lib", "F32", "F64"]
+__all__ = ["Mesh", "MaternPrior", "PatError", "draw_normals", "rto_sample_multi", "lib", "F32", "F64"]
 
 F32, F64 = 0, 1
 MESH_SKIP_STABILITY, MESH_KEEP_ZEROS, MESH_SINGLE_COEF, MESH_HOST_ONLY, MESH_TWO_LEVEL, MESH_NO_GRAPHS = (
@@ -353,6 +353,70 @@ class Mesh:
             "gamma": view(off[5], K, torch.float64, (K,)),
             "status": ws[off[6]:off[6] + 4].view(torch.int32),
         }
+
+
+class MaternPrior:
+    """Whittle-Matern prior on a periodic box grid of n_grid^3 points carried to
+    the nodes of an FP32 mesh (pat_matern_create), and RTO in its latent space."""
+
+    def __init__(self, mesh, n_grid, box_lo, box_len, ell, s, sigma):
+        lo = _f64c(box_lo)
+        h = C.c_void_p()
+        _lib.check(lib().pat_matern_create(mesh._h, int(n_grid), lo.ctypes.data, float(box_len), float(ell),
+                                           float(s), float(sigma), C.byref(h)))
+        self._h, self.mesh, self.n_grid = h, mesh, int(n_grid)
+        self.G = self.n_grid ** 3
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._LIB is not None:
+            _lib._LIB.pat_matern_destroy(h)
+            self._h = None
+
+    def workspace(self, K):
+        nb = C.c_size_t()
+        _lib.check(lib().pat_matern_workspace_bytes(self.mesh._h, self._h, K, C.byref(nb)))
+        ws = self._ws.get(K)
+        if ws is None or ws.numel() < nb.value + 256:
+            ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.mesh.device)
+            self._ws[K] = ws
+        off = (-ws.data_ptr()) % 256
+        return ws[off:off + nb.value]
+
+    def apply(self, op, field):
+        """op "T" (grid -> grid), "P" (grid -> nodes), "PT" (nodes -> grid) or
+        "PT_T" = P T (grid -> nodes) on a float32 CUDA field [points, K]."""
+        code = {"T": 0, "P": 1, "PT": 2, "PT_T": 3}[op]
+        K = field.shape[1]
+        rows = self.mesh.N if code in (1, 3) else self.G
+        out = torch.empty((rows, K), dtype=torch.float32, device=field.device)
+        ws = self.workspace(K)
+        _lib.check(lib().pat_matern_apply(self.mesh._h, self._h, code, _ptr(field), K, _ptr(out), _ptr(ws),
+                                          ws.numel(), _stream()))
+        return out
+
+    def rto_sample(self, y_obs, sigma, K, n_iter, eta=None, xi=None, seed=0, latent=False, samples=True,
+                   mean=True, stdev=None):
+        """K latent-space RTO samples (pat_rto_sample_matern): nodal samples
+        P T z [N, K] float64, their mean and std, and with latent the z [G, K]."""
+        m = self.mesh
+        stdev = (K >= 2) if stdev is None else stdev
+        dev = m.device
+        out = {"z": torch.empty((self.G, K), dtype=torch.float64, device=dev) if latent else None,
+               "samples": torch.empty((m.N, K), dtype=torch.float64, device=dev) if samples else None,
+               "mean": torch.empty(m.N, dtype=torch.float64, device=dev) if mean else None,
+               "std": torch.empty(m.N, dtype=torch.float64, device=dev) if stdev else None}
+        ws = self.workspace(K)
+        _lib.check(lib().pat_rto_sample_matern(
+            m._h, self._h, _ptr(y_obs), float(sigma), K, int(n_iter), _ptr(eta), _ptr(xi), C.c_uint64(seed),
+            _ptr(out["z"]), _ptr(out["samples"]), _ptr(out["mean"]), _ptr(out["std"]), _ptr(ws), ws.numel(),
+            _stream()))
+        return out
+
+    def status(self, K):
+        ws = self.workspace(K)
+        _lib.check(lib().pat_rto_status(self.mesh._h, K, _ptr(ws), _stream()))
 
 
 def rto_sample_multi(jobs, n_iter, samples=True):

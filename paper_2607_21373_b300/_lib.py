@@ -89,6 +89,15 @@ SIGNATURES = {
                                   C.c_void_p]),
     "pat_moments_finish": (C.c_int, [C.c_int64, C.c_double, C.c_int32, C.c_void_p, C.c_void_p]),
     "pat_draw_normals": (C.c_int, [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pat_matern_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                    C.c_double, C.POINTER(C.c_void_p)]),
+    "pat_matern_destroy": (C.c_int, [C.c_void_p]),
+    "pat_matern_workspace_bytes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, c_size_p]),
+    "pat_matern_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                   C.c_void_p, C.c_size_t, C.c_void_p]),
+    "pat_rto_sample_matern": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
+                                        C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "pat_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(TuneEntry),
                                C.POINTER(C.c_int32), C.c_void_p]),
     "pat_select_variant": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(TuneEntry)]),

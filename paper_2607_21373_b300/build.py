@@ -14,7 +14,8 @@ import tempfile
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpat.so")
-SOURCES = ["pat_host.cpp", "pat_kernels.cu", "pat_grad.cu", "pat_multi.cu", "pat_noalloc.cu", "pat_api.cu"]
+SOURCES = ["pat_host.cpp", "pat_kernels.cu", "pat_grad.cu", "pat_multi.cu", "pat_noalloc.cu", "pat_matern.cu",
+           "pat_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = [*ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3", "-Xptxas", "-v"]
 

@@ -100,6 +100,10 @@ pat_status upload_rows(const HostRows& r, bool split, DevCSR& d) {
   return PAT_OK;
 }
 
+}  // namespace
+
+namespace pat {
+
 bool check_device(const pat_mesh* mesh, const char* fn) {
   if (mesh->d.host_only) {
     set_error("%s: the mesh was created with PAT_MESH_HOST_ONLY", fn);
@@ -135,6 +139,10 @@ bool bad_K(int32_t K, const char* fn) {
   }
   return false;
 }
+
+}  // namespace pat
+
+namespace {
 
 // Tiles of kTileRows consecutive rows: the union of the source rows of their
 // stiffness / boundary entries as contiguous ranges (gaps of up to 4 rows are

@@ -181,6 +181,14 @@ struct DeviceMesh {
   mutable std::mutex tune_mutex;
 };
 
+// Argument checks shared by the entry points (pat_api.cu): the mesh has device
+// copies on the current device; K is in range; a workspace for op (as in
+// pat_workspace_bytes) is large enough and 256-byte aligned.  Each sets the
+// error message and reports failure.
+bool check_device(const pat_mesh* mesh, const char* fn);
+bool bad_K(int32_t K, const char* fn);
+pat_status check_ws(const pat_mesh* mesh, int op, int K, const void* ws, size_t bytes, const char* fn);
+
 }  // namespace pat
 
 struct pat_mesh {

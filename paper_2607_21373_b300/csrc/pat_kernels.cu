@@ -695,21 +695,6 @@ pat_status adjoint(const DeviceMesh& m, const void* Yh, int K, void* out, double
 // draw keyed by (seed, stream, sample k, element e) uses outputs 2c+1 and 2c+2
 // with c = ((k << 1 | stream) << 40) | e as two uniforms for Box-Muller
 // (cosine branch): z = sqrt(-2 ln u1) cos(2 pi u2), u1 in (0, 1].
-__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t i) {
-  uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ double normal_draw(uint64_t seed, int stream, uint64_t k, uint64_t e) {
-  const uint64_t c = (((k << 1) | (uint64_t)stream) << 40) | e;
-  const uint64_t h1 = splitmix_out(seed, 2 * c + 1);
-  const uint64_t h2 = splitmix_out(seed, 2 * c + 2);
-  const double u1 = ((double)(h1 >> 11) + 1.0) * 0x1.0p-53;
-  const double u2 = (double)(h2 >> 11) * 0x1.0p-53;
-  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
-}
-
 __global__ void draw_normals_kernel(uint64_t seed, int stream, int64_t n_elem, int K, double* out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_elem * K) return;
@@ -979,7 +964,7 @@ static inline unsigned nblocks(int64_t n, int bs = 256) { return (unsigned)((n +
 // CGLS loop, replayed from a CUDA graph captured on first use (N_T + 1 or
 // N_T + 2 launches become one graph launch).  Falls back to direct launches
 // when the stream is already being captured or graphs are disabled.
-static pat_status cgls_solve(const DeviceMesh& m, int dir, int K, double sigma, char* ws, cudaStream_t st) {
+pat_status cgls_solve(const DeviceMesh& m, int dir, int K, double sigma, char* ws, cudaStream_t st) {
   const RtoLayout L = rto_layout(m, K);
   auto direct = [&](cudaStream_t s) {
     return dir == 0 ? forward(m, ws + L.d, K, ws + L.q_d, 1.0 / sigma, ws + L.state, s)

@@ -526,6 +526,26 @@ __global__ void __launch_bounds__(256) step3_group_kernel(const __grid_constant_
 // row walked in predicated chunks so that a row's neighbour loads are issued
 // together, the (hi, lo) coefficient pair read as one 8-byte load.
 // ---------------------------------------------------------------------------
+// Counter-based N(0,1) draws (SplitMix64, Steele, Lea and Flood 2014, and the
+// Box-Muller cosine branch): the draw keyed by (seed, stream, sample k,
+// element e) uses outputs 2c+1 and 2c+2 of SplitMix64 seeded with `seed`,
+// c = ((k << 1 | stream) << 40) | e, as the uniforms u1 in (0, 1], u2 in [0, 1).
+__device__ __forceinline__ uint64_t splitmix_out(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + i * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double normal_draw(uint64_t seed, int stream, uint64_t k, uint64_t e) {
+  const uint64_t c = (((k << 1) | (uint64_t)stream) << 40) | e;
+  const uint64_t h1 = splitmix_out(seed, 2 * c + 1);
+  const uint64_t h2 = splitmix_out(seed, 2 * c + 2);
+  const double u1 = ((double)(h1 >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(h2 >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+
 typedef unsigned long long u64;
 
 __device__ __forceinline__ u64 dup2(float c) {

@@ -23,7 +23,8 @@ static __device__ __align__(256) unsigned char g_forward_scratch[kScratchBytes];
 
 // Host code must not use g_forward_scratch directly: on the host that name is a
 // stand-in object, not a device address.  The device address is looked up once
-// per device, with that device current, and cached here.
+// per device, with that device current, and cached here for the life of the
+// process (a cudaDeviceReset, which reloads the module, is not supported).
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
@@ -59,19 +60,8 @@ extern "C" pat_status pat_forward_noalloc(const pat_mesh* mesh, const void* p0, 
     set_error("pat_forward_noalloc: NULL argument");
     return PAT_EINVAL;
   }
-  if (mesh->d.host_only) {
-    set_error("pat_forward_noalloc: the mesh was created with PAT_MESH_HOST_ONLY");
-    return PAT_EINVAL;
-  }
-  if (K < 1 || K > 1024) {
-    set_error("pat_forward_noalloc: K = %d must be in [1, 1024]", K);
-    return PAT_EINVAL;
-  }
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev != mesh->d.device) {
-    set_error("pat_forward_noalloc: current device %d is not the mesh's device %d", dev, mesh->d.device);
-    return PAT_EINVAL;
-  }
+  // the same argument rules as pat_forward
+  if (bad_K(K, "pat_forward_noalloc") || !check_device(mesh, "pat_forward_noalloc")) return PAT_EINVAL;
   const size_t need = state_bytes(mesh->d, K);
   if (need > kScratchBytes) {
     set_error("pat_forward_noalloc: N*K = %lld needs %zu bytes of time-stepping state, more than the fixed "

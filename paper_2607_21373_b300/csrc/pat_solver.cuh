@@ -42,6 +42,9 @@ pat_status cgls_iterate(const DeviceMesh& m, double sigma, int K, int n_iter, do
 pat_status cgls_finish(const DeviceMesh& m, int K, double* samples, double* mean, double* stdev, char* ws,
                        cudaStream_t st);
 pat_status residual_norms(const DeviceMesh& m, int K, double* out, char* ws, cudaStream_t st, bool blocks);
+// One wave solve of the CGLS loop on an RTO workspace (dir 0: q_d = G d / sigma
+// from the d field; dir 1: s = G^T r_d / sigma), replayed from a CUDA graph.
+pat_status cgls_solve(const DeviceMesh& m, int dir, int K, double sigma, char* ws, cudaStream_t st);
 // Pooled-statistics passes over the CGLS / LSQR iterate x held in ws (moments_kernel)
 // and their in-place finish (moments_finish_kernel).
 pat_status rto_moments(const DeviceMesh& m, int K, const double* center, double* out, char* ws, cudaStream_t st);
