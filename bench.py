@@ -80,9 +80,10 @@ def parse(argv=None):
     ap.add_argument("--solver", default="cgls", choices=["cgls", "lsqr"],
                     help="least-squares solver of every RTO sample (the configured workload names CGLS)")
     ap.add_argument("--variant", default="", help="force a step-kernel variant for K: " + " | ".join(sorted(FORCED)))
-    ap.add_argument("--workload", default="rto", choices=["rto", "uneven"],
+    ap.add_argument("--workload", default="rto", choices=["rto", "uneven", "matern"],
                     help="rto: one mesh, K samples per batch (default); uneven: six cubes 16^3..58^3 cells with "
-                         "K 256..8 and N_T 276..1000 in one grouped solve per step (k = 50)")
+                         "K 256..8 and N_T 276..1000 in one grouped solve per step (k = 50); matern: the rto "
+                         "workload with the Whittle-Matern prior (128^3 latent grid, l = 0.15, s = 1.5, sigma = 3)")
     return ap.parse_args(argv)
 
 
@@ -611,6 +612,64 @@ def run_uneven(a, rank, world, local_rank, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_matern(a, rank, world, local_rank, dist):
+    """The rto workload's mesh, sensors and data with the Whittle-Matern prior of
+    Section 6.4 (l = 0.15, s = 1.5, sigma = 3, 128^3 grid on a periodic box
+    holding the cube with 0.5 to spare on every side): K latent-space RTO
+    samples (CGLS, k iterations) per step."""
+    import torch
+
+    from paper_2607_21373_b300 import MaternPrior, Mesh
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    xyz, tets, det, p0, dt = problem(a)
+    mesh = Mesh(xyz, tets, det, dt, a.n_steps, precision="f32", flags=mesh_flags(a))
+    mesh.set_first_sample(rank * a.K)
+    ng = 128
+    prior = MaternPrior(mesh, ng, (-0.5, -0.5, -0.5), 2.0, 0.15, 1.5, 3.0)
+    Y = mesh.forward(torch.tensor(p0, dtype=torch.float32, device=dev))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(S.BATCHED.seed + 2)
+    eta0 = torch.randn(Y.shape, generator=gen, device=dev, dtype=torch.float32)
+    sigma = float(S.BATCHED.noise * torch.linalg.vector_norm(Y.double()) / torch.linalg.vector_norm(eta0.double()))
+    y_obs = (Y + sigma * eta0).contiguous()
+    K, k = a.K, a.k_iter
+    if a.autotune:
+        mesh.autotune(K, n_probe=30)
+    for i in range(a.warmup):
+        prior.rto_sample(y_obs, sigma, K, k, seed=i, samples=False)
+    prior.status(K)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    mesh.profile_enable(True)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(a.steps):
+        prior.rto_sample(y_obs, sigma, K, k, seed=100 + i, samples=False)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = mesh.profile_read()
+    mesh.profile_enable(False)
+    clk = clocks.stop()
+    prior.status(K)
+    sec = ms / 1e3
+    wave_ms = prof["fwd_ms"] + prof["adj_ms"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * K * a.steps / sec, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded mesh, phantom, noise, device draws)",
+            "config": dict(workload_config(a), prior="Whittle-Matern: 128^3 periodic grid on [-0.5, 1.5)^3, l=0.15, "
+                                                     "s=1.5, sigma=3; RTO in the latent space (CGLS k=%d)" % k),
+            "wave_solve_share": wave_ms / ms, "cpu_baseline": None, "e2e": None, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -629,6 +688,8 @@ def main():
         run_reference(a, rank, world)
     elif a.workload == "uneven":
         run_uneven(a, rank, world, local_rank, dist)
+    elif a.workload == "matern":
+        run_matern(a, rank, world, local_rank, dist)
     else:
         run_ours(a, rank, world, local_rank, dist)
     if dist is not None:
