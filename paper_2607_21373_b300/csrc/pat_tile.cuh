@@ -391,6 +391,68 @@ __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<flo
   if constexpr (V == 8) *reinterpret_cast<float4*>(p + hs) = make_float4(x.v[4], x.v[5], x.v[6], x.v[7]);
 }
 
+// The tail of a fixed-width row of WD slots: its stiffness / boundary entries
+// beyond the slots (acting on x, coefficient c) and the xp parts of its
+// boundary entries (the last nb of its eA entries, acting on pk with -c).  The
+// entries are taken in pairs whose two gathers are in flight together (more
+// would spill at the register budget of the persistent kernels), and their
+// products are accumulated in entry order, exactly as a one-entry-at-a-time
+// walk would: the boundary rows of a cube carry up to 18 entries and 7
+// corrections, and a serial walk makes them several times slower than an
+// interior row and holds up the warp that has one.
+template <int V, bool W, int WD>
+__device__ __forceinline__ void fixed_row_tail(const Step3Args<float>& A, int64_t row, int eA, int nb,
+                                               const float* xk, const float* pk, int64_t hs, uint32_t Ku,
+                                               u64 (&acc)[V / 2], u64 (&accl)[V / 2]) {
+  constexpr int P = V / 2, TB = 2;
+  if (eA <= WD && (nb == 0 || pk == nullptr)) return;
+  const int64_t o0 = (int64_t)A.ovf_ptr[row] - WD;  // overflow index of entry e >= WD: o0 + e
+  auto fetch = [&](int e, uint32_t* col, float2* c) {
+    if (e < WD) {
+      *col = A.ell_col[row * WD + e];
+      *c = A.ell_hl[row * WD + e];
+    } else {
+      *col = A.ovf_col[o0 + e];
+      *c = A.ovf_hl[o0 + e];
+    }
+  };
+  auto batch = [&](int e0, int e1, const float* src, float sign) {
+    for (; e0 < e1; e0 += TB) {
+      uint32_t cq[TB];
+      float2 cf[TB];
+      u64 x[TB][P];
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        cq[q] = 0u;
+        cf[q] = make_float2(0.0f, 0.0f);
+        if (e0 + q < e1) fetch(e0 + q, &cq[q], &cf[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        if (e0 + q < e1) {
+          ld_runs<V, W>(src + (size_t)cq[q] * Ku, hs, x[q]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        if (e0 + q < e1) {
+          const u64 ch = dup2(sign * cf[q].x), cl = dup2(sign * cf[q].y);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            acc[p] = ffma2(ch, x[q][p], acc[p]);
+            accl[p] = ffma2(cl, x[q][p], accl[p]);
+          }
+        }
+      }
+    }
+  };
+  batch(WD, eA, xk, 1.0f);
+  if (nb > 0 && pk != nullptr) batch(eA - nb, eA, pk, -1.0f);
+}
+
 template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false, int NB = 4, bool PB = (NB == 2)>
 __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int64_t t,
                                            const EllStage* sm = nullptr, int64_t r0 = 0) {
@@ -529,36 +591,10 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
         ell_half<P>(xk, Ku, cq, ha, hb, acc, accl);
       }
     }
-    for (int e = 8; e < eA; ++e) {  // overflow of long (boundary) rows
-      uint32_t col;
-      float2 c;
-      ell_entry<V>(A, row, e, &col, &c);
-      u64 x[P];
-      ld_runs<V, W>(xk + (size_t)col * Ku, hs, x);
-      const u64 ch = dup2(c.x), cl = dup2(c.y);
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        acc[p] = ffma2(ch, x[p], acc[p]);
-        accl[p] = ffma2(cl, x[p], accl[p]);
-      }
-    }
-    if (nb > 0 && A.prev_mode != 2) {
-      // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
-      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + base;
-      for (int e = eA - nb; e < eA; ++e) {
-        uint32_t col;
-        float2 c;
-        ell_entry<V>(A, row, e, &col, &c);
-        u64 x[P];
-        ld_runs<V, W>(pk + (size_t)col * Ku, hs, x);
-        const u64 ch = dup2(-c.x), cl = dup2(-c.y);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          acc[p] = ffma2(ch, x[p], acc[p]);
-          accl[p] = ffma2(cl, x[p], accl[p]);
-        }
-      }
-    }
+    // entries beyond the 8 slots, then the xp parts of the boundary entries
+    // (boundary entries act on w_j = x_j - xp_j)
+    const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
+    fixed_row_tail<V, W, 8>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
   }
   float src[V];
 #pragma unroll

@@ -92,9 +92,18 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
           cols[NB * h + 4 * q + 2] = c.z, cols[NB * h + 4 * q + 3] = c.w;
         }
       }
+      // slots past the row's count hold a zero coefficient: their gathers are
+      // skipped (a zero row adds exactly what the zero coefficient would)
       u64 x[NB][P];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
+      for (int q = 0; q < NB; ++q) {
+        if (NB * h + q < eA) {
+          ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+        }
+      }
       float2 cf[NB];
 #pragma unroll
       for (int q = 0; q < NB; q += 2) {
@@ -112,36 +121,10 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
         }
       }
     }
-    for (int e = kWide; e < eA; ++e) {  // overflow of long (boundary) rows
-      uint32_t col;
-      float2 c;
-      wide_entry(A, row, e, &col, &c);
-      u64 x[P];
-      ld_runs<V>(xk + (size_t)col * Ku, hs, x);
-      const u64 ch = dup2(c.x), cl = dup2(c.y);
-#pragma unroll
-      for (int p = 0; p < P; ++p) {
-        acc[p] = ffma2(ch, x[p], acc[p]);
-        accl[p] = ffma2(cl, x[p], accl[p]);
-      }
-    }
-    if (nb > 0 && A.prev_mode != 2) {
-      // boundary entries act on w_j = x_j - xp_j: remove their xp_j part
-      const float* pk = (A.prev_mode == 0 ? A.xp : A.x) + base;
-      for (int e = eA - nb; e < eA; ++e) {
-        uint32_t col;
-        float2 c;
-        wide_entry(A, row, e, &col, &c);
-        u64 x[P];
-        ld_runs<V>(pk + (size_t)col * Ku, hs, x);
-        const u64 ch = dup2(-c.x), cl = dup2(-c.y);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          acc[p] = ffma2(ch, x[p], acc[p]);
-          accl[p] = ffma2(cl, x[p], accl[p]);
-        }
-      }
-    }
+    // entries beyond the 16 slots, then the xp parts of the boundary entries
+    // (boundary entries act on w_j = x_j - xp_j)
+    const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
+    fixed_row_tail<V, false, kWide>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
   }
   float src[V];
 #pragma unroll

@@ -73,8 +73,8 @@ def test_latent_rto_first_iterations_match_oracle(k):
     xi = as_precision(S.standard_normal((G, K), 91), "f32")
     out = prior.rto_sample(dev(y), P["sigma"], K, k, eta=dev(eta), xi=dev(xi), latent=True)
     prior.status(K)
-    z, p, _ = matern.latent_rto_samples(P["ops"], P["dt"], P["n_steps"], y, P["sigma"], eta, xi, filt, idx, w, k,
-                                        solver="cgls")
+    z, p, _ = matern.latent_rto_samples(P["ops"], P["dt"], P["n_steps"], y, P["sigma"], eta,
+                                        xi.reshape(NG, NG, NG, K), filt, idx, w, k, solver="cgls")
     assert rel_l2(out["z"].cpu().numpy(), z.reshape(G, K)) < 2e-4
     assert rel_l2(out["samples"].cpu().numpy(), p) < 2e-4
     mo, so = rto.ergodic_mean_std(out["samples"].cpu().numpy())
