@@ -250,12 +250,24 @@ pat_status build_tiles(DeviceMesh& m, const HostRows& F, const HostRows& A3, con
 
 // Fixed-width copy of a three-level CSR for the ELL kernels (FP32 split only):
 // W = 8 or 16 slots per row.  The descriptor word is written with the 8-slot
-// copy and shared by both.
+// copy and shared by both.  The 8-slot copy is row-major ([row][slot]); the
+// 16-slot copy interleaves each quad of consecutive rows so that one 16-byte
+// chunk of 4 columns (or of 2 coefficient pairs) of the quad's 4 rows is 64
+// contiguous bytes: column e of row i at (i/4)*64 + (e/4)*16 + (i%4)*4 + e%4,
+// pair e at (i/4)*64 + (e/2)*8 + (i%4)*2 + e%2 (rows padded to a multiple of 4).
+static int64_t ell_col_index(int64_t i, int e, int W) {
+  return W == 8 ? i * 8 + e : (i / 4) * 64 + (e / 4) * 16 + (i % 4) * 4 + e % 4;
+}
+static int64_t ell_hl_index(int64_t i, int e, int W) {
+  return W == 8 ? i * 8 + e : (i / 4) * 64 + (e / 2) * 8 + (i % 4) * 2 + e % 2;
+}
+
 pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const std::vector<uint8_t>& ninj,
                      DevCSR& d, int W) {
   const int64_t N = (int64_t)R.ptr.size() - 1;
-  std::vector<uint32_t> col(N * W), desc(N);
-  std::vector<float2> hl(N * W);
+  const int64_t Np = W == 8 ? N : (N + 3) / 4 * 4;
+  std::vector<uint32_t> col(Np * W, 0u), desc(N);
+  std::vector<float2> hl(Np * W, make_float2(0.0f, 0.0f));
   std::vector<int32_t> optr(N + 1, 0);
   std::vector<uint32_t> ocol;
   std::vector<float2> ohl;
@@ -277,11 +289,11 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
     const int nA = n - (int)ninj[i];
     for (int q = 0; q < W; ++q) {
       if (q < nA) {
-        col[i * W + q] = R.col[e0 + q] & kIdxMask;
-        hl[i * W + q] = pair(R.val[e0 + q]);
+        col[ell_col_index(i, q, W)] = R.col[e0 + q] & kIdxMask;
+        hl[ell_hl_index(i, q, W)] = pair(R.val[e0 + q]);
       } else {
-        col[i * W + q] = (uint32_t)i;  // padding reads the row itself with a zero coefficient
-        hl[i * W + q] = make_float2(0.0f, 0.0f);
+        col[ell_col_index(i, q, W)] = (uint32_t)i;  // padding reads the row itself with a zero coefficient
+        hl[ell_hl_index(i, q, W)] = make_float2(0.0f, 0.0f);
       }
     }
     for (int q = std::min(nA, W); q < n; ++q) {

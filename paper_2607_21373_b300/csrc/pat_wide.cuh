@@ -9,10 +9,15 @@
 // coefficient pairs arrive in one round of broadcast loads and its source rows
 // in two to four rounds of independent gathers.
 //
-// Layout (per direction): col [N][16] uint32, hl [N][16] float2 (hi, lo), the
-// descriptor word of the 8-slot layout, and an overflow CSR holding the
-// stiffness / boundary entries beyond 16 followed by every sensor entry.  A
-// slot past the row's count reads the row itself with a zero coefficient.
+// Layout (per direction): 16 columns (uint32) and 16 (hi, lo) coefficient
+// pairs (float2) per row, interleaved by quads of consecutive rows: the
+// 16-byte chunk q (columns 4q..4q+3, or pairs 2q, 2q+1) of the quad's 4 rows
+// lies in 64 contiguous bytes, so a warp holding 4 consecutive rows (K = 64:
+// 8 lanes per row) fetches one chunk of all 4 with one 64-byte access instead
+// of 4 scattered ones; the descriptor word of the 8-slot layout; an overflow
+// CSR holding the stiffness / boundary entries beyond 16 followed by every
+// sensor entry.  A slot past the row's count holds the row itself with a zero
+// coefficient.
 // Entries are visited in the row's CSR order, hi and lo products accumulated
 // separately, so every variant gives the same bits as the 8-slot and CSR
 // kernels.
@@ -28,8 +33,8 @@ constexpr int kWide = 16;
 __device__ __forceinline__ void wide_entry(const Step3Args<float>& A, int64_t row, int e, uint32_t* col,
                                            float2* c) {
   if (e < kWide) {
-    *col = A.ell_col[row * kWide + e];
-    *c = A.ell_hl[row * kWide + e];
+    *col = A.ell_col[slot_col_at<kWide>(row, e)];
+    *c = A.ell_hl[slot_hl_at<kWide>(row, e)];
   } else {
     const int64_t o = A.ovf_ptr[row] + (e - kWide);
     *col = A.ovf_col[o];
@@ -67,8 +72,9 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;
   const uint32_t Ku = (uint32_t)A.K;
-  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col + row * kWide);
-  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl + row * kWide);
+  // chunk q of this row: cp[4 q] (4 columns), hp[4 q] (2 coefficient pairs)
+  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col) + (row >> 2) * 16 + (row & 3);
+  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl) + (row >> 2) * 32 + (row & 3);
   u64 acc[P], accl[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
@@ -78,7 +84,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     if constexpr (!PB) {
 #pragma unroll
       for (int q = 0; q < kWide / 4; ++q) {
-        const uint4 c = cp[q];
+        const uint4 c = cp[4 * q];
         cols[4 * q] = c.x, cols[4 * q + 1] = c.y, cols[4 * q + 2] = c.z, cols[4 * q + 3] = c.w;
       }
     }
@@ -87,7 +93,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       if constexpr (PB) {
 #pragma unroll
         for (int q = 0; q < NB / 4; ++q) {
-          const uint4 c = cp[h * (NB / 4) + q];
+          const uint4 c = cp[4 * (h * (NB / 4) + q)];
           cols[NB * h + 4 * q] = c.x, cols[NB * h + 4 * q + 1] = c.y;
           cols[NB * h + 4 * q + 2] = c.z, cols[NB * h + 4 * q + 3] = c.w;
         }
@@ -107,7 +113,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       float2 cf[NB];
 #pragma unroll
       for (int q = 0; q < NB; q += 2) {
-        const float4 hq = hp[(NB * h + q) / 2];
+        const float4 hq = hp[4 * ((NB * h + q) / 2)];
         cf[q] = make_float2(hq.x, hq.y);
         cf[q + 1] = make_float2(hq.z, hq.w);
       }
@@ -221,22 +227,22 @@ __global__ void __launch_bounds__(256) step3w1_kernel(const Step3Args<float> A) 
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;
-  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col + row * kWide);
-  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl + row * kWide);
+  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col) + (row >> 2) * 16 + (row & 3);
+  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl) + (row >> 2) * 32 + (row & 3);
   float acc = 0.0f, accl = 0.0f;
   if (A.x) {
     uint32_t cols[kWide];
 #pragma unroll
     for (int q = 0; q < kWide / 4; ++q) {
-      const uint4 c = cp[q];
+      const uint4 c = cp[4 * q];
       cols[4 * q] = c.x, cols[4 * q + 1] = c.y, cols[4 * q + 2] = c.z, cols[4 * q + 3] = c.w;
     }
     float xv[kWide];
 #pragma unroll
-    for (int q = 0; q < kWide; ++q) xv[q] = A.x[cols[q]];
+    for (int q = 0; q < kWide; ++q) xv[q] = q < eA ? A.x[cols[q]] : 0.0f;
 #pragma unroll
     for (int q = 0; q < kWide; q += 2) {
-      const float4 h = hp[q / 2];
+      const float4 h = hp[4 * (q / 2)];
       acc = fmaf(h.x, xv[q], acc);
       accl = fmaf(h.y, xv[q], accl);
       acc = fmaf(h.z, xv[q + 1], acc);
