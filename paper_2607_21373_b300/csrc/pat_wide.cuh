@@ -98,18 +98,11 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
           cols[NB * h + 4 * q + 2] = c.z, cols[NB * h + 4 * q + 3] = c.w;
         }
       }
-      // slots past the row's count hold a zero coefficient: their gathers are
-      // skipped (a zero row adds exactly what the zero coefficient would)
+      // slots past the row's count read the row itself with a zero coefficient:
+      // no per-slot test, the gathers of a round issue back to back
       u64 x[NB][P];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (NB * h + q < eA) {
-          ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
-        } else {
-#pragma unroll
-          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
-        }
-      }
+      for (int q = 0; q < NB; ++q) ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
       float2 cf[NB];
 #pragma unroll
       for (int q = 0; q < NB; q += 2) {
