@@ -98,6 +98,7 @@ FORCED = {
     "w16b8": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8),
     "w16b8c": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8, early=True),
     "w16big": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, big_blocks=True),
+    "w16cs": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
 }
 
 
@@ -311,9 +312,10 @@ def kernel_name(e, adj):
             return "step3w1_kernel<%s> (16 slots, one sample)" % tf
         nb = e.get("gather_batch") or 4
         big = bool(e.get("big_blocks"))
-        return "step3w_persist_kernel<%s> (16 slots, rounds of %d%s%s)" % (
+        return "step3w_persist_kernel<%s> (16 slots, rounds of %d%s%s%s)" % (
             tf, nb, ", columns per round" if e.get("early") else "",
-            ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""))
+            ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
+            ", serial tail" if e.get("tail_serial") else "")
     if packed == 2:
         return "step3t_kernel<8,%s>" % tf
     if packed == 4:

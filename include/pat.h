@@ -495,7 +495,7 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  */
 typedef struct {
   int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent, pdl,
-      wide_loads, l2_hints, gather_batch;
+      wide_loads, l2_hints, gather_batch, tail_serial;
   double us_per_step;
 } pat_tune_entry;
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,
@@ -508,7 +508,9 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
  * fixed-width kernel for meshes with rows wider than 8 entries (the full P1
  * graph), persistent, V = 8 (or V = 1 for K = 1), gather_batch 4 or 8 source
  * rows per round, early = each round's columns loaded with it, big_blocks =
- * 1024-thread blocks, min_blocks 3 with rounds of 8) for direction 0 (forward) or 1
+ * 1024-thread blocks, min_blocks 3 with rounds of 8, tail_serial = a row's
+ * entries past the slots and its boundary corrections walked one at a time
+ * instead of in pairs) for direction 0 (forward) or 1
  * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not
  * exist for this K and precision.  Every variant gives bit-identical results. */
 pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* variant);

@@ -363,7 +363,9 @@ static void launch_wide(Step3Args<float> a, const TuneCfg& c, int64_t threads, c
            : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2>
                        : step3w_persist_kernel<ADJ, 8, false, 256, 2>;
   } else if (c.early) {
-    kern = step3w_persist_kernel<ADJ, 4, true, 256, 4>;
+    kern = c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1> : step3w_persist_kernel<ADJ, 4, true, 256, 4>;
+  } else if (c.tail) {
+    kern = step3w_persist_kernel<ADJ, 4, false, 256, 4, 1>;
   }
   const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
   const int64_t grid =
@@ -1659,6 +1661,8 @@ static const TuneVariant kTuneVariants[] = {
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 8, 1, 1, 0},  // 50 16 slots, rounds of 8, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 8, 3, 1, 0},  // 51 the same, 3 blocks/SM
     {5, 0, 4, 0, 1, 0, 1, 1, 0, 0, 4, 1, 1, 0},  // 52 16 slots, 1024-thread blocks, rounds of 4
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 0},  // 53 16 slots, rounds of 4, tail walked one entry at a time
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 0},  // 54 the same, columns per round
 };
 
 // Whether variant t exists for V samples per thread and K samples on mesh m.
@@ -1666,7 +1670,7 @@ static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, in
   if (t.only_v && V != t.only_v) return false;
   if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1
     return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (V == 8 || (V == 1 && K == 1 && t.batch == 4 &&
-                                                                         !t.early && !t.big));
+                                                                         !t.early && !t.big && !t.hint));
   if ((t.batch || t.hint || t.wide || t.big) && V != 8) return false;
   if (t.persist == 3 && (V != 8 || K / V < 4)) return false;  // staged metadata: <= kStageRows rows per chunk
   if ((t.pf || t.persist) && V == 1) return false;
@@ -1723,6 +1727,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.wide = t.wide;
         g_force.hint = t.hint;
         g_force.batch = t.batch;
+        g_force.tail = t.packed == 5 ? t.hint : 0;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1731,7 +1736,8 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         if (table && n < kTuneTableMax)
           table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
                                     t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
-                                    t.wide, t.hint,  t.batch, (double)us};
+                                    t.wide, t.packed == 5 ? 0 : t.hint, t.batch,
+                                    t.packed == 5 ? t.hint : 0, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

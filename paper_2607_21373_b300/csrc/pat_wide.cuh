@@ -54,7 +54,7 @@ __device__ __forceinline__ void wide_inj(const Step3Args<float>& A, int64_t row,
 // 8-slot kernel), NB source rows gathered per round.  PB: each round's columns
 // and coefficient pairs are loaded with it (fewer live registers); otherwise
 // all 16 columns arrive up front and the coefficient pairs per round.
-template <bool ADJ, int NB, bool PB>
+template <bool ADJ, int NB, bool PB, int TB = 2>
 __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t) {
   constexpr int V = 8, P = 4;
   static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
@@ -123,7 +123,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     // entries beyond the 16 slots, then the xp parts of the boundary entries
     // (boundary entries act on w_j = x_j - xp_j)
     const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
-    fixed_row_tail<V, false, kWide>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
+    fixed_row_tail<V, false, kWide, TB>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
   }
   float src[V];
 #pragma unroll
@@ -172,7 +172,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // Persistent grid-stride form (as the 8-slot persistent kernel): a resident
 // wave of blocks whose warps walk 32-thread chunks with the grid's stride,
 // launched as a programmatic dependent of the previous step.
-template <bool ADJ, int NB, bool PB, int BS, int MINB>
+template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
   const int wpb = BS >> 5;
   const int64_t S = (int64_t)gridDim.x * wpb;
   for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S)
-    step3w_row<ADJ, NB, PB>(A, c * 32 + lane);
+    step3w_row<ADJ, NB, PB, TB>(A, c * 32 + lane);
 }
 
 // Uneven batch: one persistent grid over the 32-thread chunks of several jobs
