@@ -99,6 +99,8 @@ FORCED = {
     "w16b8c": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=8, early=True),
     "w16big": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, big_blocks=True),
     "w16cs": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
+    "w16r": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4),
+    "w16rc": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True),
 }
 
 
@@ -307,13 +309,13 @@ def kernel_name(e, adj):
     """Readable name of the step-kernel variant an autotune entry describes."""
     tf = "true" if adj else "false"
     packed = e.get("packed")
-    if packed == 5:
+    if packed in (5, 6):
         if e.get("V") == 1:
             return "step3w1_kernel<%s> (16 slots, one sample)" % tf
         nb = e.get("gather_batch") or 4
         big = bool(e.get("big_blocks"))
-        return "step3w_persist_kernel<%s> (16 slots, rounds of %d%s%s%s)" % (
-            tf, nb, ", columns per round" if e.get("early") else "",
+        return "step3w_persist_kernel<%s> (16 slots%s, rounds of %d%s%s%s)" % (
+            tf, " row-major" if packed == 6 else "", nb, ", columns per round" if e.get("early") else "",
             ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
             ", serial tail" if e.get("tail_serial") else "")
     if packed == 2:

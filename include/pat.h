@@ -510,7 +510,8 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
  * rows per round, early = each round's columns loaded with it, big_blocks =
  * 1024-thread blocks, min_blocks 3 with rounds of 8, tail_serial = a row's
  * entries past the slots and its boundary corrections walked one at a time
- * instead of in pairs) for direction 0 (forward) or 1
+ * instead of in pairs; packed 6 = the same kernel reading a row-major copy of
+ * the 16 slots instead of the quad-interleaved one, V = 8 only) for direction 0 (forward) or 1
  * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not
  * exist for this K and precision.  Every variant gives bit-identical results. */
 pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* variant);

@@ -55,7 +55,8 @@ void free_device(DeviceMesh& m) {
                  (void**)&m.fwd.w16_col, (void**)&m.fwd.w16_hl, (void**)&m.fwd.w16_ovf_ptr,
                  (void**)&m.fwd.w16_ovf_col, (void**)&m.fwd.w16_ovf_hl, (void**)&m.adj3.w16_col,
                  (void**)&m.adj3.w16_hl, (void**)&m.adj3.w16_ovf_ptr, (void**)&m.adj3.w16_ovf_col,
-                 (void**)&m.adj3.w16_ovf_hl,
+                 (void**)&m.adj3.w16_ovf_hl, (void**)&m.fwd.w16r_col, (void**)&m.fwd.w16r_hl,
+                 (void**)&m.adj3.w16r_col, (void**)&m.adj3.w16r_hl,
                  &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
                  &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
                  (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
@@ -317,6 +318,16 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
   } else {
     s = upload(col, &d.w16_col);
     if (!s) s = upload(hl, &d.w16_hl);
+    // the row-major copy of the same slots (the quad layout's alternative)
+    std::vector<uint32_t> colr(N * W);
+    std::vector<float2> hlr(N * W);
+    for (int64_t i = 0; i < N; ++i)
+      for (int q = 0; q < W; ++q) {
+        colr[i * W + q] = col[ell_col_index(i, q, W)];
+        hlr[i * W + q] = hl[ell_hl_index(i, q, W)];
+      }
+    if (!s) s = upload(colr, &d.w16r_col);
+    if (!s) s = upload(hlr, &d.w16r_hl);
     if (!s) s = upload(optr, &d.w16_ovf_ptr);
     if (!s) s = upload(ocol, &d.w16_ovf_col);
     if (!s) s = upload(ohl, &d.w16_ovf_hl);
@@ -1073,8 +1084,10 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   }
   if (bad_K(K, "pat_select_variant")) return PAT_EINVAL;
   const bool f32s = mesh->d.prec == PAT_F32 && mesh->d.split;
-  if (v->packed == 5) {  // 16-slot fixed-width rows
-    const bool ok = f32s && mesh->d.fwd.w16_col && K % 8 == 0 ? v->V == 8 : (f32s && mesh->d.fwd.w16_col && K == 1 && v->V == 1);
+  if (v->packed == 5 || v->packed == 6) {  // 16-slot fixed-width rows (quad-interleaved / row-major)
+    const bool ok = f32s && mesh->d.fwd.w16_col && K % 8 == 0
+                        ? v->V == 8
+                        : (f32s && mesh->d.fwd.w16_col && K == 1 && v->V == 1 && v->packed == 5);
     const int nb = v->gather_batch ? v->gather_batch : 4;
     if (!ok || (nb != 4 && nb != 8) || (v->min_blocks != 1 && !(v->min_blocks == 3 && nb == 8))) {
       set_error("pat_select_variant: 16-slot variant V=%d gather_batch=%d min_blocks=%d is not available for K=%d on "
@@ -1084,7 +1097,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     }
     TuneCfg c;
     c.V = v->V;
-    c.packed = 5;
+    c.packed = v->packed;
     c.persist = 1;
     c.pdl = v->pdl;
     c.batch = nb;

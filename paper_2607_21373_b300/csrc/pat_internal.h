@@ -89,8 +89,10 @@ struct DevCSR {
   float2* ovf_hl = nullptr;
   // the same with 16 fixed slots per row (built when some row has more than 8
   // stiffness / boundary entries: the full P1 graph, unstructured meshes)
-  uint32_t* w16_col = nullptr;
+  uint32_t* w16_col = nullptr;   // quad-interleaved
   float2* w16_hl = nullptr;
+  uint32_t* w16r_col = nullptr;  // the same slots row-major ([row][16])
+  float2* w16r_hl = nullptr;
   int32_t* w16_ovf_ptr = nullptr;
   uint32_t* w16_ovf_col = nullptr;
   float2* w16_ovf_hl = nullptr;

@@ -350,23 +350,29 @@ static void launch_persist(Step3Args<float> a, const TuneCfg& c, int64_t threads
 // blocks as a programmatic dependent of the previous step.  c.batch: source
 // rows per gather round (4 or 8); c.early: each round's columns loaded with
 // it; c.big: 1024-thread blocks; c.minb: 3 asks for 3 resident blocks of 256.
+template <bool ADJ, bool QUAD>
+static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int64_t) {
+  *bs = 256;
+  if (c.big) {
+    *bs = 1024;
+    return step3w_persist_kernel<ADJ, 4, true, 1024, 1, 2, QUAD>;
+  }
+  if (c.batch == 8) {
+    return c.minb == 3 ? step3w_persist_kernel<ADJ, 8, true, 256, 3, 2, QUAD>
+           : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2, 2, QUAD>
+                       : step3w_persist_kernel<ADJ, 8, false, 256, 2, 2, QUAD>;
+  }
+  if (c.early)
+    return c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, QUAD>;
+  return c.tail ? step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, QUAD>;
+}
+
 template <bool ADJ>
 static void launch_wide(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
   const int64_t n_chunks = (threads + 31) / 32;
   int bs = 256;
-  void (*kern)(const Step3Args<float>, int64_t) = step3w_persist_kernel<ADJ, 4, false, 256, 4>;
-  if (c.big) {
-    bs = 1024;
-    kern = step3w_persist_kernel<ADJ, 4, true, 1024, 1>;
-  } else if (c.batch == 8) {
-    kern = c.minb == 3 ? step3w_persist_kernel<ADJ, 8, true, 256, 3>
-           : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2>
-                       : step3w_persist_kernel<ADJ, 8, false, 256, 2>;
-  } else if (c.early) {
-    kern = c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1> : step3w_persist_kernel<ADJ, 4, true, 256, 4>;
-  } else if (c.tail) {
-    kern = step3w_persist_kernel<ADJ, 4, false, 256, 4, 1>;
-  }
+  void (*kern)(const Step3Args<float>, int64_t) =
+      c.packed == 6 ? pick_wide<ADJ, false>(c, &bs) : pick_wide<ADJ, true>(c, &bs);
   const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
   const int64_t grid =
       std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + bs / 32 - 1) / (bs / 32)));
@@ -397,9 +403,9 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
   }
   if constexpr (sizeof(T) == 4 && SPLIT && (V == 1 || V == 8)) {
     const DevCSR& E = ADJ ? m.adj3 : m.fwd;
-    if (c.packed == 5 && E.w16_col && (V == 8 || a.K == 1)) {  // 16-slot fixed-width rows
-      a.ell_col = E.w16_col;
-      a.ell_hl = E.w16_hl;
+    if ((c.packed == 5 || (c.packed == 6 && V == 8)) && E.w16_col && (V == 8 || a.K == 1)) {  // 16-slot rows
+      a.ell_col = c.packed == 6 ? E.w16r_col : E.w16_col;
+      a.ell_hl = c.packed == 6 ? E.w16r_hl : E.w16_hl;
       a.ell_desc = E.ell_desc;
       a.ovf_ptr = E.w16_ovf_ptr;
       a.ovf_col = E.w16_ovf_col;
@@ -1663,11 +1669,17 @@ static const TuneVariant kTuneVariants[] = {
     {5, 0, 4, 0, 1, 0, 1, 1, 0, 0, 4, 1, 1, 0},  // 52 16 slots, 1024-thread blocks, rounds of 4
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 0},  // 53 16 slots, rounds of 4, tail walked one entry at a time
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 0},  // 54 the same, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},  // 55 16 slots row-major, rounds of 4
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8},  // 56 16 slots row-major, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8},  // 57 16 slots row-major, serial tail
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8},  // 58 16 slots row-major, columns per round, serial tail
+    {6, 0, 4, 0, 1, 0, 1, 1, 0, 0, 4, 1, 1, 8},  // 59 16 slots row-major, 1024-thread blocks
 };
 
 // Whether variant t exists for V samples per thread and K samples on mesh m.
 static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, int K) {
   if (t.only_v && V != t.only_v) return false;
+  if (t.packed == 6) return m.prec == PAT_F32 && m.split && m.fwd.w16r_col && V == 8;
   if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1
     return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (V == 8 || (V == 1 && K == 1 && t.batch == 4 &&
                                                                          !t.early && !t.big && !t.hint));
@@ -1727,7 +1739,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.wide = t.wide;
         g_force.hint = t.hint;
         g_force.batch = t.batch;
-        g_force.tail = t.packed == 5 ? t.hint : 0;
+        g_force.tail = t.packed >= 5 ? t.hint : 0;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1736,8 +1748,8 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         if (table && n < kTuneTableMax)
           table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
                                     t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
-                                    t.wide, t.packed == 5 ? 0 : t.hint, t.batch,
-                                    t.packed == 5 ? t.hint : 0, (double)us};
+                                    t.wide, t.packed >= 5 ? 0 : t.hint, t.batch,
+                                    t.packed >= 5 ? t.hint : 0, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

@@ -400,20 +400,20 @@ __device__ __forceinline__ void st_run_pack(float* p, int64_t hs, const Pack<flo
 // walk would: the boundary rows of a cube carry up to 18 entries and 7
 // corrections, and a serial walk makes them several times slower than an
 // interior row and holds up the warp that has one.
-// Positions of slot e of a fixed-width row: row-major for 8 slots, quad-
-// interleaved for 16 (see the 16-slot layout in pat_wide.cuh).
-template <int WD>
+// Positions of slot e of a fixed-width row of WD slots: row-major, or (QUAD,
+// 16 slots) interleaved by quads of rows (see the 16-slot layout in pat_wide.cuh).
+template <int WD, bool QUAD>
 __device__ __forceinline__ int64_t slot_col_at(int64_t row, int e) {
-  if constexpr (WD == 16) return (row >> 2) * 64 + (e >> 2) * 16 + (row & 3) * 4 + (e & 3);
+  if constexpr (QUAD) return (row >> 2) * (4 * WD) + (e >> 2) * 16 + (row & 3) * 4 + (e & 3);
   return row * WD + e;
 }
-template <int WD>
+template <int WD, bool QUAD>
 __device__ __forceinline__ int64_t slot_hl_at(int64_t row, int e) {
-  if constexpr (WD == 16) return (row >> 2) * 64 + (e >> 1) * 8 + (row & 3) * 2 + (e & 1);
+  if constexpr (QUAD) return (row >> 2) * (4 * WD) + (e >> 1) * 8 + (row & 3) * 2 + (e & 1);
   return row * WD + e;
 }
 
-template <int V, bool W, int WD, int TB = 2>
+template <int V, bool W, int WD, int TB = 2, bool QUAD = false>
 __device__ __forceinline__ void fixed_row_tail(const Step3Args<float>& A, int64_t row, int eA, int nb,
                                                const float* xk, const float* pk, int64_t hs, uint32_t Ku,
                                                u64 (&acc)[V / 2], u64 (&accl)[V / 2]) {
@@ -422,8 +422,8 @@ __device__ __forceinline__ void fixed_row_tail(const Step3Args<float>& A, int64_
   const int64_t o0 = (int64_t)A.ovf_ptr[row] - WD;  // overflow index of entry e >= WD: o0 + e
   auto fetch = [&](int e, uint32_t* col, float2* c) {
     if (e < WD) {
-      *col = A.ell_col[slot_col_at<WD>(row, e)];
-      *c = A.ell_hl[slot_hl_at<WD>(row, e)];
+      *col = A.ell_col[slot_col_at<WD, QUAD>(row, e)];
+      *c = A.ell_hl[slot_hl_at<WD, QUAD>(row, e)];
     } else {
       *col = A.ovf_col[o0 + e];
       *c = A.ovf_hl[o0 + e];

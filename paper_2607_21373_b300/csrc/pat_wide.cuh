@@ -29,12 +29,12 @@ namespace pat {
 
 constexpr int kWide = 16;
 
-// Stiffness / boundary entry e (< the row's count eA) of a 16-slot row.
+// Stiffness / boundary entry e (< the row's count eA) of a quad-interleaved 16-slot row.
 __device__ __forceinline__ void wide_entry(const Step3Args<float>& A, int64_t row, int e, uint32_t* col,
                                            float2* c) {
   if (e < kWide) {
-    *col = A.ell_col[slot_col_at<kWide>(row, e)];
-    *c = A.ell_hl[slot_hl_at<kWide>(row, e)];
+    *col = A.ell_col[slot_col_at<kWide, true>(row, e)];
+    *c = A.ell_hl[slot_hl_at<kWide, true>(row, e)];
   } else {
     const int64_t o = A.ovf_ptr[row] + (e - kWide);
     *col = A.ovf_col[o];
@@ -54,7 +54,7 @@ __device__ __forceinline__ void wide_inj(const Step3Args<float>& A, int64_t row,
 // 8-slot kernel), NB source rows gathered per round.  PB: each round's columns
 // and coefficient pairs are loaded with it (fewer live registers); otherwise
 // all 16 columns arrive up front and the coefficient pairs per round.
-template <bool ADJ, int NB, bool PB, int TB = 2>
+template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true>
 __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t) {
   constexpr int V = 8, P = 4;
   static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
@@ -72,9 +72,10 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;
   const uint32_t Ku = (uint32_t)A.K;
-  // chunk q of this row: cp[4 q] (4 columns), hp[4 q] (2 coefficient pairs)
-  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col) + (row >> 2) * 16 + (row & 3);
-  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl) + (row >> 2) * 32 + (row & 3);
+  // chunk q of this row: cp[CS q] (4 columns), hp[CS q] (2 coefficient pairs)
+  constexpr int CS = QUAD ? 4 : 1;
+  const uint4* cp = reinterpret_cast<const uint4*>(A.ell_col) + (QUAD ? (row >> 2) * 16 + (row & 3) : row * 4);
+  const float4* hp = reinterpret_cast<const float4*>(A.ell_hl) + (QUAD ? (row >> 2) * 32 + (row & 3) : row * 8);
   u64 acc[P], accl[P];
 #pragma unroll
   for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
@@ -84,7 +85,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     if constexpr (!PB) {
 #pragma unroll
       for (int q = 0; q < kWide / 4; ++q) {
-        const uint4 c = cp[4 * q];
+        const uint4 c = cp[CS * q];
         cols[4 * q] = c.x, cols[4 * q + 1] = c.y, cols[4 * q + 2] = c.z, cols[4 * q + 3] = c.w;
       }
     }
@@ -93,7 +94,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       if constexpr (PB) {
 #pragma unroll
         for (int q = 0; q < NB / 4; ++q) {
-          const uint4 c = cp[4 * (h * (NB / 4) + q)];
+          const uint4 c = cp[CS * (h * (NB / 4) + q)];
           cols[NB * h + 4 * q] = c.x, cols[NB * h + 4 * q + 1] = c.y;
           cols[NB * h + 4 * q + 2] = c.z, cols[NB * h + 4 * q + 3] = c.w;
         }
@@ -106,7 +107,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       float2 cf[NB];
 #pragma unroll
       for (int q = 0; q < NB; q += 2) {
-        const float4 hq = hp[4 * ((NB * h + q) / 2)];
+        const float4 hq = hp[CS * ((NB * h + q) / 2)];
         cf[q] = make_float2(hq.x, hq.y);
         cf[q + 1] = make_float2(hq.z, hq.w);
       }
@@ -123,7 +124,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     // entries beyond the 16 slots, then the xp parts of the boundary entries
     // (boundary entries act on w_j = x_j - xp_j)
     const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
-    fixed_row_tail<V, false, kWide, TB>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
+    fixed_row_tail<V, false, kWide, TB, QUAD>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
   }
   float src[V];
 #pragma unroll
@@ -172,7 +173,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // Persistent grid-stride form (as the 8-slot persistent kernel): a resident
 // wave of blocks whose warps walk 32-thread chunks with the grid's stride,
 // launched as a programmatic dependent of the previous step.
-template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2>
+template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
   const int wpb = BS >> 5;
   const int64_t S = (int64_t)gridDim.x * wpb;
   for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S)
-    step3w_row<ADJ, NB, PB, TB>(A, c * 32 + lane);
+    step3w_row<ADJ, NB, PB, TB, QUAD>(A, c * 32 + lane);
 }
 
 // Uneven batch: one persistent grid over the 32-thread chunks of several jobs
