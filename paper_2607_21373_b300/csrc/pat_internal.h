@@ -132,6 +132,7 @@ struct TuneCfg {
   int batch = 0;   // persistent kernel, V = 8: source rows in flight per batch (0: 4 with the row's
                    // metadata loaded up front; 8; 2 or 4 with each batch's metadata loaded with it)
   int tail = 0;    // 16-slot kernel: 1 walks a row's tail entries one at a time (0: in pairs)
+  int own = 0;     // 16-slot kernel: 1 copies the row's own x_s, x_{s-1} to shared memory by cp.async
 };
 
 struct DeviceMesh {

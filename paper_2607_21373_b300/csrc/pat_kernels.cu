@@ -362,6 +362,9 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
            : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2, 2, QUAD>
                        : step3w_persist_kernel<ADJ, 8, false, 256, 2, 2, QUAD>;
   }
+  if (c.own)
+    return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, true>
+                   : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, true>;
   if (c.early)
     return c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, QUAD>;
   return c.tail ? step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, QUAD>;
@@ -1610,7 +1613,7 @@ static pat_status probe_t(const DeviceMesh& m, int K, char* ws, int n_probe, int
 constexpr int kTuneTableMax = 256;  // entries pat_autotune writes at most
 
 struct TuneVariant {
-  int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v;
+  int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v, own = 0;
 };
 static const TuneVariant kTuneVariants[] = {
     // packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v
@@ -1674,6 +1677,9 @@ static const TuneVariant kTuneVariants[] = {
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8},  // 57 16 slots row-major, serial tail
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8},  // 58 16 slots row-major, columns per round, serial tail
     {6, 0, 4, 0, 1, 0, 1, 1, 0, 0, 4, 1, 1, 8},  // 59 16 slots row-major, 1024-thread blocks
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1},  // 60 16 slots row-major, serial tail, own rows by cp.async
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1},  // 61 the same, columns per round
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1},  // 62 16 slots quad, columns per round, serial tail, own async
 };
 
 // Whether variant t exists for V samples per thread and K samples on mesh m.
@@ -1740,6 +1746,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.hint = t.hint;
         g_force.batch = t.batch;
         g_force.tail = t.packed >= 5 ? t.hint : 0;
+        g_force.own = t.packed >= 5 ? t.own : 0;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1749,7 +1756,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
           table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
                                     t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
                                     t.wide, t.packed >= 5 ? 0 : t.hint, t.batch,
-                                    t.packed >= 5 ? t.hint : 0, (double)us};
+                                    t.packed >= 5 ? t.hint : 0, t.own, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

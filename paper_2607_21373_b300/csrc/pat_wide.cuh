@@ -54,8 +54,15 @@ __device__ __forceinline__ void wide_inj(const Step3Args<float>& A, int64_t row,
 // 8-slot kernel), NB source rows gathered per round.  PB: each round's columns
 // and coefficient pairs are loaded with it (fewer live registers); otherwise
 // all 16 columns arrive up front and the coefficient pairs per round.
-template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true>
-__device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t) {
+//
+// OA: the row's own values of x_s and x_{s-1} (the last loads the update
+// needs) are copied global -> shared memory by cp.async when the row starts,
+// so they arrive while the gathers run instead of costing one more round trip
+// after them; `own` is this thread's 4 x 16-byte slot (4 float4 at a stride of
+// `own_stride` float4).
+template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true, bool OA = false>
+__device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t, float4* own = nullptr,
+                                           int own_stride = 0) {
   constexpr int V = 8, P = 4;
   static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
   const int KV = A.K / V;
@@ -68,6 +75,17 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
   const int64_t hs = A.K / 2;
   const int64_t base = (int64_t)kv * 4;
   const int64_t off = row * A.K + base;
+  if constexpr (OA) {
+    if (A.x) {
+      cp_async16(own, A.x + off);
+      cp_async16(own + own_stride, A.x + off + hs);
+    }
+    if (A.prev_mode == 0) {
+      cp_async16_cg(own + 2 * own_stride, A.xp + off);
+      cp_async16_cg(own + 3 * own_stride, A.xp + off + hs);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;
@@ -148,14 +166,25 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     }
   }
   Pack<float, V> xi, xpi, xo;
+  if constexpr (OA) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  auto unpack4 = [](float4 a, float4 b, Pack<float, V>& o) {
+    o.v[0] = a.x, o.v[1] = a.y, o.v[2] = a.z, o.v[3] = a.w;
+    o.v[4] = b.x, o.v[5] = b.y, o.v[6] = b.z, o.v[7] = b.w;
+  };
   if (A.x) {
-    xi = ld_run_pack<V>(A.x + off, hs);
+    if constexpr (OA)
+      unpack4(own[0], own[own_stride], xi);
+    else
+      xi = ld_run_pack<V>(A.x + off, hs);
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
   }
   if (A.prev_mode == 0) {
-    xpi = ld_run_pack<V>(A.xp + off, hs);
+    if constexpr (OA)
+      unpack4(own[2 * own_stride], own[3 * own_stride], xpi);
+    else
+      xpi = ld_run_pack<V>(A.xp + off, hs);
   } else {
 #pragma unroll
     for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
@@ -173,15 +202,18 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // Persistent grid-stride form (as the 8-slot persistent kernel): a resident
 // wave of blocks whose warps walk 32-thread chunks with the grid's stride,
 // launched as a programmatic dependent of the previous step.
-template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true>
+template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, bool OA = false>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
+  // per-thread slots of the own-row copies, slot q of thread i at [q][i]
+  // (consecutive threads contiguous: conflict-free 16-byte accesses)
+  __shared__ float4 own_buf[OA ? 4 * BS : 1];
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31;
   const int wpb = BS >> 5;
   const int64_t S = (int64_t)gridDim.x * wpb;
   for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S)
-    step3w_row<ADJ, NB, PB, TB, QUAD>(A, c * 32 + lane);
+    step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA ? threadIdx.x : 0), BS);
 }
 
 // Uneven batch: one persistent grid over the 32-thread chunks of several jobs
