@@ -79,7 +79,8 @@ def parse(argv=None):
     ap.add_argument("--tune-log", default="", help="write the autotuner's full timing table (JSON) to this file")
     ap.add_argument("--solver", default="cgls", choices=["cgls", "lsqr"],
                     help="least-squares solver of every RTO sample (the configured workload names CGLS)")
-    ap.add_argument("--variant", default="", help="force a step-kernel variant for K: " + " | ".join(sorted(FORCED)))
+    ap.add_argument("--variant", default="", help="force a step-kernel variant for K (FWD or FWD,ADJ): "
+                    + " | ".join(sorted(FORCED)))
     ap.add_argument("--workload", default="rto", choices=["rto", "uneven", "matern"],
                     help="rto: one mesh, K samples per batch (default); uneven: six cubes 16^3..58^3 cells with "
                          "K 256..8 and N_T 276..1000 in one grouped solve per step (k = 50); matern: the rto "
@@ -102,6 +103,7 @@ FORCED = {
     "w16r": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4),
     "w16rc": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True),
     "w16ro": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True),
+    "w16rcs": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
 }
 
 
@@ -386,11 +388,13 @@ def run_ours(a, rank, world, local_rank, dist):
     two_level = bool(mesh_flags(a) & MESH_TWO_LEVEL)
     # pick the step-kernel variant per direction for both sample counts (not timed)
     tune = {}
-    forced = FORCED.get(a.variant)
+    names = a.variant.split(",") if a.variant else []
+    forced = [FORCED[n] for n in names] if names else None
     if forced:
-        for d in ("fwd", "adj"):
-            mesh.select_variant(K, d, **forced)
-        tune["K%d" % K] = [dict(dict(direction=d, us_per_step=0.0), **forced) for d in ("fwd", "adj")]
+        forced = forced if len(forced) == 2 else forced * 2
+        for d, v in zip(("fwd", "adj"), forced):
+            mesh.select_variant(K, d, **v)
+        tune["K%d" % K] = [dict(dict(direction=d, us_per_step=0.0), **v) for d, v in zip(("fwd", "adj"), forced)]
     elif a.autotune and not two_level:
         tune["K%d" % K] = mesh.autotune(K, n_probe=30)
     if a.autotune and not two_level and a.plain_steps > 0:

@@ -78,24 +78,26 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// In-place radix-2 FFT of the KC lines in sh[ng][KC] (already bit-reversed);
-// inverse uses the conjugate twiddles.
-__device__ __forceinline__ void fft_stages(float2* sh, const float2* tw, int ng, int log2ng, int KC, bool inverse) {
-  const int nb = (ng / 2) * KC;  // butterflies per stage
+// In-place radix-2 FFT of the KC = 2^lkc lines in sh[ng][KC] (already
+// bit-reversed); inverse uses the conjugate twiddles.  Index arithmetic by
+// shifts and masks (n_g and KC are powers of two).
+__device__ __forceinline__ void fft_stages(float2* sh, const float2* tw, int log2ng, int lkc, bool inverse) {
+  const int nb = 1 << (log2ng - 1 + lkc);  // butterflies per stage
+  const int kmask = (1 << lkc) - 1;
   for (int st = 1; st <= log2ng; ++st) {
-    const int half = 1 << (st - 1);
-    const int tstep = ng >> st;  // twiddle index stride
+    const int hmask = (1 << (st - 1)) - 1;
+    const int tshift = log2ng - st;  // twiddle index stride n_g / 2^st
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int k = b % KC;
-      const int j = b / KC;                 // butterfly index within the line, 0 .. ng/2-1
-      const int grp = j / half, pos = j - grp * half;
-      const int i0 = grp * 2 * half + pos, i1 = i0 + half;
-      float2 w = tw[pos * tstep];
+      const int k = b & kmask;
+      const int j = b >> lkc;  // butterfly index within the line, 0 .. ng/2-1
+      const int pos = j & hmask;
+      const int i0 = ((j >> (st - 1)) << st) + pos, i1 = i0 + hmask + 1;
+      float2 w = tw[pos << tshift];
       if (inverse) w.y = -w.y;
-      const float2 a = sh[i0 * KC + k];
-      const float2 c = cmul(w, sh[i1 * KC + k]);
-      sh[i0 * KC + k] = make_float2(a.x + c.x, a.y + c.y);
-      sh[i1 * KC + k] = make_float2(a.x - c.x, a.y - c.y);
+      const float2 a = sh[(i0 << lkc) + k];
+      const float2 c = cmul(w, sh[(i1 << lkc) + k]);
+      sh[(i0 << lkc) + k] = make_float2(a.x + c.x, a.y + c.y);
+      sh[(i1 << lkc) + k] = make_float2(a.x - c.x, a.y - c.y);
     }
     __syncthreads();
   }
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(const void* in, void* out
                                                        int KC, int axis, const float2* __restrict__ tw,
                                                        const float* __restrict__ filt, float scale) {
   extern __shared__ float2 sh[];
+  const int lkc = __ffs(KC) - 1, kmask = KC - 1;
   const int chunks = K / KC;
   const int64_t line = blockIdx.x / chunks;
   const int kc0 = (int)(blockIdx.x - line * chunks) * KC;
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(const void* in, void* out
   }
   const int n = ng * KC;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int j = e / KC, k = e - j * KC;
+    const int j = e >> lkc, k = e & kmask;
     const int64_t off = (g0 + (int64_t)j * stride) * K + kc0 + k;
     float2 v;
     if constexpr (MODE == 0) {
@@ -137,36 +140,36 @@ __global__ void __launch_bounds__(256) fft_pass_kernel(const void* in, void* out
     } else {
       v = static_cast<const float2*>(in)[off];
     }
-    sh[bitrev(j, log2ng) * KC + k] = v;
+    sh[(bitrev(j, log2ng) << lkc) + k] = v;
   }
   __syncthreads();
-  fft_stages(sh, tw, ng, log2ng, KC, MODE >= 3);
+  fft_stages(sh, tw, log2ng, lkc, MODE >= 3);
   if constexpr (MODE == 2) {
     // multiply by sqrt(S) at (a, b, j), then inverse along z
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const int j = e / KC, k = e - j * KC;
+      const int j = e >> lkc, k = e & kmask;
       const float f = filt[g0 + j];
-      const float2 v = sh[j * KC + k];
-      sh[j * KC + k] = make_float2(f * v.x, f * v.y);
+      const float2 v = sh[(j << lkc) + k];
+      sh[(j << lkc) + k] = make_float2(f * v.x, f * v.y);
     }
     __syncthreads();
     // bit-reverse the filtered line for the inverse transform (in place, pairwise swaps)
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      const int j = e / KC, k = e - j * KC;
+      const int j = e >> lkc, k = e & kmask;
       const int r = bitrev(j, log2ng);
       if (r > j) {
-        const float2 t = sh[j * KC + k];
-        sh[j * KC + k] = sh[r * KC + k];
-        sh[r * KC + k] = t;
+        const float2 t = sh[(j << lkc) + k];
+        sh[(j << lkc) + k] = sh[(r << lkc) + k];
+        sh[(r << lkc) + k] = t;
       }
     }
     __syncthreads();
-    fft_stages(sh, tw, ng, log2ng, KC, true);
+    fft_stages(sh, tw, log2ng, lkc, true);
   }
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const int j = e / KC, k = e - j * KC;
+    const int j = e >> lkc, k = e & kmask;
     const int64_t off = (g0 + (int64_t)j * stride) * K + kc0 + k;
-    const float2 v = sh[j * KC + k];
+    const float2 v = sh[(j << lkc) + k];
     if constexpr (MODE == 4) {
       static_cast<float*>(out)[off] = scale * v.x + (addend ? addend[off] : 0.0f);
     } else {
