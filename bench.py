@@ -104,6 +104,8 @@ FORCED = {
     "w16rc": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True),
     "w16ro": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True),
     "w16rcs": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
+    "pairs": dict(V=8, packed=7, persistent=1, pdl=True),
+    "pairs3": dict(V=8, packed=7, persistent=1, pdl=True, min_blocks=3),
 }
 
 
@@ -312,6 +314,8 @@ def kernel_name(e, adj):
     """Readable name of the step-kernel variant an autotune entry describes."""
     tf = "true" if adj else "false"
     packed = e.get("packed")
+    if packed == 7:
+        return "step3u_persist_kernel<%s> (row pairs, %d blocks/SM)" % (tf, 3 if e.get("min_blocks") == 3 else 2)
     if packed in (5, 6):
         if e.get("V") == 1:
             return "step3w1_kernel<%s> (16 slots, one sample)" % tf

@@ -56,7 +56,9 @@ void free_device(DeviceMesh& m) {
                  (void**)&m.fwd.w16_ovf_col, (void**)&m.fwd.w16_ovf_hl, (void**)&m.adj3.w16_col,
                  (void**)&m.adj3.w16_hl, (void**)&m.adj3.w16_ovf_ptr, (void**)&m.adj3.w16_ovf_col,
                  (void**)&m.adj3.w16_ovf_hl, (void**)&m.fwd.w16r_col, (void**)&m.fwd.w16r_hl,
-                 (void**)&m.adj3.w16r_col, (void**)&m.adj3.w16r_hl,
+                 (void**)&m.adj3.w16r_col, (void**)&m.adj3.w16r_hl, (void**)&m.fwd.pair_col,
+                 (void**)&m.fwd.pair_cf, (void**)&m.fwd.pair_n, (void**)&m.adj3.pair_col, (void**)&m.adj3.pair_cf,
+                 (void**)&m.adj3.pair_n,
                  &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
                  &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
                  (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
@@ -335,6 +337,73 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
   return s;
 }
 
+// Row pairs of a three-level CSR (see DevCSR): per pair the merge of the two
+// rows' stiffness entries by column, then of their boundary entries, with both
+// rows' coefficient pairs per slot.  Returns PAT_OK without building anything
+// when some pair needs more than kPairSlots slots (the pair kernel is then not
+// offered for the mesh).
+pat_status build_pairs(const HostRows& R, const std::vector<uint8_t>& nb, const std::vector<uint8_t>& ninj,
+                       DevCSR& d) {
+  const int64_t N = (int64_t)R.ptr.size() - 1, P = (N + 1) / 2, U = kPairSlots;
+  std::vector<uint32_t> col(P * U);
+  std::vector<float4> cf(P * U);
+  std::vector<uint8_t> cnt(P);
+  auto split = [](double v) {
+    const float h = (float)v;
+    return std::make_pair(h, (float)(v - (double)h));
+  };
+  struct Slot {
+    uint32_t col;
+    double a, b;
+  };
+  std::vector<Slot> part, all;
+  for (int64_t p = 0; p < P; ++p) {
+    const int64_t ra = 2 * p, rb = 2 * p + 1;
+    auto range = [&](int64_t r, bool boundary, int32_t* lo, int32_t* hi) {
+      if (r >= N) {
+        *lo = *hi = 0;
+        return;
+      }
+      const int32_t e0 = R.ptr[r], eA = R.ptr[r + 1] - (int32_t)ninj[r];
+      *lo = boundary ? eA - (int32_t)nb[r] : e0;
+      *hi = boundary ? eA : eA - (int32_t)nb[r];
+    };
+    all.clear();
+    for (int boundary = 0; boundary < 2; ++boundary) {
+      int32_t a0, a1, b0, b1;
+      range(ra, boundary != 0, &a0, &a1);
+      range(rb, boundary != 0, &b0, &b1);
+      part.clear();
+      while (a0 < a1 || b0 < b1) {
+        const uint32_t ca = a0 < a1 ? (R.col[a0] & kIdxMask) : 0xffffffffu;
+        const uint32_t cb = b0 < b1 ? (R.col[b0] & kIdxMask) : 0xffffffffu;
+        Slot sl{std::min(ca, cb), 0.0, 0.0};
+        if (ca <= cb) sl.a = R.val[a0++];
+        if (cb <= ca) sl.b = R.val[b0++];
+        part.push_back(sl);
+      }
+      all.insert(all.end(), part.begin(), part.end());
+    }
+    if ((int64_t)all.size() > U) return PAT_OK;  // does not fit: no pair copy
+    const int64_t used = ((int64_t)all.size() + 3) / 4 * 4;
+    cnt[p] = (uint8_t)used;
+    for (int64_t q = 0; q < U; ++q) {
+      if (q < (int64_t)all.size()) {
+        const auto ha = split(all[q].a), hb = split(all[q].b);
+        col[p * U + q] = all[q].col;
+        cf[p * U + q] = make_float4(ha.first, ha.second, hb.first, hb.second);
+      } else {
+        col[p * U + q] = (uint32_t)ra;  // padding reads row 2p with zero coefficients
+        cf[p * U + q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+    }
+  }
+  pat_status s = upload(col, &d.pair_col);
+  if (!s) s = upload(cf, &d.pair_cf);
+  if (!s) s = upload(cnt, &d.pair_n);
+  return s;
+}
+
 // Most stiffness / boundary entries of any row of a three-level CSR.
 static int widest_row(const HostRows& R, const std::vector<uint8_t>& ninj) {
   int w = 0;
@@ -503,6 +572,9 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
     // 16-slot copies where some row spills out of 8 slots (the full P1 graph)
     if (!s && widest_row(F, no_inj) > 8) s = build_ell(F, row_nb, no_inj, m.fwd, kEllWide);
     if (!s && widest_row(A3, row_ninj) > 8) s = build_ell(A3, row_nb, row_ninj, m.adj3, kEllWide);
+    // row pairs for the pair kernel (which finishes boundary rows from the 16-slot copy)
+    if (!s && m.fwd.w16_col) s = build_pairs(F, row_nb, no_inj, m.fwd);
+    if (!s && m.adj3.w16_col) s = build_pairs(A3, row_nb, row_ninj, m.adj3);
   }
   if (!s && !m.host_only) {
     cudaStream_t cs = nullptr;
@@ -1084,6 +1156,27 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
   }
   if (bad_K(K, "pat_select_variant")) return PAT_EINVAL;
   const bool f32s = mesh->d.prec == PAT_F32 && mesh->d.split;
+  if (v->packed == 7) {  // row pairs
+    if (!(f32s && mesh->d.fwd.pair_col && mesh->d.adj3.pair_col && v->V == 8 && K % 8 == 0) ||
+        (v->min_blocks != 1 && v->min_blocks != 3)) {
+      set_error("pat_select_variant: the row-pair kernel needs FP32 split coefficients, pair tables (rows wider "
+                "than 8 slots, every pair within %d union slots), V = 8 and min_blocks 1 or 3", kPairSlots);
+      return PAT_EINVAL;
+    }
+    TuneCfg c;
+    c.V = 8;
+    c.packed = 7;
+    c.persist = 1;
+    c.pdl = v->pdl;
+    c.minb = v->min_blocks;
+    std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
+    mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
+    std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);
+    for (auto& kv : mesh->d.graphs)
+      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+    mesh->d.graphs.clear();
+    return PAT_OK;
+  }
   if (v->packed == 5 || v->packed == 6) {  // 16-slot fixed-width rows (quad-interleaved / row-major)
     const bool ok = f32s && mesh->d.fwd.w16_col && K % 8 == 0
                         ? v->V == 8

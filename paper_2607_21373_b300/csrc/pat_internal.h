@@ -93,12 +93,21 @@ struct DevCSR {
   float2* w16_hl = nullptr;
   uint32_t* w16r_col = nullptr;  // the same slots row-major ([row][16])
   float2* w16r_hl = nullptr;
+  // row pairs (2p, 2p+1): the union of the two rows' stiffness entries, then
+  // of their boundary entries, kPairSlots slots per pair ([pair][slot]); per
+  // slot the column and both rows' (hi, lo) pairs (zero where a row has no
+  // such entry); pair_n = slots used, a multiple of 4 (padding: column 2p,
+  // zero coefficients).  Built when every pair fits.
+  uint32_t* pair_col = nullptr;
+  float4* pair_cf = nullptr;
+  uint8_t* pair_n = nullptr;
   int32_t* w16_ovf_ptr = nullptr;
   uint32_t* w16_ovf_col = nullptr;
   float2* w16_ovf_hl = nullptr;
 };
 
 constexpr int kEllWide = 16;  // slots of the wide fixed-width copy
+constexpr int kPairSlots = 40;  // union slots of a row pair
 
 // The draw counter c = ((k << 1 | stream) << 40) | e leaves 23 bits for the
 // sample index k: first_sample + K must stay below 2^23.

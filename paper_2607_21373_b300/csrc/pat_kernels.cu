@@ -395,6 +395,35 @@ static void launch_wide(Step3Args<float> a, const TuneCfg& c, int64_t threads, c
   kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
 }
 
+// Row-pair launch (variant packed == 7): persistent grid-stride blocks over the
+// pairs' chunks, as a programmatic dependent of the previous step.
+template <bool ADJ>
+static void launch_pairs(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
+  const int KV = a.K / 8;
+  const int64_t gather = threads - a.row_threads;  // sensor-gather threads
+  a.row_threads = a.row_threads > 0 ? (a.N + 1) / 2 * KV : 0;
+  const int64_t n_chunks = (a.row_threads + gather + 31) / 32;
+  const int bs = 256;
+  void (*kern)(const Step3Args<float>, int64_t) =
+      c.minb == 3 ? step3u_persist_kernel<ADJ, 256, 3> : step3u_persist_kernel<ADJ, 256, 2>;
+  const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
+  a.pf_rows = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)bs);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = c.pdl ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, kern, a, n_chunks) == cudaSuccess) return;
+  cudaGetLastError();
+  kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
+}
+
 template <typename T, int V, bool SPLIT, bool ADJ>
 static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, cudaStream_t st) {
   const int64_t blocks = (threads + 255) / 256;
@@ -406,6 +435,21 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
   }
   if constexpr (sizeof(T) == 4 && SPLIT && (V == 1 || V == 8)) {
     const DevCSR& E = ADJ ? m.adj3 : m.fwd;
+    if constexpr (V == 8) {
+      if (c.packed == 7 && E.pair_col && E.w16r_col) {  // row pairs
+        a.pair_col = E.pair_col;
+        a.pair_cf = E.pair_cf;
+        a.pair_n = E.pair_n;
+        a.ell_col = E.w16r_col;
+        a.ell_hl = E.w16r_hl;
+        a.ell_desc = E.ell_desc;
+        a.ovf_ptr = E.w16_ovf_ptr;
+        a.ovf_col = E.w16_ovf_col;
+        a.ovf_hl = E.w16_ovf_hl;
+        launch_pairs<ADJ>(a, c, threads, st);
+        return;
+      }
+    }
     if ((c.packed == 5 || (c.packed == 6 && V == 8)) && E.w16_col && (V == 8 || a.K == 1)) {  // 16-slot rows
       a.ell_col = c.packed == 6 ? E.w16r_col : E.w16_col;
       a.ell_hl = c.packed == 6 ? E.w16r_hl : E.w16_hl;
@@ -1680,12 +1724,16 @@ static const TuneVariant kTuneVariants[] = {
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1},  // 60 16 slots row-major, serial tail, own rows by cp.async
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1},  // 61 the same, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1},  // 62 16 slots quad, columns per round, serial tail, own async
+    {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},     // 63 row pairs (union of two rows' sources), 2 blocks/SM
+    {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 3, 0, 8},     // 64 row pairs, 3 blocks/SM
 };
 
 // Whether variant t exists for V samples per thread and K samples on mesh m.
 static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, int K) {
   if (t.only_v && V != t.only_v) return false;
   if (t.packed == 6) return m.prec == PAT_F32 && m.split && m.fwd.w16r_col && V == 8;
+  if (t.packed == 7)
+    return m.prec == PAT_F32 && m.split && m.fwd.pair_col && m.adj3.pair_col && m.fwd.w16r_col && V == 8;
   if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1
     return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (V == 8 || (V == 1 && K == 1 && t.batch == 4 &&
                                                                          !t.early && !t.big && !t.hint));

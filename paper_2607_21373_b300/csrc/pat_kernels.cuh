@@ -266,6 +266,10 @@ struct Step3Args {
   int64_t pf_rows;    // > 0: prefetch into L2 the streamed data of the rows this many rows ahead
   const float2* __restrict__ hl;     // (hi, lo) pairs of FP32 split coefficients
   const int32_t* __restrict__ order; // processing order of the rows (nullptr: 0, 1, 2, ...)
+  // row pairs (pair kernel): union columns and both rows' (hi, lo) pairs per slot
+  const uint32_t* __restrict__ pair_col;
+  const float4* __restrict__ pair_cf;
+  const uint8_t* __restrict__ pair_n;
   // fixed-width copy of the rows (ELL kernel)
   const uint32_t* __restrict__ ell_col;
   const float2* __restrict__ ell_hl;

@@ -216,6 +216,129 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
     step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA ? threadIdx.x : 0), BS);
 }
 
+// Row pairs: each of the K / 8 threads of a pair (K = 64: 8 threads, four
+// pairs per warp) holds 8 samples of both rows 2p and 2p+1.  Every source row of the pair's union (the
+// two rows' stiffness entries merged by column, then their boundary entries)
+// is gathered once and multiplied into both rows' accumulators, with a zero
+// coefficient where a row has no such entry: consecutive rows of a lattice or a
+// bandwidth-reduced mesh share most of their neighbours (22 sources for 30
+// entries in the interior of the Kuhn cube's full graph), so the gathers per
+// row drop by about a quarter.  Each row visits its entries in its CSR order
+// (zero products interleaved), so the results equal the per-row kernels'.  The
+// boundary entries' x_{s-1} corrections, the sensor entries and the update
+// then run per row from the row-major 16-slot copy (ell_* arguments).
+template <bool ADJ>
+__device__ __forceinline__ void row_finish(const Step3Args<float>& A, int64_t row, int64_t hs, int64_t base,
+                                           u64 (&acc)[4], u64 (&accl)[4]) {
+  constexpr int V = 8, P = 4;
+  const int64_t off = row * A.K + base;
+  const uint32_t desc = A.ell_desc[row];
+  const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
+  const int eA = n - ni;
+  if (A.x) {
+    const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
+    fixed_row_tail<V, false, kWide, 1, false, true>(A, row, eA, nb, A.x + base, pk, hs, (uint32_t)A.K, acc, accl);
+  }
+  float src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  if constexpr (ADJ) {
+    for (int e = 0; e < ni; ++e) {
+      uint32_t col;
+      float2 c;
+      wide_inj(A, row, e, eA, &col, &c);
+      const int64_t j = (int64_t)col;
+      if (A.ya) {
+        const Pack<float, V> y = ld_run_pack<V>(A.ya + j * A.K + base, hs);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+      }
+      if (A.yb) {
+        const Pack<float, V> y = ld_run_pack<V>(A.yb + j * A.K + base, hs);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+      }
+    }
+  }
+  Pack<float, V> xi, xpi, xo;
+  if (A.x) {
+    xi = ld_run_pack<V>(A.x + off, hs);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
+  }
+  if (A.prev_mode == 0) {
+    xpi = ld_run_pack<V>(A.xp + off, hs);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+    const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+    xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+    xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+  }
+  st_run_pack<V>(A.xn + off, hs, xo);
+}
+
+template <bool ADJ>
+__device__ __forceinline__ void step3u_pair(const Step3Args<float>& A, const int64_t t) {
+  constexpr int V = 8, P = 4;
+  const int KV = A.K / V;
+  if (t >= A.row_threads) {  // A.row_threads counts pair threads here
+    gather_obs<V>(A, t - A.row_threads);
+    return;
+  }
+  const int64_t pr = div_kv(t, KV);
+  const int kv = (int)(t - pr * KV);
+  const int64_t ra = 2 * pr, rb = ra + 1;
+  const int64_t hs = A.K / 2, base = (int64_t)kv * 4;
+  u64 accA[P], acclA[P], accB[P], acclB[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) accA[p] = acclA[p] = accB[p] = acclB[p] = 0ull;
+  if (A.x) {
+    const float* xk = A.x + base;
+    const uint32_t Ku = (uint32_t)A.K;
+    const int used = A.pair_n[pr];
+    const uint4* cp = reinterpret_cast<const uint4*>(A.pair_col + pr * kPairSlots);
+    const float4* fp = A.pair_cf + pr * kPairSlots;
+    for (int s0 = 0; s0 < used; s0 += 4) {
+      const uint4 c = cp[s0 >> 2];
+      const uint32_t cols[4] = {c.x, c.y, c.z, c.w};
+      u64 x[4][P];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) ld_runs<V>(xk + (size_t)cols[q] * Ku, hs, x[q]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 f = fp[s0 + q];
+        const u64 ha = dup2(f.x), la = dup2(f.y), hb = dup2(f.z), lb = dup2(f.w);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          accA[p] = ffma2(ha, x[q][p], accA[p]);
+          acclA[p] = ffma2(la, x[q][p], acclA[p]);
+          accB[p] = ffma2(hb, x[q][p], accB[p]);
+          acclB[p] = ffma2(lb, x[q][p], acclB[p]);
+        }
+      }
+    }
+  }
+  row_finish<ADJ>(A, ra, hs, base, accA, acclA);
+  if (rb < A.N) row_finish<ADJ>(A, rb, hs, base, accB, acclB);
+}
+
+template <bool ADJ, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) step3u_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int wpb = BS >> 5;
+  const int64_t S = (int64_t)gridDim.x * wpb;
+  for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S)
+    step3u_pair<ADJ>(A, c * 32 + lane);
+}
+
 // Uneven batch: one persistent grid over the 32-thread chunks of several jobs
 // (meshes with their own sizes, sensor sets, time-step counts and K).  Job g
 // owns chunks block_off[g] <= c < block_off[g + 1] (each job's row threads and

@@ -16,7 +16,7 @@ import bench  # noqa: E402
 def test_every_autotune_entry_has_a_kernel_name():
     seen = set()
     for packed, persist, big, pdl, pf, wide, hint, gb, mb, V, early in itertools.product(
-            range(7), range(4), (0, 1), (0, 1), (0, 1, 2), (0, 1), (0, 1), (0, 2, 4, 8), (1, 3, 5, 6), (1, 2, 4, 8),
+            range(8), range(4), (0, 1), (0, 1), (0, 1, 2), (0, 1), (0, 1), (0, 2, 4, 8), (1, 3, 5, 6), (1, 2, 4, 8),
             (0, 1)):
         e = dict(direction="fwd", V=V, staged=False, packed=packed, chunk=4, min_blocks=mb, early=bool(early),
                  zorder=False, big_blocks=bool(big), prefetch=pf, persistent=persist, pdl=bool(pdl),
