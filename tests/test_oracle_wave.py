@@ -73,8 +73,6 @@ def test_plane_wave_dispersion_in_the_interior():
     deep = np.all((ijk > m) & (ijk < n - m), axis=1)
     assert deep.sum() > 50
     assert np.abs(p[deep] - np.cos(m * wdt) * u[deep]).max() < 1e-12
-    # the oracle's forward observes exactly these pressures
-    ops2 = fem.build(xyz, tets, xyz[deep][:4], n) if False else None
 
 
 @pytest.mark.parametrize("n,K", [(3, None), (4, 3)])
