@@ -45,10 +45,12 @@ UNIT = "samples/s"
 MESH_KEEP_ZEROS = 0x2
 MESH_TWO_LEVEL = 0x10
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one step launch of a
-# kernel variant, from one ncu capture on the named workload (K = 64, 1024 sensors,
-# profiles/).  Used for the roofline's "traffic" only when the timed run uses that
+# kernel variant, from one ncu capture on the named workload (K = 64, 1024 sensors;
+# profiles/step3w_persist_kernel_cube58_full_K64.md, step3e_persist_kernel_cube58_K64.md).  Used for the roofline's "traffic" only when the timed run uses that
 # variant on that workload; null otherwise.
 PROFILED_TRAFFIC = {
+    ("cube", "step3w_persist_kernel<false> (16 slots row-major, rounds of 4, serial tail) (own rows async)"):
+        179.551744e6,
     ("pruned", "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)"): 160.643584e6,
     ("pruned", "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)"): 159.604480e6,
     ("pruned", "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)"): 159.210752e6,
