@@ -15,12 +15,13 @@ import bench  # noqa: E402
 
 def test_every_autotune_entry_has_a_kernel_name():
     seen = set()
-    for packed, persist, big, pdl, pf, wide, hint, gb, mb, V, early in itertools.product(
+    for packed, persist, big, pdl, pf, wide, hint, gb, mb, V, early, tail, own in itertools.product(
             range(8), range(4), (0, 1), (0, 1), (0, 1, 2), (0, 1), (0, 1), (0, 2, 4, 8), (1, 3, 5, 6), (1, 2, 4, 8),
-            (0, 1)):
+            (0, 1), (0, 1), (0, 1)):
         e = dict(direction="fwd", V=V, staged=False, packed=packed, chunk=4, min_blocks=mb, early=bool(early),
                  zorder=False, big_blocks=bool(big), prefetch=pf, persistent=persist, pdl=bool(pdl),
-                 wide_loads=bool(wide), l2_hints=bool(hint), gather_batch=gb, us_per_step=1.0)
+                 wide_loads=bool(wide), l2_hints=bool(hint), gather_batch=gb, tail_serial=bool(tail),
+                 own_async=bool(own), us_per_step=1.0)
         for adj in (False, True):
             seen.add(bench.kernel_name(e, adj))
     assert "step3e_stage_kernel<8,false> (256-thread blocks, PDL)" in seen
