@@ -294,11 +294,11 @@ def cpu_baseline(a, data, nsps):
     procs = a.cpu_procs or min(host_cores(), 64)
     pool = OraclePool(a, procs, data)
     pool.rate(2)
-    n_all = 100
+    n_all = min(a.n_steps, 600)      # about 10 s of every core's time
     rate_all, sec_all = pool.rate(n_all)
     pool.close()
     one = OraclePool(a, 1, data)
-    n_one = 200
+    n_one = min(a.n_steps, 1000)
     rate_one, sec_one = one.rate(n_one)
     return {"value": rate_all / nsps, "unit": UNIT, "cores": procs, "kind": "oracle",
             "sample": f"{procs} concurrent oracle processes (FP64 SciPy, one thread each), each one forward and one "
