@@ -495,7 +495,7 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  */
 typedef struct {
   int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent, pdl,
-      wide_loads, l2_hints, gather_batch, tail_serial, own_async;
+      wide_loads, l2_hints, gather_batch, tail_serial, own_async, prefetch_meta;
   double us_per_step;
 } pat_tune_entry;
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,
@@ -511,7 +511,8 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
  * 1024-thread blocks, min_blocks 3 with rounds of 8, tail_serial = a row's
  * entries past the slots and its boundary corrections walked one at a time
  * instead of in pairs, own_async = the row's own x_s and x_{s-1} copied to
- * shared memory by cp.async while its gathers run; packed 6 = the same kernel
+ * shared memory by cp.async while its gathers run, prefetch_meta (packed 6) =
+ * each warp asks L1 to prefetch its next chunk's row metadata; packed 6 = the same kernel
  * reading a row-major copy of the 16 slots instead of the quad-interleaved
  * one, V = 8 only) for direction 0 (forward) or 1
  * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not

@@ -1199,6 +1199,8 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     c.minb = v->min_blocks;
     c.tail = (v->tail_serial || v->own_async) && nb == 4 && !c.big;
     c.own = v->own_async && nb == 4 && !c.big;
+    c.pfm = v->prefetch_meta && v->packed == 6 && nb == 4 && !c.big;
+    if (c.pfm) c.tail = 1;
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);

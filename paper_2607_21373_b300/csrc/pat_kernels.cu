@@ -362,6 +362,13 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
            : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2, 2, QUAD>
                        : step3w_persist_kernel<ADJ, 8, false, 256, 2, 2, QUAD>;
   }
+  if constexpr (!QUAD) {
+    if (c.pfm) {
+      if (c.own) return step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, true, true>;
+      return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, false, true>
+                     : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, false, true>;
+    }
+  }
   if (c.own)
     return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, true>
                    : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, true>;
@@ -1657,7 +1664,8 @@ static pat_status probe_t(const DeviceMesh& m, int K, char* ws, int n_probe, int
 constexpr int kTuneTableMax = 256;  // entries pat_autotune writes at most
 
 struct TuneVariant {
-  int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v, own = 0;
+  int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v, own = 0,
+      pfm = 0;
 };
 static const TuneVariant kTuneVariants[] = {
     // packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v
@@ -1724,6 +1732,9 @@ static const TuneVariant kTuneVariants[] = {
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1},  // 60 16 slots row-major, serial tail, own rows by cp.async
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1},  // 61 the same, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1},  // 62 16 slots quad, columns per round, serial tail, own async
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 65 row-major, serial tail, own async, next metadata to L1
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 66 row-major, serial tail, next metadata to L1
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 0, 1},  // 67 the same, columns per round
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},     // 63 row pairs (union of two rows' sources), 2 blocks/SM
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 3, 0, 8},     // 64 row pairs, 3 blocks/SM
 };
@@ -1795,6 +1806,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.batch = t.batch;
         g_force.tail = t.packed >= 5 ? t.hint : 0;
         g_force.own = t.packed >= 5 ? t.own : 0;
+        g_force.pfm = t.packed == 6 ? t.pfm : 0;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1804,7 +1816,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
           table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
                                     t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
                                     t.wide, t.packed >= 5 ? 0 : t.hint, t.batch,
-                                    t.packed >= 5 ? t.hint : 0, t.own, (double)us};
+                                    t.packed >= 5 ? t.hint : 0, t.own, t.pfm, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

@@ -202,7 +202,11 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // Persistent grid-stride form (as the 8-slot persistent kernel): a resident
 // wave of blocks whose warps walk 32-thread chunks with the grid's stride,
 // launched as a programmatic dependent of the previous step.
-template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, bool OA = false>
+// PFM: before a warp works on a chunk it asks L1 to prefetch the row metadata
+// (descriptor, columns, coefficient pairs; row-major slots) of its next chunk,
+// so that chunk starts with L1 hits instead of a round trip to L2.
+template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, bool OA = false,
+          bool PFM = false>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   // per-thread slots of the own-row copies, slot q of thread i at [q][i]
   // (consecutive threads contiguous: conflict-free 16-byte accesses)
@@ -212,8 +216,22 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
   const int lane = threadIdx.x & 31;
   const int wpb = BS >> 5;
   const int64_t S = (int64_t)gridDim.x * wpb;
-  for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S)
+  const int KV = A.K / 8;
+  for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S) {
+    if constexpr (PFM && !QUAD) {
+      const int64_t tn = (c + S) * 32 + lane;
+      if (tn < A.row_threads) {
+        const int64_t rn = div_kv(tn, KV);
+        const int kv = (int)(tn - rn * KV);
+        // lanes 0, 1, 2 of a row: columns (64 B), coefficient pairs (128 B), descriptor
+        const void* p = kv == 0 ? (const void*)(A.ell_col + rn * kWide)
+                        : kv == 1 ? (const void*)(A.ell_hl + rn * kWide)
+                                  : (const void*)(A.ell_desc + rn);
+        if (kv < 3) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+      }
+    }
     step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA ? threadIdx.x : 0), BS);
+  }
 }
 
 // Row pairs: each of the K / 8 threads of a pair (K = 64: 8 threads, four
