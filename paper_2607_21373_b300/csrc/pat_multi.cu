@@ -26,7 +26,7 @@ static int group_layout(const std::vector<const DeviceMesh*>& ms) {
   bool w16 = true, ell = true;
   for (const DeviceMesh* m : ms) {
     const bool f32s = m->prec == PAT_F32 && m->split;
-    w16 = w16 && f32s && m->fwd.w16r_col && m->adj3.w16r_col;
+    w16 = w16 && f32s && m->fwd.w16_col && m->adj3.w16_col;
     ell = ell && f32s && m->fwd.ell_col && m->adj3.ell_col;
   }
   return w16 ? 2 : ell ? 1 : 0;
@@ -46,8 +46,8 @@ static void launch_group_fixed(const std::vector<const DeviceMesh*>& ms, const s
       G.block_off[g] = off;  // in 32-thread chunks
       G.a[g] = a[base + g];
       G.a[g].ell_desc = E.ell_desc;
-      G.a[g].ell_col = layout == 2 ? E.w16r_col : E.ell_col;  // row-major 16-slot copy
-      G.a[g].ell_hl = layout == 2 ? E.w16r_hl : E.ell_hl;
+      G.a[g].ell_col = layout == 2 ? E.w16_col : E.ell_col;  // quad-interleaved 16-slot copy
+      G.a[g].ell_hl = layout == 2 ? E.w16_hl : E.ell_hl;
       G.a[g].ovf_ptr = layout == 2 ? E.w16_ovf_ptr : E.ovf_ptr;
       G.a[g].ovf_col = layout == 2 ? E.w16_ovf_col : E.ovf_col;
       G.a[g].ovf_hl = layout == 2 ? E.w16_ovf_hl : E.ovf_hl;

@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256, 4) step3g_persist_kernel(const __grid_con
     while (g + 1 < G.n && c >= G.block_off[g + 1]) ++g;
     const int64_t t = (c - G.block_off[g]) * 32 + lane;
     if constexpr (WIDE)
-      step3w_row<ADJ, 4, false, 1, false>(G.a[g], t);  // row-major slots, serial tail (the K = 64 choice)
+      step3w_row<ADJ, 4, true>(G.a[g], t);  // quad-interleaved slots (faster than row-major on this mix of K)
     else
       step3e_row<8, ADJ>(G.a[g], t);
   }
