@@ -430,6 +430,12 @@ pat_status pat_draw_normals(uint64_t seed, int32_t stream_id, int64_t n_elem, in
  *       NULL): z_samples [G][K]; p_samples [N][K] = P T z; mean, stdev [N] of
  *       the nodal samples (eq. ergodic).  PAT_ENUMERIC is reported by
  *       pat_rto_status(mesh, K, workspace, stream) as for the other solvers.
+ *   pat_matern_layout  byte offsets into the workspace of the latent CGLS
+ *       state after pat_rto_sample_matern: off[0] z [G][K] double, off[1]
+ *       direction d [G][K] float, off[2] latent residual block [G][K] float,
+ *       off[3] s = A^T r [G][K] float, off[4] gamma [K] double, off[5] data
+ *       residual block [N_T][N_obs][K] float, off[6] status word.  s is
+ *       overwritten when p_samples, mean or stdev was requested.
  */
 typedef struct pat_matern pat_matern;
 pat_status pat_matern_create(const pat_mesh* mesh, int32_t n_grid, const double* box_lo /* [3] */, double box_len,
@@ -438,6 +444,7 @@ pat_status pat_matern_destroy(pat_matern* prior);
 pat_status pat_matern_workspace_bytes(const pat_mesh* mesh, const pat_matern* prior, int32_t K, size_t* bytes);
 pat_status pat_matern_apply(const pat_mesh* mesh, const pat_matern* prior, int32_t op, const float* in, int32_t K,
                             float* out, void* workspace, size_t workspace_bytes, void* stream);
+pat_status pat_matern_layout(const pat_mesh* mesh, const pat_matern* prior, int32_t K, size_t* offsets /* [7] */);
 pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* prior, const void* y_obs, double sigma,
                                  int32_t K, int32_t n_iter, const void* eta, const float* xi, uint64_t seed,
                                  double* z_samples, double* p_samples, double* mean, double* stdev, void* workspace,

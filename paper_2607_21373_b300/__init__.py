@@ -422,6 +422,23 @@ class MaternPrior:
         ws = self.workspace(K)
         _lib.check(lib().pat_rto_status(self.mesh._h, K, _ptr(ws), _stream()))
 
+    def state(self, K):
+        """Views of the latent CGLS state left in the workspace by rto_sample
+        (pat_matern_layout): z, d, r_p (latent residual), s, gamma, r_d, status."""
+        off = (C.c_size_t * 7)()
+        _lib.check(lib().pat_matern_layout(self.mesh._h, self._h, K, off))
+        ws = self.workspace(K)
+        m, G = self.mesh, self.G
+
+        def view(o, n, dtype, shape):
+            return ws[o:o + n * (8 if dtype == torch.float64 else 4)].view(dtype).view(shape)
+
+        return {"z": view(off[0], G * K, torch.float64, (G, K)), "d": view(off[1], G * K, torch.float32, (G, K)),
+                "r_p": view(off[2], G * K, torch.float32, (G, K)), "s": view(off[3], G * K, torch.float32, (G, K)),
+                "gamma": view(off[4], K, torch.float64, (K,)),
+                "r_d": view(off[5], m.n_steps * m.n_obs * K, torch.float32, (m.n_steps, m.n_obs, K)),
+                "status": ws[off[6]:off[6] + 4].view(torch.int32)}
+
 
 def rto_sample_multi(jobs, n_iter, samples=True):
     """Uneven batch (pat_rto_sample_multi): ``jobs`` is a list of dicts with keys

@@ -94,6 +94,7 @@ SIGNATURES = {
     "pat_matern_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                     C.c_double, C.POINTER(C.c_void_p)]),
     "pat_matern_destroy": (C.c_int, [C.c_void_p]),
+    "pat_matern_layout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, c_size_p]),
     "pat_matern_workspace_bytes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, c_size_p]),
     "pat_matern_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.c_size_t, C.c_void_p]),

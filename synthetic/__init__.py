@@ -245,6 +245,15 @@ def standard_normal(shape, seed: int, dtype=np.float64):
     return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
 
 
+def device_standard_normal(shape, seed: int, device):
+    """Seeded i.i.d. N(0,1) float32 tensor drawn on a torch device (for inputs
+    too large to draw on the host); the tests read back the columns they check."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    return torch.randn(shape, generator=gen, device=device, dtype=torch.float32)
+
+
 # ----------------------------------------------------------------------------
 # Workload definitions
 # ----------------------------------------------------------------------------

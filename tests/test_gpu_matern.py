@@ -35,13 +35,33 @@ def dev(a):
     return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda")
 
 
-@pytest.mark.parametrize("ng,K", [(16, 8), (32, 3), (64, 32)])
+@pytest.mark.parametrize("ng,K", [(8, 2), (16, 8), (32, 3), (64, 32), (128, 4), (64, 5)])
 def test_filter_T_matches_oracle(ng, K):
+    """Every line length's four-step split (n_g = 8 .. 128: 1, 2, 4 or 8 threads
+    per line and sample), sample chunks of 1 .. 16, even K (two samples per
+    complex field) and odd K (real-input passes)."""
     P, m, prior, filt, idx, w = setup(ng=ng)
     z = as_precision(S.standard_normal((ng ** 3, K), 70 + K), "f32")
     out = prior.apply("T", dev(z)).cpu().numpy()
     ref = matern.apply_T(z.reshape(ng, ng, ng, K), filt).reshape(-1, K)
     assert rel_l2(out, ref) < 1e-5
+
+
+def test_filter_T_largest_grid_matches_oracle():
+    """n_g = 256 with 64 samples (32 complex pairs per chunk): 512-thread
+    blocks and 64 KB of shared memory; two of the 64 columns against the oracle
+    (T acts on each sample separately), and one sample alone (the unpacked
+    real-input passes)."""
+    ng, K = 256, 64
+    P, m, prior, filt, idx, w = setup(ng=ng)
+    z = S.device_standard_normal((ng ** 3, K), 77, "cuda")
+    out = prior.apply("T", z)
+    for c in (0, K - 1):
+        zc = z[:, c].cpu().double().numpy()
+        ref = matern.apply_T(zc.reshape(ng, ng, ng), filt).reshape(-1)
+        assert rel_l2(out[:, c].cpu().numpy(), ref) < 1e-5
+        one = prior.apply("T", z[:, c:c + 1].contiguous())
+        assert rel_l2(one[:, 0].cpu().numpy(), ref) < 1e-5
 
 
 def test_interpolation_and_transpose_match_oracle():
@@ -80,6 +100,41 @@ def test_latent_rto_first_iterations_match_oracle(k):
     mo, so = rto.ergodic_mean_std(out["samples"].cpu().numpy())
     assert rel_l2(out["mean"].cpu().numpy(), mo) < 1e-13
     assert rel_l2(out["std"].cpu().numpy(), so) < 1e-12
+
+
+def test_latent_rto_one_oracle_step_from_the_gpu_state():
+    """Deep iterations amplify rounding (the Krylov floor of the other parity
+    tests), so the depth is checked one step at a time: the oracle's CGLS step
+    from the GPU's latent state after 6 iterations against the GPU's state after
+    7 (the solve is deterministic, so its first 6 iterations repeat bit for bit)."""
+    P, m, prior, filt, idx, w = setup()
+    K, G = 4, NG ** 3
+    y = dev(as_precision(P["y_obs"], "f32"))
+    eta = dev(as_precision(S.standard_normal((P["n_steps"], 16, K), 92), "f32"))
+    xi = dev(as_precision(S.standard_normal((G, K), 93), "f32"))
+
+    def run(k):
+        prior.rto_sample(y, P["sigma"], K, k, eta=eta, xi=xi, latent=True, samples=False, mean=False,
+                         stdev=False)
+        prior.status(K)
+        return {k_: v.clone() for k_, v in prior.state(K).items()}
+
+    st, nxt = run(6), run(7)
+    assert int(nxt["status"].item()) == 0
+    grid = (NG, NG, NG, K)
+    np64 = lambda t: t.cpu().double().numpy()
+    state = {"x": np64(st["z"]).reshape(grid), "d": np64(st["d"]).reshape(grid),
+             "r": (np64(st["r_d"]), np64(st["r_p"]).reshape(grid)), "s": np64(st["s"]).reshape(grid),
+             "gamma": np64(st["gamma"])}
+    A, AT = matern.latent_operator(P["ops"], P["dt"], P["n_steps"], P["sigma"], filt, idx, w)
+    ref = rto.cgls_step(A, AT, state, True)
+    assert rel_l2(np64(nxt["z"]), ref["x"].reshape(G, K)) < 1e-5
+    assert rel_l2(np64(nxt["d"]), ref["d"].reshape(G, K)) < 1e-4
+    assert rel_l2(np64(nxt["s"]), ref["s"].reshape(G, K)) < 1e-4
+    assert rel_l2(np64(nxt["r_d"]), ref["r"][0]) < 1e-4
+    assert rel_l2(np64(nxt["r_p"]), ref["r"][1].reshape(G, K)) < 1e-4
+    g = np64(nxt["gamma"])
+    assert np.all(np.abs(g - ref["gamma"]) <= 1e-4 * np.abs(ref["gamma"]))
 
 
 def test_latent_rto_library_draws_are_the_published_generator():
