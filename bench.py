@@ -69,6 +69,8 @@ def parse(argv=None):
     ap.add_argument("--n-obs", type=int, default=1024)
     ap.add_argument("--K", type=int, default=64)
     ap.add_argument("--k-iter", type=int, default=100)
+    ap.add_argument("--order", default="native", choices=["native", "rcm", "morton"],
+                    help="node numbering of the mesh handed to the library (reorder.py)")
     ap.add_argument("--mesh", default="cube", choices=["cube", "pruned", "jitter"],
                     help="cube: full P1 graph (default); pruned: exact-zero entries of the lattice dropped; "
                          "jitter: interior nodes moved by up to 0.15 h per axis (nothing cancels)")
@@ -140,6 +142,11 @@ def problem(a):
         xyz, tets = S.jittered_cube_mesh(a.cells, 0.15, S.BATCHED.seed + 200)
     else:
         xyz, tets = S.cube_mesh(a.cells)
+    if a.order != "native":
+        from paper_2607_21373_b300 import reorder
+        perm = (reorder.rcm_permutation(tets, xyz.shape[0]) if a.order == "rcm"
+                else reorder.morton_permutation(xyz))
+        xyz, tets = reorder.renumber(xyz, tets, perm)
     det = S.detector_points(a.n_obs, S.LIMITED_VIEW_FACES, S.BATCHED.seed)
     p0 = S.phantom(xyz, "blobs20+vessels", S.BATCHED.seed + 100, a.cells)
     return xyz, tets, det, p0, 0.3 / a.cells

@@ -184,6 +184,25 @@ def test_rcm_renumbering_is_a_permutation_that_narrows_the_band():
     assert np.array_equal(xr[tr], xs[ts])
 
 
+def test_morton_renumbering_is_a_permutation_along_the_z_curve():
+    """On the 8^3-cell cube with 16 quantisation cells per axis (lattice point
+    i in cell 2i, the far face in cell 15) the Morton order starts with the 8
+    corners of the first 2 x 2 x 2 cell block, x slowest, keeps the first 64
+    nodes in blocks of 8 that each span one lattice cell, and keeps the mesh."""
+    from paper_2607_21373_b300.reorder import morton_permutation, renumber
+    xyz, tets = S.cube_mesh(8)
+    perm = morton_permutation(xyz, bits=4)
+    assert np.array_equal(np.sort(perm), np.arange(len(xyz)))
+    xr, tr = renumber(xyz, tets, perm)
+    assert np.array_equal(xr[tr], xyz[tets])
+    lattice = np.rint(xr * 8).astype(int)
+    assert lattice[:8].tolist() == [[0, 0, 0], [0, 0, 1], [0, 1, 0], [0, 1, 1],
+                                    [1, 0, 0], [1, 0, 1], [1, 1, 0], [1, 1, 1]]
+    for b in range(0, 64, 8):
+        span = lattice[b:b + 8].max(axis=0) - lattice[b:b + 8].min(axis=0)
+        assert np.all(span == 1)
+
+
 def test_sensors_inside_tetrahedra_match_the_oracle():
     """Detectors on the physical unit sphere inside the carved ball: the library's
     holding tetrahedron and weights equal the oracle's brute-force search; a point
