@@ -286,6 +286,25 @@ static int resident_blocks(const void* fn, int bdim) {
     cudaGetLastError();
     per_sm = 0;
   }
+  // The step kernels live on L1 hits of the neighbour gathers: ask for the
+  // smallest shared-memory carveout that still holds the static shared memory
+  // of the blocks found resident (the default may reserve far more, e.g. a
+  // 132 KB carveout for 68 KB of blocks), so the rest of the SM's 256 KB stays
+  // L1; kept only if the occupancy does not change.
+  cudaFuncAttributes fa{};
+  int dev = 0, smem_sm = 0, reserved = 0;
+  if (per_sm > 0 && cudaFuncGetAttributes(&fa, fn) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+      smem_sm > 0) {
+    const int64_t need = (int64_t)per_sm * ((int64_t)fa.sharedSizeBytes + reserved);
+    const int pct = (int)std::min<int64_t>(100, (need * 100 + smem_sm - 1) / smem_sm);
+    int after = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&after, fn, bdim, 0) != cudaSuccess || after < per_sm)
+      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutDefault);
+  }
+  cudaGetLastError();
   cache[{fn, bdim}] = per_sm;
   return per_sm;
 }
