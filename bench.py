@@ -107,6 +107,7 @@ FORCED = {
     "w16r": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4),
     "w16rc": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True),
     "w16ro": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True),
+    "w16rb": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=2),
     "w16rcs": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
                    prefetch_meta=True),
@@ -335,7 +336,7 @@ def kernel_name(e, adj):
         return "step3w_persist_kernel<%s> (16 slots%s, rounds of %d%s%s%s)" % (
             tf, " row-major" if packed == 6 else "", nb, ", columns per round" if e.get("early") else "",
             ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
-            ", serial tail" if e.get("tail_serial") else "") + (" (own rows async)" if e.get("own_async") else "") + (
+            ", serial tail" if e.get("tail_serial") else "") + (" (own rows by bulk copy)" if e.get("own_async") == 2 else " (own rows async)" if e.get("own_async") else "") + (
             " (next metadata to L1)" if e.get("prefetch_meta") else "")
     if packed == 2:
         return "step3t_kernel<8,%s>" % tf

@@ -518,7 +518,11 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
  * 1024-thread blocks, min_blocks 3 with rounds of 8, tail_serial = a row's
  * entries past the slots and its boundary corrections walked one at a time
  * instead of in pairs, own_async = the row's own x_s and x_{s-1} copied to
- * shared memory by cp.async while its gathers run, prefetch_meta (packed 6) =
+ * shared memory while its gathers run (1: by cp.async, each thread its own
+ * values; 2, packed 6 with K <= 256: by two bulk asynchronous copies per warp
+ * of its rows, completing on an mbarrier whose wait is bounded by the mesh's
+ * wait budget, pat_mesh_set_wait_cycles, PAT_ETIMEOUT through pat_rto_status
+ * when it runs out), prefetch_meta (packed 6) =
  * each warp asks L1 to prefetch its next chunk's row metadata; packed 6 = the same kernel
  * reading a row-major copy of the 16 slots instead of the quad-interleaved
  * one, V = 8 only) for direction 0 (forward) or 1

@@ -244,7 +244,7 @@ class Mesh:
                  "early": bool(e.early), "zorder": bool(e.zorder), "big_blocks": bool(e.big_blocks),
                  "prefetch": e.prefetch, "persistent": int(e.persistent), "pdl": bool(e.pdl),
                  "wide_loads": bool(e.wide_loads), "l2_hints": bool(e.l2_hints), "gather_batch": int(e.gather_batch),
-                 "tail_serial": bool(e.tail_serial), "own_async": bool(e.own_async),
+                 "tail_serial": bool(e.tail_serial), "own_async": int(e.own_async),
                  "prefetch_meta": bool(e.prefetch_meta),
                  "us_per_step": e.us_per_step}
                 for e in table[:min(n.value, 256)]]

@@ -575,6 +575,11 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
     // row pairs for the pair kernel (which finishes boundary rows from the 16-slot copy)
     if (!s && m.fwd.w16_col) s = build_pairs(F, row_nb, no_inj, m.fwd);
     if (!s && m.adj3.w16_col) s = build_pairs(A3, row_nb, row_ninj, m.adj3);
+    // the status word of the kernels with bounded waits (16-slot rows with bulk-copied own rows)
+    if (!s && m.fwd.w16_col && !m.d_status) {
+      std::vector<int32_t> z(1, 0);
+      s = upload(z, &m.d_status);
+    }
   }
   if (!s && !m.host_only) {
     cudaStream_t cs = nullptr;
@@ -1197,8 +1202,14 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     c.early = v->early;
     c.big = v->big_blocks && nb == 4;
     c.minb = v->min_blocks;
-    c.tail = (v->tail_serial || v->own_async) && nb == 4 && !c.big;
-    c.own = v->own_async && nb == 4 && !c.big;
+    if (v->own_async == 2 && (v->packed != 6 || K > 256 || K % 8 || 32 % (K / 8) || !mesh->d.d_status ||
+                              nb != 4 || c.big || v->prefetch_meta)) {
+      set_error("pat_select_variant: own rows by bulk copies (own_async = 2) need the row-major 16-slot rows "
+                "(packed 6), rounds of 4, 256-thread blocks, no metadata prefetch and K in {8, 16, ..., 256}");
+      return PAT_EINVAL;
+    }
+    c.own = v->own_async == 2 ? 2 : (v->own_async && nb == 4 && !c.big ? 1 : 0);
+    c.tail = (v->tail_serial || c.own == 1) && nb == 4 && !c.big;
     c.pfm = v->prefetch_meta && v->packed == 6 && nb == 4 && !c.big;
     if (c.pfm) c.tail = 1;
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);

@@ -383,14 +383,23 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
   }
   if constexpr (!QUAD) {
     if (c.pfm) {
-      if (c.own) return step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, true, true>;
+      if (c.own) return step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 1, true>;
       return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, false, true>
                      : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, false, true>;
     }
   }
+  if constexpr (!QUAD) {
+    if (c.own == 2) {
+      if (c.tail)
+        return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, 2>
+                       : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 2>;
+      return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, false, 2>
+                     : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, false, 2>;
+    }
+  }
   if (c.own)
-    return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, true>
-                   : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, true>;
+    return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, 1>
+                   : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, 1>;
   if (c.early)
     return c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, QUAD>;
   return c.tail ? step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, QUAD>;
@@ -483,6 +492,8 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.ovf_ptr = E.w16_ovf_ptr;
       a.ovf_col = E.w16_ovf_col;
       a.ovf_hl = E.w16_ovf_hl;
+      a.status = m.d_status;
+      a.wait_cycles = m.tile_wait_cycles;
       if constexpr (V == 1)
         step3w1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
       else
@@ -1754,6 +1765,10 @@ static const TuneVariant kTuneVariants[] = {
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 65 row-major, serial tail, own async, next metadata to L1
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 66 row-major, serial tail, next metadata to L1
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 0, 1},  // 67 the same, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 2},  // 68 row-major, serial tail, own rows by bulk copies per warp
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 2},  // 69 the same, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 2},  // 70 row-major, paired tail, own rows by bulk copies
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8, 2},  // 71 the same, columns per round
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},     // 63 row pairs (union of two rows' sources), 2 blocks/SM
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 3, 0, 8},     // 64 row pairs, 3 blocks/SM
 };
@@ -1761,7 +1776,9 @@ static const TuneVariant kTuneVariants[] = {
 // Whether variant t exists for V samples per thread and K samples on mesh m.
 static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, int K) {
   if (t.only_v && V != t.only_v) return false;
-  if (t.packed == 6) return m.prec == PAT_F32 && m.split && m.fwd.w16r_col && V == 8;
+  if (t.packed == 6)
+    return m.prec == PAT_F32 && m.split && m.fwd.w16r_col && V == 8 &&
+           (t.own != 2 || (K >= 8 && K <= 256 && 32 % (K / 8) == 0 && m.d_status != nullptr));  // whole rows per chunk
   if (t.packed == 7)
     return m.prec == PAT_F32 && m.split && m.fwd.pair_col && m.adj3.pair_col && m.fwd.w16r_col && V == 8;
   if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1

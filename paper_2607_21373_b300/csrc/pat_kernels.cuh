@@ -295,6 +295,10 @@ struct Step3Args {
   const T* __restrict__ det_w;
   T* __restrict__ y_out;
   T scale;
+  // bounded waits of the kernels that stage rows by bulk copies: the status
+  // word that gets PAT_ETIMEOUT and the SM cycles a warp waits before it gives up
+  int32_t* status;
+  long long wait_cycles;
 };
 
 // Row metadata staging.  With STAGE, the block first copies the column /

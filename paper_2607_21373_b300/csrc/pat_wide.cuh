@@ -56,13 +56,20 @@ __device__ __forceinline__ void wide_inj(const Step3Args<float>& A, int64_t row,
 // all 16 columns arrive up front and the coefficient pairs per round.
 //
 // OA: the row's own values of x_s and x_{s-1} (the last loads the update
-// needs) are copied global -> shared memory by cp.async when the row starts,
-// so they arrive while the gathers run instead of costing one more round trip
-// after them; `own` is this thread's 4 x 16-byte slot (4 float4 at a stride of
-// `own_stride` float4).
-template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true, bool OA = false>
+// needs) are copied global -> shared memory while the gathers run, instead of
+// costing one more round trip after them.  OA = 1: by cp.async, each thread
+// its own 4 x 16 bytes (`own`: 4 float4 at a stride of `own_stride` float4).
+// OA = 2: by two bulk copies per warp chunk (its rows of x_s and x_{s-1}, 1 KB
+// each) that one lane issued before the call, completing on the warp's
+// mbarrier `bar` in phase `phase`; `ob` points at this thread's first value in
+// the chunk's x_s copy (x_{s-1} 256 floats further).  `staged` says whether
+// the copies were issued (the warp's rows exist and x is not the zero state).
+// A wait that runs past A.wait_cycles reports PAT_ETIMEOUT, lets the copies
+// land (bounded again) and carries on with whatever arrived.
+template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true, int OA = 0>
 __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t, float4* own = nullptr,
-                                           int own_stride = 0) {
+                                           int own_stride = 0, const float* ob = nullptr, uint32_t bar = 0,
+                                           uint32_t phase = 0, bool staged = false) {
   constexpr int V = 8, P = 4;
   static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
   const int KV = A.K / V;
@@ -75,7 +82,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
   const int64_t hs = A.K / 2;
   const int64_t base = (int64_t)kv * 4;
   const int64_t off = row * A.K + base;
-  if constexpr (OA) {
+  if constexpr (OA == 1) {
     if (A.x) {
       cp_async16(own, A.x + off);
       cp_async16(own + own_stride, A.x + off + hs);
@@ -166,13 +173,21 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     }
   }
   Pack<float, V> xi, xpi, xo;
-  if constexpr (OA) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if constexpr (OA == 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if constexpr (OA == 2) {
+    if (staged && !mbar_wait_parity(bar, phase, A.wait_cycles)) {
+      atomicExch(A.status, (int)PAT_ETIMEOUT);
+      mbar_wait_parity(bar, phase, kDrainWait);
+    }
+  }
   auto unpack4 = [](float4 a, float4 b, Pack<float, V>& o) {
     o.v[0] = a.x, o.v[1] = a.y, o.v[2] = a.z, o.v[3] = a.w;
     o.v[4] = b.x, o.v[5] = b.y, o.v[6] = b.z, o.v[7] = b.w;
   };
   if (A.x) {
-    if constexpr (OA)
+    if (OA == 2 && staged)
+      unpack4(*reinterpret_cast<const float4*>(ob), *reinterpret_cast<const float4*>(ob + hs), xi);
+    else if constexpr (OA == 1)
       unpack4(own[0], own[own_stride], xi);
     else
       xi = ld_run_pack<V>(A.x + off, hs);
@@ -181,7 +196,9 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
   }
   if (A.prev_mode == 0) {
-    if constexpr (OA)
+    if (OA == 2 && staged)
+      unpack4(*reinterpret_cast<const float4*>(ob + 256), *reinterpret_cast<const float4*>(ob + 256 + hs), xpi);
+    else if constexpr (OA == 1)
       unpack4(own[2 * own_stride], own[3 * own_stride], xpi);
     else
       xpi = ld_run_pack<V>(A.xp + off, hs);
@@ -205,19 +222,68 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // PFM: before a warp works on a chunk it asks L1 to prefetch the row metadata
 // (descriptor, columns, coefficient pairs; row-major slots) of its next chunk,
 // so that chunk starts with L1 hits instead of a round trip to L2.
-template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, bool OA = false,
+//
+// OA = 2 (K / 8 divides 32, so a 32-thread chunk covers whole rows: 32 / (K/8)
+// rows, 1 KB of each state array): each warp owns a 2 KB shared-memory copy of its
+// chunk's x_s and x_{s-1} rows and an mbarrier; lane 0 issues the chunk's two
+// bulk copies once every lane is done with the previous chunk's copy.
+template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, int OA = 0,
           bool PFM = false>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   // per-thread slots of the own-row copies, slot q of thread i at [q][i]
   // (consecutive threads contiguous: conflict-free 16-byte accesses)
-  __shared__ float4 own_buf[OA ? 4 * BS : 1];
+  __shared__ float4 own_buf[OA == 1 ? 4 * BS : 1];
+  __shared__ __align__(128) float own_rows[OA == 2 ? (BS / 32) * 512 : 1];
+  __shared__ __align__(8) uint64_t own_bar[OA == 2 ? BS / 32 : 1];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  uint32_t bar = 0, phase = 0;
+  float* ow = own_rows + (OA == 2 ? warp * 512 : 0);
+  if constexpr (OA == 2) {
+    bar = smem_u32(&own_bar[warp]);
+    if (lane == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+  }
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const int lane = threadIdx.x & 31;
   const int wpb = BS >> 5;
   const int64_t S = (int64_t)gridDim.x * wpb;
   const int KV = A.K / 8;
-  for (int64_t c = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks; c += S) {
+  for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < n_chunks; c += S) {
+    bool staged = false;
+    const float* ob = nullptr;
+    if constexpr (OA == 2) {
+      const int64_t t0 = c * 32;
+      const int64_t row0 = t0 / KV;
+      const int64_t nr = (A.x && t0 < A.row_threads) ? min((int64_t)(32 / KV), A.N - row0) : 0;
+      staged = nr > 0;
+      if (staged) {
+        __syncwarp();  // every lane is done with the previous chunk's copy
+        if (lane == 0) {
+          const uint32_t bytes = (uint32_t)(nr * A.K * 4);
+          const uint32_t total = A.prev_mode == 0 ? 2 * bytes : bytes;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total) : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(ow)),
+              "l"(A.x + row0 * A.K), "r"(bytes), "r"(bar)
+              : "memory");
+          if (A.prev_mode == 0)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(ow + 256)),
+                "l"(A.xp + row0 * A.K), "r"(bytes), "r"(bar)
+                : "memory");
+        }
+        const int64_t t = t0 + lane;
+        const int64_t row = t / KV;
+        ob = ow + (row - row0) * A.K + (t - row * KV) * 4;
+      }
+    }
     if constexpr (PFM && !QUAD) {
       const int64_t tn = (c + S) * 32 + lane;
       if (tn < A.row_threads) {
@@ -230,7 +296,9 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
         if (kv < 3) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
       }
     }
-    step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA ? threadIdx.x : 0), BS);
+    step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA == 1 ? threadIdx.x : 0), BS, ob, bar,
+                                          phase, staged);
+    if (staged) phase ^= 1u;
   }
 }
 
