@@ -50,7 +50,7 @@ MESH_TWO_LEVEL = 0x10
 # variant on that workload; null otherwise.
 PROFILED_TRAFFIC = {
     ("cube", "step3w_persist_kernel<false> (16 slots row-major, rounds of 4, serial tail) (own rows async)"):
-        179.551744e6,
+        180.555520e6,
     ("pruned", "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)"): 160.643584e6,
     ("pruned", "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)"): 159.604480e6,
     ("pruned", "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)"): 159.210752e6,
@@ -109,6 +109,8 @@ FORCED = {
     "w16ro": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True),
     "w16rb": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=2),
     "w16rcs": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
+    "w16rco": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
+                   own_async=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
                    prefetch_meta=True),
     "pairs": dict(V=8, packed=7, persistent=1, pdl=True),
