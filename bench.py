@@ -114,6 +114,8 @@ FORCED = {
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
                    prefetch_meta=True),
     "pairs": dict(V=8, packed=7, persistent=1, pdl=True),
+    "quads": dict(V=8, packed=8, persistent=1, pdl=True),
+    "quadso": dict(V=8, packed=8, persistent=1, pdl=True, own_async=True),
     "pairs3": dict(V=8, packed=7, persistent=1, pdl=True, min_blocks=3),
 }
 
@@ -330,6 +332,8 @@ def kernel_name(e, adj):
     packed = e.get("packed")
     if packed == 7:
         return "step3u_persist_kernel<%s> (row pairs, %d blocks/SM)" % (tf, 3 if e.get("min_blocks") == 3 else 2)
+    if packed == 8:
+        return "step3q_persist_kernel<%s> (row quads%s)" % (tf, ", own rows async" if e.get("own_async") else "")
     if packed in (5, 6):
         if e.get("V") == 1:
             return "step3w1_kernel<%s> (16 slots, one sample)" % tf

@@ -58,7 +58,9 @@ void free_device(DeviceMesh& m) {
                  (void**)&m.adj3.w16_ovf_hl, (void**)&m.fwd.w16r_col, (void**)&m.fwd.w16r_hl,
                  (void**)&m.adj3.w16r_col, (void**)&m.adj3.w16r_hl, (void**)&m.fwd.pair_col,
                  (void**)&m.fwd.pair_cf, (void**)&m.fwd.pair_n, (void**)&m.adj3.pair_col, (void**)&m.adj3.pair_cf,
-                 (void**)&m.adj3.pair_n,
+                 (void**)&m.adj3.pair_n, (void**)&m.fwd.quad_ptr, (void**)&m.fwd.quad_n, (void**)&m.fwd.quad_col,
+                 (void**)&m.fwd.quad_cf, (void**)&m.adj3.quad_ptr, (void**)&m.adj3.quad_n, (void**)&m.adj3.quad_col,
+                 (void**)&m.adj3.quad_cf,
                  &m.minv_hi, (void**)&m.minv_lo, (void**)&m.ml, (void**)&m.sqrt_ml, (void**)&m.det_node,
                  &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
                  (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
@@ -404,6 +406,90 @@ pat_status build_pairs(const HostRows& R, const std::vector<uint8_t>& nb, const 
   return s;
 }
 
+// Row quads of a three-level CSR (see DevCSR): per quad of rows the merge of
+// the four rows' stiffness entries by column, then of their boundary entries
+// (both acting on x_s), then the boundary entries again with negated
+// coefficients (acting on x_{s-1}).  A merge takes the smallest column among
+// the rows' next entries and consumes that column from every row whose next
+// entry it is, so each row meets its own entries in its CSR order and the
+// products it accumulates are the per-row kernels' (zero products between).
+pat_status build_quads(const HostRows& R, const std::vector<uint8_t>& nb, const std::vector<uint8_t>& ninj,
+                       DevCSR& d) {
+  const int64_t N = (int64_t)R.ptr.size() - 1, Q = (N + 3) / 4;
+  std::vector<int32_t> qptr(Q + 1, 0);
+  std::vector<uint32_t> qn(Q), qcol;
+  std::vector<float4> qcf;
+  auto split = [](double v) {
+    const float h = (float)v;
+    return std::make_pair(h, (float)(v - (double)h));
+  };
+  struct Entry {
+    uint32_t col;
+    double c[4];
+  };
+  std::vector<Entry> list;
+  auto merge = [&](int64_t q, int part, double sign) {
+    int32_t lo[4], hi[4];
+    for (int g = 0; g < 4; ++g) {
+      const int64_t r = 4 * q + g;
+      if (r >= N) {
+        lo[g] = hi[g] = 0;
+        continue;
+      }
+      const int32_t e0 = R.ptr[r], eA = R.ptr[r + 1] - (int32_t)ninj[r], eB = eA - (int32_t)nb[r];
+      lo[g] = part == 0 ? e0 : eB;
+      hi[g] = part == 0 ? eB : eA;
+    }
+    for (;;) {
+      uint32_t cmin = 0xffffffffu;
+      for (int g = 0; g < 4; ++g)
+        if (lo[g] < hi[g]) cmin = std::min(cmin, R.col[lo[g]] & kIdxMask);
+      if (cmin == 0xffffffffu) break;
+      Entry en{cmin, {0.0, 0.0, 0.0, 0.0}};
+      for (int g = 0; g < 4; ++g)
+        if (lo[g] < hi[g] && (R.col[lo[g]] & kIdxMask) == cmin) en.c[g] = sign * R.val[lo[g]++];
+      list.push_back(en);
+    }
+  };
+  auto flush = [&](int64_t q, size_t from) {  // pad the list from `from` to a multiple of 4 and append it
+    while ((list.size() - from) % 4) list.push_back(Entry{(uint32_t)(4 * q), {0.0, 0.0, 0.0, 0.0}});
+    const size_t n = list.size() - from;
+    for (size_t e = from; e < list.size(); e += 2) {
+      for (int g = 0; g < 4; ++g) {
+        const auto a = split(list[e].c[g]), b = split(list[e + 1].c[g]);
+        qcf.push_back(make_float4(a.first, a.second, b.first, b.second));
+      }
+      qcol.push_back(list[e].col);
+      qcol.push_back(list[e + 1].col);
+    }
+    return n;
+  };
+  for (int64_t q = 0; q < Q; ++q) {
+    list.clear();
+    merge(q, 0, 1.0);
+    merge(q, 1, 1.0);
+    const size_t nx = flush(q, 0);
+    const size_t from = list.size();
+    merge(q, 1, -1.0);
+    const size_t np = flush(q, from);
+    if (nx > 0xffff || np > 0xffff) {
+      set_error("pat_mesh_create: a row quad has more than 65535 entries");
+      return PAT_EUNSUPPORTED;
+    }
+    qn[q] = (uint32_t)nx | ((uint32_t)np << 16);
+    qptr[q + 1] = (int32_t)qcol.size();
+  }
+  if (qcol.empty()) {
+    qcol.push_back(0);
+    for (int g = 0; g < 4; ++g) qcf.push_back(make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+  }
+  pat_status s = upload(qptr, &d.quad_ptr);
+  if (!s) s = upload(qn, &d.quad_n);
+  if (!s) s = upload(qcol, &d.quad_col);
+  if (!s) s = upload(qcf, &d.quad_cf);
+  return s;
+}
+
 // Most stiffness / boundary entries of any row of a three-level CSR.
 static int widest_row(const HostRows& R, const std::vector<uint8_t>& ninj) {
   int w = 0;
@@ -575,6 +661,9 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
     // row pairs for the pair kernel (which finishes boundary rows from the 16-slot copy)
     if (!s && m.fwd.w16_col) s = build_pairs(F, row_nb, no_inj, m.fwd);
     if (!s && m.adj3.w16_col) s = build_pairs(A3, row_nb, row_ninj, m.adj3);
+    // row quads for the quad-union kernel (which finishes rows from the 16-slot copy)
+    if (!s && m.fwd.w16_col) s = build_quads(F, row_nb, no_inj, m.fwd);
+    if (!s && m.adj3.w16_col) s = build_quads(A3, row_nb, row_ninj, m.adj3);
     // the status word of the kernels with bounded waits (16-slot rows with bulk-copied own rows)
     if (!s && m.fwd.w16_col && !m.d_status) {
       std::vector<int32_t> z(1, 0);
@@ -1174,6 +1263,27 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     c.persist = 1;
     c.pdl = v->pdl;
     c.minb = v->min_blocks;
+    std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
+    mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
+    std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);
+    for (auto& kv : mesh->d.graphs)
+      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+    mesh->d.graphs.clear();
+    return PAT_OK;
+  }
+  if (v->packed == 8) {  // row quads
+    if (!(f32s && mesh->d.fwd.quad_col && mesh->d.adj3.quad_col && mesh->d.fwd.w16r_col && v->V == 8 &&
+          K == 64) || v->own_async == 2) {
+      set_error("pat_select_variant: the row-quad kernel needs FP32 split coefficients, the 16-slot copy (rows "
+                "wider than 8 slots), V = 8, K = 64 and own_async 0 or 1");
+      return PAT_EINVAL;
+    }
+    TuneCfg c;
+    c.V = 8;
+    c.packed = 8;
+    c.persist = 1;
+    c.pdl = v->pdl;
+    c.own = v->own_async ? 1 : 0;
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);

@@ -101,6 +101,18 @@ struct DevCSR {
   uint32_t* pair_col = nullptr;
   float4* pair_cf = nullptr;
   uint8_t* pair_n = nullptr;
+  // row quads (4q .. 4q+3): the union of the four rows' stiffness entries,
+  // then of their boundary entries (the x list), then of their boundary
+  // entries again with negated coefficients (the x_{s-1} list), each list
+  // merged by column in every row's own order and padded to a multiple of 4
+  // (column 4q, zero coefficients).  quad_ptr[q]: first entry of quad q;
+  // quad_n[q] = x-list length | x_{s-1}-list length << 16; quad_col[e]: the
+  // entry's source row; quad_cf[(e/2)*4 + g] = (hi, lo) of entries e, e+1 for
+  // row 4q+g (zero where the row has no such entry).
+  int32_t* quad_ptr = nullptr;
+  uint32_t* quad_n = nullptr;
+  uint32_t* quad_col = nullptr;
+  float4* quad_cf = nullptr;
   int32_t* w16_ovf_ptr = nullptr;
   uint32_t* w16_ovf_col = nullptr;
   float2* w16_ovf_hl = nullptr;

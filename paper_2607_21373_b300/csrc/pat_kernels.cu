@@ -459,6 +459,33 @@ static void launch_pairs(Step3Args<float> a, const TuneCfg& c, int64_t threads, 
   kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
 }
 
+// Row-quad launch (variant packed == 8, K = 64): persistent grid-stride blocks
+// over the quads' chunks (then the sensor-gather chunks), as a programmatic
+// dependent of the previous step.  c.own: the rows' own values by cp.async.
+template <bool ADJ>
+static void launch_quads(Step3Args<float> a, const TuneCfg& c, int64_t threads, cudaStream_t st) {
+  const int64_t n_chunks = (threads + 31) / 32;
+  const int bs = 256;
+  void (*kern)(const Step3Args<float>, int64_t) =
+      c.own ? step3q_persist_kernel<ADJ, true> : step3q_persist_kernel<ADJ, false>;
+  const int per_sm = std::max(1, resident_blocks((const void*)kern, bs));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sm_count(), (n_chunks + 7) / 8));
+  a.pf_rows = 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)bs);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = c.pdl ? 1 : 0;
+  if (cudaLaunchKernelEx(&cfg, kern, a, n_chunks) == cudaSuccess) return;
+  cudaGetLastError();
+  kern<<<(unsigned)grid, (unsigned)bs, 0, st>>>(a, n_chunks);
+}
+
 template <typename T, int V, bool SPLIT, bool ADJ>
 static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, cudaStream_t st) {
   const int64_t blocks = (threads + 255) / 256;
@@ -471,6 +498,18 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
   if constexpr (sizeof(T) == 4 && SPLIT && (V == 1 || V == 8)) {
     const DevCSR& E = ADJ ? m.adj3 : m.fwd;
     if constexpr (V == 8) {
+      if (c.packed == 8 && E.quad_col && E.w16r_col && a.K == 64) {  // row quads
+        a.quad_ptr = E.quad_ptr;
+        a.quad_n = E.quad_n;
+        a.quad_col = E.quad_col;
+        a.quad_cf = E.quad_cf;
+        a.ell_desc = E.ell_desc;
+        a.ovf_ptr = E.w16_ovf_ptr;
+        a.ovf_col = E.w16_ovf_col;
+        a.ovf_hl = E.w16_ovf_hl;
+        launch_quads<ADJ>(a, c, threads, st);
+        return;
+      }
       if (c.packed == 7 && E.pair_col && E.w16r_col) {  // row pairs
         a.pair_col = E.pair_col;
         a.pair_cf = E.pair_cf;
@@ -1769,6 +1808,8 @@ static const TuneVariant kTuneVariants[] = {
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 2},  // 69 the same, columns per round
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 2},  // 70 row-major, paired tail, own rows by bulk copies
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8, 2},  // 71 the same, columns per round
+    {8, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 0},  // 72 row quads (union of four rows' sources), K = 64
+    {8, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 1},  // 73 row quads, own rows by cp.async
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},     // 63 row pairs (union of two rows' sources), 2 blocks/SM
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 3, 0, 8},     // 64 row pairs, 3 blocks/SM
 };
@@ -1781,6 +1822,9 @@ static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, in
            (t.own != 2 || (K >= 8 && K <= 256 && 32 % (K / 8) == 0 && m.d_status != nullptr));  // whole rows per chunk
   if (t.packed == 7)
     return m.prec == PAT_F32 && m.split && m.fwd.pair_col && m.adj3.pair_col && m.fwd.w16r_col && V == 8;
+  if (t.packed == 8)
+    return m.prec == PAT_F32 && m.split && m.fwd.quad_col && m.adj3.quad_col && m.fwd.w16r_col && V == 8 &&
+           K == 64;
   if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1
     return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (V == 8 || (V == 1 && K == 1 && t.batch == 4 &&
                                                                          !t.early && !t.big && !t.hint));

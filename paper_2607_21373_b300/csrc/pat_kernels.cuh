@@ -270,6 +270,11 @@ struct Step3Args {
   const uint32_t* __restrict__ pair_col;
   const float4* __restrict__ pair_cf;
   const uint8_t* __restrict__ pair_n;
+  // row quads (quad kernel): see DevCSR
+  const int32_t* __restrict__ quad_ptr;
+  const uint32_t* __restrict__ quad_n;
+  const uint32_t* __restrict__ quad_col;
+  const float4* __restrict__ quad_cf;
   // fixed-width copy of the rows (ELL kernel)
   const uint32_t* __restrict__ ell_col;
   const float2* __restrict__ ell_hl;

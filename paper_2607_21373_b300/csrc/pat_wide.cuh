@@ -425,6 +425,162 @@ __global__ void __launch_bounds__(BS, MINB) step3u_persist_kernel(const Step3Arg
     step3u_pair<ADJ>(A, c * 32 + lane);
 }
 
+// Row quads (K = 64: a warp's 32 threads are the 8 threads x 8 samples of each
+// of the 4 rows 4q .. 4q+3).  Every entry of the quad's union is one source row
+// that all four rows' threads gather together: the four 8-thread groups read
+// the same addresses, so one warp access fetches the source row once for the
+// whole quad, and consecutive rows of a lattice-like numbering share most of
+// their neighbours (about 36 sources for the 60 entries of four interior rows
+// of the Kuhn cube's full graph).  Each group multiplies with its own row's
+// coefficient pair (zero where the row has no such entry), in its CSR order,
+// so every row accumulates the per-row kernels' products in their order.
+// One round: the 4 entries' columns in one broadcast load, their source rows
+// gathered together, each group's coefficient pairs for the 4 entries in two
+// 16-byte loads (the quad's 4 rows side by side: 64 contiguous bytes).
+template <int V, int P>
+__device__ __forceinline__ void quad_list(const Step3Args<float>& A, int32_t e, int n, const float* src, int g,
+                                          int64_t hs, uint32_t Ku, u64 (&acc)[P], u64 (&accl)[P]) {
+  for (int h = 0; h < n; h += 4, e += 4) {
+    const uint4 c = *reinterpret_cast<const uint4*>(A.quad_col + e);
+    const uint32_t cols[4] = {c.x, c.y, c.z, c.w};
+    u64 x[4][P];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ld_runs<V>(src + (size_t)cols[q] * Ku, hs, x[q]);
+    const float4 f01 = A.quad_cf[(e >> 1) * 4 + g], f23 = A.quad_cf[((e >> 1) + 1) * 4 + g];
+    const float2 cf[4] = {make_float2(f01.x, f01.y), make_float2(f01.z, f01.w), make_float2(f23.x, f23.y),
+                          make_float2(f23.z, f23.w)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const u64 ch = dup2(cf[q].x), cl = dup2(cf[q].y);
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        acc[p] = ffma2(ch, x[q][p], acc[p]);
+        accl[p] = ffma2(cl, x[q][p], accl[p]);
+      }
+    }
+  }
+}
+
+// Chunk c of the quad kernel: quad c's rows, or (past the quads) 32 sensor-gather
+// threads.  OA: the rows' own x_s, x_{s-1} copied to shared memory by cp.async
+// while the union is gathered (`own`: this thread's 4 float4 at a stride of
+// `own_stride`).  The sensor entries (transposed step) and the update then run
+// per row from the row-major 16-slot copy's descriptor and overflow lists.
+template <bool ADJ, bool OA>
+__device__ __forceinline__ void step3q_chunk(const Step3Args<float>& A, int64_t c, int lane, float4* own,
+                                             int own_stride) {
+  constexpr int V = 8, P = 4;
+  const int64_t t = c * 32 + lane;
+  const int64_t rows = A.row_threads >> 3;  // 0 on a launch that only observes
+  const int64_t nq = (rows + 3) >> 2;
+  if (c >= nq) {
+    gather_obs<V>(A, t - A.row_threads);
+    return;
+  }
+  const int g = lane >> 3, kv = lane & 7;
+  const int64_t row = 4 * c + g;
+  const bool is_row = row < rows;  // else a sensor-gather thread of the last chunk
+  const int64_t hs = A.K / 2, base = (int64_t)kv * 4;
+  const int64_t off = row * A.K + base;
+  if constexpr (OA) {
+    if (is_row) {
+      if (A.x) {
+        cp_async16(own, A.x + off);
+        cp_async16(own + own_stride, A.x + off + hs);
+      }
+      if (A.prev_mode == 0) {
+        cp_async16_cg(own + 2 * own_stride, A.xp + off);
+        cp_async16_cg(own + 3 * own_stride, A.xp + off + hs);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  u64 acc[P], accl[P];
+#pragma unroll
+  for (int p = 0; p < P; ++p) acc[p] = accl[p] = 0ull;
+  if (A.x) {
+    const uint32_t Ku = (uint32_t)A.K;
+    const int32_t e0 = A.quad_ptr[c];
+    const uint32_t qn = A.quad_n[c];
+    const int nx = (int)(qn & 0xffffu), np = (int)(qn >> 16);
+    quad_list<V, P>(A, e0, nx, A.x + base, g, hs, Ku, acc, accl);
+    if (A.prev_mode != 2 && np > 0)
+      quad_list<V, P>(A, e0 + nx, np, (A.prev_mode == 0 ? A.xp : A.x) + base, g, hs, Ku, acc, accl);
+  }
+  if (!is_row) {
+    if constexpr (OA) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    gather_obs<V>(A, t - A.row_threads);
+    return;
+  }
+  float src[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  if constexpr (ADJ) {
+    const uint32_t desc = A.ell_desc[row];
+    const int n = (int)(desc & 255u), ni = (int)((desc >> 16) & 255u);
+    const int eA = n - ni;
+    for (int e = 0; e < ni; ++e) {
+      uint32_t col;
+      float2 cf;
+      wide_inj(A, row, e, eA, &col, &cf);
+      const int64_t j = (int64_t)col;
+      if (A.ya) {
+        const Pack<float, V> y = ld_run_pack<V>(A.ya + j * A.K + base, hs);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(cf.x, y.v[q], src[q]);
+      }
+      if (A.yb) {
+        const Pack<float, V> y = ld_run_pack<V>(A.yb + j * A.K + base, hs);
+#pragma unroll
+        for (int q = 0; q < V; ++q) src[q] = fmaf(cf.x, y.v[q], src[q]);
+      }
+    }
+  }
+  auto unpack4 = [](float4 a, float4 b, Pack<float, V>& o) {
+    o.v[0] = a.x, o.v[1] = a.y, o.v[2] = a.z, o.v[3] = a.w;
+    o.v[4] = b.x, o.v[5] = b.y, o.v[6] = b.z, o.v[7] = b.w;
+  };
+  if constexpr (OA) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  Pack<float, V> xi, xpi, xo;
+  if (A.x) {
+    if constexpr (OA)
+      unpack4(own[0], own[own_stride], xi);
+    else
+      xi = ld_run_pack<V>(A.x + off, hs);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xi.v[q] = 0.0f;
+  }
+  if (A.prev_mode == 0) {
+    if constexpr (OA)
+      unpack4(own[2 * own_stride], own[3 * own_stride], xpi);
+    else
+      xpi = ld_run_pack<V>(A.xp + off, hs);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V; ++q) xpi.v[q] = (A.prev_mode == 1) ? xi.v[q] : 0.0f;
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const float2 a = unpack2(acc[p]), al = unpack2(accl[p]);
+    const float w0 = xi.v[2 * p] - xpi.v[2 * p], w1 = xi.v[2 * p + 1] - xpi.v[2 * p + 1];
+    xo.v[2 * p] = xi.v[2 * p] + (w0 - (a.x + al.x) + A.inj_scale * src[2 * p]);
+    xo.v[2 * p + 1] = xi.v[2 * p + 1] + (w1 - (a.y + al.y) + A.inj_scale * src[2 * p + 1]);
+  }
+  st_run_pack<V>(A.xn + off, hs, xo);
+}
+
+template <bool ADJ, bool OA>
+__global__ void __launch_bounds__(256, 4) step3q_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
+  __shared__ float4 own_buf[OA ? 4 * 256 : 1];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int lane = threadIdx.x & 31;
+  const int64_t S = (int64_t)gridDim.x * 8;
+  for (int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); c < n_chunks; c += S)
+    step3q_chunk<ADJ, OA>(A, c, lane, own_buf + (OA ? threadIdx.x : 0), 256);
+}
+
 // Uneven batch: one persistent grid over the 32-thread chunks of several jobs
 // (meshes with their own sizes, sensor sets, time-step counts and K).  Job g
 // owns chunks block_off[g] <= c < block_off[g + 1] (each job's row threads and

@@ -38,6 +38,9 @@ WIDE_VARIANTS = [dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, prefetch_meta=True),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=2),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, own_async=2)]
+# the row-quad kernel (K = 64 only: a warp is the 4 rows of a quad)
+QUAD_VARIANTS = [dict(V=8, packed=8, persistent=1, pdl=True), dict(V=8, packed=8, persistent=1, pdl=True, own_async=True),
+                 dict(V=8, packed=8, persistent=1, pdl=False)]
 OTHER_VARIANTS = [dict(V=8, packed=3, persistent=1, pdl=True, prefetch=1), dict(V=8, packed=1, chunk=2),
                   dict(V=4, packed=0)]
 
@@ -67,7 +70,7 @@ def test_wide_variants_are_bit_identical(mesh_kind, K):
     p0 = dev(S.standard_normal((len(xyz), K), 3))
     yh = dev(S.standard_normal((nt, n_obs, K), 4))
     Y0, g0 = m.forward(p0).clone(), m.adjoint(yh).clone()
-    for v in WIDE_VARIANTS + OTHER_VARIANTS:
+    for v in WIDE_VARIANTS + OTHER_VARIANTS + (QUAD_VARIANTS if K == 64 else []):
         for d in ("fwd", "adj"):
             m.select_variant(K, d, **v)
         assert torch.equal(m.forward(p0), Y0), v
@@ -105,15 +108,16 @@ def test_wide_variant_refused_where_it_does_not_exist():
     m32.select_variant(8, "fwd", **WIDE_VARIANTS[0])
 
 
-@pytest.mark.parametrize("K", [1, 16])
+@pytest.mark.parametrize("K", [1, 16, 64])
 def test_jittered_mesh_matches_oracle(K):
     """Forward, transpose and dot test on a jittered 12^3 mesh (every graph entry
-    nonzero) with the 16-slot kernels, against the FP64 oracle."""
+    nonzero) with the 16-slot kernels (K = 64: the row-quad kernel, 2197 rows:
+    a ragged last quad), against the FP64 oracle."""
     from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
     n, n_obs, nt = 12, 40, 150
     xyz, tets, det, ops, dt = jitter_problem(n, n_obs, nt, 21)
     m = Mesh(xyz, tets, det, dt, nt, precision="f32", flags=MESH_KEEP_ZEROS)
-    v = dict(V=1, packed=5, gather_batch=4) if K == 1 else WIDE_VARIANTS[1]
+    v = dict(V=1, packed=5, gather_batch=4) if K == 1 else WIDE_VARIANTS[1] if K == 16 else QUAD_VARIANTS[1]
     for d in ("fwd", "adj"):
         m.select_variant(K, d, **v)
     shape = (len(xyz),) if K == 1 else (len(xyz), K)
