@@ -858,7 +858,10 @@ __global__ void rhs_kernel(int64_t n_data, int64_t N, int K, const T* __restrict
 
 // Deterministic per-sample reductions: block b sums rows b*rpb + r0 + j*grid*rpb
 // for its sample column k = tid % K, then the rpb partial sums of a block are
-// added in order; partial[b][k].  Mode 0: sum x^2; mode 1: sum w_r x^2.
+// combined in a fixed order (warp shuffles first when K divides 32,
+// block_partial); partial[b][k].  A finishing kernel then sums the blocks'
+// partials of a sample with one warp (warp_colsum).  Mode 0: sum x^2; mode 1:
+// sum w_r x^2.
 struct RedShape {
   int rpb, bdim, grid;
 };
@@ -869,6 +872,13 @@ static RedShape red_shape(int K, int64_t rows, int n_part) {
   r.grid = (int)std::max<int64_t>(1, std::min<int64_t>(n_part, (rows + r.rpb - 1) / r.rpb));
   return r;
 }
+
+// Finishing kernels: one warp per sample column (128-thread blocks).
+inline unsigned fin_blocks(int K) { return (unsigned)(((int64_t)K * 32 + 127) / 128); }
+#define PAT_FIN_K()                                                    \
+  const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); \
+  if (k >= K) return;                                                  \
+  const bool lead = (threadIdx.x & 31) == 0
 
 template <typename T, bool WEIGHTED>
 __global__ void sumsq_kernel(const T* __restrict__ X, const double* __restrict__ w, int64_t rows, int K, int rpb,
@@ -881,13 +891,7 @@ __global__ void sumsq_kernel(const T* __restrict__ X, const double* __restrict__
     const double x = (double)X[r * K + k];
     acc += WEIGHTED ? w[r] * x * x : x * x;
   }
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  if (r0 == 0) {
-    double s = 0.0;
-    for (int j = 0; j < rpb; ++j) s += sh[j * K + k];
-    partial[(int64_t)blockIdx.x * K + k] = s;
-  }
+  block_partial(acc, K, rpb, sh, partial);
 }
 
 // s = ah + sqrt(M_L) r_p (eq. lsqr-transpose-action), optionally d = s, and sum s^2.
@@ -906,13 +910,7 @@ __global__ void combine_s_kernel(const T* ah, const T* __restrict__ r_p, const d
     if (d_out) d_out[i] = s;
     acc += (double)s * (double)s;
   }
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  if (r0 == 0) {
-    double t = 0.0;
-    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
-    partial[(int64_t)blockIdx.x * K + k] = t;
-  }
+  block_partial(acc, K, rpb, sh, partial);
 }
 
 __global__ void set_double_kernel(double* p, double v) { *p = v; }
@@ -921,10 +919,9 @@ __device__ __forceinline__ void flag(int* status, int code) { atomicCAS(status, 
 
 // gamma = sum of partial slot A (first CGLS scalar)
 __global__ void finalize_gamma0_kernel(const double* pa, int na, int K, double* gamma, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k);
+  if (!lead) return;
   if (!isfinite(s)) flag(status, PAT_ENUMERIC);
   gamma[k] = s;
 }
@@ -932,11 +929,9 @@ __global__ void finalize_gamma0_kernel(const double* pa, int na, int K, double* 
 // alpha = gamma / ||q||^2, ||q||^2 = ||q_d||^2 + ||M^{1/2} d||^2
 __global__ void finalize_alpha_kernel(const double* pa, int na, const double* pb, int nb, int K, const double* gamma,
                                       double* alpha, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
-  for (int b = 0; b < nb; ++b) s += pb[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k) + warp_colsum(pb, nb, K, k);
+  if (!lead) return;
   double a = 0.0;
   if (gamma[k] == 0.0) {
     a = 0.0;  // converged exactly: keep the iterate
@@ -950,10 +945,9 @@ __global__ void finalize_alpha_kernel(const double* pa, int na, const double* pb
 
 // gamma' = ||s||^2, beta = gamma'/gamma, gamma = gamma'
 __global__ void finalize_beta_kernel(const double* pa, int na, int K, double* gamma, double* beta, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k);
+  if (!lead) return;
   double bt = 0.0;
   if (gamma[k] > 0.0 && isfinite(s)) {
     bt = s / gamma[k];
@@ -967,22 +961,17 @@ __global__ void finalize_beta_kernel(const double* pa, int na, int K, double* ga
 // out[2k] = sum of the data-block partials, out[2k+1] = sum of the prior-block
 // partials of sample k (the two blocks of ||r||^2 separately)
 __global__ void finalize_blocks_kernel(const double* pa, int na, const double* pb, int nb, int K, double* out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double sa = 0.0, sb = 0.0;
-  for (int b = 0; b < na; ++b) sa += pa[(int64_t)b * K + k];
-  for (int b = 0; b < nb; ++b) sb += pb[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double sa = warp_colsum(pa, na, K, k), sb = warp_colsum(pb, nb, K, k);
+  if (!lead) return;
   out[2 * k] = sa;
   out[2 * k + 1] = sb;
 }
 
 __global__ void finalize_sum2_kernel(const double* pa, int na, const double* pb, int nb, int K, double* out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
-  for (int b = 0; b < nb; ++b) s += pb[(int64_t)b * K + k];
-  out[k] = s;
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k) + warp_colsum(pb, nb, K, k);
+  if (lead) out[k] = s;
 }
 
 // x += alpha d (FP64), r_p -= alpha sqrt(M_L) d
@@ -1174,7 +1163,7 @@ pat_status begin_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
   double* part = (double*)(ws + L.partial);
   combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
       (T*)(ws + L.s), (T*)(ws + L.r_p), m.sqrt_ml, m.N, K, rsN.rpb, (T*)(ws + L.s), (T*)(ws + L.d), part);
-  finalize_gamma0_kernel<<<nblocks(K, 128), 128, 0, st>>>(part, rsN.grid, K, (double*)(ws + L.gamma),
+  finalize_gamma0_kernel<<<fin_blocks(K), 128, 0, st>>>(part, rsN.grid, K, (double*)(ws + L.gamma),
                                                            (int*)(ws + L.status));
   count(m, 2);
   return cuda_check(cudaGetLastError(), "cgls_begin launch");
@@ -1196,7 +1185,7 @@ pat_status iter_mid(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
   sumsq_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>((T*)(ws + L.q_d), nullptr, ndata, K,
                                                                                  rsD.rpb, pa);
   sumsq_kernel<T, true><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(d, m.ml, m.N, K, rsN.rpb, pb);
-  finalize_alpha_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, (double*)(ws + L.gamma),
+  finalize_alpha_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, (double*)(ws + L.gamma),
                                                           alpha, (int*)(ws + L.status));
   update_x_rp_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, alpha, d, m.sqrt_ml, (double*)(ws + L.x),
                                                           (T*)(ws + L.r_p));
@@ -1215,7 +1204,7 @@ pat_status iter_post(const DeviceMesh& m, int K, char* ws, cudaStream_t st) {
   double* beta = (double*)(ws + L.beta);
   combine_s_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(s, (T*)(ws + L.r_p), m.sqrt_ml, m.N, K,
                                                                              rsN.rpb, s, nullptr, pa);
-  finalize_beta_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, (double*)(ws + L.gamma), beta,
+  finalize_beta_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsN.grid, K, (double*)(ws + L.gamma), beta,
                                                          (int*)(ws + L.status));
   update_d_kernel<T><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, beta, s, (T*)(ws + L.d));
   count(m, 3);
@@ -1247,9 +1236,9 @@ static pat_status residual_t(const DeviceMesh& m, int K, double* out, char* ws, 
   sumsq_kernel<T, false><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>((T*)(ws + L.r_p), nullptr, m.N, K,
                                                                                  rsN.rpb, pb);
   if (blocks)
-    finalize_blocks_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
+    finalize_blocks_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
   else
-    finalize_sum2_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
+    finalize_sum2_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, out);
   count(m, 3);
   return cuda_check(cudaGetLastError(), "residual launch");
 }
@@ -1350,13 +1339,7 @@ __global__ void lsqr_u_kernel(const T* __restrict__ q, const double* __restrict_
     ub[i] = u;
     acc += (double)u * (double)u;
   }
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  if (r0 == 0) {
-    double t = 0.0;
-    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
-    partial[(int64_t)blockIdx.x * K + k] = t;
-  }
+  block_partial(acc, K, rpb, sh, partial);
 }
 
 // t = (ah + sqrt(M_L) ub_p) / beta - beta v (v NULL at the start) into out, and sum t^2
@@ -1377,13 +1360,7 @@ __global__ void lsqr_t_kernel(const T* ah, const T* __restrict__ ub_p, const dou
     out[i] = tv;
     acc += (double)tv * (double)tv;
   }
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  if (r0 == 0) {
-    double t = 0.0;
-    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
-    partial[(int64_t)blockIdx.x * K + k] = t;
-  }
+  block_partial(acc, K, rpb, sh, partial);
 }
 
 __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0 ? a / b : 0.0; }
@@ -1391,11 +1368,9 @@ __device__ __forceinline__ double safe_div(double a, double b) { return b != 0.0
 // beta_1 = ||b||: phibar = beta, 1 / beta
 __global__ void lsqr_beta0_kernel(const double* pa, int na, const double* pb, int nb, int K, double* lsq,
                                   int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
-  for (int b = 0; b < nb; ++b) s += pb[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k) + warp_colsum(pb, nb, K, k);
+  if (!lead) return;
   if (!isfinite(s)) flag(status, PAT_ENUMERIC);
   const double beta = sqrt(s);
   lsq[kBeta * K + k] = beta;
@@ -1405,10 +1380,9 @@ __global__ void lsqr_beta0_kernel(const double* pa, int na, const double* pb, in
 
 // alpha_1 = ||A^T u_1||: rhobar = alpha, 1 / alpha
 __global__ void lsqr_alpha0_kernel(const double* pa, int na, int K, double* lsq, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k);
+  if (!lead) return;
   if (!isfinite(s)) flag(status, PAT_ENUMERIC);
   const double alpha = sqrt(s);
   lsq[kAlpha * K + k] = alpha;
@@ -1420,11 +1394,9 @@ __global__ void lsqr_alpha0_kernel(const double* pa, int na, int K, double* lsq,
 // rho = (rhobar^2 + beta^2)^{1/2}, c = rhobar / rho, s = beta / rho, phi = c phibar, phibar = s phibar
 __global__ void lsqr_beta_kernel(const double* pa, int na, const double* pb, int nb, int K, double* lsq,
                                  int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s2 = 0.0;
-  for (int b = 0; b < na; ++b) s2 += pa[(int64_t)b * K + k];
-  for (int b = 0; b < nb; ++b) s2 += pb[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s2 = warp_colsum(pa, na, K, k) + warp_colsum(pb, nb, K, k);
+  if (!lead) return;
   if (!isfinite(s2)) flag(status, PAT_ENUMERIC);
   const double beta = sqrt(s2), rhobar = lsq[kRhoBar * K + k], phibar = lsq[kPhiBar * K + k];
   const double rho = sqrt(rhobar * rhobar + beta * beta);
@@ -1440,10 +1412,9 @@ __global__ void lsqr_beta_kernel(const double* pa, int na, const double* pb, int
 
 // alpha_{i+1} = ||t||, theta = s alpha, rhobar = -c alpha, x / w coefficients phi / rho, theta / rho
 __global__ void lsqr_alpha_kernel(const double* pa, int na, int K, double* lsq, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s2 = 0.0;
-  for (int b = 0; b < na; ++b) s2 += pa[(int64_t)b * K + k];
+  PAT_FIN_K();
+  const double s2 = warp_colsum(pa, na, K, k);
+  if (!lead) return;
   if (!isfinite(s2)) flag(status, PAT_ENUMERIC);
   const double alpha = sqrt(s2), rho = lsq[kRho * K + k];
   const double theta = lsq[kS * K + k] * alpha;
@@ -1497,13 +1468,13 @@ static pat_status lsqr_begin_t(const DeviceMesh& m, const T* y_obs, double sigma
                                                                                  rsD.rpb, pa);
   sumsq_kernel<T, false><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>((T*)(ws + L.r_p), nullptr, m.N, K,
                                                                                  rsN.rpb, pb);
-  lsqr_beta0_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, lsq, status);
+  lsqr_beta0_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, lsq, status);
   // t = A^T ub_1 / beta_1; alpha_1 = ||t||; v_1 = t / alpha_1; w_1 = v_1
   PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
   T* s = (T*)(ws + L.s);
   lsqr_t_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
       s, (T*)(ws + L.r_p), m.sqrt_ml, nullptr, m.N, K, rsN.rpb, lsq, s, pa);
-  lsqr_alpha0_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, lsq, status);
+  lsqr_alpha0_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsN.grid, K, lsq, status);
   lsqr_vxw_kernel<T, false><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, s, lsq, (T*)(ws + L.d), (T*)(ws + L.w),
                                                               (double*)(ws + L.x));
   count(m, 6);
@@ -1534,12 +1505,12 @@ static pat_status lsqr_iterate_t(const DeviceMesh& m, double sigma, int K, int n
         (T*)(ws + L.q_d), nullptr, (T*)(ws + L.r_d), ndata, K, rsD.rpb, lsq, pa);
     lsqr_u_kernel<T, true><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
         v, m.sqrt_ml, (T*)(ws + L.r_p), m.N, K, rsN.rpb, lsq, pb);
-    lsqr_beta_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, lsq, status);
+    lsqr_beta_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsD.grid, pb, rsN.grid, K, lsq, status);
     // t = A^T ub / beta - beta v, alpha = ||t||, v = t / alpha, x and w updates
     PAT_TRY(cgls_solve(m, 1, K, sigma, ws, st));
     lsqr_t_kernel<T><<<rsN.grid, rsN.bdim, rsN.bdim * sizeof(double), st>>>(
         s, (T*)(ws + L.r_p), m.sqrt_ml, v, m.N, K, rsN.rpb, lsq, s, pa);
-    lsqr_alpha_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsN.grid, K, lsq, status);
+    lsqr_alpha_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsN.grid, K, lsq, status);
     lsqr_vxw_kernel<T, true><<<nblocks(m.N * K), 256, 0, st>>>(m.N, K, s, lsq, v, (T*)(ws + L.w),
                                                                (double*)(ws + L.x));
     count(m, 6);
@@ -1594,21 +1565,13 @@ __global__ void misfit_kernel(const T* __restrict__ Y, const T* __restrict__ y_o
     const double d = (double)Y[r * K + k] - (double)y_obs[r];
     acc += d * d;
   }
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  if (r0 == 0) {
-    double t = 0.0;
-    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
-    partial[(int64_t)blockIdx.x * K + k] = t;
-  }
+  block_partial(acc, K, rpb, sh, partial);
 }
 
 __global__ void misfit_finish_kernel(const double* pa, int na, int K, double scale, double* out) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double s = 0.0;
-  for (int b = 0; b < na; ++b) s += pa[(int64_t)b * K + k];
-  out[k] = sqrt(s) * scale;
+  PAT_FIN_K();
+  const double s = warp_colsum(pa, na, K, k);
+  if (lead) out[k] = sqrt(s) * scale;
 }
 
 template <typename T>
@@ -1625,7 +1588,7 @@ static pat_status misfit_t(const DeviceMesh& m, const double* x, const T* y_obs,
   double* pa = (double*)(ws + L.partial);
   const RedShape rsD = red_shape(K, ndata, L.n_part);
   misfit_kernel<T><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>(Y, y_obs, ndata, K, rsD.rpb, pa);
-  misfit_finish_kernel<<<nblocks(K, 128), 128, 0, st>>>(pa, rsD.grid, K, 1.0 / (sigma * std::sqrt((double)ndata)),
+  misfit_finish_kernel<<<fin_blocks(K), 128, 0, st>>>(pa, rsD.grid, K, 1.0 / (sigma * std::sqrt((double)ndata)),
                                                          out);
   count(m, 2);
   return cuda_check(cudaGetLastError(), "misfit launch");

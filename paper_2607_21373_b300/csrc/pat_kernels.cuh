@@ -843,4 +843,43 @@ __global__ void __launch_bounds__(256) adj3_finish_kernel(int64_t row_threads, i
   st<T, V>(out + off, o);
 }
 
+// The rpb row lanes' sums of each sample column k of a block into
+// partial[block][k], in a fixed order: with K dividing 32 the 32/K row lanes
+// of a warp first combine by warp shuffles (a fixed tree), then the block's
+// warps are added in order; otherwise the rpb row lanes are added in order
+// through shared memory.  Every thread of the block calls it.
+__device__ __forceinline__ void block_partial(double acc, int K, int rpb, double* sh, double* __restrict__ partial) {
+  const int k = threadIdx.x % K;
+  if (K < 32 && (32 % K) == 0) {  // blockDim.x = 256: whole warps
+    for (int off = 16; off >= K; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < K) sh[warp * K + lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double t = 0.0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += sh[j * K + k];
+      partial[(int64_t)blockIdx.x * K + k] = t;
+    }
+    return;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int j = 0; j < rpb; ++j) t += sh[j * K + k];
+    partial[(int64_t)blockIdx.x * K + k] = t;
+  }
+}
+
+// Column k of the [na][K] block partials summed by the 32 lanes of a warp:
+// lane j adds blocks j, j + 32, ... in order, then a butterfly of warp
+// shuffles; every lane ends with the same bits (each level adds the same two
+// values in either order).
+__device__ __forceinline__ double warp_colsum(const double* __restrict__ pa, int na, int K, int k) {
+  double s = 0.0;
+  for (int b = (int)(threadIdx.x & 31); b < na; b += 32) s += pa[(int64_t)b * K + k];
+  for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
 }  // namespace pat

@@ -354,8 +354,8 @@ __global__ void interp_t_kernel(int64_t G, int K, int lk, const int32_t* __restr
 // (l < R = 256 / min(K, 256) row lanes of block b; samples over blockIdx.y
 // when K > 256).  A lane adds runs of 8 of its rows in FP32 (non-negative
 // terms: a run's relative error is at most 8 units of FP32 rounding) and the
-// runs in FP64, and the R lanes are added in lane order: a fixed order, so
-// the sums are deterministic.  (B300 issues FP64 arithmetic at a small
+// runs in FP64, and the R lanes are added in a fixed order (warp shuffles,
+// then the warps in order, when K divides 32): the sums are deterministic.  (B300 issues FP64 arithmetic at a small
 // fraction of its FP32 rate; a double operation per element would bound
 // these passes by the FP64 pipe, not by memory.)
 __global__ void __launch_bounds__(256) sq_partial_kernel(const float* __restrict__ X, int64_t rows, int K,
@@ -384,6 +384,19 @@ __global__ void __launch_bounds__(256) sq_partial_kernel(const float* __restrict
     }
     acc += (double)run;
   }
+  if (KB < 32 && (32 % KB) == 0) {
+    // the 32 / KB row lanes of a warp by warp shuffles (a fixed tree), then the warps in order
+    for (int off = 16; off >= KB; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < KB) red[warp * KB + lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < KB && k < K) {
+      double sum = 0.0;
+      for (int j = 0; j < 8; ++j) sum += red[j * KB + kl];
+      part[(int64_t)blockIdx.x * K + k] = sum;
+    }
+    return;
+  }
   red[threadIdx.x] = acc;
   __syncthreads();
   if (l == 0 && k < K) {
@@ -393,19 +406,20 @@ __global__ void __launch_bounds__(256) sq_partial_kernel(const float* __restrict
   }
 }
 
-__device__ __forceinline__ double colsum(const double* part, int nb, int K, int k) {
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[(int64_t)b * K + k];
-  return s;
-}
-
 __device__ __forceinline__ bool bad(double v) { return !(v > 0.0) || !isfinite(v); }
+
+// The scalar kernels run one warp per sample (128-thread blocks); the warp
+// sums the sample's block partials by warp_colsum and its first lane finishes.
+#define LAT_WARP_K()                                                   \
+  const int k = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); \
+  if (k >= K) return;                                                  \
+  const bool lead = (threadIdx.x & 31) == 0
 
 // gamma = ||s||^2 (begin)
 __global__ void gamma0_kernel(const double* part, int nb, int K, double* gamma, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const double g = colsum(part, nb, K, k);
+  LAT_WARP_K();
+  const double g = warp_colsum(part, nb, K, k);
+  if (!lead) return;
   if (!isfinite(g)) atomicExch(status, (int)PAT_ENUMERIC);
   gamma[k] = g;
 }
@@ -414,9 +428,9 @@ __global__ void gamma0_kernel(const double* part, int nb, int K, double* gamma, 
 // FP32 residual updates
 __global__ void alpha_kernel(const double* pq, const double* pd, int nb, int K, const double* gamma, double* alpha,
                              float* alphaf, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const double qq = colsum(pq, nb, K, k) + colsum(pd, nb, K, k);
+  LAT_WARP_K();
+  const double qq = warp_colsum(pq, nb, K, k) + warp_colsum(pd, nb, K, k);
+  if (!lead) return;
   double a = 0.0;
   if (gamma[k] > 0.0) {
     if (bad(qq)) atomicExch(status, (int)PAT_ENUMERIC);
@@ -428,9 +442,9 @@ __global__ void alpha_kernel(const double* pq, const double* pd, int nb, int K, 
 
 // beta = ||s||^2 / gamma (and rounded to FP32); gamma = ||s||^2
 __global__ void beta_kernel(const double* part, int nb, int K, double* gamma, float* betaf, int* status) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  const double g = colsum(part, nb, K, k);
+  LAT_WARP_K();
+  const double g = warp_colsum(part, nb, K, k);
+  if (!lead) return;
   double b = 0.0;
   if (!isfinite(g)) atomicExch(status, (int)PAT_ENUMERIC);
   else if (gamma[k] > 0.0) b = g / gamma[k];
@@ -890,7 +904,7 @@ pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* m, cons
   PAT_TRY(transpose_into_s());
   PAT_TRY(cuda_check(cudaMemcpyAsync(dz, sz, (size_t)G * K * 4, cudaMemcpyDeviceToDevice, st), "latent copy"));
   PAT_TRY(sq_partials(sz, G, K, L.nb, pa, st));
-  gamma0_kernel<<<nblk(K, 128), 128, 0, st>>>(pa, L.nb, K, gamma, status);
+  gamma0_kernel<<<nblk((int64_t)K * 32, 128), 128, 0, st>>>(pa, L.nb, K, gamma, status);
   for (int it = 0; it < n_iter; ++it) {
     // q_d = G P T d / sigma
     PAT_TRY(apply_T(g, dz, K, tmp, nullptr, cbuf, st));
@@ -898,12 +912,12 @@ pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* m, cons
     PAT_TRY(cgls_solve(dm, 0, K, sigma, w, st));
     PAT_TRY(sq_partials(q_d, ndata, K, L.nb, pa, st));
     PAT_TRY(sq_partials(dz, G, K, L.nb, pb, st));
-    alpha_kernel<<<nblk(K, 128), 128, 0, st>>>(pa, pb, L.nb, K, gamma, alpha, alphaf, status);
+    alpha_kernel<<<nblk((int64_t)K * 32, 128), 128, 0, st>>>(pa, pb, L.nb, K, gamma, alpha, alphaf, status);
     lat_update_x_kernel<<<vb, 256, 0, st>>>(G * K, K, lk, alpha, alphaf, dz, x, rz);
     lat_axpy_kernel<<<vbd, 256, 0, st>>>(ndata * K, K, lk, alphaf, -1.0f, q_d, r_d, r_d);  // r_d -= alpha q_d
     PAT_TRY(transpose_into_s());
     PAT_TRY(sq_partials(sz, G, K, L.nb, pa, st));
-    beta_kernel<<<nblk(K, 128), 128, 0, st>>>(pa, L.nb, K, gamma, betaf, status);
+    beta_kernel<<<nblk((int64_t)K * 32, 128), 128, 0, st>>>(pa, L.nb, K, gamma, betaf, status);
     lat_axpy_kernel<<<vb, 256, 0, st>>>(G * K, K, lk, betaf, 1.0f, dz, sz, dz);  // d = s + beta d
   }
   PAT_TRY(cuda_check(cudaGetLastError(), "pat_rto_sample_matern launch"));
