@@ -109,6 +109,8 @@ FORCED = {
     "w16ro": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True),
     "w16rb": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=2),
     "w16rcs": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
+    "w16qop": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
+                   prefetch_meta=True),
     "w16rco": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                    own_async=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
@@ -343,7 +345,8 @@ def kernel_name(e, adj):
             tf, " row-major" if packed == 6 else "", nb, ", columns per round" if e.get("early") else "",
             ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
             ", serial tail" if e.get("tail_serial") else "") + (" (own rows by bulk copy)" if e.get("own_async") == 2 else " (own rows async)" if e.get("own_async") else "") + (
-            " (next metadata to L1)" if e.get("prefetch_meta") else "")
+            ((" (quad's coefficient lines to L1)" if packed == 5 else " (next metadata to L1)")
+             if e.get("prefetch_meta") else ""))
     if packed == 2:
         return "step3t_kernel<8,%s>" % tf
     if packed == 4:

@@ -1320,7 +1320,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     }
     c.own = v->own_async == 2 ? 2 : (v->own_async && nb == 4 && !c.big ? 1 : 0);
     c.tail = (v->tail_serial || c.own == 1) && nb == 4 && !c.big;
-    c.pfm = v->prefetch_meta && v->packed == 6 && nb == 4 && !c.big;
+    c.pfm = v->prefetch_meta && (v->packed == 6 || (v->packed == 5 && K == 64)) && nb == 4 && !c.big;
     if (c.pfm) c.tail = 1;
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;

@@ -381,6 +381,15 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
            : c.early   ? step3w_persist_kernel<ADJ, 8, true, 256, 2, 2, QUAD>
                        : step3w_persist_kernel<ADJ, 8, false, 256, 2, 2, QUAD>;
   }
+  if constexpr (QUAD) {
+    if (c.pfm) {  // the quad's coefficient lines prefetched into L1; serial tail
+      if (c.own)
+        return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, true, 1, true>
+                       : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, true, 1, true>;
+      return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, true, 0, true>
+                     : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, true, 0, true>;
+    }
+  }
   if constexpr (!QUAD) {
     if (c.pfm) {
       if (c.own) return step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 1, true>;
@@ -1771,6 +1780,9 @@ static const TuneVariant kTuneVariants[] = {
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 2},  // 69 the same, columns per round
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 2},  // 70 row-major, paired tail, own rows by bulk copies
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8, 2},  // 71 the same, columns per round
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 74 quad slots, serial tail, own async, quad's pairs to L1
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 1},  // 75 the same, columns per round
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 76 quad slots, serial tail, quad's pairs to L1
     {8, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 0},  // 72 row quads (union of four rows' sources), K = 64
     {8, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 1},  // 73 row quads, own rows by cp.async
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},     // 63 row pairs (union of two rows' sources), 2 blocks/SM
@@ -1789,8 +1801,8 @@ static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, in
     return m.prec == PAT_F32 && m.split && m.fwd.quad_col && m.adj3.quad_col && m.fwd.w16r_col && V == 8 &&
            K == 64;
   if (t.packed == 5)  // 16-slot rows: V = 8 persistent, or one thread per row for K = 1
-    return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (V == 8 || (V == 1 && K == 1 && t.batch == 4 &&
-                                                                         !t.early && !t.big && !t.hint));
+    return m.prec == PAT_F32 && m.split && m.fwd.w16_col && (!t.pfm || K == 64) &&
+           (V == 8 || (V == 1 && K == 1 && t.batch == 4 && !t.early && !t.big && !t.hint));
   if ((t.batch || t.hint || t.wide || t.big) && V != 8) return false;
   if (t.persist == 3 && (V != 8 || K / V < 4)) return false;  // staged metadata: <= kStageRows rows per chunk
   if ((t.pf || t.persist) && V == 1) return false;
@@ -1849,7 +1861,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.batch = t.batch;
         g_force.tail = t.packed >= 5 ? t.hint : 0;
         g_force.own = t.packed >= 5 ? t.own : 0;
-        g_force.pfm = t.packed == 6 ? t.pfm : 0;
+        g_force.pfm = (t.packed == 5 || t.packed == 6) ? t.pfm : 0;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);

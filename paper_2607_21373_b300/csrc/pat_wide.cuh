@@ -221,7 +221,11 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // launched as a programmatic dependent of the previous step.
 // PFM: before a warp works on a chunk it asks L1 to prefetch the row metadata
 // (descriptor, columns, coefficient pairs; row-major slots) of its next chunk,
-// so that chunk starts with L1 hits instead of a round trip to L2.
+// so that chunk starts with L1 hits instead of a round trip to L2.  With the
+// quad-interleaved slots (K = 64: a chunk is one quad) it instead prefetches
+// the current quad's four 128-byte lines of coefficient pairs: each round of
+// 4 sources reads a new line of them, which would otherwise cost every round
+// its own L2 round trip.
 //
 // OA = 2 (K / 8 divides 32, so a 32-thread chunk covers whole rows: 32 / (K/8)
 // rows, 1 KB of each state array): each warp owns a 2 KB shared-memory copy of its
@@ -283,6 +287,11 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
         const int64_t row = t / KV;
         ob = ow + (row - row0) * A.K + (t - row * KV) * 4;
       }
+    }
+    if constexpr (PFM && QUAD) {
+      const int64_t t0 = c * 32;
+      if (lane < 4 && t0 < A.row_threads && KV == 8)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(A.ell_hl + (t0 / 32) * 64 + lane * 16));
     }
     if constexpr (PFM && !QUAD) {
       const int64_t tn = (c + S) * 32 + lane;
