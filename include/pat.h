@@ -59,7 +59,7 @@ typedef enum {
   PAT_EUNSTABLE = 4,    /* the time step makes the propagator grow (create)     */
   PAT_ENUMERIC = 5,     /* non-finite or non-positive CGLS scalar               */
   PAT_ETIMEOUT = 6,     /* a bounded device wait ran out                        */
-  PAT_EUNSUPPORTED = 7  /* valid request this build does not handle             */
+  PAT_EUNSUPPORTED = 7  /* valid request the library does not handle           */
 } pat_status;
 
 typedef enum { PAT_F32 = 0, PAT_F64 = 1 } pat_prec;
