@@ -18,6 +18,11 @@ Modules
              ergodic mean/std (eq. ergodic), dense posterior (Appendix A)
   gradient   derivative of a data misfit with respect to per-element c^2,
              by finite differences of the forward map (no adjoint trick)
+  matern     Whittle-Matern field by a spectral filter on a periodic box grid,
+             trilinear interpolation to the nodes and its transpose, RTO in the
+             latent space (Section 4.1.2 eq. matern-cov-op, Section 6.4)
+  rng        counter-based N(0,1) draws (SplitMix64 and Box-Muller, from their
+             published definitions) keyed by seed, stream, sample and element
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 against a closed form, an invariant or a brute-force evaluation, except the
