@@ -111,6 +111,10 @@ FORCED = {
     "w16rcs": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True),
     "w16qop": dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
                    prefetch_meta=True),
+    "w16rod": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
+                   dyn_chunks=True),
+    "w16rcod": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
+                    own_async=True, dyn_chunks=True),
     "w16rco": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                    own_async=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
@@ -346,7 +350,7 @@ def kernel_name(e, adj):
             ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
             ", serial tail" if e.get("tail_serial") else "") + (" (own rows by bulk copy)" if e.get("own_async") == 2 else " (own rows async)" if e.get("own_async") else "") + (
             ((" (quad's coefficient lines to L1)" if packed == 5 else " (next metadata to L1)")
-             if e.get("prefetch_meta") else ""))
+             if e.get("prefetch_meta") else "") + (" (chunks by counter)" if e.get("dyn_chunks") else ""))
     if packed == 2:
         return "step3t_kernel<8,%s>" % tf
     if packed == 4:

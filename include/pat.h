@@ -502,7 +502,7 @@ pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, i
  */
 typedef struct {
   int32_t direction, V, staged, packed, chunk, min_blocks, early, zorder, big_blocks, prefetch, persistent, pdl,
-      wide_loads, l2_hints, gather_batch, tail_serial, own_async, prefetch_meta;
+      wide_loads, l2_hints, gather_batch, tail_serial, own_async, prefetch_meta, dyn_chunks;
   double us_per_step;
 } pat_tune_entry;
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,
@@ -522,7 +522,10 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
  * values; 2, packed 6 with K <= 256: by two bulk asynchronous copies per warp
  * of its rows, completing on an mbarrier whose wait is bounded by the mesh's
  * wait budget, pat_mesh_set_wait_cycles, PAT_ETIMEOUT through pat_rto_status
- * when it runs out), prefetch_meta (packed 6) =
+ * when it runs out), dyn_chunks (packed 6, three-level form) = the warps'
+ * 32-thread chunks handed out in row order by an atomic counter (kept in
+ * the workspace's fourth state buffer) instead of the grid stride,
+ * prefetch_meta (packed 6) =
  * each warp asks L1 to prefetch its next chunk's row metadata; packed 6 = the same kernel
  * reading a row-major copy of the 16 slots instead of the quad-interleaved
  * one, V = 8 only) for direction 0 (forward) or 1

@@ -245,19 +245,19 @@ class Mesh:
                  "prefetch": e.prefetch, "persistent": int(e.persistent), "pdl": bool(e.pdl),
                  "wide_loads": bool(e.wide_loads), "l2_hints": bool(e.l2_hints), "gather_batch": int(e.gather_batch),
                  "tail_serial": bool(e.tail_serial), "own_async": int(e.own_async),
-                 "prefetch_meta": bool(e.prefetch_meta),
+                 "prefetch_meta": bool(e.prefetch_meta), "dyn_chunks": bool(e.dyn_chunks),
                  "us_per_step": e.us_per_step}
                 for e in table[:min(n.value, 256)]]
 
     def select_variant(self, K, direction, V, packed=1, chunk=4, staged=False, min_blocks=1, early=False,
                        zorder=False, big_blocks=False, prefetch=0, persistent=False, pdl=False, wide_loads=False,
                        l2_hints=False, gather_batch=0, tail_serial=False, own_async=False,
-                       prefetch_meta=False):
+                       prefetch_meta=False, dyn_chunks=False):
         """Force a step-kernel variant (pat_select_variant); direction 'fwd' or 'adj'."""
         e = _lib.TuneEntry(0 if direction == "fwd" else 1, V, int(staged), int(packed), int(chunk), int(min_blocks),
                            int(early), int(zorder), int(big_blocks), int(prefetch), int(persistent),
                            int(pdl), int(wide_loads), int(l2_hints), int(gather_batch), int(tail_serial),
-                           int(own_async), int(prefetch_meta), 0.0)
+                           int(own_async), int(prefetch_meta), int(dyn_chunks), 0.0)
         _lib.check(lib().pat_select_variant(self._h, K, 0 if direction == "fwd" else 1, C.byref(e)))
 
     def profile_enable(self, on=True):

@@ -38,7 +38,7 @@ class TuneEntry(C.Structure):
                 ("big_blocks", C.c_int32), ("prefetch", C.c_int32), ("persistent", C.c_int32),
                 ("pdl", C.c_int32), ("wide_loads", C.c_int32), ("l2_hints", C.c_int32), ("gather_batch", C.c_int32),
                 ("tail_serial", C.c_int32), ("own_async", C.c_int32),
-                ("prefetch_meta", C.c_int32),
+                ("prefetch_meta", C.c_int32), ("dyn_chunks", C.c_int32),
                 ("us_per_step", C.c_double)]
 
 

@@ -1322,6 +1322,14 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     c.tail = (v->tail_serial || c.own == 1) && nb == 4 && !c.big;
     c.pfm = v->prefetch_meta && (v->packed == 6 || (v->packed == 5 && K == 64)) && nb == 4 && !c.big;
     if (c.pfm) c.tail = 1;
+    if (v->dyn_chunks && (v->packed != 6 || nb != 4 || c.big || c.pfm || c.own == 2 || !mesh->d.three_level)) {
+      set_error("pat_select_variant: chunks handed out by a counter (dyn_chunks) need the row-major 16-slot rows "
+                "(packed 6) of the three-level form, rounds of 4, 256-thread blocks, no metadata prefetch and "
+                "own_async 0 or 1");
+      return PAT_EINVAL;
+    }
+    c.dyn = v->dyn_chunks ? 1 : 0;
+    if (c.dyn) c.tail = 1;
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);

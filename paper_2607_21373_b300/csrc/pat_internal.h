@@ -155,6 +155,7 @@ struct TuneCfg {
   int tail = 0;    // 16-slot kernel: 1 walks a row's tail entries one at a time (0: in pairs)
   int own = 0;     // 16-slot kernel: 1 copies the row's own x_s, x_{s-1} to shared memory by cp.async
   int pfm = 0;     // 16-slot row-major kernel: 1 prefetches the next chunk's row metadata into L1
+  int dyn = 0;     // 16-slot row-major kernel: 1 hands the chunks out by an atomic counter
 };
 
 struct DeviceMesh {

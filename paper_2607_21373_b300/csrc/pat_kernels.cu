@@ -406,6 +406,15 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
                      : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, false, 2>;
     }
   }
+  if constexpr (!QUAD) {
+    if (c.dyn) {  // chunks handed out by an atomic counter (own rows by cp.async, serial tail)
+      if (c.own)
+        return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, 1, false, true>
+                       : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 1, false, true>;
+      return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, 0, false, true>
+                     : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 0, false, true>;
+    }
+  }
   if (c.own)
     return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, 1>
                    : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, 1>;
@@ -643,10 +652,26 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
 // Launch i (0 <= i <= N_T) of a three-level forward solve: steps 0..N_T-1, then
 // the observation of state N_T.  Step s reads x_s (p0 for s = 0) and x_{s-1}
 // and writes x_{s+1} into b[s % 3]; it observes state s (s >= 1).
+// The chunk counters of the dynamic hand-out: two words at the start of the
+// fourth state buffer (unused by the three-level form); launch i counts on
+// word i % 2 and zeroes word (i + 1) % 2 for launch i + 1.  A solve zeroes
+// both before its first launch (zero_dyn_counters).
+template <typename T>
+void dyn_counters(Step3Args<T>& A, T* const b[3], int64_t NK, int i) {
+  unsigned int* w = reinterpret_cast<unsigned int*>(b[2] + NK);
+  A.dyn_ctr = w + (i & 1);
+  A.dyn_next = w + ((i + 1) & 1);
+}
+template <typename T>
+pat_status zero_dyn_counters(T* const b[3], int64_t NK, cudaStream_t st) {
+  return cuda_check(cudaMemsetAsync(b[2] + NK, 0, 2 * sizeof(unsigned int), st), "chunk counter reset");
+}
+
 template <typename T>
 Step3Args<T> fwd3_args(const DeviceMesh& m, int K, int V, const T* p0, T* Y, T scale, T* const b[3], int i,
                        int64_t* threads) {
   Step3Args<T> A{};
+  dyn_counters(A, b, m.N * (int64_t)K, i);
   A.N = m.N;
   A.K = K;
   A.n_obs = m.n_obs;
@@ -691,6 +716,7 @@ template <typename T>
 Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale, T* const b[3], int i,
                        int64_t* threads) {
   Step3Args<T> A{};
+  dyn_counters(A, b, m.N * (int64_t)K, i);
   A.N = m.N;
   A.K = K;
   A.n_obs = m.n_obs;
@@ -728,6 +754,7 @@ template <typename T, int V, bool SPLIT>
 static pat_status forward3_t(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
   const int64_t NK = m.N * (int64_t)K;
   T* const b[3] = {ws, ws + NK, ws + 2 * NK};
+  PAT_TRY(zero_dyn_counters(b, NK, st));
   const size_t pp = prof_begin(m, 0, st);
   for (int i = 0; i <= m.n_steps; ++i) {
     int64_t threads = 0;
@@ -742,6 +769,7 @@ template <typename T, int V, bool SPLIT>
 static pat_status adjoint3_t(const DeviceMesh& m, const T* Yhat, int K, T* out, T scale, T* ws, cudaStream_t st) {
   const int64_t NK = m.N * (int64_t)K;
   T* const b[3] = {ws, ws + NK, ws + 2 * NK};
+  PAT_TRY(zero_dyn_counters(b, NK, st));
   const int NT = m.n_steps;
   const size_t pp = prof_begin(m, 1, st);
   for (int i = 0; i <= NT; ++i) {
@@ -1646,6 +1674,7 @@ static pat_status probe_t(const DeviceMesh& m, int K, char* ws, int n_probe, int
   PAT_TRY(cuda_check(cudaEventCreate(&e1), "autotune event"));
   const int V = std::min(g_force.V, pick_vec<T>(K, {ws + L.d, ws + L.q_d, ws + L.r_d, ws + L.state}));
   auto run = [&](bool timed) {
+    zero_dyn_counters(b, NK, st);
     if (timed) cudaEventRecord(e0, st);
     for (int i = 0; i < n_probe; ++i) {
       int64_t thr = 0;
@@ -1706,7 +1735,7 @@ constexpr int kTuneTableMax = 256;  // entries pat_autotune writes at most
 
 struct TuneVariant {
   int packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v, own = 0,
-      pfm = 0;
+      pfm = 0, dyn = 0;
 };
 static const TuneVariant kTuneVariants[] = {
     // packed, stage, chunk, zorder, big, pf, persist, pdl, wide, hint, batch, minb, early, only_v
@@ -1783,6 +1812,9 @@ static const TuneVariant kTuneVariants[] = {
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 74 quad slots, serial tail, own async, quad's pairs to L1
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 1},  // 75 the same, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 76 quad slots, serial tail, quad's pairs to L1
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 0, 1},  // 77 row-major, serial tail, own async, chunks by counter
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 0, 1},  // 78 the same, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 0, 0, 1},  // 79 row-major, serial tail, columns per round, by counter
     {8, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 0},  // 72 row quads (union of four rows' sources), K = 64
     {8, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 1},  // 73 row quads, own rows by cp.async
     {7, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8},     // 63 row pairs (union of two rows' sources), 2 blocks/SM
@@ -1793,7 +1825,7 @@ static const TuneVariant kTuneVariants[] = {
 static bool tune_applicable(const TuneVariant& t, const DeviceMesh& m, int V, int K) {
   if (t.only_v && V != t.only_v) return false;
   if (t.packed == 6)
-    return m.prec == PAT_F32 && m.split && m.fwd.w16r_col && V == 8 &&
+    return m.prec == PAT_F32 && m.split && m.fwd.w16r_col && V == 8 && (!t.dyn || m.three_level) &&
            (t.own != 2 || (K >= 8 && K <= 256 && 32 % (K / 8) == 0 && m.d_status != nullptr));  // whole rows per chunk
   if (t.packed == 7)
     return m.prec == PAT_F32 && m.split && m.fwd.pair_col && m.adj3.pair_col && m.fwd.w16r_col && V == 8;
@@ -1862,6 +1894,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
         g_force.tail = t.packed >= 5 ? t.hint : 0;
         g_force.own = t.packed >= 5 ? t.own : 0;
         g_force.pfm = (t.packed == 5 || t.packed == 6) ? t.pfm : 0;
+        g_force.dyn = t.packed == 6 ? t.dyn : 0;
         float us = 0.0f;
         pat_status s = m.prec == PAT_F64 ? probe_t<double>(m, K, ws, n_probe, dir, st, &us)
                                          : probe_t<float>(m, K, ws, n_probe, dir, st, &us);
@@ -1871,7 +1904,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
           table[n] = pat_tune_entry{dir,    V,       t.stage, t.packed, t.packed ? t.chunk : 0,
                                     t.minb, t.early, t.zorder, t.big, t.pf, t.persist, t.pdl,
                                     t.wide, t.packed >= 5 ? 0 : t.hint, t.batch,
-                                    t.packed >= 5 ? t.hint : 0, t.own, t.pfm, (double)us};
+                                    t.packed >= 5 ? t.hint : 0, t.own, t.pfm, t.dyn, (double)us};
         ++n;
         if (us < best_us) {
           best_us = us;

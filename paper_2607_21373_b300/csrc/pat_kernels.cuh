@@ -304,6 +304,11 @@ struct Step3Args {
   // word that gets PAT_ETIMEOUT and the SM cycles a warp waits before it gives up
   int32_t* status;
   long long wait_cycles;
+  // dynamic chunk hand-out (persistent kernels): this launch's chunk counter
+  // and the next launch's, which this launch zeroes (both in the unused
+  // fourth state buffer of the three-level form)
+  unsigned int* dyn_ctr;
+  unsigned int* dyn_next;
 };
 
 // Row metadata staging.  With STAGE, the block first copies the column /

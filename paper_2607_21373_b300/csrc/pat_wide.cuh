@@ -231,8 +231,14 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // rows, 1 KB of each state array): each warp owns a 2 KB shared-memory copy of its
 // chunk's x_s and x_{s-1} rows and an mbarrier; lane 0 issues the chunk's two
 // bulk copies once every lane is done with the previous chunk's copy.
+//
+// DYN: chunks are handed out by an atomic counter instead of the grid stride:
+// a warp that is done takes the next chunk in row order, so warps whose
+// chunks hold slow rows (boundary rows with long tails, sensor rows) no longer
+// set the end of the step.  Lane 0 asks for the following chunk when it
+// starts one, so the counter's round trip hides behind the chunk's work.
 template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, int OA = 0,
-          bool PFM = false>
+          bool PFM = false, bool DYN = false>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   // per-thread slots of the own-row copies, slot q of thread i at [q][i]
   // (consecutive threads contiguous: conflict-free 16-byte accesses)
@@ -256,7 +262,16 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
   const int wpb = BS >> 5;
   const int64_t S = (int64_t)gridDim.x * wpb;
   const int KV = A.K / 8;
-  for (int64_t c = (int64_t)blockIdx.x * wpb + warp; c < n_chunks; c += S) {
+  unsigned int c_next = 0;
+  if constexpr (DYN) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.dyn_next = 0u;  // the next launch starts from chunk 0
+    if (lane == 0) c_next = atomicAdd(A.dyn_ctr, 1u);
+    c_next = __shfl_sync(0xffffffffu, c_next, 0);
+  }
+  for (int64_t c = DYN ? (int64_t)c_next : (int64_t)blockIdx.x * wpb + warp; c < n_chunks;) {
+    if constexpr (DYN) {
+      if (lane == 0) c_next = atomicAdd(A.dyn_ctr, 1u);  // used at the end of this chunk
+    }
     bool staged = false;
     const float* ob = nullptr;
     if constexpr (OA == 2) {
@@ -308,6 +323,10 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
     step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA == 1 ? threadIdx.x : 0), BS, ob, bar,
                                           phase, staged);
     if (staged) phase ^= 1u;
+    if constexpr (DYN)
+      c = (int64_t)__shfl_sync(0xffffffffu, c_next, 0);
+    else
+      c += S;
   }
 }
 

@@ -24,6 +24,12 @@ def test_every_autotune_entry_has_a_kernel_name():
                  own_async=bool(own), us_per_step=1.0)
         for adj in (False, True):
             seen.add(bench.kernel_name(e, adj))
+    for packed, own, pfm, dyn, early, tail in itertools.product((5, 6, 7, 8), (0, 1, 2), (0, 1), (0, 1), (0, 1),
+                                                                (0, 1)):
+        e = dict(direction="adj", V=8, packed=packed, gather_batch=4, early=bool(early), tail_serial=bool(tail),
+                 own_async=own, prefetch_meta=bool(pfm), dyn_chunks=bool(dyn), us_per_step=1.0)
+        for adj in (False, True):
+            seen.add(bench.kernel_name(e, adj))
     assert "step3e_stage_kernel<8,false> (256-thread blocks, PDL)" in seen
     assert "step3e_persist_kernel<8,true> (1024-thread blocks, PDL)" in seen
     assert "step3w_persist_kernel<false> (16 slots, rounds of 8, columns per round)" in seen
