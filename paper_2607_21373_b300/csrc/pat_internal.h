@@ -172,6 +172,11 @@ struct DeviceMesh {
   uint32_t flags = 0;
   uint8_t* row_nb = nullptr;    // [N] boundary entries per forward / three-level adjoint row
   uint8_t* row_ninj = nullptr;  // [N] sensor entries per three-level adjoint row
+  // rows with sensor entries (ascending) and each row's index among them (-1: none);
+  // the transposed 16-slot kernels prepare these rows' sensor terms one launch ahead
+  int32_t* inj_rows = nullptr;
+  int32_t* inj_slot = nullptr;
+  int64_t n_inj = 0;
   // tiles of 32 rows for the tile-staged kernel: per tile, contiguous source-row
   // ranges to stage in shared memory, and per CSR entry its 16-bit slot
   int32_t n_tiles = 0, tile_max_slots = 0;

@@ -551,10 +551,13 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.ovf_hl = E.w16_ovf_hl;
       a.status = m.d_status;
       a.wait_cycles = m.tile_wait_cycles;
-      if constexpr (V == 1)
+      if constexpr (V == 1) {
         step3w1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
-      else
-        launch_wide<ADJ>(a, c, threads, st);
+      } else {
+        // the transposed kernel's extra threads prepare the next launch's sensor terms
+        const int64_t prep = (ADJ && a.inj_next) ? a.n_inj * (a.K / 8) : 0;
+        launch_wide<ADJ>(a, c, threads + prep, st);
+      }
       return;
     }
   }
@@ -746,6 +749,24 @@ Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale
     A.prev_mode = (i == 1) ? 2 : 0;  // u_{N_T+1} = 0
     A.ya = Yhat + (int64_t)(mstep - 1) * ystride;                          // yhat^m
     A.yb = (mstep >= 2) ? Yhat + (int64_t)(mstep - 2) * ystride : nullptr;  // yhat^{m-1}
+  }
+  // sensor terms one launch ahead: two [n_inj][K] buffers after the chunk
+  // counters in the fourth state buffer (launch i reads buffer i % 2, which
+  // launch i - 1 wrote, and writes buffer (i + 1) % 2 for launch i + 1)
+  const int64_t NK = m.N * (int64_t)K;
+  if (m.n_inj > 0 && 2 * m.n_inj * K + 64 <= NK) {
+    T* const S0 = b[2] + NK + 64;
+    T* const S[2] = {S0, S0 + m.n_inj * K};
+    A.inj_rows = m.inj_rows;
+    A.inj_slot = m.inj_slot;
+    A.n_inj = m.n_inj;
+    A.inj_cur = i >= 1 ? S[i & 1] : nullptr;
+    if (i + 1 <= NT) {
+      const int mn = NT - i;  // the step of launch i + 1
+      A.inj_next = S[(i + 1) & 1];
+      A.ya_next = Yhat + (int64_t)(mn - 1) * ystride;
+      A.yb_next = (mn >= 2) ? Yhat + (int64_t)(mn - 2) * ystride : nullptr;
+    }
   }
   return A;
 }

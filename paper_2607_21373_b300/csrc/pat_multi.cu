@@ -179,6 +179,8 @@ static void grouped_adjoint(const std::vector<Job>& jobs, int max_nt, cudaStream
       int64_t t = 0;
       ms.push_back(j.m);
       a.push_back(adj3_args<T>(*j.m, j.K, V, (const T*)(j.ws + L.r_d), (T)(1.0 / j.sigma), b, i, &t));
+      a.back().inj_cur = nullptr;  // the grouped kernels compute the sensor terms in the row
+      a.back().inj_next = nullptr;
       thr.push_back(t);
     }
     launch_group<T, V, SPLIT, true>(ms, a, thr, st);

@@ -50,6 +50,54 @@ __device__ __forceinline__ void wide_inj(const Step3Args<float>& A, int64_t row,
   *c = A.ovf_hl[o];
 }
 
+// The sensor term of row `row` for 8 samples (two runs of 4 at base, base + hs):
+// src = sum over the row's sensor entries e of c_e (ya + yb)[col_e], in entry
+// order, ya then yb (either may be absent).  One routine for the term computed
+// in the row and for the term prepared a launch ahead, so both give the same bits.
+__device__ __forceinline__ void sensor_term(const Step3Args<float>& A, int64_t row, int ni, int eA,
+                                            const float* ya, const float* yb, int64_t base, int64_t hs,
+                                            float (&src)[8]) {
+  constexpr int V = 8;
+#pragma unroll
+  for (int q = 0; q < V; ++q) src[q] = 0.0f;
+  for (int e = 0; e < ni; ++e) {
+    uint32_t col;
+    float2 c;
+    wide_inj(A, row, e, eA, &col, &c);
+    const int64_t j = (int64_t)col;
+    if (ya) {
+      const Pack<float, V> y = ld_run_pack<V>(ya + j * A.K + base, hs);
+#pragma unroll
+      for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+    }
+    if (yb) {
+      const Pack<float, V> y = ld_run_pack<V>(yb + j * A.K + base, hs);
+#pragma unroll
+      for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+    }
+  }
+}
+
+// Extra thread g of a transposed launch: the next launch's sensor term of
+// sensor row g / (K/8), samples of thread g % (K/8), into A.inj_next.
+__device__ __forceinline__ void sensor_prep(const Step3Args<float>& A, int64_t g) {
+  constexpr int V = 8;
+  const int KV = A.K / V;
+  const int64_t slot = div_kv(g, KV);
+  if (slot >= A.n_inj) return;
+  const int kv = (int)(g - slot * KV);
+  const int64_t row = A.inj_rows[slot];
+  const uint32_t desc = A.ell_desc[row];
+  const int n = (int)(desc & 255u), ni = (int)((desc >> 16) & 255u);
+  const int64_t hs = A.K / 2, base = (int64_t)kv * 4;
+  float src[V];
+  sensor_term(A, row, ni, n - ni, A.ya_next, A.yb_next, base, hs, src);
+  Pack<float, V> o;
+#pragma unroll
+  for (int q = 0; q < V; ++q) o.v[q] = src[q];
+  st_run_pack<V>(A.inj_next + slot * A.K + base, hs, o);
+}
+
 // Thread t of the row threads: 8 samples of one row (two runs of 4, as in the
 // 8-slot kernel), NB source rows gathered per round.  PB: each round's columns
 // and coefficient pairs are loaded with it (fewer live registers); otherwise
@@ -74,7 +122,11 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
   static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
   const int KV = A.K / V;
   if (t >= A.row_threads) {
-    gather_obs<V>(A, t - A.row_threads);
+    if constexpr (ADJ) {
+      if (A.inj_next) sensor_prep(A, t - A.row_threads);
+    } else {
+      gather_obs<V>(A, t - A.row_threads);
+    }
     return;
   }
   const int64_t row = div_kv(t, KV);
@@ -155,20 +207,13 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 #pragma unroll
   for (int q = 0; q < V; ++q) src[q] = 0.0f;
   if constexpr (ADJ) {
-    for (int e = 0; e < ni; ++e) {
-      uint32_t col;
-      float2 c;
-      wide_inj(A, row, e, eA, &col, &c);
-      const int64_t j = (int64_t)col;
-      if (A.ya) {
-        const Pack<float, V> y = ld_run_pack<V>(A.ya + j * A.K + base, hs);
+    if (ni > 0) {
+      if (A.inj_cur) {  // prepared by the previous launch: one contiguous read
+        const Pack<float, V> y = ld_run_pack<V>(A.inj_cur + (int64_t)A.inj_slot[row] * A.K + base, hs);
 #pragma unroll
-        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
-      }
-      if (A.yb) {
-        const Pack<float, V> y = ld_run_pack<V>(A.yb + j * A.K + base, hs);
-#pragma unroll
-        for (int q = 0; q < V; ++q) src[q] = fmaf(c.x, y.v[q], src[q]);
+        for (int q = 0; q < V; ++q) src[q] = y.v[q];
+      } else {
+        sensor_term(A, row, ni, eA, A.ya, A.yb, base, hs, src);
       }
     }
   }
