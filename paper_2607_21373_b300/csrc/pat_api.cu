@@ -1333,7 +1333,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
       return PAT_EINVAL;
     }
     c.own = v->own_async == 2 ? 2 : (v->own_async && nb == 4 && !c.big ? 1 : 0);
-    c.tail = (v->tail_serial || c.own == 1) && nb == 4 && !c.big;
+    c.tail = v->tail_serial && nb == 4 && !c.big;
     c.pfm = v->prefetch_meta && (v->packed == 6 || (v->packed == 5 && K == 64)) && nb == 4 && !c.big;
     if (c.pfm) c.tail = 1;
     if (v->dyn_chunks && (v->packed != 6 || nb != 4 || c.big || c.pfm || c.own == 2 || !mesh->d.three_level)) {

@@ -415,9 +415,13 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
                      : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 0, false, true>;
     }
   }
-  if (c.own)
-    return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, 1>
-                   : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, 1>;
+  if (c.own) {
+    if (c.tail)
+      return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, 1>
+                     : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD, 1>;
+    return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, QUAD, 1>
+                   : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, QUAD, 1>;
+  }
   if (c.early)
     return c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, QUAD>;
   return c.tail ? step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, QUAD> : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, QUAD>;
@@ -1833,6 +1837,8 @@ static const TuneVariant kTuneVariants[] = {
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 74 quad slots, serial tail, own async, quad's pairs to L1
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 1},  // 75 the same, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 76 quad slots, serial tail, quad's pairs to L1
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 1},  // 80 row-major, paired tail, own rows by cp.async
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8, 1},  // 81 the same, columns per round
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 0, 1},  // 77 row-major, serial tail, own async, chunks by counter
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 0, 1},  // 78 the same, columns per round
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 0, 0, 1},  // 79 row-major, serial tail, columns per round, by counter
