@@ -115,6 +115,7 @@ FORCED = {
                    dyn_chunks=True),
     "w16rcod": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                     own_async=True, dyn_chunks=True),
+    "w16rcop2": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, own_async=True),
     "w16rco": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                    own_async=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
