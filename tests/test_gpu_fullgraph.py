@@ -86,6 +86,30 @@ def test_wide_variants_are_bit_identical(mesh_kind, K):
         assert torch.equal(m.adjoint(yh), g0), v
 
 
+def test_sensor_terms_computed_in_the_row_where_the_buffer_does_not_fit():
+    """The transposed 16-slot kernels prepare the sensor rows' terms one launch
+    ahead in the fourth state buffer when 2 x (sensor rows) x K fits there;
+    on a 4^3 cube with sensors on every face most nodes are sensor rows, so the
+    rows compute their terms themselves: the same bits as the other kernels
+    and the oracle's transpose."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
+    n, n_obs, nt, K = 4, 96, 30, 8
+    xyz, tets = S.jittered_cube_mesh(n, 0.15, 13)
+    det = S.detector_points(n_obs, S.ALL_FACES, 8)
+    ops = fem.build(xyz, tets, det, n)
+    m = Mesh(xyz, tets, det, 0.3 / n, nt, precision="f32", flags=MESH_KEEP_ZEROS)
+    ex = m.export()
+    sensor_rows = len({int(j) for row, w in zip(ex["det_nodes"], ex["det_w"]) for j, x in zip(row, w) if x > 0})
+    assert 2 * sensor_rows * K + 64 > len(xyz) * K  # the inline path
+    yh = as_precision(S.standard_normal((nt, n_obs, K), 9), "f32")
+    m.select_variant(K, "adj", V=4, packed=0)
+    g0 = m.adjoint(dev(yh)).clone()
+    for v in (WIDE_VARIANTS[9], WIDE_VARIANTS[10]):
+        m.select_variant(K, "adj", **v)
+        assert torch.equal(m.adjoint(dev(yh)), g0), v
+    assert rel_l2(g0.cpu().numpy(), wave.adjoint(ops, yh, 0.3 / n)) < 1e-5
+
+
 def test_wide_single_sample_kernel_is_bit_identical():
     from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
     n, n_obs, nt = 10, 48, 60
