@@ -753,6 +753,7 @@ const char* pat_version(void) { return "pat-b300 0.1 (sm_103a)"; }
 pat_status pat_mesh_create(const double* xyz, int64_t n_nodes, const int32_t* tets, int64_t n_tets,
                            const double* c2_elem, const double* det_xyz, int32_t n_obs, double dt, int32_t n_steps,
                            pat_prec prec, uint32_t flags, pat_mesh** out) {
+  PAT_RANGE("pat_mesh_create");
   clear_error();
   if (!out || !xyz || !tets || (!det_xyz && n_obs > 0)) {
     set_error("pat_mesh_create: NULL argument");
@@ -894,6 +895,7 @@ pat_status pat_workspace_bytes(const pat_mesh* mesh, int32_t op, int32_t K, size
 
 pat_status pat_forward(const pat_mesh* mesh, const void* p0, int32_t K, void* Y, double scale, void* ws,
                        size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_forward");
   clear_error();
   if (!mesh || !p0 || !Y) {
     set_error("pat_forward: NULL argument");
@@ -907,6 +909,7 @@ pat_status pat_forward(const pat_mesh* mesh, const void* p0, int32_t K, void* Y,
 
 pat_status pat_adjoint(const pat_mesh* mesh, const void* Yhat, int32_t K, void* p_hat, double scale, void* ws,
                        size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_adjoint");
   clear_error();
   if (!mesh || !Yhat || !p_hat) {
     set_error("pat_adjoint: NULL argument");
@@ -973,6 +976,7 @@ pat_status pat_cgls_begin(const pat_mesh* mesh, const void* y_obs, double sigma,
 
 pat_status pat_cgls_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32_t n_iter, double* resid, void* ws,
                             size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_cgls_iterate");
   clear_error();
   if (!mesh || n_iter < 0) {
     set_error("pat_cgls_iterate: NULL mesh or n_iter < 0");
@@ -1004,6 +1008,7 @@ pat_status pat_cgls_finish(const pat_mesh* mesh, int32_t K, double* samples, dou
 pat_status pat_rto_sample(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, int32_t n_iter,
                           const void* eta, const void* xi, uint64_t seed, double* samples, double* mean,
                           double* stdev, double* resid, void* ws, size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_rto_sample");
   pat_status s = pat_cgls_begin(mesh, y_obs, sigma, K, eta, xi, seed, ws, ws_bytes, stream);
   if (s) return s;
   if (resid) {
@@ -1040,6 +1045,7 @@ pat_status pat_lsqr_begin(const pat_mesh* mesh, const void* y_obs, double sigma,
 
 pat_status pat_lsqr_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32_t n_iter, double* resid, void* ws,
                             size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_lsqr_iterate");
   clear_error();
   if (!mesh || n_iter < 0) {
     set_error("pat_lsqr_iterate: NULL mesh or n_iter < 0");
@@ -1054,6 +1060,7 @@ pat_status pat_lsqr_iterate(const pat_mesh* mesh, double sigma, int32_t K, int32
 pat_status pat_rto_sample_lsqr(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t K, int32_t n_iter,
                                const void* eta, const void* xi, uint64_t seed, double* samples, double* mean,
                                double* stdev, double* resid, void* ws, size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_rto_sample_lsqr");
   clear_error();
   if (n_iter < 0 || (stdev && K < 2)) {
     set_error("pat_rto_sample_lsqr: n_iter < 0, or stdev asked with K < 2");
@@ -1073,6 +1080,7 @@ pat_status pat_rto_sample_lsqr(const pat_mesh* mesh, const void* y_obs, double s
 
 pat_status pat_map_estimate(const pat_mesh* mesh, const void* y_obs, double sigma, int32_t n_iter, int32_t solver,
                             double* x_map, double* resid, void* ws, size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_map_estimate");
   clear_error();
   if (n_iter < 0 || (solver != 0 && solver != 1) || !x_map) {
     set_error("pat_map_estimate: n_iter < 0, solver not 0 (CGLS) or 1 (LSQR), or NULL x_map");
@@ -1123,6 +1131,7 @@ pat_status pat_whitened_misfit(const pat_mesh* mesh, const double* x, const void
 }
 
 pat_status pat_rto_sample_multi(int32_t n_jobs, const pat_rto_job* jobs, int32_t n_iter, void* stream) {
+  PAT_RANGE("pat_rto_sample_multi");
   clear_error();
   if (n_jobs < 1 || !jobs || n_iter < 0) {
     set_error("pat_rto_sample_multi: need n_jobs >= 1, jobs and n_iter >= 0");
@@ -1245,6 +1254,7 @@ pat_status pat_mesh_set_wait_cycles(pat_mesh* mesh, int64_t cycles) {
 
 pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, int32_t K, double* g_c2,
                        void* p0_grad, void* ws, size_t ws_bytes, void* stream) {
+  PAT_RANGE("pat_grad_c2");
   clear_error();
   if (!mesh || !p0 || !Yhat || !g_c2) {
     set_error("pat_grad_c2: NULL argument");
@@ -1405,6 +1415,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
 
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* ws, size_t ws_bytes, int32_t n_probe, pat_tune_entry* table,
                         int32_t* n_entries, void* stream) {
+  PAT_RANGE("pat_autotune");
   clear_error();
   if (!mesh || n_probe < 1) {
     set_error("pat_autotune: NULL mesh or n_probe < 1");

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host assembly, the kernels and the C ABI.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <map>
 #include <tuple>
@@ -13,6 +14,21 @@
 #include "../../include/pat.h"
 
 namespace pat {
+
+// NVTX ranges around the library's calls, solves and solver iterations, so a
+// timeline tool (Nsight Systems, or ncu's range filters) shows where a run's
+// time goes; without an attached tool each range costs a couple of function
+// calls.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define PAT_RANGE_CAT2(a, b) a##b
+#define PAT_RANGE_CAT(a, b) PAT_RANGE_CAT2(a, b)
+#define PAT_RANGE(name) ::pat::NvtxRange PAT_RANGE_CAT(pat_nvtx_range_, __LINE__)(name)
+
 
 // Thread-local error message behind pat_last_error().
 void set_error(const char* fmt, ...);

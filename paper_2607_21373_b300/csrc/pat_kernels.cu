@@ -778,6 +778,7 @@ Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale
 template <typename T, int V, bool SPLIT>
 static pat_status forward3_t(const DeviceMesh& m, const T* p0, int K, T* Y, T scale, T* ws, cudaStream_t st) {
   const int64_t NK = m.N * (int64_t)K;
+  PAT_RANGE("forward solve");
   T* const b[3] = {ws, ws + NK, ws + 2 * NK};
   PAT_TRY(zero_dyn_counters(b, NK, st));
   const size_t pp = prof_begin(m, 0, st);
@@ -793,6 +794,7 @@ static pat_status forward3_t(const DeviceMesh& m, const T* p0, int K, T* Y, T sc
 template <typename T, int V, bool SPLIT>
 static pat_status adjoint3_t(const DeviceMesh& m, const T* Yhat, int K, T* out, T scale, T* ws, cudaStream_t st) {
   const int64_t NK = m.N * (int64_t)K;
+  PAT_RANGE("transposed solve");
   T* const b[3] = {ws, ws + NK, ws + 2 * NK};
   PAT_TRY(zero_dyn_counters(b, NK, st));
   const int NT = m.n_steps;
@@ -1314,6 +1316,7 @@ static pat_status iterate_t(const DeviceMesh& m, double sigma, int K, int n_iter
     return PAT_EINVAL;
   }
   for (int it = 0; it < n_iter; ++it) {
+    PAT_RANGE("CGLS iteration");
     // q = A d: q_d = G d / sigma (forward), q_p = M^{1/2} d (implicit)
     PAT_TRY(cgls_solve(m, 0, K, sigma, ws, st));
     PAT_TRY(iter_mid<T>(m, K, ws, st));
@@ -1561,6 +1564,7 @@ static pat_status lsqr_iterate_t(const DeviceMesh& m, double sigma, int K, int n
   T* v = (T*)(ws + L.d);
   T* s = (T*)(ws + L.s);
   for (int it = 0; it < n_iter; ++it) {
+    PAT_RANGE("LSQR iteration");
     // ub = A v - (alpha / beta) ub: data block from q_d = G v / sigma, prior block sqrt(M_L) v
     PAT_TRY(cgls_solve(m, 0, K, sigma, ws, st));
     lsqr_u_kernel<T, false><<<rsD.grid, rsD.bdim, rsD.bdim * sizeof(double), st>>>(

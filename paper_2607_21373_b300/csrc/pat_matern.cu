@@ -864,6 +864,7 @@ pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* m, cons
                                  int32_t n_iter, const void* eta, const float* xi, uint64_t seed, double* z_samples,
                                  double* p_samples, double* mean, double* stdev, void* ws, size_t ws_bytes,
                                  void* stream) {
+  PAT_RANGE("pat_rto_sample_matern");
   clear_error();
   pat_status s = matern_ws_check(mesh, m, K, ws, ws_bytes, "pat_rto_sample_matern");
   if (s) return s;
@@ -906,6 +907,7 @@ pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* m, cons
   PAT_TRY(sq_partials(sz, G, K, L.nb, pa, st));
   gamma0_kernel<<<nblk((int64_t)K * 32, 128), 128, 0, st>>>(pa, L.nb, K, gamma, status);
   for (int it = 0; it < n_iter; ++it) {
+    PAT_RANGE("latent CGLS iteration");
     // q_d = G P T d / sigma
     PAT_TRY(apply_T(g, dz, K, tmp, nullptr, cbuf, st));
     PAT_TRY(interp(g, tmp, K, node_in, st));

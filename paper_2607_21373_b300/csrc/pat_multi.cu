@@ -268,6 +268,7 @@ static pat_status multi_t(const std::vector<Job>& jobs, int n_iter, cudaStream_t
     if (s) return s;
   }
   for (int it = 0; it < n_iter; ++it) {
+    PAT_RANGE("grouped CGLS iteration");
     PAT_TRY(solves.run(0, st));
     for (const Job& j : jobs) {
       pat_status s = iter_mid<T>(*j.m, j.K, j.ws, st);
