@@ -418,12 +418,15 @@ __device__ __forceinline__ int64_t slot_hl_at(int64_t row, int e) {
 
 // CORR_ONLY: only the xp parts of the boundary entries (the caller has
 // accumulated every entry's x part already).
-template <int V, bool W, int WD, int TB = 2, bool QUAD = false, bool CORR_ONLY = false>
+// T0: the first entry the tail takes (the caller's slot loop covered entries
+// 0 .. T0-1; entries T0 .. WD-1 are read from their slots, the rest from the
+// overflow list).
+template <int V, bool W, int WD, int TB = 2, bool QUAD = false, bool CORR_ONLY = false, int T0 = WD>
 __device__ __forceinline__ void fixed_row_tail(const Step3Args<float>& A, int64_t row, int eA, int nb,
                                                const float* xk, const float* pk, int64_t hs, uint32_t Ku,
                                                u64 (&acc)[V / 2], u64 (&accl)[V / 2]) {
   constexpr int P = V / 2;
-  if ((CORR_ONLY || eA <= WD) && (nb == 0 || pk == nullptr)) return;
+  if ((CORR_ONLY || eA <= T0) && (nb == 0 || pk == nullptr)) return;
   const int64_t o0 = (int64_t)A.ovf_ptr[row] - WD;  // overflow index of entry e >= WD: o0 + e
   auto fetch = [&](int e, uint32_t* col, float2* c) {
     if (e < WD) {
@@ -467,7 +470,7 @@ __device__ __forceinline__ void fixed_row_tail(const Step3Args<float>& A, int64_
       }
     }
   };
-  if constexpr (!CORR_ONLY) batch(WD, eA, xk, 1.0f);
+  if constexpr (!CORR_ONLY) batch(T0, eA, xk, 1.0f);
   if (nb > 0 && pk != nullptr) batch(eA - nb, eA, pk, -1.0f);
 }
 

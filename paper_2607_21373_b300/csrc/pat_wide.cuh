@@ -28,6 +28,7 @@
 namespace pat {
 
 constexpr int kWide = 16;
+constexpr int kMainSlots = 15;  // slots the 16-slot kernels' round loop gathers (the rest: the tail)
 
 // Stiffness / boundary entry e (< the row's count eA) of a quad-interleaved 16-slot row.
 __device__ __forceinline__ void wide_entry(const Step3Args<float>& A, int64_t row, int e, uint32_t* col,
@@ -177,10 +178,14 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
         }
       }
       // slots past the row's count read the row itself with a zero coefficient:
-      // no per-slot test, the gathers of a round issue back to back
+      // no per-slot test, the gathers of a round issue back to back.  The last
+      // slot (kMainSlots = 15: an interior row of a P1 mesh has about 15
+      // entries, and the Kuhn cube's exactly 15) is left to the tail, which
+      // reads it only for rows that use it.
       u64 x[NB][P];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
+      for (int q = 0; q < NB; ++q)
+        if (NB * h + q < kMainSlots) ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
       float2 cf[NB];
 #pragma unroll
       for (int q = 0; q < NB; q += 2) {
@@ -190,6 +195,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       }
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
+        if (NB * h + q >= kMainSlots) continue;
         const u64 ch = dup2(cf[q].x), cl = dup2(cf[q].y);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -198,10 +204,10 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
         }
       }
     }
-    // entries beyond the 16 slots, then the xp parts of the boundary entries
-    // (boundary entries act on w_j = x_j - xp_j)
+    // entries 15 and beyond (slot 15, then the overflow list), then the xp
+    // parts of the boundary entries (boundary entries act on w_j = x_j - xp_j)
     const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
-    fixed_row_tail<V, false, kWide, TB, QUAD>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
+    fixed_row_tail<V, false, kWide, TB, QUAD, false, kMainSlots>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
   }
   float src[V];
 #pragma unroll
