@@ -51,6 +51,8 @@ MESH_TWO_LEVEL = 0x10
 PROFILED_TRAFFIC = {
     ("cube", "step3w_persist_kernel<false> (16 slots row-major, rounds of 4, serial tail) (own rows async)"):
         180.555520e6,
+    ("cube", "step3w_persist_kernel<false> (16 slots row-major, rounds of 4, columns per round, serial tail) "
+             "(own rows async)"): 180.403968e6,
     ("pruned", "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)"): 160.643584e6,
     ("pruned", "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)"): 159.604480e6,
     ("pruned", "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)"): 159.210752e6,
@@ -116,6 +118,7 @@ FORCED = {
     "w16rcod": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                     own_async=True, dyn_chunks=True),
     "w16rcop2": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, own_async=True),
+    "w16rop2": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=True),
     "w16rco": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                    own_async=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
