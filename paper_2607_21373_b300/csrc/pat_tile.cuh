@@ -416,6 +416,11 @@ __device__ __forceinline__ int64_t slot_hl_at(int64_t row, int e) {
   return row * WD + e;
 }
 
+// Slots the V = 8 eight-slot rows gather in their rounds: an interior row of
+// the pruned Kuhn lattice has 7 entries, so the eighth slot would only read the
+// row itself with a zero coefficient; entry 7 onward goes to the tail.
+constexpr int kMain8 = 7;
+
 // CORR_ONLY: only the xp parts of the boundary entries (the caller has
 // accumulated every entry's x part already).
 // T0: the first entry the tail takes (the caller's slot loop covered entries
@@ -559,7 +564,8 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
         }
         u64 x[NB][P];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) ld_runs<V, W>(xk + (size_t)cq[q] * Ku, hs, x[q]);
+        for (int q = 0; q < NB; ++q)
+          if (NB * h + q < kMain8) ld_runs<V, W>(xk + (size_t)cq[q] * Ku, hs, x[q]);
         float2 cf[NB];
 #pragma unroll
         for (int q = 0; q < NB; q += 2) {
@@ -569,6 +575,7 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
         }
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
+          if (NB * h + q >= kMain8) continue;
           const u64 ch = dup2(cf[q].x), cl = dup2(cf[q].y);
 #pragma unroll
           for (int p = 0; p < P; ++p) {
@@ -591,9 +598,11 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
         // the 8 slots hold only stiffness / boundary entries and padding (the
         // row itself with a zero coefficient): no per-entry test
 #pragma unroll
-        for (int q = 0; q < NB; ++q) ld_runs<V, W>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
+        for (int q = 0; q < NB; ++q)
+          if (NB * h + q < kMain8) ld_runs<V, W>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
+          if (NB * h + q >= kMain8) continue;
           const float2 c = cf[NB * h + q];
           const u64 ch = dup2(c.x), cl = dup2(c.y);
 #pragma unroll
@@ -615,7 +624,8 @@ __device__ __forceinline__ void step3e_row(const Step3Args<float>& A, const int6
     // entries beyond the 8 slots, then the xp parts of the boundary entries
     // (boundary entries act on w_j = x_j - xp_j)
     const float* pk = A.prev_mode == 2 ? nullptr : (A.prev_mode == 0 ? A.xp : A.x) + base;
-    fixed_row_tail<V, W, 8>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
+    // (V = 8: the rounds covered slots 0 .. 6, the tail starts at entry 7)
+    fixed_row_tail<V, W, 8, 2, false, false, (V == 8 ? kMain8 : 8)>(A, row, eA, nb, xk, pk, hs, Ku, acc, accl);
   }
   float src[V];
 #pragma unroll
