@@ -65,8 +65,7 @@ void free_device(DeviceMesh& m) {
                  &m.det_w, (void**)&m.etets, &m.eK0, (void**)&m.row_nb, (void**)&m.row_ninj,
                  (void**)&m.tile_range_ptr, (void**)&m.tile_range_src, (void**)&m.tile_range_cnt,
                  (void**)&m.tile_range_slot, (void**)&m.tile_slots, (void**)&m.tile_slot_fwd,
-                 (void**)&m.tile_slot_adj, (void**)&m.d_status, (void**)&m.row_order, (void**)&m.inj_rows,
-                 (void**)&m.inj_slot};
+                 (void**)&m.tile_slot_adj, (void**)&m.d_status, (void**)&m.row_order, (void**)&m.inj_rows};
   for (void** p : ps) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -334,6 +333,7 @@ pat_status build_ell(const HostRows& R, const std::vector<uint8_t>& nb, const st
     if (!s) s = upload(colr, &d.w16r_col);
     if (!s) s = upload(hlr, &d.w16r_hl);
     if (!s) s = upload(optr, &d.w16_ovf_ptr);
+    d.w16_ovf_n = optr.back();
     if (!s) s = upload(ocol, &d.w16_ovf_col);
     if (!s) s = upload(ohl, &d.w16_ovf_hl);
   }
@@ -680,16 +680,12 @@ pat_status build_device(pat_mesh* mesh, uint32_t flags) {
   if (!s && !m.host_only) s = upload(row_ninj, &m.row_ninj);
   if (!s && !m.host_only) {
     // the sensor rows, for the transposed 16-slot kernels' one-launch-ahead sensor terms
-    std::vector<int32_t> rows, slot(N, -1);
+    std::vector<int32_t> rows;
     for (int64_t i = 0; i < N; ++i)
-      if (row_ninj[i]) {
-        slot[i] = (int32_t)rows.size();
-        rows.push_back((int32_t)i);
-      }
+      if (row_ninj[i]) rows.push_back((int32_t)i);
     m.n_inj = (int64_t)rows.size();
     if (rows.empty()) rows.push_back(0);
     s = upload(rows, &m.inj_rows);
-    if (!s) s = upload(slot, &m.inj_slot);
   }
   if (!s && !m.host_only) {
     // element data of the c^2 gradient: vertices and K_e^0 (upper triangle, c = 1)

@@ -132,6 +132,7 @@ struct DevCSR {
   int32_t* w16_ovf_ptr = nullptr;
   uint32_t* w16_ovf_col = nullptr;
   float2* w16_ovf_hl = nullptr;
+  int64_t w16_ovf_n = 0;  // overflow entries of the 16-slot copy (a sensor row owns at least one)
 };
 
 constexpr int kEllWide = 16;  // slots of the wide fixed-width copy
@@ -188,10 +189,10 @@ struct DeviceMesh {
   uint32_t flags = 0;
   uint8_t* row_nb = nullptr;    // [N] boundary entries per forward / three-level adjoint row
   uint8_t* row_ninj = nullptr;  // [N] sensor entries per three-level adjoint row
-  // rows with sensor entries (ascending) and each row's index among them (-1: none);
-  // the transposed 16-slot kernels prepare these rows' sensor terms one launch ahead
+  // rows with sensor entries (ascending): the transposed 16-slot kernels prepare
+  // these rows' sensor terms one launch ahead, each at its row's first overflow
+  // entry (every sensor row has one: its sensor entries live there)
   int32_t* inj_rows = nullptr;
-  int32_t* inj_slot = nullptr;
   int64_t n_inj = 0;
   // tiles of 32 rows for the tile-staged kernel: per tile, contiguous source-row
   // ranges to stage in shared memory, and per CSR entry its 16-bit slot

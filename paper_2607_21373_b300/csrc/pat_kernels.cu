@@ -754,15 +754,16 @@ Step3Args<T> adj3_args(const DeviceMesh& m, int K, int V, const T* Yhat, T scale
     A.ya = Yhat + (int64_t)(mstep - 1) * ystride;                          // yhat^m
     A.yb = (mstep >= 2) ? Yhat + (int64_t)(mstep - 2) * ystride : nullptr;  // yhat^{m-1}
   }
-  // sensor terms one launch ahead: two [n_inj][K] buffers after the chunk
-  // counters in the fourth state buffer (launch i reads buffer i % 2, which
-  // launch i - 1 wrote, and writes buffer (i + 1) % 2 for launch i + 1)
+  // sensor terms one launch ahead: two [overflow entries][K] buffers after
+  // the chunk counters in the fourth state buffer (launch i reads buffer
+  // i % 2, which launch i - 1 wrote, and writes buffer (i + 1) % 2 for launch
+  // i + 1); a sensor row's term sits at its first overflow entry
   const int64_t NK = m.N * (int64_t)K;
-  if (m.n_inj > 0 && 2 * m.n_inj * K + 64 <= NK) {
+  const int64_t n_ovf = m.adj3.w16_ovf_n;
+  if (m.n_inj > 0 && n_ovf > 0 && 2 * n_ovf * K + 64 <= NK) {
     T* const S0 = b[2] + NK + 64;
-    T* const S[2] = {S0, S0 + m.n_inj * K};
+    T* const S[2] = {S0, S0 + n_ovf * K};
     A.inj_rows = m.inj_rows;
-    A.inj_slot = m.inj_slot;
     A.n_inj = m.n_inj;
     A.inj_cur = i >= 1 ? S[i & 1] : nullptr;
     if (i + 1 <= NT) {

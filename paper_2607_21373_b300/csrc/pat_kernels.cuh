@@ -313,13 +313,13 @@ struct Step3Args {
   // of this launch, prepared by the previous launch (inj_cur; null: computed
   // in the row), and the next launch's, which this launch's extra threads
   // prepare from that launch's data slices ya_next, yb_next (inj_next; null:
-  // none); [n_inj][K] in the fourth state buffer
+  // none); a row's term at its first overflow entry, [overflow entries][K],
+  // in the fourth state buffer
   const T* __restrict__ inj_cur;
   T* __restrict__ inj_next;
   const T* __restrict__ ya_next;
   const T* __restrict__ yb_next;
   const int32_t* __restrict__ inj_rows;
-  const int32_t* __restrict__ inj_slot;
   int64_t n_inj;
 };
 

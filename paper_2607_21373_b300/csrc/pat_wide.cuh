@@ -80,7 +80,8 @@ __device__ __forceinline__ void sensor_term(const Step3Args<float>& A, int64_t r
 }
 
 // Extra thread g of a transposed launch: the next launch's sensor term of
-// sensor row g / (K/8), samples of thread g % (K/8), into A.inj_next.
+// sensor row g / (K/8), samples of thread g % (K/8), into A.inj_next at the
+// row's first overflow entry.
 __device__ __forceinline__ void sensor_prep(const Step3Args<float>& A, int64_t g) {
   constexpr int V = 8;
   const int KV = A.K / V;
@@ -96,7 +97,7 @@ __device__ __forceinline__ void sensor_prep(const Step3Args<float>& A, int64_t g
   Pack<float, V> o;
 #pragma unroll
   for (int q = 0; q < V; ++q) o.v[q] = src[q];
-  st_run_pack<V>(A.inj_next + slot * A.K + base, hs, o);
+  st_run_pack<V>(A.inj_next + (int64_t)A.ovf_ptr[row] * A.K + base, hs, o);
 }
 
 // Thread t of the row threads: 8 samples of one row (two runs of 4, as in the
@@ -215,7 +216,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
   if constexpr (ADJ) {
     if (ni > 0) {
       if (A.inj_cur) {  // prepared by the previous launch: one contiguous read
-        const Pack<float, V> y = ld_run_pack<V>(A.inj_cur + (int64_t)A.inj_slot[row] * A.K + base, hs);
+        const Pack<float, V> y = ld_run_pack<V>(A.inj_cur + (int64_t)A.ovf_ptr[row] * A.K + base, hs);
 #pragma unroll
         for (int q = 0; q < V; ++q) src[q] = y.v[q];
       } else {

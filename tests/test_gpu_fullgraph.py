@@ -88,10 +88,10 @@ def test_wide_variants_are_bit_identical(mesh_kind, K):
 
 def test_sensor_terms_computed_in_the_row_where_the_buffer_does_not_fit():
     """The transposed 16-slot kernels prepare the sensor rows' terms one launch
-    ahead in the fourth state buffer when 2 x (sensor rows) x K fits there;
-    on a 4^3 cube with sensors on every face most nodes are sensor rows, so the
-    rows compute their terms themselves: the same bits as the other kernels
-    and the oracle's transpose."""
+    ahead in the fourth state buffer when 2 x (overflow entries) x K fits
+    there; on a 4^3 cube with sensors on every face most nodes are sensor rows
+    (each owning at least one overflow entry), so the rows compute their terms
+    themselves: the same bits as the other kernels and the oracle's transpose."""
     from paper_2607_21373_b300 import MESH_KEEP_ZEROS, Mesh
     n, n_obs, nt, K = 4, 96, 30, 8
     xyz, tets = S.jittered_cube_mesh(n, 0.15, 13)
