@@ -350,7 +350,9 @@ def kernel_name(e, adj):
         nb = e.get("gather_batch") or 4
         big = bool(e.get("big_blocks"))
         return "step3w_persist_kernel<%s> (16 slots%s, rounds of %d%s%s%s)" % (
-            tf, " row-major" if packed == 6 else "", nb, ", columns per round" if e.get("early") else "",
+            tf, " row-major" if packed == 6 else "", nb,
+            (", columns per round" if e.get("early") else "") + (
+                ", 256-bit metadata" if packed == 6 and e.get("wide_loads") else ""),
             ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
             ", serial tail" if e.get("tail_serial") else "") + (" (own rows by bulk copy)" if e.get("own_async") == 2 else " (own rows async)" if e.get("own_async") else "") + (
             ((" (quad's coefficient lines to L1)" if packed == 5 else " (next metadata to L1)")

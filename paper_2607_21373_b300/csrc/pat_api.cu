@@ -1350,6 +1350,8 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     }
     c.dyn = v->dyn_chunks ? 1 : 0;
     if (c.dyn) c.tail = 1;
+    // 256-bit metadata loads: row-major slots, each round's columns with it
+    c.wide = v->wide_loads && v->packed == 6 && c.early && nb == 4 && !c.big && !c.pfm && !c.dyn && c.own != 2;
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);

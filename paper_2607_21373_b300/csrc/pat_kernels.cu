@@ -415,6 +415,15 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
                      : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 0, false, true>;
     }
   }
+  if constexpr (!QUAD) {
+    if (c.wide && c.early) {  // 256-bit metadata loads (own rows by cp.async when c.own)
+      if (c.own)
+        return c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, 1, false, false, true>
+                      : step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, false, 1, false, false, true>;
+      return c.tail ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, 0, false, false, true>
+                    : step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, false, 0, false, false, true>;
+    }
+  }
   if (c.own) {
     if (c.tail)
       return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, QUAD, 1>
@@ -1845,6 +1854,9 @@ static const TuneVariant kTuneVariants[] = {
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 74 quad slots, serial tail, own async, quad's pairs to L1
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 1},  // 75 the same, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 76 quad slots, serial tail, quad's pairs to L1
+    {6, 0, 4, 0, 0, 0, 1, 1, 1, 1, 4, 1, 1, 8, 1},  // 82 row-major, 256-bit metadata, serial tail, own async
+    {6, 0, 4, 0, 0, 0, 1, 1, 1, 0, 4, 1, 1, 8, 1},  // 83 the same, paired tail
+    {6, 0, 4, 0, 0, 0, 1, 1, 1, 1, 4, 1, 1, 8, 0},  // 84 row-major, 256-bit metadata, serial tail
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 1},  // 80 row-major, paired tail, own rows by cp.async
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8, 1},  // 81 the same, columns per round
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 0, 1},  // 77 row-major, serial tail, own async, chunks by counter

@@ -116,12 +116,18 @@ __device__ __forceinline__ void sensor_prep(const Step3Args<float>& A, int64_t g
 // the copies were issued (the warp's rows exist and x is not the zero state).
 // A wait that runs past A.wait_cycles reports PAT_ETIMEOUT, lets the copies
 // land (bounded again) and carries on with whatever arrived.
-template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true, int OA = 0>
+//
+// WL (row-major slots, rounds of 4): the row's metadata in 256-bit loads — a
+// round's four coefficient pairs in one, two rounds' columns in one — so the
+// 4 rows of a warp fetch 32 bytes per row and line instead of 16 (half the L1
+// wavefronts for the metadata).
+template <bool ADJ, int NB, bool PB, int TB = 2, bool QUAD = true, int OA = 0, bool WL = false>
 __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int64_t t, float4* own = nullptr,
                                            int own_stride = 0, const float* ob = nullptr, uint32_t bar = 0,
                                            uint32_t phase = 0, bool staged = false) {
   constexpr int V = 8, P = 4;
   static_assert(NB == 4 || NB == 8, "rounds of 4 or 8 source rows");
+  static_assert(!WL || (!QUAD && NB == 4 && PB), "256-bit metadata loads: row-major slots, rounds of 4 with their columns");
   const int KV = A.K / V;
   if (t >= A.row_threads) {
     if constexpr (ADJ) {
@@ -170,7 +176,15 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     }
 #pragma unroll
     for (int h = 0; h < kWide / NB; ++h) {
-      if constexpr (PB) {
+      if constexpr (WL) {
+        if (h % 2 == 0) {  // columns of rounds h and h + 1
+          uint32_t* cq = cols + 4 * h;
+          asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+              : "=r"(cq[0]), "=r"(cq[1]), "=r"(cq[2]), "=r"(cq[3]), "=r"(cq[4]), "=r"(cq[5]), "=r"(cq[6]),
+                "=r"(cq[7])
+              : "l"(cp + h));
+        }
+      } else if constexpr (PB) {
 #pragma unroll
         for (int q = 0; q < NB / 4; ++q) {
           const uint4 c = cp[CS * (h * (NB / 4) + q)];
@@ -188,11 +202,20 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       for (int q = 0; q < NB; ++q)
         if (NB * h + q < kMainSlots) ld_runs<V>(xk + (size_t)cols[NB * h + q] * Ku, hs, x[q]);
       float2 cf[NB];
+      if constexpr (WL) {
+        float f[8];
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]), "=f"(f[7])
+            : "l"(hp + 2 * h));
 #pragma unroll
-      for (int q = 0; q < NB; q += 2) {
-        const float4 hq = hp[CS * ((NB * h + q) / 2)];
-        cf[q] = make_float2(hq.x, hq.y);
-        cf[q + 1] = make_float2(hq.z, hq.w);
+        for (int q = 0; q < NB; ++q) cf[q] = make_float2(f[2 * q], f[2 * q + 1]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < NB; q += 2) {
+          const float4 hq = hp[CS * ((NB * h + q) / 2)];
+          cf[q] = make_float2(hq.x, hq.y);
+          cf[q + 1] = make_float2(hq.z, hq.w);
+        }
       }
 #pragma unroll
       for (int q = 0; q < NB; ++q) {
@@ -290,7 +313,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
 // set the end of the step.  Lane 0 asks for the following chunk when it
 // starts one, so the counter's round trip hides behind the chunk's work.
 template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = true, int OA = 0,
-          bool PFM = false, bool DYN = false>
+          bool PFM = false, bool DYN = false, bool WL = false>
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   // per-thread slots of the own-row copies, slot q of thread i at [q][i]
   // (consecutive threads contiguous: conflict-free 16-byte accesses)
@@ -372,8 +395,8 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
         if (kv < 3) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
       }
     }
-    step3w_row<ADJ, NB, PB, TB, QUAD, OA>(A, c * 32 + lane, own_buf + (OA == 1 ? threadIdx.x : 0), BS, ob, bar,
-                                          phase, staged);
+    step3w_row<ADJ, NB, PB, TB, QUAD, OA, WL>(A, c * 32 + lane, own_buf + (OA == 1 ? threadIdx.x : 0), BS, ob,
+                                              bar, phase, staged);
     if (staged) phase ^= 1u;
     if constexpr (DYN)
       c = (int64_t)__shfl_sync(0xffffffffu, c_next, 0);
