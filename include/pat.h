@@ -508,29 +508,35 @@ typedef struct {
 pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t workspace_bytes, int32_t n_probe,
                         pat_tune_entry* table, int32_t* n_entries, void* stream);
 
-/* Use the given variant (fields as in pat_tune_entry; packed 2 = the
- * tile-staged kernel, which stages each 32-row tile's source rows in shared
- * memory by bulk asynchronous copies; packed 3 = the fixed-width kernel, whose
- * rows' first 8 entries sit at fixed positions; packed 5 = the 16-slot
- * fixed-width kernel for meshes with rows wider than 8 entries (the full P1
- * graph), persistent, V = 8 (or V = 1 for K = 1), gather_batch 4 or 8 source
- * rows per round, early = each round's columns loaded with it, big_blocks =
- * 1024-thread blocks, min_blocks 3 with rounds of 8, tail_serial = a row's
- * entries past the slots and its boundary corrections walked one at a time
- * instead of in pairs, own_async = the row's own x_s and x_{s-1} copied to
- * shared memory while its gathers run (1: by cp.async, each thread its own
- * values; 2, packed 6 with K <= 256: by two bulk asynchronous copies per warp
- * of its rows, completing on an mbarrier whose wait is bounded by the mesh's
- * wait budget, pat_mesh_set_wait_cycles, PAT_ETIMEOUT through pat_rto_status
- * when it runs out), dyn_chunks (packed 6, three-level form) = the warps'
- * 32-thread chunks handed out in row order by an atomic counter (kept in
- * the workspace's fourth state buffer) instead of the grid stride,
- * prefetch_meta (packed 6) =
- * each warp asks L1 to prefetch its next chunk's row metadata; packed 6 = the same kernel
- * reading a row-major copy of the 16 slots instead of the quad-interleaved
- * one, V = 8 only) for direction 0 (forward) or 1
- * (transposed) and K samples on this mesh.  PAT_EINVAL if the variant does not
- * exist for this K and precision.  Every variant gives bit-identical results. */
+/* Use the given variant (fields as in pat_tune_entry) for direction 0
+ * (forward) or 1 (transposed) and K samples on this mesh.  PAT_EINVAL if the
+ * variant does not exist for this K and precision.  Every variant gives
+ * bit-identical results.  packed selects the kernel family:
+ *   2  the tile-staged kernel: each 32-row tile's source rows staged in shared
+ *      memory by bulk asynchronous copies (bounded mbarrier waits);
+ *   3  the 8-slot fixed-width kernel (the rows' first 8 entries at fixed
+ *      positions, the rest in an overflow list);
+ *   5  the 16-slot fixed-width kernel for meshes with rows wider than 8 entries
+ *      (the full P1 graph), quad-interleaved slots, persistent, V = 8 (or V = 1
+ *      for K = 1); 6 the same reading a row-major copy of the slots (V = 8);
+ *   7  row pairs (the union of two rows' sources gathered once);
+ *   8  row quads (K = 64: the union of four rows' sources gathered once).
+ * Fields of the 16-slot kernels: gather_batch 4 or 8 source rows per round;
+ * early = each round's columns loaded with it; big_blocks = 1024-thread blocks;
+ * min_blocks 3 with rounds of 8; tail_serial = a row's entries past the round
+ * loop and its boundary corrections walked one at a time instead of in pairs;
+ * own_async = the row's own x_s and x_{s-1} copied to shared memory while its
+ * gathers run (1: by cp.async, each thread its own values; 2, packed 6 with
+ * K / 8 dividing 32: by two bulk asynchronous copies per warp of its rows,
+ * completing on an mbarrier whose wait is bounded by the mesh's wait budget,
+ * pat_mesh_set_wait_cycles, PAT_ETIMEOUT through pat_rto_status when it runs
+ * out); prefetch_meta = each warp asks L1 for its next chunk's row metadata
+ * (packed 6) or for the quad's coefficient lines (packed 5, K = 64);
+ * dyn_chunks (packed 6, three-level form) = the warps' 32-thread chunks handed
+ * out in row order by an atomic counter (kept in the workspace's fourth state
+ * buffer) instead of the grid stride; wide_loads (packed 6 with early) = the
+ * row metadata in 256-bit loads (for packed 3: 8 contiguous samples per
+ * 256-bit load). */
 pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, const pat_tune_entry* variant);
 
 /*
