@@ -475,8 +475,52 @@ __device__ __forceinline__ void fixed_row_tail(const Step3Args<float>& A, int64_
       }
     }
   };
-  if constexpr (!CORR_ONLY) batch(T0, eA, xk, 1.0f);
-  if (nb > 0 && pk != nullptr) batch(eA - nb, eA, pk, -1.0f);
+  if constexpr (TB == 1) {
+    if constexpr (!CORR_ONLY) batch(T0, eA, xk, 1.0f);
+    if (nb > 0 && pk != nullptr) batch(eA - nb, eA, pk, -1.0f);
+  } else {
+    // the tail's x entries and the corrections as one sequence, so a batch can
+    // hold the last x entry and the first correction (one round trip fewer
+    // when the x entries are odd in number); the products keep their order
+    const int nx = CORR_ONLY ? 0 : max(eA - T0, 0);
+    const int nc = (nb > 0 && pk != nullptr) ? nb : 0;
+    const int c0 = eA - nb;  // first boundary entry
+    for (int v0 = 0; v0 < nx + nc; v0 += TB) {
+      uint32_t cq[TB];
+      float2 cf[TB];
+      u64 x[TB][P];
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        const int v = v0 + q;
+        cq[q] = 0u;
+        cf[q] = make_float2(0.0f, 0.0f);
+        if (v < nx + nc) fetch(v < nx ? T0 + v : c0 + (v - nx), &cq[q], &cf[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        const int v = v0 + q;
+        if (v < nx + nc) {
+          ld_runs<V, W>((v < nx ? xk : pk) + (size_t)cq[q] * Ku, hs, x[q]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p) x[q][p] = 0ull;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < TB; ++q) {
+        const int v = v0 + q;
+        if (v < nx + nc) {
+          const float sign = v < nx ? 1.0f : -1.0f;
+          const u64 ch = dup2(sign * cf[q].x), cl = dup2(sign * cf[q].y);
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            acc[p] = ffma2(ch, x[q][p], acc[p]);
+            accl[p] = ffma2(cl, x[q][p], accl[p]);
+          }
+        }
+      }
+    }
+  }
 }
 
 template <int V, bool ADJ, bool W = false, bool H = false, bool SMD = false, int NB = 4, bool PB = (NB == 2)>
