@@ -36,6 +36,8 @@ WIDE_VARIANTS = [dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                       own_async=True, wide_loads=True),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, wide_loads=True),
+                 dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
+                      own_async=True, min_blocks=3),
                  dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4, early=True, own_async=True),
                  dict(V=8, packed=7, persistent=1, pdl=True), dict(V=8, packed=7, persistent=1, min_blocks=3),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=True, prefetch_meta=True),
