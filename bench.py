@@ -123,6 +123,9 @@ FORCED = {
                    own_async=True),
     "w16rop": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
                    prefetch_meta=True),
+    "w16rcox": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
+                    own_async=3),
+    "w16rox": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=3),
     "pairs": dict(V=8, packed=7, persistent=1, pdl=True),
     "quads": dict(V=8, packed=8, persistent=1, pdl=True),
     "quadso": dict(V=8, packed=8, persistent=1, pdl=True, own_async=True),
@@ -354,7 +357,8 @@ def kernel_name(e, adj):
             (", columns per round" if e.get("early") else "") + (
                 ", 256-bit metadata" if packed == 6 and e.get("wide_loads") else ""),
             ", 1024-thread blocks" if big else (", 3 blocks/SM" if e.get("min_blocks") == 3 else ""),
-            ", serial tail" if e.get("tail_serial") else "") + (" (own rows by bulk copy)" if e.get("own_async") == 2 else " (own rows async)" if e.get("own_async") else "") + (
+            ", serial tail" if e.get("tail_serial") else "") + (" (own rows by bulk copy)" if e.get("own_async") == 2 else " (own x_{s-1} rows async)"
+                                                    if e.get("own_async") == 3 else " (own rows async)" if e.get("own_async") else "") + (
             ((" (quad's coefficient lines to L1)" if packed == 5 else " (next metadata to L1)")
              if e.get("prefetch_meta") else "") + (" (chunks by counter)" if e.get("dyn_chunks") else ""))
     if packed == 2:

@@ -530,7 +530,8 @@ pat_status pat_autotune(pat_mesh* mesh, int32_t K, void* workspace, size_t works
  * K / 8 dividing 32: by two bulk asynchronous copies per warp of its rows,
  * completing on an mbarrier whose wait is bounded by the mesh's wait budget,
  * pat_mesh_set_wait_cycles, PAT_ETIMEOUT through pat_rto_status when it runs
- * out); prefetch_meta = each warp asks L1 for its next chunk's row metadata
+ * out; 3, packed 6 with rounds of 4 and no other option: x_{s-1} alone by
+ * cp.async, x_s read from L1 after the row's diagonal gather); prefetch_meta = each warp asks L1 for its next chunk's row metadata
  * (packed 6) or for the quad's coefficient lines (packed 5, K = 64);
  * dyn_chunks (packed 6, three-level form) = the warps' 32-thread chunks handed
  * out in row order by an atomic counter (kept in the workspace's fourth state

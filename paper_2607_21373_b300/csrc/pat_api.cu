@@ -1339,7 +1339,13 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
                 "(packed 6), rounds of 4, 256-thread blocks, no metadata prefetch and K in {8, 16, ..., 256}");
       return PAT_EINVAL;
     }
-    c.own = v->own_async == 2 ? 2 : (v->own_async && nb == 4 && !c.big ? 1 : 0);
+    if (v->own_async == 3 && (v->packed != 6 || nb != 4 || c.big || v->prefetch_meta || v->dyn_chunks ||
+                              v->wide_loads || v->min_blocks != 1)) {
+      set_error("pat_select_variant: own x_{s-1} rows only (own_async = 3) need the row-major 16-slot rows "
+                "(packed 6), rounds of 4, 256-thread blocks and no other option");
+      return PAT_EINVAL;
+    }
+    c.own = v->own_async == 2 ? 2 : v->own_async == 3 ? 3 : (v->own_async && nb == 4 && !c.big ? 1 : 0);
     c.tail = v->tail_serial && nb == 4 && !c.big;
     c.pfm = v->prefetch_meta && (v->packed == 6 || (v->packed == 5 && K == 64)) && nb == 4 && !c.big;
     if (c.pfm) c.tail = 1;

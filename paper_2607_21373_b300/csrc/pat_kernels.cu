@@ -416,6 +416,13 @@ static void (*pick_wide(const TuneCfg& c, int* bs))(const Step3Args<float>, int6
     }
   }
   if constexpr (!QUAD) {
+    if (c.own == 3) {  // own x_{s-1} rows only by cp.async
+      if (c.tail)
+        return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 1, false, 3>
+                       : step3w_persist_kernel<ADJ, 4, false, 256, 4, 1, false, 3>;
+      return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 4, 2, false, 3>
+                     : step3w_persist_kernel<ADJ, 4, false, 256, 4, 2, false, 3>;
+    }
     if (c.minb == 3 && c.own == 1) {  // 3 blocks of 256 per SM: up to 85 registers a thread
       if (c.tail)
         return c.early ? step3w_persist_kernel<ADJ, 4, true, 256, 3, 1, false, 1>
@@ -1861,6 +1868,10 @@ static const TuneVariant kTuneVariants[] = {
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 1, 1},  // 74 quad slots, serial tail, own async, quad's pairs to L1
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 1, 1},  // 75 the same, columns per round
     {5, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 0, 1},  // 76 quad slots, serial tail, quad's pairs to L1
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 1, 8, 3},  // 89 row-major, own x_{s-1} async, serial tail, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 0, 8, 3},  // 90 row-major, own x_{s-1} async, paired tail
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 1, 1, 8, 3},  // 91 the same, columns per round
+    {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 1, 0, 8, 3},  // 92 row-major, own x_{s-1} async, serial tail
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 3, 1, 8, 1},  // 85 row-major, own async, serial tail, 3 blocks/SM
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 3, 0, 8, 1},  // 86 row-major, own async, paired tail, 3 blocks/SM
     {6, 0, 4, 0, 0, 0, 1, 1, 0, 1, 4, 3, 0, 8, 1},  // 87 row-major, own async, serial tail, 3 blocks/SM, no early

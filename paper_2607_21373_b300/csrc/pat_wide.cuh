@@ -153,6 +153,14 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
+  if constexpr (OA == 3) {  // x_{s-1} only (own: 2 float4); x_s is read at the update, an L1 hit after
+                            // the row's own diagonal gather
+    if (A.prev_mode == 0) {
+      cp_async16_cg(own, A.xp + off);
+      cp_async16_cg(own + own_stride, A.xp + off + hs);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   const uint32_t desc = A.ell_desc[row];
   const int n = (int)(desc & 255u), nb = (int)((desc >> 8) & 255u), ni = (int)((desc >> 16) & 255u);
   const int eA = n - ni;
@@ -248,7 +256,7 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
     }
   }
   Pack<float, V> xi, xpi, xo;
-  if constexpr (OA == 1) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if constexpr (OA == 1 || OA == 3) asm volatile("cp.async.wait_group 0;" ::: "memory");
   if constexpr (OA == 2) {
     if (staged && !mbar_wait_parity(bar, phase, A.wait_cycles)) {
       atomicExch(A.status, (int)PAT_ETIMEOUT);
@@ -275,6 +283,8 @@ __device__ __forceinline__ void step3w_row(const Step3Args<float>& A, const int6
       unpack4(*reinterpret_cast<const float4*>(ob + 256), *reinterpret_cast<const float4*>(ob + 256 + hs), xpi);
     else if constexpr (OA == 1)
       unpack4(own[2 * own_stride], own[3 * own_stride], xpi);
+    else if constexpr (OA == 3)
+      unpack4(own[0], own[own_stride], xpi);
     else
       xpi = ld_run_pack<V>(A.xp + off, hs);
   } else {
@@ -317,7 +327,7 @@ template <bool ADJ, int NB, bool PB, int BS, int MINB, int TB = 2, bool QUAD = t
 __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Args<float> A, int64_t n_chunks) {
   // per-thread slots of the own-row copies, slot q of thread i at [q][i]
   // (consecutive threads contiguous: conflict-free 16-byte accesses)
-  __shared__ float4 own_buf[OA == 1 ? 4 * BS : 1];
+  __shared__ float4 own_buf[OA == 1 ? 4 * BS : OA == 3 ? 2 * BS : 1];
   __shared__ __align__(128) float own_rows[OA == 2 ? (BS / 32) * 512 : 1];
   __shared__ __align__(8) uint64_t own_bar[OA == 2 ? BS / 32 : 1];
   const int lane = threadIdx.x & 31;
@@ -395,8 +405,8 @@ __global__ void __launch_bounds__(BS, MINB) step3w_persist_kernel(const Step3Arg
         if (kv < 3) asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
       }
     }
-    step3w_row<ADJ, NB, PB, TB, QUAD, OA, WL>(A, c * 32 + lane, own_buf + (OA == 1 ? threadIdx.x : 0), BS, ob,
-                                              bar, phase, staged);
+    step3w_row<ADJ, NB, PB, TB, QUAD, OA, WL>(A, c * 32 + lane, own_buf + ((OA == 1 || OA == 3) ? threadIdx.x : 0),
+                                              BS, ob, bar, phase, staged);
     if (staged) phase ^= 1u;
     if constexpr (DYN)
       c = (int64_t)__shfl_sync(0xffffffffu, c_next, 0);

@@ -51,7 +51,10 @@ WIDE_VARIANTS = [dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, tail_serial=True, own_async=True,
                       dyn_chunks=True),
                  dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
-                      dyn_chunks=True)]
+                      dyn_chunks=True),
+                 dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
+                      own_async=3),
+                 dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=3)]
 # the row-quad kernel (K = 64 only: a warp is the 4 rows of a quad)
 QUAD_VARIANTS = [dict(V=8, packed=8, persistent=1, pdl=True), dict(V=8, packed=8, persistent=1, pdl=True, own_async=True),
                  dict(V=8, packed=8, persistent=1, pdl=False)]
