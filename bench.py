@@ -53,6 +53,8 @@ PROFILED_TRAFFIC = {
         180.555520e6,
     ("cube", "step3w_persist_kernel<false> (16 slots row-major, rounds of 4, columns per round, serial tail) "
              "(own rows async)"): 180.403968e6,
+    ("cube", "step3w_persist_kernel<true> (16 slots row-major, rounds of 4) (own x_{s-1} rows async)"):
+        181.347328e6,
     ("pruned", "step3e_persist_kernel<8,false> (256-thread blocks, PDL, L2 prefetch 1)"): 160.643584e6,
     ("pruned", "step3e_persist_kernel<8,true> (256-thread blocks, PDL, L2 prefetch 1)"): 159.604480e6,
     ("pruned", "step3e_persist_kernel<8,false> (1024-thread blocks, PDL)"): 159.210752e6,
@@ -525,7 +527,8 @@ def run_ours(a, rank, world, local_rank, dist):
                       "rule": "12 B/node/sample (three-level state) + stored operator + sensor I/O"},
             "adjoint": {"kernel": aname, "avg_launch_us": 1e3 * adj_ms_launch,
                         "achieved": gbs(alg_step, adj_ms_launch), "frac": gbs(alg_step, adj_ms_launch) / peak,
-                        "moved_frac": gbs(adj_moved, adj_ms_launch) / peak}}
+                        "moved_frac": gbs(adj_moved, adj_ms_launch) / peak,
+                        "traffic": PROFILED_TRAFFIC.get((a.mesh, aname)) if default_shape else None}}
 
     # plain one-sample form on the same library and workload
     plain = None
