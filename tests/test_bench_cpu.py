@@ -24,7 +24,7 @@ def test_every_autotune_entry_has_a_kernel_name():
                  own_async=bool(own), us_per_step=1.0)
         for adj in (False, True):
             seen.add(bench.kernel_name(e, adj))
-    for packed, own, pfm, dyn, early, tail in itertools.product((5, 6, 7, 8), (0, 1, 2), (0, 1), (0, 1), (0, 1),
+    for packed, own, pfm, dyn, early, tail in itertools.product((5, 6, 7, 8), (0, 1, 2, 3), (0, 1), (0, 1), (0, 1),
                                                                 (0, 1)):
         e = dict(direction="adj", V=8, packed=packed, gather_batch=4, early=bool(early), tail_serial=bool(tail),
                  own_async=own, prefetch_meta=bool(pfm), dyn_chunks=bool(dyn), us_per_step=1.0)
