@@ -89,11 +89,18 @@ def parse(argv=None):
                     help="least-squares solver of every RTO sample (the configured workload names CGLS)")
     ap.add_argument("--variant", default="", help="force a step-kernel variant for K (FWD or FWD,ADJ): "
                     + " | ".join(sorted(FORCED)))
-    ap.add_argument("--workload", default="rto", choices=["rto", "uneven", "matern"],
+    ap.add_argument("--workload", default="rto", choices=["rto", "uneven", "matern", "grad"],
                     help="rto: one mesh, K samples per batch (default); uneven: six cubes 16^3..58^3 cells with "
                          "K 256..8 and N_T 276..1000 in one grouped solve per step (k = 50); matern: the rto "
-                         "workload with the Whittle-Matern prior (128^3 latent grid, l = 0.15, s = 1.5, sigma = 3)")
-    return ap.parse_args(argv)
+                         "workload with the Whittle-Matern prior (128^3 latent grid, l = 0.15, s = 1.5, sigma = 3); "
+                         "grad: c2 and p0 gradients on a 32^3-cell cube, 1000 steps, K = 1 (sizes the options give "
+                         "explicitly override these)")
+    a = ap.parse_args(argv)
+    given = sys.argv[1:] if argv is None else list(argv)
+    for opt, attr in (("--cells", "cells_given"), ("--n-steps", "n_steps_given"), ("--n-obs", "n_obs_given"),
+                      ("--K", "K_given")):
+        setattr(a, attr, any(x == opt or x.startswith(opt + "=") for x in given))
+    return a
 
 
 # step-kernel variants that --variant can force (fields of pat_select_variant)
@@ -722,6 +729,143 @@ def run_matern(a, rank, world, local_rank, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_grad(a, rank, world, local_rank, dist):
+    """Differentiation workload: 32^3-cell cube (35,937 nodes), 1000 steps, 256
+    sensors on five faces, per-element c = sqrt(c2) from a smoothed N(0, 1)
+    field (amplitude 0.1), FP32 state on the full P1 graph.  One step = one
+    gradient evaluation of L = 1/2 ||G(c2) p0 - y||^2 for K stacked p0
+    (pat_grad_c2: dL/dc2 summed over the samples and dL/dp0, the forward
+    trajectory recomputed from ceil(sqrt(N_T)) checkpoints)."""
+    import torch
+
+    from paper_2607_21373_b300 import Mesh
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = S.DIFFERENTIATION
+    n = a.cells if a.cells_given else w.n
+    nt = a.n_steps if a.n_steps_given else w.n_steps
+    n_obs = a.n_obs if a.n_obs_given else w.n_obs
+    K = a.K if a.K_given else w.K
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, w.faces, w.seed)
+    c2 = S.smoothed_speed_field(n, w.seed + 7)
+    dt = w.dt_factor / n / float(np.sqrt(c2.max()))
+    mesh = Mesh(xyz, tets, det, dt, nt, precision="f32", c2=c2, flags=MESH_KEEP_ZEROS)
+    N, E = mesh.N, mesh.info["n_tets"]
+    p0 = S.phantom(xyz, w.phantom, w.seed + 100, n)
+    P = np.stack([p0 * (1.0 + 0.05 * k) for k in range(K)], axis=1) if K > 1 else p0
+    p_d = torch.tensor(P, dtype=torch.float32, device=dev)
+    # data from a 10 % weaker initial pressure, so the misfit cotangent is not zero
+    y = mesh.forward(0.9 * p_d)
+    tune = []
+    if a.variant:
+        forced = [FORCED[v] for v in a.variant.split(",")]
+        forced = forced if len(forced) == 2 else forced * 2
+        for d, v in zip(("fwd", "adj"), forced):
+            mesh.select_variant(K, d, **v)
+        tune = [dict(dict(direction=d, us_per_step=0.0), **v) for d, v in zip(("fwd", "adj"), forced)]
+    elif a.autotune:
+        tune = mesh.autotune(K, n_probe=30)
+    if a.tune_log and rank == 0:
+        with open(a.tune_log, "w") as f:
+            json.dump({"K%d" % K: tune}, f)
+
+    def best(direction):
+        rows = [e for e in tune if e["direction"] == direction]
+        return min(rows, key=lambda e: e["us_per_step"]) if rows else None
+
+    yhat = (mesh.forward(p_d) - y).contiguous()
+    g = torch.empty(E, dtype=torch.float64, device=dev)
+    pg = torch.empty_like(p_d)
+    for i in range(a.warmup):
+        mesh.grad_c2(p_d, yhat, out=(g, pg))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    e0.record(st)
+    for i in range(a.steps):
+        mesh.grad_c2(p_d, yhat, out=(g, pg))
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if not (torch.isfinite(g).all() and torch.isfinite(pg).all()):
+        raise RuntimeError("non-finite gradient")
+    # end to end: p0 and the cotangent from pinned host memory, both gradients back
+    p_h, y_h = p_d.cpu().pin_memory(), yhat.cpu().pin_memory()
+    g_h = torch.empty(E, dtype=torch.float64).pin_memory()
+    pg_h = torch.empty(pg.shape, dtype=torch.float32).pin_memory()
+    p_in, y_in = torch.empty_like(p_d), torch.empty_like(yhat)
+    e2 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(a.steps):
+        p_in.copy_(p_h, non_blocking=True)
+        y_in.copy_(y_h, non_blocking=True)
+        mesh.grad_c2(p_in, y_in, out=(g, pg))
+        g_h.copy_(g, non_blocking=True)
+        pg_h.copy_(pg, non_blocking=True)
+    e2.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e2)
+    if dist is not None:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    L = int(np.ceil(np.sqrt(nt)))
+    n_ck = (nt + L - 1) // L
+    launches = (nt - 1) + (nt - n_ck) + (nt + 1)  # forward sweep, recomputation, transposed sweep
+    node_steps = launches * N * K
+    op_bytes = graph_operator_bytes(mesh.info, N)
+    elem_bytes = n_ck * E * (16 + 40 + 16) + nt * E * 8 * K * 1.0  # tets, coefficients, g; 8 state values a step
+    alg_bytes = launches * (16.0 * N * K + op_bytes) + elem_bytes
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(peaks_path))["hbm_gbs"] if os.path.exists(peaks_path) else 6400.0
+    sec = ms / 1e3
+    cpu = None
+    if rank == 0 and a.cpu_baseline:
+        from oracle import fem, gradient
+        steps_cpu = min(nt, 200)
+        ops = gradient.with_c2(fem.build(xyz, tets, det, n), tets, c2)
+        y_cpu = (y[:steps_cpu, :, 0] if K > 1 else y[:steps_cpu]).double().cpu().numpy()
+        t0 = time.perf_counter()
+        gradient.gradients(ops, tets, p0, y_cpu, dt)
+        t_cpu = (time.perf_counter() - t0) * nt / steps_cpu
+        cpu = {"value": 1.0 / (t_cpu * K), "unit": "gradients/s", "cores": 1, "kind": "oracle",
+               "sample": "one FP64 oracle gradient (forward and reverse sweep, all states kept) over %d of the %d "
+                         "steps, one sample, %.1f s; extrapolated by steps" % (steps_cpu, nt, t_cpu * steps_cpu / nt)}
+    if rank == 0:
+        line = {
+            "metric": "grad_c2_evaluations_per_s", "value": world * a.steps / sec, "unit": "gradients/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded mesh, sound-speed field, phantom)",
+            "config": {"workload": "cube%d_grad: unit cube %d^3 cells x 6 tets (full P1 graph), %d nodes, N_T=%d, "
+                                   "%d sensors on 5 faces, c = sqrt(c2) smoothed field (amplitude 0.1), K=%d "
+                                   "stacked misfits, %d checkpoints" % (n, n, N, nt, n_obs, K, n_ck),
+                       "n_nodes": N, "n_tets": E, "n_steps": nt, "K": K, "checkpoints": n_ck,
+                       "l2": "state and operator (%.0f MB) stay in L2" % ((4 * N * K * 4 + op_bytes) / 1e6)},
+            "node_steps_per_s": world * node_steps * a.steps / sec,
+            "roofline": {"bound": "hbm", "kernel": "whole evaluation (step kernels and segment element passes)",
+                         "achieved": alg_bytes * a.steps / sec / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg_bytes * a.steps / sec / 1e9 / peak, "traffic": None,
+                         "note": "scope bytes of every step launch plus the element passes over the whole "
+                                 "evaluation; the working set stays in L2, so the launches are latency-bound"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * a.steps / (ms_e2e / 1e3), "unit": "gradients/s",
+                    "h2d_bytes_per_step": int(p_h.numel() * 4 + y_h.numel() * 4),
+                    "d2h_bytes_per_step": int(E * 8 + pg_h.numel() * 4)},
+            "gpu_launches": a.steps * (launches + n_ck + 1), "clocks": clk,
+            "variants": {d: ({"kernel": kernel_name(b, d == "adj"), "us_per_step": b["us_per_step"]}
+                             if b else "library default") for d, b in (("fwd", best("fwd")), ("adj", best("adj")))},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -742,6 +886,8 @@ def main():
         run_uneven(a, rank, world, local_rank, dist)
     elif a.workload == "matern":
         run_matern(a, rank, world, local_rank, dist)
+    elif a.workload == "grad":
+        run_grad(a, rank, world, local_rank, dist)
     else:
         run_ours(a, rank, world, local_rank, dist)
     if dist is not None:

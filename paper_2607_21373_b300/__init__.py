@@ -218,14 +218,23 @@ class Mesh:
             raise ValueError(f"c2 must have shape ({self.info['n_tets']},)")
         _lib.check(lib().pat_mesh_set_c2(self._h, c2.ctypes.data))
 
-    def grad_c2(self, p0, Yhat, want_p0_grad=True):
+    def grad_c2(self, p0, Yhat, want_p0_grad=True, out=None):
         """(dL/dc2 [n_tets] float64 summed over samples, G^T Yhat or None) for the misfit
-        cotangent Yhat = dL/dY (pat_grad_c2)."""
+        cotangent Yhat = dL/dY (pat_grad_c2).  out = (g, p0_grad or None) reuses output
+        buffers: repeated calls on the same buffers replay one captured CUDA graph."""
         K = 1 if p0.dim() == 1 else p0.shape[1]
         self._check_field(p0, (self.N,) if p0.dim() == 1 else (self.N, K), "p0")
         self._check_field(Yhat, (self.n_steps, self.n_obs) + (() if p0.dim() == 1 else (K,)), "Yhat")
-        g = torch.empty(self.info["n_tets"], dtype=torch.float64, device=self.device)
-        pg = torch.empty_like(p0) if want_p0_grad else None
+        if out is not None:
+            g, pg = out
+            if not (isinstance(g, torch.Tensor) and g.is_cuda and g.dtype == torch.float64 and g.is_contiguous()
+                    and tuple(g.shape) == (self.info["n_tets"],)):
+                raise TypeError("out[0] must be a contiguous CUDA float64 tensor of shape (n_tets,)")
+            if pg is not None:
+                self._check_field(pg, tuple(p0.shape), "out[1]")
+        else:
+            g = torch.empty(self.info["n_tets"], dtype=torch.float64, device=self.device)
+            pg = torch.empty_like(p0) if want_p0_grad else None
         ws = self.workspace(3, K)
         _lib.check(lib().pat_grad_c2(self._h, _ptr(p0), _ptr(Yhat), K, _ptr(g), _ptr(pg), _ptr(ws), ws.numel(),
                                      _stream()))

@@ -13,6 +13,15 @@
 
 using namespace pat;
 
+void pat::drop_graphs_locked(const DeviceMesh& m) {
+  for (auto& kv : m.graphs)
+    if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+  m.graphs.clear();
+  for (auto& kv : m.grad_graphs)
+    if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+  m.grad_graphs.clear();
+}
+
 namespace {
 
 template <typename T>
@@ -37,9 +46,7 @@ void free_device(DeviceMesh& m) {
   }
   {
     std::lock_guard<std::mutex> lock(m.graph_mutex);
-    for (auto& kv : m.graphs)
-      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-    m.graphs.clear();
+    drop_graphs_locked(m);
   }
   for (void* e : m.prof.events)
     if (e) cudaEventDestroy((cudaEvent_t)e);
@@ -1242,9 +1249,7 @@ pat_status pat_mesh_set_wait_cycles(pat_mesh* mesh, int64_t cycles) {
   mesh->d.tile_wait_cycles = cycles > 0 ? (long long)cycles : 4000000000ll;
   // captured solves carry the previous budget in their kernel arguments
   std::lock_guard<std::mutex> lock(mesh->d.graph_mutex);
-  for (auto& kv : mesh->d.graphs)
-    if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-  mesh->d.graphs.clear();
+  drop_graphs_locked(mesh->d);
   return PAT_OK;
 }
 
@@ -1286,9 +1291,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);
-    for (auto& kv : mesh->d.graphs)
-      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-    mesh->d.graphs.clear();
+    drop_graphs_locked(mesh->d);
     return PAT_OK;
   }
   if (v->packed == 8) {  // row quads
@@ -1307,9 +1310,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);
-    for (auto& kv : mesh->d.graphs)
-      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-    mesh->d.graphs.clear();
+    drop_graphs_locked(mesh->d);
     return PAT_OK;
   }
   if (v->packed == 5 || v->packed == 6) {  // 16-slot fixed-width rows (quad-interleaved / row-major)
@@ -1362,9 +1363,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     std::lock_guard<std::mutex> lock(mesh->d.tune_mutex);
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
     std::lock_guard<std::mutex> lock2(mesh->d.graph_mutex);
-    for (auto& kv : mesh->d.graphs)
-      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-    mesh->d.graphs.clear();
+    drop_graphs_locked(mesh->d);
     return PAT_OK;
   }
   const bool ok_v = (v->V == 1 || v->V == 2 || v->V == 4 || v->V == 8) && K % v->V == 0 &&
@@ -1412,9 +1411,7 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
     mesh->d.tuned[std::make_pair((int)direction, (int)K)] = c;
   }
   std::lock_guard<std::mutex> lock(mesh->d.graph_mutex);
-  for (auto& kv : mesh->d.graphs)
-    if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-  mesh->d.graphs.clear();
+  drop_graphs_locked(mesh->d);
   return PAT_OK;
 }
 

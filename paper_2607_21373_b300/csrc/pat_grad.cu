@@ -15,21 +15,27 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "pat_kernels.cuh"
 #include "pat_solver.cuh"
 
 namespace pat {
 
-// g[e] += scale * sum_k u[t_a, k] K0_ab x[t_b, k]   (FP64 accumulation per element)
+// One checkpoint segment's element passes, all at once:
+//   g[e] += scale * sum_{q < nq} sum_k u_{s0+1+q}[t_a, k] K0_ab x_{s0+q}[t_b, k]
+// (FP64 accumulation per element).  x_{s0+q} = xseg + q NK; u_m sits in slot
+// m % R of the ring urings (R slots of NK).  Each element's coefficients are
+// read and its g updated once per segment instead of once per step.
 template <typename T>
-__global__ void __launch_bounds__(256) grad_c2_kernel(int64_t E, int K, const int32_t* __restrict__ tets,
-                                                      const T* __restrict__ k0, const T* __restrict__ u,
-                                                      const T* __restrict__ x, double scale, double* __restrict__ g) {
+__global__ void __launch_bounds__(256) grad_c2_seg_kernel(int64_t E, int K, int64_t NK, const int32_t* __restrict__ tets,
+                                                          const T* __restrict__ k0, const T* __restrict__ uring,
+                                                          int R, int s0, const T* __restrict__ xseg, int nq,
+                                                          double scale, double* __restrict__ g) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int4 t = *reinterpret_cast<const int4*>(tets + 4 * e);
-  const int64_t n[4] = {t.x, t.y, t.z, t.w};
+  const int64_t n[4] = {(int64_t)t.x * K, (int64_t)t.y * K, (int64_t)t.z * K, (int64_t)t.w * K};
   T km[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) km[q] = k0[10 * e + q];
@@ -39,29 +45,39 @@ __global__ void __launch_bounds__(256) grad_c2_kernel(int64_t E, int K, const in
                       {km[2], km[5], km[7], km[8]},
                       {km[3], km[6], km[8], km[9]}};
   double acc = 0.0;
-  for (int k = 0; k < K; ++k) {
-    T uu[4], xx[4];
+  for (int q = nq - 1; q >= 0; --q) {
+    const T* u = uring + (int64_t)((s0 + 1 + q) % R) * NK;
+    const T* x = xseg + (int64_t)q * NK;
+    for (int k = 0; k < K; ++k) {
+      T uu[4], xx[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      uu[a] = u[n[a] * K + k];
-      xx[a] = x[n[a] * K + k];
+      for (int a = 0; a < 4; ++a) {
+        uu[a] = u[n[a] + k];
+        xx[a] = x[n[a] + k];
+      }
+      T s = T(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T r = T(0);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) r = fma(Km[a][b], xx[b], r);
+        s = fma(uu[a], r, s);
+      }
+      acc += (double)s;
     }
-    T s = T(0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      T r = T(0);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) r = fma(Km[a][b], xx[b], r);
-      s = fma(uu[a], r, s);
-    }
-    acc += (double)s;
   }
   g[e] += scale * acc;
 }
 
+// Workspace: checkpoints (x_{jL}, x_{jL-1}) of every segment, the segment's
+// recomputed states x_{s0} .. x_{s0+L-1}, the ring of transposed states
+// (L + 2 slots: a segment's passes need u_{s0+1} .. u_{s1}, its steps also
+// u_{s0} and u_{s1+1}), four state buffers (the first sweep's rotation, then
+// the transposed launches' chunk counters and sensor terms in the fourth),
+// the segment recomputation's two chunk counters, and g.
 struct GradLayout {
-  size_t ck, seg, adj, g, total;
-  int L, n_ck;
+  size_t ck, seg, ring, rot, ctr, g, total;
+  int L, n_ck, R;
 };
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -72,126 +88,207 @@ GradLayout grad_layout(const DeviceMesh& m, int K) {
   const size_t NK = (size_t)m.N * K;
   G.L = (int)std::ceil(std::sqrt((double)m.n_steps));
   G.n_ck = (m.n_steps + G.L - 1) / G.L;
+  G.R = G.L + 2;
   size_t o = 0;
   G.ck = o; o = al256(o + (size_t)G.n_ck * 2 * NK * rs);
-  G.seg = o; o = al256(o + (size_t)std::max(G.L + 1, 3) * NK * rs);  // also the rotation of the first sweep
-  G.adj = o; o = al256(o + 3 * NK * rs);
+  G.seg = o; o = al256(o + (size_t)G.L * NK * rs);
+  G.ring = o; o = al256(o + (size_t)G.R * NK * rs);
+  G.rot = o; o = al256(o + 4 * NK * rs);
+  G.ctr = o; o = al256(o + 2 * sizeof(unsigned int));
   G.g = o; o = al256(o + (size_t)m.E * 8);
   G.total = o;
   return G;
 }
 
-template <typename T, int V, bool SPLIT>
-static void step(const DeviceMesh& m, const DevCSR& csr, int K, const T* x, const T* xp, int prev_mode, T* xn,
-                 const T* ya, const T* yb, T inj_scale, cudaStream_t st) {
-  Step3Args<T> A{};
-  A.N = m.N;
-  A.K = K;
-  A.n_obs = m.n_obs;
-  A.row_threads = m.N * (int64_t)K / V;
-  A.prev_mode = prev_mode;
-  A.ptr = csr.ptr;
-  A.col = csr.col;
-  A.hi = static_cast<const T*>(csr.hi);
-  A.lo = csr.lo;
-  A.nb = m.row_nb;
-  A.ninj = m.row_ninj;
-  A.x = x;
-  A.xp = xp;
-  A.xn = xn;
-  A.ya = ya;
-  A.yb = yb;
-  A.inj_scale = inj_scale;
-  const unsigned blocks = (unsigned)((A.row_threads + 255) / 256);
-  A.stage_cap = 0;  // V = 1, K small: one thread per row, no staging
-  if (&csr == &m.adj3)
-    step3_kernel<T, V, SPLIT, true, false><<<blocks, 256, 0, st>>>(A);
-  else
-    step3_kernel<T, V, SPLIT, false, false><<<blocks, 256, 0, st>>>(A);
+// One step launch: the mesh's tuned variant (three-level form), else the
+// generic three-level kernel with one sample per thread.
+template <typename T>
+static void launch_one(const DeviceMesh& m, bool adj, int V, Step3Args<T> A, int64_t threads, cudaStream_t st) {
+  if (m.three_level) {
+    step_tuned<T>(m, adj, V, A, threads, st);
+    return;
+  }
+  A.stage_cap = 0;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  constexpr bool SPLIT = sizeof(T) == 4;
+  if (m.split || sizeof(T) == 8) {
+    if (adj)
+      step3_kernel<T, 1, SPLIT, true, false><<<blocks, 256, 0, st>>>(A);
+    else
+      step3_kernel<T, 1, SPLIT, false, false><<<blocks, 256, 0, st>>>(A);
+  } else {
+    if (adj)
+      step3_kernel<T, 1, false, true, false><<<blocks, 256, 0, st>>>(A);
+    else
+      step3_kernel<T, 1, false, false, false><<<blocks, 256, 0, st>>>(A);
+  }
 }
 
 template <typename T, int V, bool SPLIT>
-static pat_status grad_t(const DeviceMesh& m, const T* p0, const T* Yhat, int K, double* g_out, T* p0_grad,
-                         char* ws, cudaStream_t st) {
+static void finish_as(const DeviceMesh& m, int K, const T* u_last, const T* u_prev, T* out, cudaStream_t st) {
+  const int64_t rt = m.N * (int64_t)K / V;
+  adj3_finish_kernel<T, V, SPLIT><<<(unsigned)((rt + 255) / 256), 256, 0, st>>>(
+      rt, K, m.fwd.ptr, m.fwd.col, static_cast<const T*>(m.fwd.hi), m.fwd.lo, m.ml, u_last, u_prev, out);
+}
+
+template <typename T>
+static void finish(const DeviceMesh& m, int V, int K, const T* u_last, const T* u_prev, T* out, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (m.split) {
+      if (V == 8) return finish_as<T, 8, true>(m, K, u_last, u_prev, out, st);
+      if (V == 4) return finish_as<T, 4, true>(m, K, u_last, u_prev, out, st);
+      if (V == 2) return finish_as<T, 2, true>(m, K, u_last, u_prev, out, st);
+      return finish_as<T, 1, true>(m, K, u_last, u_prev, out, st);
+    }
+    if (V == 8) return finish_as<T, 8, false>(m, K, u_last, u_prev, out, st);
+    if (V == 4) return finish_as<T, 4, false>(m, K, u_last, u_prev, out, st);
+    if (V == 2) return finish_as<T, 2, false>(m, K, u_last, u_prev, out, st);
+    return finish_as<T, 1, false>(m, K, u_last, u_prev, out, st);
+  } else {
+    if (V == 2) return finish_as<T, 2, false>(m, K, u_last, u_prev, out, st);
+    return finish_as<T, 1, false>(m, K, u_last, u_prev, out, st);
+  }
+}
+
+// Every launch of one gradient evaluation on stream st.  Vf / Va: samples per
+// thread of the forward / transposed step launches.
+template <typename T>
+static pat_status grad_body(const DeviceMesh& m, const T* p0, const T* Yhat, int K, double* g_out, T* p0_grad,
+                            char* ws, int Vf, int Va, cudaStream_t st) {
   const GradLayout G = grad_layout(m, K);
   const int64_t NK = m.N * (int64_t)K;
   const size_t fb = (size_t)NK * sizeof(T);
   T* ck = (T*)(ws + G.ck);
   T* seg = (T*)(ws + G.seg);
-  T* ub[3] = {(T*)(ws + G.adj), (T*)(ws + G.adj) + NK, (T*)(ws + G.adj) + 2 * NK};
+  T* ring = (T*)(ws + G.ring);
+  T* const b[3] = {(T*)(ws + G.rot), (T*)(ws + G.rot) + NK, (T*)(ws + G.rot) + 2 * NK};
+  unsigned int* fctr = (unsigned int*)(ws + G.ctr);
   double* g = (double*)(ws + G.g);
-  const int NT = m.n_steps, L = G.L;
-  pat_status s = cuda_check(cudaMemsetAsync(g, 0, (size_t)m.E * 8, st), "grad memset");
-  if (s) return s;
-  // 1. forward sweep keeping (x_{jL}, x_{jL-1}) for every segment j (x_{-1} = x_0)
+  const int NT = m.n_steps, L = G.L, R = G.R;
+  auto slot = [&](int mstep) { return ring + (int64_t)(mstep % R) * NK; };
+  PAT_TRY(cuda_check(cudaMemsetAsync(g, 0, (size_t)m.E * 8, st), "grad memset"));
+  PAT_TRY(cuda_check(cudaMemsetAsync(fctr, 0, 2 * sizeof(unsigned int), st), "grad counters"));
+  PAT_TRY(cuda_check(cudaMemsetAsync(b[2] + NK, 0, 2 * sizeof(unsigned int), st), "grad counters"));
+  // 1. forward sweep (launch i: x_{i+1} into b[i % 3]) keeping (x_{jL}, x_{jL-1}), x_{-1} = x_0
   {
-    T* rot[3] = {seg, seg + NK, seg + 2 * NK};
-    const T* cur = p0;
-    const T* prev = p0;
-    for (int st_i = 0; st_i < NT; ++st_i) {
-      if (st_i % L == 0) {
-        T* slot = ck + (size_t)(st_i / L) * 2 * NK;
-        cudaMemcpyAsync(slot, cur, fb, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(slot + NK, prev, fb, cudaMemcpyDeviceToDevice, st);
+    PAT_RANGE("gradient: forward sweep");
+    for (int i = 0; i < NT; ++i) {
+      if (i % L == 0) {
+        const T* cur = i == 0 ? p0 : b[(i - 1) % 3];
+        const T* prev = i <= 1 ? p0 : b[(i - 2) % 3];
+        T* c = ck + (size_t)(i / L) * 2 * NK;
+        PAT_TRY(cuda_check(cudaMemcpyAsync(c, cur, fb, cudaMemcpyDeviceToDevice, st), "checkpoint"));
+        PAT_TRY(cuda_check(cudaMemcpyAsync(c + NK, prev, fb, cudaMemcpyDeviceToDevice, st), "checkpoint"));
       }
-      T* out = rot[st_i % 3];
-      step<T, V, SPLIT>(m, m.fwd, K, cur, st_i == 0 ? nullptr : prev, st_i == 0 ? 1 : 0, out, nullptr, nullptr,
-                        T(0), st);
-      prev = cur;
-      cur = out;
+      if (i == NT - 1) break;  // x_{N_T} is not needed
+      int64_t thr = 0;
+      Step3Args<T> A = fwd3_args<T>(m, K, Vf, p0, ck, T(0), b, i, &thr);
+      A.y_out = nullptr;  // no observations
+      launch_one<T>(m, false, Vf, A, A.row_threads, st);
     }
   }
-  // 2. reverse sweep: transposed three-level recursion, segment by segment
-  const int64_t ystride = (int64_t)m.n_obs * K;
-  // u_{N_T} = M^{-1} I_{N_T} / 2
-  step<T, V, SPLIT>(m, m.adj3, K, nullptr, nullptr, 2, ub[0], Yhat + (int64_t)(NT - 1) * ystride, nullptr, T(1),
-                    st);
-  const T* ucur = ub[0];
-  const T* uprev = nullptr;
-  int nb = 1;
+  // 2. reverse sweep: the transposed launches i = 0 .. N_T of a transposed
+  // solve (launch i >= 1 takes u_{m-1} from u_m, u_{m+1}, m = N_T - i + 1),
+  // their states in the ring; each segment's forward states recomputed first
+  // and its element passes run once its u's exist
+  PAT_TRY(cuda_check(cudaMemsetAsync(b[2] + NK, 0, 2 * sizeof(unsigned int), st), "grad counters"));
+  PAT_RANGE("gradient: reverse sweep");
+  int64_t thr = 0;
+  {
+    Step3Args<T> A = adj3_args<T>(m, K, Va, Yhat, T(1), b, 0, &thr);
+    A.xn = slot(NT);
+    launch_one<T>(m, true, Va, A, thr, st);
+  }
+  int i = 1, li = 0;
   const int64_t eblocks = (m.E + 255) / 256;
   for (int j = G.n_ck - 1; j >= 0; --j) {
     const int s0 = j * L;
     const int s1 = std::min(NT, s0 + L);  // states x_{s0} .. x_{s1-1} are needed
-    // recompute the segment: seg[i] = x_{s0+i}
     const T* c0 = ck + (size_t)j * 2 * NK;
-    cudaMemcpyAsync(seg, c0, fb, cudaMemcpyDeviceToDevice, st);
-    for (int i = 1; i < s1 - s0; ++i) {
-      const T* xprev = (i == 1) ? c0 + NK : seg + (size_t)(i - 2) * NK;
-      step<T, V, SPLIT>(m, m.fwd, K, seg + (size_t)(i - 1) * NK, (s0 == 0 && i == 1) ? nullptr : xprev,
-                        (s0 == 0 && i == 1) ? 1 : 0, seg + (size_t)i * NK, nullptr, nullptr, T(0), st);
+    PAT_TRY(cuda_check(cudaMemcpyAsync(seg, c0, fb, cudaMemcpyDeviceToDevice, st), "segment start"));
+    for (int q = 1; q < s1 - s0; ++q) {  // seg[q] = x_{s0+q}
+      Step3Args<T> A = fwd3_args<T>(m, K, Vf, p0, ck, T(0), b, 1, &thr);
+      A.x = seg + (size_t)(q - 1) * NK;
+      const bool first = s0 == 0 && q == 1;  // x_{-1} = x_0
+      A.xp = first ? nullptr : (q == 1 ? c0 + NK : seg + (size_t)(q - 2) * NK);
+      A.prev_mode = first ? 1 : 0;
+      A.xn = seg + (size_t)q * NK;
+      A.y_out = nullptr;
+      A.dyn_ctr = fctr + (li & 1);
+      A.dyn_next = fctr + ((li + 1) & 1);
+      ++li;
+      launch_one<T>(m, false, Vf, A, A.row_threads, st);
     }
-    for (int mstep = s1; mstep > s0; --mstep) {
-      // dL/dtheta += -dt^2 u_m^T K0 x_{m-1}
-      grad_c2_kernel<T><<<(unsigned)eblocks, 256, 0, st>>>(m.E, K, m.etets, static_cast<const T*>(m.eK0), ucur,
-                                                           seg + (size_t)(mstep - 1 - s0) * NK, -m.dt * m.dt, g);
-      T* out = ub[nb % 3];
-      step<T, V, SPLIT>(m, m.adj3, K, ucur, uprev, uprev ? 0 : 2, out, Yhat + (int64_t)(mstep - 1) * ystride,
-                        mstep >= 2 ? Yhat + (int64_t)(mstep - 2) * ystride : nullptr, T(1), st);
-      uprev = ucur;
-      ucur = out;
-      ++nb;
+    // transposed launches down to u_{s0}: m = s1 .. s0 + 1
+    for (int mstep = s1; mstep > s0; --mstep, ++i) {
+      Step3Args<T> A = adj3_args<T>(m, K, Va, Yhat, T(1), b, i, &thr);
+      A.x = slot(mstep);
+      A.xp = i == 1 ? nullptr : slot(mstep + 1);
+      A.xn = slot(mstep - 1);
+      launch_one<T>(m, true, Va, A, thr, st);
     }
+    // dL/dtheta += -dt^2 sum_{m = s0+1}^{s1} u_m^T K0 x_{m-1}
+    grad_c2_seg_kernel<T><<<(unsigned)eblocks, 256, 0, st>>>(m.E, K, NK, m.etets, static_cast<const T*>(m.eK0), ring,
+                                                             R, s0, seg, s1 - s0, -m.dt * m.dt, g);
   }
-  if (p0_grad) {
-    const int64_t rt = NK / V;
-    adj3_finish_kernel<T, V, SPLIT><<<(unsigned)((rt + 255) / 256), 256, 0, st>>>(
-        rt, K, m.fwd.ptr, m.fwd.col, static_cast<const T*>(m.fwd.hi), m.fwd.lo, m.ml, ucur, uprev, p0_grad);
-  }
-  s = cuda_check(cudaMemcpyAsync(g_out, g, (size_t)m.E * 8, cudaMemcpyDeviceToDevice, st), "grad copy");
-  if (s) return s;
+  if (p0_grad) finish<T>(m, Va, K, slot(0), slot(1), p0_grad, st);
+  PAT_TRY(cuda_check(cudaMemcpyAsync(g_out, g, (size_t)m.E * 8, cudaMemcpyDeviceToDevice, st), "grad copy"));
   return cuda_check(cudaGetLastError(), "grad launch");
+}
+
+// The whole evaluation is captured once per (K, buffers) into a CUDA graph and
+// replayed (direct launches when graphs are off or st is being captured).
+template <typename T>
+static pat_status grad_t(const DeviceMesh& m, const T* p0, const T* Yhat, int K, double* g_out, T* p0_grad,
+                         char* ws, cudaStream_t st) {
+  const int Vb = vec_width(m, K, {p0, Yhat, p0_grad, ws});
+  const int Vf = m.three_level ? std::min(Vb, tuned_vec(m, 0, K)) : 1;
+  const int Va = m.three_level ? std::min(Vb, tuned_vec(m, 1, K)) : 1;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((m.flags & PAT_MESH_NO_GRAPHS) || !m.capture_stream || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return grad_body<T>(m, p0, Yhat, K, g_out, p0_grad, ws, Vf, Va, st);
+  }
+  const std::array<uintptr_t, 6> key = {(uintptr_t)p0, (uintptr_t)Yhat, (uintptr_t)g_out, (uintptr_t)p0_grad, (uintptr_t)ws,
+                       (uintptr_t)K};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(m.graph_mutex);
+    auto it = m.grad_graphs.find(key);
+    if (it != m.grad_graphs.end()) exec = (cudaGraphExec_t)it->second;
+  }
+  if (!exec) {
+    cudaStream_t cap = (cudaStream_t)m.capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return grad_body<T>(m, p0, Yhat, K, g_out, p0_grad, ws, Vf, Va, st);
+    }
+    const pat_status s = grad_body<T>(m, p0, Yhat, K, g_out, p0_grad, ws, Vf, Va, cap);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(cap, &gr);
+    if (s != PAT_OK || e != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      return s != PAT_OK ? s : cuda_check(e, "gradient capture");
+    }
+    e = cudaGraphInstantiate(&exec, gr, 0);
+    cudaGraphDestroy(gr);
+    PAT_TRY(cuda_check(e, "gradient graph instantiate"));
+    std::lock_guard<std::mutex> lock(m.graph_mutex);
+    m.grad_graphs[key] = (void*)exec;
+  }
+  return cuda_check(cudaGraphLaunch(exec, st), "gradient graph launch");
 }
 
 size_t grad_workspace_bytes(const DeviceMesh& m, int K) { return grad_layout(m, K).total; }
 
 pat_status grad_c2(const DeviceMesh& m, const void* p0, const void* Yhat, int K, double* g, void* p0_grad, char* ws,
                    cudaStream_t st) {
-  if (m.prec == PAT_F64) return grad_t<double, 1, false>(m, (const double*)p0, (const double*)Yhat, K, g,
-                                                          (double*)p0_grad, ws, st);
-  if (m.split)
-    return grad_t<float, 1, true>(m, (const float*)p0, (const float*)Yhat, K, g, (float*)p0_grad, ws, st);
-  return grad_t<float, 1, false>(m, (const float*)p0, (const float*)Yhat, K, g, (float*)p0_grad, ws, st);
+  if (m.prec == PAT_F64)
+    return grad_t<double>(m, (const double*)p0, (const double*)Yhat, K, g, (double*)p0_grad, ws, st);
+  return grad_t<float>(m, (const float*)p0, (const float*)Yhat, K, g, (float*)p0_grad, ws, st);
 }
 
 }  // namespace pat

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <nvtx3/nvToolsExt.h>
+#include <array>
 #include <cstdint>
 #include <map>
 #include <tuple>
@@ -223,12 +224,20 @@ struct DeviceMesh {
   // CUDA graphs of whole forward / transposed solves inside the CGLS loop,
   // keyed by (direction, workspace, K, scale bits); cudaGraphExec_t handles
   mutable std::map<std::tuple<int, const void*, int, uint64_t>, void*> graphs;
+  // CUDA graphs of whole gradient evaluations (pat_grad_c2), keyed by
+  // (p0, Yhat, g_c2, p0_grad, workspace, K)
+  mutable std::map<std::array<uintptr_t, 6>, void*> grad_graphs;
   void* capture_stream = nullptr;  // private cudaStream_t the graphs are captured on
   mutable std::mutex graph_mutex;
   // variants picked by pat_autotune per (direction 0 fwd / 1 adj, K)
   mutable std::map<std::pair<int, int>, TuneCfg> tuned;
   mutable std::mutex tune_mutex;
 };
+
+// Destroys every captured graph of the mesh (solves and gradients); the
+// caller holds m.graph_mutex.  Called whenever what a graph captured (kernel
+// variants, wait budget, operators) changes.
+void drop_graphs_locked(const DeviceMesh& m);
 
 // Argument checks shared by the entry points (pat_api.cu): the mesh has device
 // copies on the current device; K is in range; a workspace for op (as in

@@ -892,6 +892,43 @@ static pat_status adjoint_disp(const DeviceMesh& m, const T* Yh, int K, T* out, 
   }
 }
 
+// One three-level step launch with the mesh's variant for (direction, K), for
+// drivers that place the states themselves (the gradient's checkpointed sweeps).
+template <typename T, bool ADJ>
+static void step_tuned_dir(const DeviceMesh& m, int V, const Step3Args<T>& A, int64_t thr, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (m.split) {
+      if (V == 8) return launch_step3<T, 8, true, ADJ>(m, A, thr, st);
+      if (V == 4) return launch_step3<T, 4, true, ADJ>(m, A, thr, st);
+      if (V == 2) return launch_step3<T, 2, true, ADJ>(m, A, thr, st);
+      return launch_step3<T, 1, true, ADJ>(m, A, thr, st);
+    }
+    if (V == 8) return launch_step3<T, 8, false, ADJ>(m, A, thr, st);
+    if (V == 4) return launch_step3<T, 4, false, ADJ>(m, A, thr, st);
+    if (V == 2) return launch_step3<T, 2, false, ADJ>(m, A, thr, st);
+    return launch_step3<T, 1, false, ADJ>(m, A, thr, st);
+  } else {
+    if (V == 2) return launch_step3<T, 2, false, ADJ>(m, A, thr, st);
+    return launch_step3<T, 1, false, ADJ>(m, A, thr, st);
+  }
+}
+
+template <typename T>
+void step_tuned(const DeviceMesh& m, bool adj, int V, const Step3Args<T>& A, int64_t threads, cudaStream_t st) {
+  if (adj)
+    step_tuned_dir<T, true>(m, V, A, threads, st);
+  else
+    step_tuned_dir<T, false>(m, V, A, threads, st);
+}
+template void step_tuned<float>(const DeviceMesh&, bool, int, const Step3Args<float>&, int64_t, cudaStream_t);
+template void step_tuned<double>(const DeviceMesh&, bool, int, const Step3Args<double>&, int64_t, cudaStream_t);
+
+int tuned_vec(const DeviceMesh& m, int dir, int K) {
+  TuneCfg c;  // untuned: the default variant's width
+  variant(m, dir, K, &c);
+  return c.V;
+}
+
 pat_status forward(const DeviceMesh& m, const void* p0, int K, void* Y, double scale, void* ws, cudaStream_t st) {
   if (m.prec == PAT_F64)
     return forward_disp<double>(m, (const double*)p0, K, (double*)Y, scale, (double*)ws, st);
@@ -1987,9 +2024,7 @@ pat_status autotune(const DeviceMesh& m, int K, char* ws, int n_probe, pat_tune_
   {
     // captured solves still hold the previous variant
     std::lock_guard<std::mutex> lock(m.graph_mutex);
-    for (auto& kv : m.graphs)
-      if (kv.second) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
-    m.graphs.clear();
+    drop_graphs_locked(m);
   }
   if (n_entries) *n_entries = n;
   return PAT_OK;

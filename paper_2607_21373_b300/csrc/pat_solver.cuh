@@ -98,6 +98,13 @@ struct Job {
 
 pat_status rto_multi(const std::vector<Job>& jobs, int n_iter, cudaStream_t st);
 
+// One three-level step launch with the mesh's variant for (direction, K) and
+// V samples per thread (a width the variant and the buffers allow: V <=
+// tuned_vec(m, dir, K), K % V == 0, buffers aligned to V elements).
+template <typename T>
+void step_tuned(const DeviceMesh& m, bool adj, int V, const Step3Args<T>& A, int64_t threads, cudaStream_t st);
+int tuned_vec(const DeviceMesh& m, int dir, int K);
+
 // Misfit gradient with respect to per-element c^2 (pat_grad.cu).
 size_t grad_workspace_bytes(const DeviceMesh& m, int K);
 pat_status grad_c2(const DeviceMesh& m, const void* p0, const void* Yhat, int K, double* g, void* p0_grad, char* ws,

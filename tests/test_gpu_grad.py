@@ -115,3 +115,81 @@ def test_autograd_backward_is_the_transpose_kernel():
     w = torch.tensor(S.standard_normal(tuple(Y.shape), 2), dtype=torch.float32, device="cuda")
     (Y * w).sum().backward()
     assert torch.equal(p0.grad, m.adjoint(w))
+
+
+def _stacked_reference(n, n_obs, nt, K, seed, flags):
+    """GPU mesh (FP32, full P1 graph) and the oracle's per-sample gradients summed over K."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS
+    m, xyz, tets, det, c2, dt, p0 = setup(n, n_obs, nt, "f32", seed=seed, flags=MESH_KEEP_ZEROS | flags)
+    ops = gradient.with_c2(fem.build(xyz, tets, det, n), tets, c2)
+    P = np.stack([p0 * (1.0 + 0.1 * k) + 0.01 * k for k in range(K)], axis=1).astype(np.float32).astype(np.float64)
+    ys = np.stack([S.standard_normal((nt, n_obs), 20 + k) * 0.1 for k in range(K)], axis=2)
+    refs = [gradient.gradients(ops, tets, P[:, k], ys[..., k], dt) for k in range(K)]
+    g_ref = sum(r[1] for r in refs)
+    pg_ref = np.stack([r[0] for r in refs], axis=1)
+    return m, P, ys, g_ref, pg_ref
+
+
+@pytest.mark.parametrize("flags", [0, "two_level"])
+def test_c2_gradient_of_stacked_samples_on_the_tuned_kernels(flags):
+    """K = 8 stacked FP32 samples on the full P1 graph: the checkpointed sweeps
+    run the mesh's selected step variants (16-slot forward and transposed
+    kernels, or the generic kernels of the two-level form), 60 steps in 8
+    segments of 8; the gradient is the oracle's sum over the samples."""
+    from paper_2607_21373_b300 import MESH_TWO_LEVEL
+    n, n_obs, nt, K = 5, 24, 60, 8
+    m, P, ys, g_ref, pg_ref = _stacked_reference(n, n_obs, nt, K, 1010, MESH_TWO_LEVEL if flags else 0)
+    if not flags:
+        m.select_variant(K, "fwd", V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True,
+                         tail_serial=True, own_async=True)
+        m.select_variant(K, "adj", V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=3)
+    p = dev(P, "f32")
+    yhat = (m.forward(p).double() - torch.tensor(ys, device="cuda")).float().contiguous()
+    g, pg = m.grad_c2(p, yhat)
+    assert rel_l2(g.cpu().numpy(), g_ref) < 1e-4
+    assert rel_l2(pg.cpu().double().numpy(), pg_ref) < 1e-4
+
+
+def test_c2_gradient_is_the_same_for_every_step_variant_and_on_replay():
+    """The step variants give the same bits, so the gradient does too; a second
+    call with the same buffers replays the captured graph, a call with other
+    buffers captures another, and a mesh without graphs launches directly."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS, MESH_NO_GRAPHS, Mesh
+    n, n_obs, nt, K = 5, 24, 45, 16
+    m, P, ys, g_ref, _ = _stacked_reference(n, n_obs, nt, K, 1011, 0)
+    p = dev(P, "f32")
+    yhat = (m.forward(p).double() - torch.tensor(ys, device="cuda")).float().contiguous()
+    outs = []
+    for fv, av in ((dict(V=4, packed=0), dict(V=4, packed=0)),
+                   (dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
+                         own_async=True), dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=3)),
+                   (dict(V=8, packed=5, persistent=1, pdl=True, gather_batch=4),
+                    dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=2))):
+        m.select_variant(K, "fwd", **fv)
+        m.select_variant(K, "adj", **av)
+        outs.append(m.grad_c2(p, yhat))
+    g2, pg2 = m.grad_c2(p, yhat)  # new output tensors: another capture with the last variants
+    for g, pg in outs[1:] + [(g2, pg2)]:
+        assert torch.equal(g, outs[0][0]) and torch.equal(pg, outs[0][1])
+    assert rel_l2(outs[0][0].cpu().numpy(), g_ref) < 1e-4
+    # the raw entry point twice on the same buffers: the second call is a replay
+    from paper_2607_21373_b300 import _lib, lib, _ptr, _stream
+    ws = m.workspace(3, K)
+    gbuf = torch.full((m.info["n_tets"],), float("nan"), dtype=torch.float64, device="cuda")
+    pbuf = torch.full_like(p, float("nan"))
+    for _ in range(2):
+        _lib.check(lib().pat_grad_c2(m._h, _ptr(p), _ptr(yhat), K, _ptr(gbuf), _ptr(pbuf), _ptr(ws), ws.numel(),
+                                     _stream()))
+        assert torch.equal(gbuf, outs[0][0]) and torch.equal(pbuf, outs[0][1])
+        gbuf.fill_(float("nan"))
+        pbuf.fill_(float("nan"))
+    # direct launches (no graphs) on an identical mesh
+    xyz, tets = S.cube_mesh(n)
+    det = S.detector_points(n_obs, S.LIMITED_VIEW_FACES, 1011)
+    c2 = S.smoothed_speed_field(n, 1011 + 7)
+    md = Mesh(xyz, tets, det, 0.3 / n / np.sqrt(c2.max()), nt, precision="f32", c2=c2,
+              flags=MESH_KEEP_ZEROS | MESH_NO_GRAPHS)
+    md.select_variant(K, "fwd", V=4, packed=0)
+    md.select_variant(K, "adj", V=4, packed=0)
+    gd, pgd = md.grad_c2(p, yhat)
+    assert torch.equal(gd, outs[0][0]) and torch.equal(pgd, outs[0][1])
