@@ -135,6 +135,8 @@ FORCED = {
     "w16rcox": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, early=True, tail_serial=True,
                     own_async=3),
     "w16rox": dict(V=8, packed=6, persistent=1, pdl=True, gather_batch=4, own_async=3),
+    "e1": dict(V=1, packed=3),
+    "g1": dict(V=1, packed=0),
     "pairs": dict(V=8, packed=7, persistent=1, pdl=True),
     "quads": dict(V=8, packed=8, persistent=1, pdl=True),
     "quadso": dict(V=8, packed=8, persistent=1, pdl=True, own_async=True),
