@@ -360,7 +360,8 @@ def kernel_name(e, adj):
         return "step3q_persist_kernel<%s> (row quads%s)" % (tf, ", own rows async" if e.get("own_async") else "")
     if packed in (5, 6):
         if e.get("V") == 1:
-            return "step3w1_kernel<%s> (16 slots, one sample)" % tf
+            return "step3w1_kernel<%s> (16 slots, one sample%s)" % (tf, ", 6 blocks/SM" if e.get("min_blocks") == 6
+                                                                     else "")
         nb = e.get("gather_batch") or 4
         big = bool(e.get("big_blocks"))
         return "step3w_persist_kernel<%s> (16 slots%s, rounds of %d%s%s%s)" % (
@@ -378,7 +379,8 @@ def kernel_name(e, adj):
         return "step3p_kernel<%s> (persistent double-buffered tiles)" % tf
     if packed == 3:
         if e.get("V") == 1:
-            return "step3e1_kernel<%s> (8 slots, one sample)" % tf
+            return "step3e1_kernel<%s> (8 slots, one sample%s)" % (tf, ", 6 blocks/SM" if e.get("min_blocks") == 6
+                                                                   else "")
         p = int(e.get("persistent") or 0)
         kind = {0: "step3e_kernel", 1: "step3e_persist_kernel", 2: "step3e_slab_kernel",
                 3: "step3e_stage_kernel"}.get(p, "step3e_persistent(%d)" % p)

@@ -1319,7 +1319,8 @@ pat_status pat_select_variant(pat_mesh* mesh, int32_t K, int32_t direction, cons
                         : (f32s && mesh->d.fwd.w16_col && K == 1 && v->V == 1 && v->packed == 5);
     const int nb = v->gather_batch ? v->gather_batch : 4;
     if (!ok || (nb != 4 && nb != 8) ||
-        (v->min_blocks != 1 && !(v->min_blocks == 3 && (nb == 8 || (v->packed == 6 && v->own_async == 1))))) {
+        (v->min_blocks != 1 && !(v->min_blocks == 3 && (nb == 8 || (v->packed == 6 && v->own_async == 1))) &&
+         !(v->min_blocks == 6 && v->V == 1))) {
       set_error("pat_select_variant: 16-slot variant V=%d gather_batch=%d min_blocks=%d is not available for K=%d on "
                 "this mesh (it needs rows wider than 8 slots, FP32 split coefficients, V = 8 or K = V = 1)",
                 v->V, v->gather_batch, v->min_blocks, K);

@@ -579,7 +579,10 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.status = m.d_status;
       a.wait_cycles = m.tile_wait_cycles;
       if constexpr (V == 1) {
-        step3w1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+        if (c.minb == 6)
+          step3w1_kernel<ADJ, 6><<<(unsigned)blocks, 256, 0, st>>>(a);
+        else
+          step3w1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
       } else {
         // the transposed kernel's extra threads prepare the next launch's sensor terms
         const int64_t prep = (ADJ && a.inj_next) ? a.n_inj * (a.K / 8) : 0;
@@ -597,7 +600,10 @@ static void launch_step3(const DeviceMesh& m, Step3Args<T> a, int64_t threads, c
       a.ovf_ptr = E.ovf_ptr;
       a.ovf_col = E.ovf_col;
       a.ovf_hl = E.ovf_hl;
-      step3e1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
+      if (c.minb == 6)
+        step3e1_kernel<ADJ, 6><<<(unsigned)blocks, 256, 0, st>>>(a);
+      else
+        step3e1_kernel<ADJ><<<(unsigned)blocks, 256, 0, st>>>(a);
       return;
     }
   }
@@ -1845,6 +1851,8 @@ static const TuneVariant kTuneVariants[] = {
     {1, 0, 2, 1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 10 packed, chunks of 2, Z-order rows
     {1, 0, 4, 1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 11 packed, chunks of 4, Z-order rows
     {3, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 12 fixed-width (ELL)
+    {3, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 6, 0, 1},  // 98 fixed-width, one sample, 6 blocks/SM (40 registers)
+    {5, 0, 4, 0, 0, 0, 1, 1, 0, 0, 4, 6, 0, 1},  // 99 16 slots, one sample, 6 blocks/SM (40 registers)
     {4, 0, 4, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 13 persistent double-buffered tiles
     {1, 0, 2, 1, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 14 packed, chunks of 2, 1024-thread blocks, Z-order
     {3, 0, 4, 1, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0},  // 15 fixed-width, 1024-thread blocks, Z-order

@@ -251,6 +251,60 @@ __device__ __forceinline__ void ell_entry(const Step3Args<float>& A, int64_t row
   }
 }
 
+// One-sample row tail: entries e0 <= e < e1 fetched by entry(e, &col, &c),
+// their sources gathered from xs and accumulated with sign sg (+1 or -1, so
+// sg * c is exact) in entry order: the same products in the same order as a
+// walk one entry at a time, with 4 entries' loads in flight per round instead
+// of two dependent loads per entry.
+template <typename Entry>
+__device__ __forceinline__ void tail1(int e0, int e1, const float* __restrict__ xs, float sg, Entry entry,
+                                      float& acc, float& accl) {
+  for (int e = e0; e < e1; e += 4) {
+    uint32_t col[4];
+    float2 c[4];
+    float x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (e + j < e1) entry(e + j, &col[j], &c[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = (e + j < e1) ? xs[col[j]] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (e + j < e1) {
+        acc = fmaf(sg * c[j].x, x[j], acc);
+        accl = fmaf(sg * c[j].y, x[j], accl);
+      }
+  }
+}
+
+// One-sample sensor term: src = sum over the row's sensor entries j < ni (in
+// order, ya then yb, either may be absent) of c_j (ya + yb)[col_j], 4 entries'
+// loads in flight per round (the same products in the same order).
+template <typename Entry>
+__device__ __forceinline__ float inj1(int ni, const float* __restrict__ ya, const float* __restrict__ yb, Entry entry) {
+  float src = 0.0f;
+  for (int e = 0; e < ni; e += 4) {
+    uint32_t col[4];
+    float2 c[4];
+    float a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (e + j < ni) entry(e + j, &col[j], &c[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      a[j] = (ya && e + j < ni) ? ya[col[j]] : 0.0f;
+      b[j] = (yb && e + j < ni) ? yb[col[j]] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (e + j < ni) {
+        if (ya) src = fmaf(c[j].x, a[j], src);
+        if (yb) src = fmaf(c[j].x, b[j], src);
+      }
+  }
+  return src;
+}
+
 // Sensor (injection) entry j of a fixed-width row with eA stiffness / boundary
 // entries: always in the overflow list, after the stiffness entries beyond 8.
 __device__ __forceinline__ void inj_entry(const Step3Args<float>& A, int64_t row, int j, int eA, uint32_t* col,
@@ -1062,8 +1116,8 @@ __global__ void __launch_bounds__(512) step3p_kernel(const Step3Args<float> A, c
 // fixed slots (columns and coefficient pairs: six 16-byte loads) arrive in one
 // round and its 8 neighbour values in the next, instead of the row-pointer ->
 // column -> value chain of the CSR walk.
-template <bool ADJ>
-__global__ void __launch_bounds__(256) step3e1_kernel(const Step3Args<float> A) {
+template <bool ADJ, int MINB = 1>  // MINB 6: at most 40 registers, 6 blocks of 256 per SM
+__global__ void __launch_bounds__(256, MINB) step3e1_kernel(const Step3Args<float> A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.row_threads) {
     gather_obs<1>(A, t - A.row_threads);
@@ -1093,36 +1147,13 @@ __global__ void __launch_bounds__(256) step3e1_kernel(const Step3Args<float> A) 
       acc = fmaf(hs[q], xv[q], acc);
       accl = fmaf(ls[q], xv[q], accl);
     }
-    for (int e = 8; e < eA; ++e) {
-      uint32_t col;
-      float2 c;
-      ell_entry<1>(A, row, e, &col, &c);
-      const float x = A.x[col];
-      acc = fmaf(c.x, x, acc);
-      accl = fmaf(c.y, x, accl);
-    }
-    if (nb > 0 && A.prev_mode != 2) {
-      const float* pk = A.prev_mode == 0 ? A.xp : A.x;
-      for (int e = eA - nb; e < eA; ++e) {
-        uint32_t col;
-        float2 c;
-        ell_entry<1>(A, row, e, &col, &c);
-        const float x = pk[col];
-        acc = fmaf(-c.x, x, acc);
-        accl = fmaf(-c.y, x, accl);
-      }
-    }
+    auto entry = [&](int e, uint32_t* col, float2* c) { ell_entry<1>(A, row, e, col, c); };
+    tail1(8, eA, A.x, 1.0f, entry, acc, accl);
+    if (nb > 0 && A.prev_mode != 2) tail1(eA - nb, eA, A.prev_mode == 0 ? A.xp : A.x, -1.0f, entry, acc, accl);
   }
   float src = 0.0f;
-  if constexpr (ADJ) {
-    for (int e = 0; e < ni; ++e) {
-      uint32_t col;
-      float2 c;
-      inj_entry(A, row, e, eA, &col, &c);
-      if (A.ya) src = fmaf(c.x, A.ya[col], src);
-      if (A.yb) src = fmaf(c.x, A.yb[col], src);
-    }
-  }
+  if constexpr (ADJ)
+    src = inj1(ni, A.ya, A.yb, [&](int e, uint32_t* col, float2* c) { inj_entry(A, row, e, eA, col, c); });
   const float xi = A.x ? A.x[row] : 0.0f;
   const float xpi = A.prev_mode == 0 ? A.xp[row] : (A.prev_mode == 1 ? xi : 0.0f);
   const float w = xi - xpi;

@@ -720,8 +720,8 @@ __global__ void __launch_bounds__(256, 4) step3g_persist_kernel(const __grid_con
 }
 
 // One sample (K = 1): one thread per row, 16 fixed slots.
-template <bool ADJ>
-__global__ void __launch_bounds__(256) step3w1_kernel(const Step3Args<float> A) {
+template <bool ADJ, int MINB = 1>  // MINB 6: at most 40 registers, 6 blocks of 256 per SM
+__global__ void __launch_bounds__(256, MINB) step3w1_kernel(const Step3Args<float> A) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= A.row_threads) {
     gather_obs<1>(A, t - A.row_threads);
@@ -752,36 +752,13 @@ __global__ void __launch_bounds__(256) step3w1_kernel(const Step3Args<float> A) 
       acc = fmaf(h.z, xv[q + 1], acc);
       accl = fmaf(h.w, xv[q + 1], accl);
     }
-    for (int e = kWide; e < eA; ++e) {
-      uint32_t col;
-      float2 c;
-      wide_entry(A, row, e, &col, &c);
-      const float x = A.x[col];
-      acc = fmaf(c.x, x, acc);
-      accl = fmaf(c.y, x, accl);
-    }
-    if (nb > 0 && A.prev_mode != 2) {
-      const float* pk = A.prev_mode == 0 ? A.xp : A.x;
-      for (int e = eA - nb; e < eA; ++e) {
-        uint32_t col;
-        float2 c;
-        wide_entry(A, row, e, &col, &c);
-        const float x = pk[col];
-        acc = fmaf(-c.x, x, acc);
-        accl = fmaf(-c.y, x, accl);
-      }
-    }
+    auto entry = [&](int e, uint32_t* col, float2* c) { wide_entry(A, row, e, col, c); };
+    tail1(kWide, eA, A.x, 1.0f, entry, acc, accl);
+    if (nb > 0 && A.prev_mode != 2) tail1(eA - nb, eA, A.prev_mode == 0 ? A.xp : A.x, -1.0f, entry, acc, accl);
   }
   float src = 0.0f;
-  if constexpr (ADJ) {
-    for (int e = 0; e < ni; ++e) {
-      uint32_t col;
-      float2 c;
-      wide_inj(A, row, e, eA, &col, &c);
-      if (A.ya) src = fmaf(c.x, A.ya[col], src);
-      if (A.yb) src = fmaf(c.x, A.yb[col], src);
-    }
-  }
+  if constexpr (ADJ)
+    src = inj1(ni, A.ya, A.yb, [&](int e, uint32_t* col, float2* c) { wide_inj(A, row, e, eA, col, c); });
   const float xi = A.x ? A.x[row] : 0.0f;
   const float xpi = A.prev_mode == 0 ? A.xp[row] : (A.prev_mode == 1 ? xi : 0.0f);
   const float w = xi - xpi;

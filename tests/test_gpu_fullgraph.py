@@ -136,7 +136,8 @@ def test_wide_single_sample_kernel_is_bit_identical():
     p0 = dev(S.standard_normal(len(xyz), 5))
     yh = dev(S.standard_normal((nt, n_obs), 6))
     Y0, g0 = m.forward(p0).clone(), m.adjoint(yh).clone()
-    for v in (dict(V=1, packed=5, gather_batch=4), dict(V=1, packed=3), dict(V=1, packed=0)):
+    for v in (dict(V=1, packed=5, gather_batch=4), dict(V=1, packed=5, gather_batch=4, min_blocks=6),
+              dict(V=1, packed=3), dict(V=1, packed=3, min_blocks=6), dict(V=1, packed=0)):
         for d in ("fwd", "adj"):
             m.select_variant(1, d, **v)
         assert torch.equal(m.forward(p0), Y0), v
