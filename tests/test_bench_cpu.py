@@ -44,6 +44,16 @@ def test_workload_config_names_the_solver_and_mesh():
     assert not bench.mesh_flags(bench.parse(["--mesh", "pruned"])) & bench.MESH_KEEP_ZEROS
 
 
+def test_gradient_workload_takes_the_differentiation_sizes_unless_given():
+    a = bench.parse(["--workload", "grad"])
+    assert a.workload == "grad" and not (a.cells_given or a.n_steps_given or a.n_obs_given or a.K_given)
+    b = bench.parse(["--workload", "grad", "--K", "8", "--cells=16"])
+    assert b.K_given and b.cells_given and b.K == 8 and b.cells == 16 and not b.n_steps_given
+    w = bench.S.DIFFERENTIATION
+    assert (w.n, w.n_steps, w.n_obs, w.K) == (32, 1000, 256, 1)
+    assert bench.kernel_name(bench.FORCED["e1"], False) == "step3e1_kernel<false> (8 slots, one sample)"
+
+
 def test_reference_arm_prints_one_parsable_line():
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--cells", "6", "--n-steps", "60",
            "--n-obs", "16", "--steps", "2", "--warmup", "1", "--cpu-procs", "2"]
