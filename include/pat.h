@@ -459,10 +459,19 @@ pat_status pat_rto_sample_matern(const pat_mesh* mesh, const pat_matern* prior, 
  *            u the transposed states (Section 5.1 recursion; K_e^0 the c = 1
  *            element stiffness of Section 3);
  *   p0_grad  device [N][K] real or NULL: G^T Yhat (dL/dp0).
- * The forward trajectory is recomputed from ceil(sqrt(N_T)) checkpoints, so the
- * call costs about two forward sweeps, one transposed sweep and N_T element
- * passes.  p0 device [N][K] real; Yhat device [N_T][N_obs][K] real;
- * workspace >= pat_workspace_bytes(mesh, 3, K).
+ * The forward trajectory is recomputed from L = ceil(sqrt(N_T)) checkpoints, so
+ * the call costs about two forward sweeps, one transposed sweep (the mesh's
+ * tuned step kernels for K) and one element pass per checkpoint segment.
+ * p0 device [N][K] real; Yhat device [N_T][N_obs][K] real;
+ * workspace >= pat_workspace_bytes(mesh, 3, K) (checkpoints, L + 2 transposed
+ * states, L recomputed states, four state buffers, g).  The first call with a
+ * given (p0, Yhat, g_c2, p0_grad, workspace, K) captures the whole evaluation
+ * into a CUDA graph on the mesh's capture stream; later calls with the same
+ * buffers replay it on `stream` (new contents, same addresses).  Graphs are
+ * dropped when a variant, the wait budget or c^2 changes; with
+ * PAT_MESH_NO_GRAPHS, or while `stream` is being captured, the kernels are
+ * launched directly.  Calls on one mesh from several host threads at once are
+ * not supported.
  */
 pat_status pat_grad_c2(const pat_mesh* mesh, const void* p0, const void* Yhat, int32_t K, double* g_c2,
                        void* p0_grad, void* workspace, size_t workspace_bytes, void* stream);
