@@ -89,6 +89,27 @@ def test_c2_gradient_directional_fd_at_full_size():
     assert abs(float((pg * dp).sum()) - fdp) < 1e-6 * abs(fdp)
 
 
+def test_fp32_c2_gradient_at_full_size_matches_oracle():
+    """The differentiation workload itself (35,937 nodes, 1000 steps, 256 sensors,
+    full P1 graph) in FP32 on the mesh's tuned one-sample kernels, against the
+    FP64 oracle's adjoint-state gradient (all states kept, no checkpoints).
+    Held to the FP32 forward-data tolerance, 1e-5 relative L2 (measured on a
+    B300: 2.5e-6 for dL/dc2, 1.3e-6 for dL/dp0)."""
+    from paper_2607_21373_b300 import MESH_KEEP_ZEROS
+    n, n_obs, nt = 32, 256, 1000
+    m, xyz, tets, det, c2, dt, p0 = setup(n, n_obs, nt, "f32", flags=MESH_KEEP_ZEROS)
+    ops = gradient.with_c2(fem.build(xyz, tets, det, n), tets, c2)
+    y = S.standard_normal((nt, n_obs), 31) * 0.05
+    gp_ref, gt_ref = gradient.gradients(ops, tets, p0, y, dt)
+    m.autotune(1, n_probe=10)
+    p = dev(p0, "f32")
+    yhat = (m.forward(p).double() - torch.tensor(y, device="cuda")).float().contiguous()
+    g, pg = m.grad_c2(p, yhat)
+    eg, ep = rel_l2(g.cpu().numpy(), gt_ref), rel_l2(pg.cpu().double().numpy(), gp_ref)
+    print(f"\nFP32 full-size gradient vs oracle: dL/dc2 {eg:.2e}, dL/dp0 {ep:.2e}")
+    assert eg < 1e-5 and ep < 1e-5
+
+
 def test_autograd_gradcheck_tiny_mesh():
     from paper_2607_21373_b300 import Mesh
     from paper_2607_21373_b300.autograd import wave_forward
