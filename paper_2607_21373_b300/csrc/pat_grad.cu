@@ -110,12 +110,12 @@ static void launch_one(const DeviceMesh& m, bool adj, int V, Step3Args<T> A, int
   }
   A.stage_cap = 0;
   const unsigned blocks = (unsigned)((threads + 255) / 256);
-  constexpr bool SPLIT = sizeof(T) == 4;
-  if (m.split || sizeof(T) == 8) {
+  // split (hi, lo) coefficients exist for FP32 meshes only
+  if (sizeof(T) == 4 && m.split) {
     if (adj)
-      step3_kernel<T, 1, SPLIT, true, false><<<blocks, 256, 0, st>>>(A);
+      step3_kernel<T, 1, sizeof(T) == 4, true, false><<<blocks, 256, 0, st>>>(A);
     else
-      step3_kernel<T, 1, SPLIT, false, false><<<blocks, 256, 0, st>>>(A);
+      step3_kernel<T, 1, sizeof(T) == 4, false, false><<<blocks, 256, 0, st>>>(A);
   } else {
     if (adj)
       step3_kernel<T, 1, false, true, false><<<blocks, 256, 0, st>>>(A);
